@@ -1,0 +1,607 @@
+/*
+ * rorbk_oracle.c -- plain, slow, FP64 CPU restatement of ROR-BK.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness oracle for the CUDA
+ * solver.  Only the test-suite, the smoke check and the benchmark's CPU
+ * baseline leg may load it.  It shares no code, header, table or helper with
+ * the CUDA path, and nothing in the product path calls it.
+ *
+ * Source: Kar & Venkatapathi, "A fast solver for ill-conditioned linear
+ * systems using randomized stable solutions of its blocks" (arXiv 2510.02156).
+ *   - Algorithm 1 (ROR-BK): setup steps (uniform contiguous aggregation,
+ *     centroids, C, P) and the iteration (3 sampled regularised block
+ *     updates, full residual, convergence test, residual top-K dynamic block).
+ *   - Section 2, the formula for P_t: Pbar_t = exp(-2 sum_j C(t,j) / n).
+ *   - Section 2, the definition of C(i,j) = |<Abar_i,Abar_j>|/(|Abar_i||Abar_j|)
+ *     with the centroid being the plain sum of the block's rows.
+ *   - Section 3.1: the static blocks' (A_t A_t^T + mu I)^{-1} are computed
+ *     once and stored; the update is x += A_t^T W_t (b_t - A_t x).
+ *   - Eq. (3) / Lemma 1 / Theorem 1 are pinned by the tests, not used here.
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - partition: block t holds rows [off_t, off_{t+1}) with
+ *     off_t = t*floor(m/k) + min(t, m mod k)  (the first m mod k blocks get
+ *     one extra row; every block has >= floor(m/k) rows as Section 2 asks);
+ *   - C(t,t) = 1; C(t,j) = 0 for j != t if either centroid is zero;
+ *   - the sampler is a Philox4x64-10 counter stream (Salmon et al., SC'11):
+ *     key = (seed, system_id), counter = (iteration, l, 0, 0), word 0,
+ *     u = (w >> 11) * 2^-53, tau = min{ t : u * cdf[k-1] < cdf[t] } with the
+ *     cdf summed sequentially in FP64 from Pbar (the normalisation of P is
+ *     folded into u * cdf[k-1]);
+ *   - convergence: ||b - A x|| / ||b|| <= tol, tested after the static updates
+ *     and before the dynamic one, as Algorithm 1 orders it; ||b|| = 0 returns
+ *     x = 0 after zero iterations;
+ *   - top-K: the K = floor(m/k) rows with the largest |r_i| (the same order as
+ *     r_i^2), ties to the lower row index, returned in ascending row order;
+ *   - the dynamic block uses r_I from the full residual (x has not changed
+ *     since it was formed, so b_I - A_I x = r_I);
+ *   - static operators W_t are formed lazily on the first draw of block t and
+ *     then kept (the paper forms them once and stores them; forming them on
+ *     first use gives the same numbers);
+ *   - W_t = L^{-T} L^{-1} with L = chol(A_t A_t^T + mu I).
+ *
+ * Fixed summation orders (so that each number has one definition):
+ *   - row dot products run over a CSR row in stored (ascending column) order,
+ *     a dense row in column order;
+ *   - (A_B^T y)_c sums over the block's rows in ascending order into a zeroed
+ *     vector delta, and then x_c += delta_c;
+ *   - Gram entries G_ij = sum_c A_ic A_jc in ascending column order;
+ *   - norms are sequential sums of squares.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Matrix view: CSR (int64 row pointers, int32 columns, FP64 values) or dense
+ * row-major FP64.  FP32-defined systems are passed widened to FP64, which is
+ * exact. */
+typedef struct {
+    int64_t m, n;
+    int32_t is_dense;
+    int32_t pad_;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const double *val;
+    const double *dense;
+    int64_t ld;
+} orc_matrix;
+
+#define ORC_OK 0
+#define ORC_NOT_CONVERGED 1
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_NOT_SPD (-4)
+#define ORC_ERR_OOM (-3)
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11).  One round maps (X0,X1,X2,X3) with key (K0,K1)
+ * to (hi(M1*X2)^X1^K0, lo(M1*X2), hi(M0*X0)^X3^K1, lo(M0*X0)); the key is
+ * bumped by the Weyl constants between rounds. */
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        unsigned __int128 p0 = (unsigned __int128)M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t n0 = hi1 ^ x1 ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ x3 ^ k1;
+        uint64_t n3 = lo0;
+        x0 = n0; x1 = n1; x2 = n2; x3 = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1, step 1: uniform contiguous aggregation into k blocks. */
+int orc_partition(int64_t m, int64_t k, int64_t *off)
+{
+    if (k < 1 || k > m) return ORC_ERR_ARG;
+    int64_t q = m / k, rem = m % k;
+    for (int64_t t = 0; t <= k; ++t)
+        off[t] = t * q + (t < rem ? t : rem);
+    return ORC_OK;
+}
+
+/* Row helpers.  dot = sum_c A_ic x_c in stored order. */
+static double row_dot(const orc_matrix *A, int64_t i, const double *x)
+{
+    double s = 0.0;
+    if (A->is_dense) {
+        const double *a = A->dense + i * A->ld;
+        for (int64_t c = 0; c < A->n; ++c) s += a[c] * x[c];
+    } else {
+        for (int64_t p = A->row_ptr[i]; p < A->row_ptr[i + 1]; ++p)
+            s += A->val[p] * x[A->col_idx[p]];
+    }
+    return s;
+}
+
+/* Gram entry <A_i, A_j> in ascending column order. */
+static double row_row_dot(const orc_matrix *A, int64_t i, int64_t j)
+{
+    double s = 0.0;
+    if (A->is_dense) {
+        const double *a = A->dense + i * A->ld, *b = A->dense + j * A->ld;
+        for (int64_t c = 0; c < A->n; ++c) s += a[c] * b[c];
+        return s;
+    }
+    int64_t p = A->row_ptr[i], pe = A->row_ptr[i + 1];
+    int64_t q = A->row_ptr[j], qe = A->row_ptr[j + 1];
+    while (p < pe && q < qe) {
+        int32_t cp = A->col_idx[p], cq = A->col_idx[q];
+        if (cp == cq) { s += A->val[p] * A->val[q]; ++p; ++q; }
+        else if (cp < cq) ++p;
+        else ++q;
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1, steps 1-2 and the Section 2 definitions: centroids
+ * Abar_t = sum of the block's rows, C(i,j) = |<Abar_i,Abar_j>|/(|Abar_i||Abar_j|).
+ * Outputs the row sums sum_j C(t,j) (always) and the full k x k matrix C when
+ * C != NULL.  Each centroid is kept as a sorted (column, value) list; the
+ * Gram matrix Abar Abar^T is formed as a sum over columns c (ascending) of
+ * the outer products of column c of Abar^T: G(i,j) = sum_c Abar_ic Abar_jc. */
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_orthogonality(const orc_matrix *A, int64_t k, const int64_t *off,
+                      double *C, double *C_rowsum)
+{
+    int64_t n = A->n;
+    int st = ORC_ERR_OOM;
+    double *acc = (double *)calloc((size_t)n, sizeof(double));
+    unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
+    int64_t *cptr = (int64_t *)calloc((size_t)k + 1, sizeof(int64_t));
+    int64_t *colcnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t cap = 1024, used = 0;
+    int32_t *ccol = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    double *cval = (double *)malloc((size_t)cap * sizeof(double));
+    int32_t *cb = NULL;
+    double *cv = NULL, *G = NULL;
+    int64_t *fill = NULL;
+    if (!acc || !seen || !cptr || !colcnt || !ccol || !cval) goto out;
+
+    /* centroids: sum of the block's rows (rows ascending) */
+    for (int64_t t = 0; t < k; ++t) {
+        int64_t need = used + (A->is_dense ? n : 0);
+        if (!A->is_dense)
+            for (int64_t i = off[t]; i < off[t + 1]; ++i)
+                need += A->row_ptr[i + 1] - A->row_ptr[i];
+        if (need > cap) {
+            while (cap < need) cap *= 2;
+            int32_t *nc = (int32_t *)realloc(ccol, (size_t)cap * sizeof(int32_t));
+            if (!nc) goto out;
+            ccol = nc;
+            double *nv = (double *)realloc(cval, (size_t)cap * sizeof(double));
+            if (!nv) goto out;
+            cval = nv;
+        }
+        int64_t len = 0;
+        for (int64_t i = off[t]; i < off[t + 1]; ++i) {
+            if (A->is_dense) {
+                for (int64_t c = 0; c < n; ++c) acc[c] += A->dense[i * A->ld + c];
+                continue;
+            }
+            for (int64_t p = A->row_ptr[i]; p < A->row_ptr[i + 1]; ++p) {
+                int32_t c = A->col_idx[p];
+                acc[c] += A->val[p];
+                if (!seen[c]) { seen[c] = 1; ccol[used + len++] = c; }
+            }
+        }
+        if (A->is_dense) {
+            for (int64_t c = 0; c < n; ++c) ccol[used + c] = (int32_t)c;
+            len = n;
+        } else {
+            qsort(ccol + used, (size_t)len, sizeof(int32_t), cmp_i32);
+        }
+        for (int64_t a = 0; a < len; ++a) {
+            int32_t c = ccol[used + a];
+            cval[used + a] = acc[c];
+            acc[c] = 0.0;
+            seen[c] = 0;
+            colcnt[c + 1]++;
+        }
+        used += len;
+        cptr[t + 1] = used;
+    }
+
+    /* column lists of Abar (blocks in ascending order), then the Gram */
+    for (int64_t c = 0; c < n; ++c) colcnt[c + 1] += colcnt[c];
+    cb = (int32_t *)malloc((size_t)(used ? used : 1) * sizeof(int32_t));
+    cv = (double *)malloc((size_t)(used ? used : 1) * sizeof(double));
+    fill = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    G = (double *)calloc((size_t)k * (size_t)k, sizeof(double));
+    if (!cb || !cv || !fill || !G) goto out;
+    for (int64_t c = 0; c < n; ++c) fill[c] = colcnt[c];
+    for (int64_t t = 0; t < k; ++t)
+        for (int64_t a = cptr[t]; a < cptr[t + 1]; ++a) {
+            int64_t pos = fill[ccol[a]]++;
+            cb[pos] = (int32_t)t;
+            cv[pos] = cval[a];
+        }
+    for (int64_t c = 0; c < n; ++c)
+        for (int64_t a = colcnt[c]; a < colcnt[c + 1]; ++a)
+            for (int64_t b2 = colcnt[c]; b2 < colcnt[c + 1]; ++b2)
+                G[(int64_t)cb[a] * k + cb[b2]] += cv[a] * cv[b2];
+
+    for (int64_t i = 0; i < k; ++i) {
+        double rsum = 0.0;
+        double ni = sqrt(G[i * k + i]);
+        for (int64_t j = 0; j < k; ++j) {
+            double nj = sqrt(G[j * k + j]);
+            double cij;
+            if (i == j) cij = 1.0;
+            else if (ni == 0.0 || nj == 0.0) cij = 0.0;
+            else cij = fabs(G[i * k + j]) / (ni * nj);
+            if (C) C[i * k + j] = cij;
+            rsum += cij;
+        }
+        C_rowsum[i] = rsum;
+    }
+    st = ORC_OK;
+out:
+    free(acc); free(seen); free(cptr); free(colcnt); free(ccol); free(cval);
+    free(cb); free(cv); free(fill); free(G);
+    return st;
+}
+
+/* Algorithm 1, steps 3-4 / Section 2: Pbar_t = exp(-2 sum_j C(t,j) / n),
+ * P = Pbar / sum(Pbar).  Also the sequential FP64 prefix sum cdf_t. */
+void orc_proposal(const double *C_rowsum, int64_t k, int64_t n, double *Pbar,
+                  double *P, double *cdf)
+{
+    double s = 0.0;
+    for (int64_t t = 0; t < k; ++t) {
+        Pbar[t] = exp(-2.0 * C_rowsum[t] / (double)n);
+        s += Pbar[t];
+        cdf[t] = s;
+    }
+    if (P) for (int64_t t = 0; t < k; ++t) P[t] = Pbar[t] / s;
+}
+
+/* Draw tau for (iteration it, static update l). */
+int64_t orc_sample(const double *cdf, int64_t k, uint64_t seed, uint64_t sysid,
+                   int64_t it, int64_t l)
+{
+    uint64_t ctr[4] = {(uint64_t)it, (uint64_t)l, 0, 0}, key[2] = {seed, sysid}, w[4];
+    orc_philox4x64_10(ctr, key, w);
+    double u = (double)(w[0] >> 11) * 0x1.0p-53;
+    double target = u * cdf[k - 1];
+    for (int64_t t = 0; t < k; ++t)
+        if (target < cdf[t]) return t;
+    return k - 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1: r = b - A x and ||r||^2 (sequential sum). */
+double orc_residual(const orc_matrix *A, const double *b, const double *x, double *r)
+{
+    double rr = 0.0;
+    for (int64_t i = 0; i < A->m; ++i) {
+        r[i] = b[i] - row_dot(A, i, x);
+        rr += r[i] * r[i];
+    }
+    return rr;
+}
+
+/* Algorithm 1 (residual-based dynamic aggregation): indices of the K largest
+ * |r_i| (ties to the lower index), written in ascending order.  A bounded
+ * min-heap keyed on (|r|, -index) keeps the current best K. */
+static int heap_less(double ka, int64_t ia, double kb, int64_t ib)
+{   /* "a ranks below b": smaller key, or equal key and larger index */
+    return ka < kb || (ka == kb && ia > ib);
+}
+int orc_topk(const double *r, int64_t m, int64_t K, int64_t *I)
+{
+    if (K < 0 || K > m) return ORC_ERR_ARG;
+    if (K == 0) return ORC_OK;
+    double *hk = (double *)malloc((size_t)K * sizeof(double));
+    int64_t *hi = (int64_t *)malloc((size_t)K * sizeof(int64_t));
+    if (!hk || !hi) { free(hk); free(hi); return ORC_ERR_OOM; }
+    int64_t size = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        double key = fabs(r[i]);
+        if (size < K) {
+            int64_t c = size++;
+            hk[c] = key; hi[c] = i;
+            while (c > 0) {
+                int64_t p = (c - 1) / 2;
+                if (heap_less(hk[c], hi[c], hk[p], hi[p])) {
+                    double tk = hk[c]; hk[c] = hk[p]; hk[p] = tk;
+                    int64_t ti = hi[c]; hi[c] = hi[p]; hi[p] = ti;
+                    c = p;
+                } else break;
+            }
+        } else if (heap_less(hk[0], hi[0], key, i)) {
+            hk[0] = key; hi[0] = i;
+            int64_t c = 0;
+            for (;;) {
+                int64_t a = 2 * c + 1, b2 = a + 1, s = c;
+                if (a < K && heap_less(hk[a], hi[a], hk[s], hi[s])) s = a;
+                if (b2 < K && heap_less(hk[b2], hi[b2], hk[s], hi[s])) s = b2;
+                if (s == c) break;
+                double tk = hk[c]; hk[c] = hk[s]; hk[s] = tk;
+                int64_t ti = hi[c]; hi[c] = hi[s]; hi[s] = ti;
+                c = s;
+            }
+        }
+    }
+    /* ascending row order (insertion sort of K indices) */
+    for (int64_t a = 0; a < K; ++a) I[a] = hi[a];
+    for (int64_t a = 1; a < K; ++a) {
+        int64_t v = I[a], b2 = a - 1;
+        while (b2 >= 0 && I[b2] > v) { I[b2 + 1] = I[b2]; --b2; }
+        I[b2 + 1] = v;
+    }
+    free(hk); free(hi);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense SPD helpers on an s x s row-major array. */
+
+/* G = A_B A_B^T + mu I for the rows listed in rows[0..s). */
+void orc_block_gram(const orc_matrix *A, const int64_t *rows, int64_t s,
+                    double mu, double *G)
+{
+    for (int64_t a = 0; a < s; ++a)
+        for (int64_t b2 = 0; b2 <= a; ++b2) {
+            double g = row_row_dot(A, rows[a], rows[b2]);
+            if (a == b2) g += mu;
+            G[a * s + b2] = g;
+            G[b2 * s + a] = g;
+        }
+}
+
+/* Cholesky G = L L^T in place (lower triangle; the strict upper triangle is
+ * zeroed).  Textbook column-by-column (Cholesky-Banachiewicz-free, i.e. the
+ * right-looking outer-product form):
+ *   for j: L_jj = sqrt(G_jj); L_ij = G_ij / L_jj (i > j);
+ *          G_ab -= L_aj L_bj for a >= b > j.  */
+int orc_cholesky(double *G, int64_t s)
+{
+    for (int64_t j = 0; j < s; ++j) {
+        double d = G[j * s + j];
+        if (!(d > 0.0)) return ORC_ERR_NOT_SPD;
+        double l = sqrt(d);
+        G[j * s + j] = l;
+        for (int64_t i = j + 1; i < s; ++i) G[i * s + j] /= l;
+        for (int64_t a = j + 1; a < s; ++a) {
+            double la = G[a * s + j];
+            for (int64_t b2 = j + 1; b2 <= a; ++b2)
+                G[a * s + b2] -= la * G[b2 * s + j];
+        }
+    }
+    for (int64_t a = 0; a < s; ++a)
+        for (int64_t b2 = a + 1; b2 < s; ++b2) G[a * s + b2] = 0.0;
+    return ORC_OK;
+}
+
+/* y = (L L^T)^{-1} r: forward z_i = (r_i - sum_{c<i} L_ic z_c)/L_ii, then
+ * backward y_i = (z_i - sum_{c>i} L_ci y_c)/L_ii, sums in ascending c. */
+void orc_chol_solve(const double *L, int64_t s, const double *r, double *y)
+{
+    for (int64_t i = 0; i < s; ++i) {
+        double acc = r[i];
+        for (int64_t c = 0; c < i; ++c) acc -= L[i * s + c] * y[c];
+        y[i] = acc / L[i * s + i];
+    }
+    for (int64_t i = s - 1; i >= 0; --i) {
+        double acc = y[i];
+        for (int64_t c = i + 1; c < s; ++c) acc -= L[c * s + i] * y[c];
+        y[i] = acc / L[i * s + i];
+    }
+}
+
+/* W = (L L^T)^{-1} = L^{-T} L^{-1}.  Linv by columns: Linv_jj = 1/L_jj,
+ * Linv_ij = -(sum_{c=j}^{i-1} L_ic Linv_cj) / L_ii; then
+ * W_ij = sum_{c >= max(i,j)} Linv_ci Linv_cj (c ascending). */
+int orc_spd_inverse(const double *L, int64_t s, double *W)
+{
+    double *Li = (double *)calloc((size_t)(s * s), sizeof(double));
+    if (!Li) return ORC_ERR_OOM;
+    for (int64_t j = 0; j < s; ++j) {
+        Li[j * s + j] = 1.0 / L[j * s + j];
+        for (int64_t i = j + 1; i < s; ++i) {
+            double acc = 0.0;
+            for (int64_t c = j; c < i; ++c) acc += L[i * s + c] * Li[c * s + j];
+            Li[i * s + j] = -acc / L[i * s + i];
+        }
+    }
+    for (int64_t i = 0; i < s; ++i)
+        for (int64_t j = 0; j <= i; ++j) {
+            double acc = 0.0;
+            for (int64_t c = i; c < s; ++c) acc += Li[c * s + i] * Li[c * s + j];
+            W[i * s + j] = acc;
+            W[j * s + i] = acc;
+        }
+    free(Li);
+    return ORC_OK;
+}
+
+/* x += A_B^T y for the rows rows[0..s): delta_c = sum over rows ascending of
+ * A_rc y_r (accumulated into the zeroed scratch delta[n]), then x_c += delta_c
+ * for every column the block touches; delta is re-zeroed on exit. */
+static void scatter_update(const orc_matrix *A, const int64_t *rows, int64_t s,
+                           const double *y, double *x, double *delta)
+{
+    if (A->is_dense) {
+        for (int64_t a = 0; a < s; ++a) {
+            const double *ar = A->dense + rows[a] * A->ld;
+            for (int64_t c = 0; c < A->n; ++c) delta[c] += ar[c] * y[a];
+        }
+        for (int64_t c = 0; c < A->n; ++c) { x[c] += delta[c]; delta[c] = 0.0; }
+        return;
+    }
+    for (int64_t a = 0; a < s; ++a)
+        for (int64_t p = A->row_ptr[rows[a]]; p < A->row_ptr[rows[a] + 1]; ++p)
+            delta[A->col_idx[p]] += A->val[p] * y[a];
+    /* a column shared by several rows is applied on its first visit; later
+     * visits add the re-zeroed delta_c = 0, which leaves x_c unchanged */
+    for (int64_t a = 0; a < s; ++a)
+        for (int64_t p = A->row_ptr[rows[a]]; p < A->row_ptr[rows[a] + 1]; ++p) {
+            int32_t c = A->col_idx[p];
+            x[c] += delta[c];
+            delta[c] = 0.0;
+        }
+}
+
+/* The paper's update (Algorithm 1, Eq. in Lemma 2's proof) with a stored
+ * inverse (Section 3.1): r_B = b_B - A_B x; y = W r_B; x += A_B^T y.
+ * W is s x s row-major; y[i] = sum_j W_ij r_j in ascending j. */
+void orc_update_with_inverse(const orc_matrix *A, const int64_t *rows, int64_t s,
+                             const double *W, const double *b, double *x,
+                             double *scratch_n, double *work_2s)
+{
+    double *rB = work_2s, *y = work_2s + s;
+    for (int64_t a = 0; a < s; ++a) rB[a] = b[rows[a]] - row_dot(A, rows[a], x);
+    for (int64_t a = 0; a < s; ++a) {
+        double acc = 0.0;
+        for (int64_t c = 0; c < s; ++c) acc += W[a * s + c] * rB[c];
+        y[a] = acc;
+    }
+    scatter_update(A, rows, s, y, x, scratch_n);
+}
+
+/* The dynamic-block update: G = A_I A_I^T + mu I, L = chol(G),
+ * y = G^{-1} rI (two triangular solves), x += A_I^T y. */
+int orc_update_with_cholesky(const orc_matrix *A, const int64_t *rows, int64_t s,
+                             double mu, const double *rI, double *x,
+                             double *scratch_n)
+{
+    double *G = (double *)malloc((size_t)(s * s) * sizeof(double));
+    double *y = (double *)malloc((size_t)(s ? s : 1) * sizeof(double));
+    if (!G || !y) { free(G); free(y); return ORC_ERR_OOM; }
+    orc_block_gram(A, rows, s, mu, G);
+    int st = orc_cholesky(G, s);
+    if (st == ORC_OK) {
+        orc_chol_solve(G, s, rI, y);
+        scatter_update(A, rows, s, y, x, scratch_n);
+    }
+    free(G); free(y);
+    return st;
+}
+
+/* Static operator W_t for block t (Section 3.1): chol then explicit inverse. */
+int orc_static_operator(const orc_matrix *A, const int64_t *off, int64_t t,
+                        double mu, double *W)
+{
+    int64_t s = off[t + 1] - off[t];
+    int64_t *rows = (int64_t *)malloc((size_t)(s ? s : 1) * sizeof(int64_t));
+    double *G = (double *)malloc((size_t)(s > 0 ? s * s : 1) * sizeof(double));
+    if (!rows || !G) { free(rows); free(G); return ORC_ERR_OOM; }
+    for (int64_t a = 0; a < s; ++a) rows[a] = off[t] + a;
+    orc_block_gram(A, rows, s, mu, G);
+    int st = orc_cholesky(G, s);
+    if (st == ORC_OK) st = orc_spd_inverse(G, s, W);
+    free(rows); free(G);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1, the whole solve.
+ *   inputs : A, k blocks (uniform partition), mu, b, x0 (NULL -> 0), tol,
+ *            maxit, seed, sysid, n_static (3 in the paper), start_iter (the
+ *            counter offset of the first iteration, so a solve can resume).
+ *   outputs: x, *iters, *rrn.
+ *   traces (each may be NULL):
+ *     tr_tau [maxit * n_static]  sampled blocks
+ *     tr_rrn [maxit]             RRN after the static updates of iteration j
+ *     tr_I   [maxit * K]         dynamic index sets (ascending)
+ *     tr_x   [maxit * n]         x at the end of each iteration (after the
+ *                                dynamic update; on the converging iteration,
+ *                                x after the static updates)
+ * Returns ORC_OK when converged, ORC_NOT_CONVERGED at maxit, or an error. */
+int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
+              const double *x0, double *x, double tol, int64_t maxit,
+              uint64_t seed, uint64_t sysid, int64_t n_static, int64_t start_iter,
+              int64_t *iters, double *rrn_out,
+              int64_t *tr_tau, double *tr_rrn, int64_t *tr_I, double *tr_x)
+{
+    int64_t m = A->m, n = A->n;
+    if (k < 1 || k > m || n_static < 0) return ORC_ERR_ARG;
+    int64_t K = m / k;
+    int64_t *off = (int64_t *)malloc((size_t)(k + 1) * sizeof(int64_t));
+    double *rs = (double *)malloc((size_t)k * sizeof(double));
+    double *Pbar = (double *)malloc((size_t)k * sizeof(double));
+    double *cdf = (double *)malloc((size_t)k * sizeof(double));
+    double *r = (double *)malloc((size_t)m * sizeof(double));
+    double *delta = (double *)calloc((size_t)n, sizeof(double));
+    double **Wcache = (double **)calloc((size_t)k, sizeof(double *));
+    int64_t *I = (int64_t *)malloc((size_t)(K ? K : 1) * sizeof(int64_t));
+    double *rI = (double *)malloc((size_t)(K ? K : 1) * sizeof(double));
+    int64_t smax = m / k + 1;
+    int64_t *rows = (int64_t *)malloc((size_t)smax * sizeof(int64_t));
+    double *work = (double *)malloc((size_t)(2 * smax) * sizeof(double));
+    int st = ORC_OK;
+    if (!off || !rs || !Pbar || !cdf || !r || !delta || !Wcache || !I || !rI ||
+        !rows || !work) { st = ORC_ERR_OOM; goto done; }
+
+    orc_partition(m, k, off);
+    st = orc_orthogonality(A, k, off, NULL, rs);
+    if (st != ORC_OK) goto done;
+    orc_proposal(rs, k, n, Pbar, NULL, cdf);
+
+    for (int64_t c = 0; c < n; ++c) x[c] = x0 ? x0[c] : 0.0;
+    double bb = 0.0;
+    for (int64_t i = 0; i < m; ++i) bb += b[i] * b[i];
+    double bnorm = sqrt(bb);
+    *iters = 0;
+    *rrn_out = 0.0;
+    if (bnorm == 0.0) {
+        for (int64_t c = 0; c < n; ++c) x[c] = 0.0;
+        st = ORC_OK;
+        goto done;
+    }
+    st = ORC_NOT_CONVERGED;
+    for (int64_t j = 0; j < maxit; ++j) {
+        for (int64_t l = 0; l < n_static; ++l) {
+            int64_t tau = orc_sample(cdf, k, seed, sysid, start_iter + j, l);
+            if (tr_tau) tr_tau[j * n_static + l] = tau;
+            int64_t s = off[tau + 1] - off[tau];
+            if (!Wcache[tau]) {
+                Wcache[tau] = (double *)malloc((size_t)(s * s) * sizeof(double));
+                if (!Wcache[tau]) { st = ORC_ERR_OOM; goto done; }
+                int e = orc_static_operator(A, off, tau, mu, Wcache[tau]);
+                if (e != ORC_OK) { st = e; goto done; }
+            }
+            for (int64_t a = 0; a < s; ++a) rows[a] = off[tau] + a;
+            orc_update_with_inverse(A, rows, s, Wcache[tau], b, x, delta, work);
+        }
+        double rr = orc_residual(A, b, x, r);
+        double rrn = sqrt(rr) / bnorm;
+        if (tr_rrn) tr_rrn[j] = rrn;
+        *iters = j + 1;
+        *rrn_out = rrn;
+        if (rrn <= tol) {
+            if (tr_x) memcpy(tr_x + j * n, x, (size_t)n * sizeof(double));
+            st = ORC_OK;
+            break;
+        }
+        orc_topk(r, m, K, I);
+        if (tr_I) memcpy(tr_I + j * K, I, (size_t)K * sizeof(int64_t));
+        for (int64_t a = 0; a < K; ++a) rI[a] = r[I[a]];
+        int e = orc_update_with_cholesky(A, I, K, mu, rI, x, delta);
+        if (e != ORC_OK) { st = e; break; }
+        if (tr_x) memcpy(tr_x + j * n, x, (size_t)n * sizeof(double));
+    }
+done:
+    if (Wcache) for (int64_t t = 0; t < k; ++t) free(Wcache[t]);
+    free(Wcache); free(off); free(rs); free(Pbar); free(cdf); free(r); free(delta);
+    free(I); free(rI); free(rows); free(work);
+    return st;
+}

@@ -1,0 +1,391 @@
+"""Pins for the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these re-types the oracle's own formula: each compares it with a
+closed form, an invariant, a library routine for a special case, or brute
+force on a tiny input (see each test's docstring for the passage it pins).
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.sparse
+
+import oracle
+from paper_2510_02156_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- sampler
+def test_philox_golden_kat():
+    """Philox4x64-10 (Salmon et al. SC'11) published all-zero KAT."""
+    for line in open(os.path.join(GOLDEN, "philox4x64_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        ctr = np.array([int(v) for v in f[0:4]], dtype=np.uint64)
+        key = np.array([int(v) for v in f[4:6]], dtype=np.uint64)
+        want = np.array([int(v, 16) for v in f[6:10]], dtype=np.uint64)
+        assert (oracle.philox4x64_10(ctr, key) == want).all()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 12345])
+def test_philox_matches_numpy(seed):
+    """numpy.random.Philox is an independent Philox4x64-10; its counter is
+    pre-incremented, so counter c-1 there gives block c here."""
+    rng = np.random.default_rng(seed)
+    for _ in range(50):
+        ctr = [int(v) for v in rng.integers(0, 2**63, 4, dtype=np.int64)]
+        ctr[0] = [0, 1, 2**64 - 1, ctr[0]][int(rng.integers(0, 4))]
+        key = rng.integers(0, 2**63, 2, dtype=np.int64).astype(np.uint64)
+        v = sum(c << (64 * i) for i, c in enumerate(ctr)) - 1
+        v %= 2**256
+        prev = np.array([(v >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
+        ref = np.random.Philox(key=key, counter=prev).random_raw(4)
+        got = oracle.philox4x64_10(np.array(ctr, dtype=np.uint64), key)
+        assert (got == ref).all()
+
+
+def test_sampler_distribution_chi2():
+    """Algorithm 1 samples tau ~ P; a chi-square test over 200k counters."""
+    import scipy.stats
+    k = 7
+    Pbar = np.array([0.5, 1.0, 2.0, 0.25, 3.0, 1.5, 0.75])
+    cdf = np.cumsum(Pbar)
+    n_draw = 200_000
+    counts = np.zeros(k)
+    lib = oracle.lib()
+    c = np.ascontiguousarray(cdf)
+    for it in range(n_draw // 2):
+        for l in range(2):
+            counts[lib.orc_sample(c.ctypes.data, k, 99, 3, it, l)] += 1
+    expected = Pbar / Pbar.sum() * n_draw
+    chi2 = ((counts - expected) ** 2 / expected).sum()
+    assert scipy.stats.chi2.sf(chi2, k - 1) > 1e-4
+
+
+def test_sampler_inverse_cdf_bruteforce():
+    """tau is the first t with u * cdf[-1] < cdf[t], u from word 0 of the
+    Philox block at counter (it, l, 0, 0), key (seed, sysid)."""
+    cdf = np.cumsum(np.array([1.0, 0.0, 2.0, 0.5, 0.0, 1.0]))   # zero-mass blocks
+    for it in range(300):
+        for l in range(3):
+            w = np.random.Philox(key=np.array([5, 9], dtype=np.uint64),
+                                 counter=np.array([(it - 1) % 2**64 if it else 2**64 - 1,
+                                                   l if it else (l - 1) % 2**64,
+                                                   0 if (it or l) else 2**64 - 1,
+                                                   0 if (it or l) else 2**64 - 1],
+                                                  dtype=np.uint64)).random_raw(1)[0]
+            u = float(int(w) >> 11) * 2.0 ** -53
+            want = int(np.searchsorted(cdf, u * cdf[-1], side="right"))
+            got = oracle.sample(cdf, 5, 9, it, l)
+            assert got == want
+            assert cdf[got] > (cdf[got - 1] if got else 0.0)   # never a zero-mass block
+
+
+# --------------------------------------------------------------- partition
+@pytest.mark.parametrize("m,k", [(2025, 32), (100, 7), (64, 64), (10, 1), (1 << 20, 4096)])
+def test_partition_contiguous_uniform(m, k):
+    """Algorithm 1 step 1 / Section 2: k contiguous blocks, each with at
+    least floor(m/k) rows, covering all rows in order."""
+    off = oracle.partition(m, k)
+    sizes = np.diff(off)
+    assert off[0] == 0 and off[-1] == m and len(sizes) == k
+    assert (sizes >= m // k).all() and (sizes <= m // k + 1).all()
+    assert (sizes[: m % k] == m // k + 1).all()
+
+
+# ------------------------------------------------------- orthogonality / P
+def _csr_system(Ad, k=2):
+    sp = scipy.sparse.csr_matrix(Ad)
+    sp.sort_indices()
+    return W.System("t", Ad.shape[0], Ad.shape[1], row_ptr=sp.indptr.astype(np.int64),
+                    col_idx=sp.indices.astype(np.int32), values=sp.data.astype(np.float64),
+                    x_true=np.zeros(Ad.shape[1]), b=np.zeros(Ad.shape[0]), num_blocks=k)
+
+
+def test_orthogonality_known_angles():
+    """Section 2: C(i,j) is the |cosine| between block centroids (sums of the
+    block's rows).  Centroids e1, e1+e2 and -e2 have cosines 1/sqrt2, 0, 1/sqrt2."""
+    Ad = np.array([[1.0, 0, 0], [0.0, 0, 0],          # block 0 -> (1,0,0)
+                   [0.5, 2, 0], [0.5, -1, 0],        # block 1 -> (1,1,0)
+                   [0.0, -3, 0], [0.0, 1, 0]])       # block 2 -> (0,-2,0)
+    Cm, rs = oracle.orthogonality(_csr_system(Ad), 3, full=True)
+    h = 1 / np.sqrt(2)
+    want = np.array([[1, h, 0], [h, 1, h], [0, h, 1]])
+    np.testing.assert_allclose(Cm, want, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(rs, want.sum(1), rtol=1e-15)
+
+
+def test_orthogonality_disjoint_supports_uniform_P():
+    """Blocks with disjoint column supports are mutually orthogonal: C = I,
+    so every Pbar_t = exp(-2/n) and P is uniform (Section 2 formula)."""
+    rng = np.random.default_rng(0)
+    k, s, n = 6, 4, 30
+    Ad = np.zeros((k * s, n))
+    for t in range(k):
+        Ad[t * s:(t + 1) * s, t * 5:(t + 1) * 5] = rng.standard_normal((s, 5))
+    Cm, rs = oracle.orthogonality(_csr_system(Ad, k), k, full=True)
+    np.testing.assert_array_equal(Cm, np.eye(k))
+    Pbar, P, cdf = oracle.proposal(rs, n)
+    np.testing.assert_allclose(Pbar, np.exp(-2.0 / n), rtol=1e-15)
+    np.testing.assert_allclose(P, 1.0 / k, rtol=1e-14)
+
+
+def test_orthogonality_parallel_blocks():
+    """Blocks whose centroids are (anti)parallel have C = all ones, so
+    Pbar_t = exp(-2k/n)."""
+    rng = np.random.default_rng(1)
+    k, n = 5, 8
+    v = rng.standard_normal(n)
+    Ad = np.vstack([(t + 1) * (-1) ** t * v for t in range(k)])
+    Cm, rs = oracle.orthogonality(_csr_system(Ad, k), k, full=True)
+    np.testing.assert_allclose(Cm, np.ones((k, k)), rtol=1e-14)
+    Pbar, P, _ = oracle.proposal(rs, n)
+    np.testing.assert_allclose(Pbar, np.exp(-2.0 * k / n), rtol=1e-13)
+
+
+def test_orthogonality_invariances_and_dense_equals_csr():
+    """|cos| is invariant to a positive or negative scaling of a block and
+    to the storage format; the zero centroid reads as orthogonal to all."""
+    rng = np.random.default_rng(2)
+    Ad = rng.standard_normal((12, 5)) * (rng.random((12, 5)) < 0.6)
+    Ad[8:12] = 0.0                                     # block 2 has a zero centroid
+    sysd = W.System("d", 12, 5, dense=Ad, x_true=np.zeros(5), b=np.zeros(12), num_blocks=3)
+    C1, _ = oracle.orthogonality(_csr_system(Ad, 3), 3, full=True)
+    C2, _ = oracle.orthogonality(sysd, 3, full=True)
+    np.testing.assert_allclose(C1, C2, rtol=1e-14, atol=1e-15)
+    Ad2 = Ad.copy()
+    Ad2[0:4] *= -3.7
+    C3, _ = oracle.orthogonality(_csr_system(Ad2, 3), 3, full=True)
+    np.testing.assert_allclose(C1, C3, rtol=1e-13, atol=1e-15)
+    assert C1[2, 2] == 1.0 and C1[2, 0] == 0.0 and C1[1, 2] == 0.0
+    assert np.allclose(C1, C1.T) and (C1 >= 0).all() and (C1 <= 1 + 1e-15).all()
+
+
+def test_proposal_normalised():
+    """P = Pbar / sum(Pbar) sums to one; the cdf ends at sum(Pbar)."""
+    rs = np.array([1.0, 3.5, 2.0, 1.25])
+    Pbar, P, cdf = oracle.proposal(rs, 10)
+    assert abs(P.sum() - 1) < 1e-15
+    np.testing.assert_allclose(Pbar, [np.exp(-0.2), np.exp(-0.7), np.exp(-0.4), np.exp(-0.25)],
+                               rtol=1e-15)
+    assert cdf[-1] == pytest.approx(Pbar.sum(), rel=1e-15)
+
+
+# ------------------------------------------------------------ residual/topk
+def test_residual_matches_scipy():
+    """r = b - A x against scipy.sparse's SpMV; ||r||^2 against numpy."""
+    s = W.random_sparse(300, 200, 0.05, seed=3)
+    x = np.random.default_rng(0).standard_normal(200)
+    r, rr = oracle.residual(s, s.b, x)
+    A = scipy.sparse.csr_matrix((s.values, s.col_idx, s.row_ptr), shape=(300, 200))
+    np.testing.assert_allclose(r, s.b - A @ x, rtol=1e-13, atol=1e-13)
+    assert rr == pytest.approx(float(r @ r), rel=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_topk_bruteforce_with_ties(seed):
+    """Algorithm 1 top floor(m/k) of r_i^2; ties broken to the lower index,
+    output ascending (brute force: stable sort on -|r|)."""
+    rng = np.random.default_rng(seed)
+    m = 500
+    r = rng.integers(-20, 20, m).astype(np.float64)     # heavy exact ties, +-
+    r[rng.choice(m, 40, replace=False)] = 0.0
+    for K in [0, 1, 7, 63, 250, m]:
+        got = oracle.topk(r, K)
+        order = np.argsort(-np.abs(r), kind="stable")
+        want = np.sort(order[:K])
+        np.testing.assert_array_equal(got, want)
+
+
+# ------------------------------------------------------------ factorisation
+def test_cholesky_inverse_solve_match_lapack():
+    """Cholesky, two triangular solves and the explicit inverse (Section 3.1
+    stores (A A^T + mu I)^{-1}) against numpy/LAPACK."""
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((40, 60))
+    G = B @ B.T + 1e-3 * np.eye(40)
+    L = oracle.cholesky(G)
+    np.testing.assert_allclose(L, np.linalg.cholesky(G), rtol=1e-11, atol=1e-12)
+    assert np.all(np.triu(L, 1) == 0)
+    r = rng.standard_normal(40)
+    np.testing.assert_allclose(oracle.chol_solve(L, r), np.linalg.solve(G, r), rtol=1e-9)
+    Wm = oracle.spd_inverse(L)
+    np.testing.assert_allclose(Wm, np.linalg.inv(G), rtol=1e-9, atol=1e-11)
+    np.testing.assert_array_equal(Wm, Wm.T)
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.cholesky(-np.eye(3))
+
+
+def test_block_gram_is_AAT_plus_mu():
+    rng = np.random.default_rng(5)
+    s = W.random_sparse(50, 30, 0.2, seed=5)
+    rows = np.array([3, 7, 8, 20, 41])
+    Ad = s.to_dense()
+    G = oracle.block_gram(s, rows, 0.25)
+    np.testing.assert_allclose(G, Ad[rows] @ Ad[rows].T + 0.25 * np.eye(5), rtol=1e-14, atol=1e-15)
+
+
+# --------------------------------------------------------- one block update
+def _dense(Ad, k=1, lam=0.0):
+    return W.System("d", Ad.shape[0], Ad.shape[1], dense=Ad, x_true=np.zeros(Ad.shape[1]),
+                    b=np.zeros(Ad.shape[0]), num_blocks=k, lam=lam)
+
+
+def test_update_mu0_projects_onto_block():
+    """Eq. (3): with mu = 0 and a full-row-rank block, x+ satisfies
+    A_B x+ = b_B, and x+ = x + pinv(A_B)(b_B - A_B x)."""
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((12, 30))
+    b = rng.standard_normal(12)
+    x = rng.standard_normal(30)
+    rows = np.arange(4, 9)
+    sysd = _dense(A)
+    L = oracle.cholesky(oracle.block_gram(sysd, rows, 0.0))
+    x1 = oracle.update_with_cholesky(sysd, rows, 0.0, b[rows] - A[rows] @ x, x)
+    np.testing.assert_allclose(A[rows] @ x1, b[rows], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(x1, x + np.linalg.pinv(A[rows]) @ (b[rows] - A[rows] @ x),
+                               rtol=1e-11, atol=1e-12)
+    Wm = oracle.spd_inverse(L)
+    x2 = oracle.update_with_inverse(sysd, rows, Wm, b, x)
+    np.testing.assert_allclose(x2, x1, rtol=1e-11, atol=1e-12)
+
+
+def test_update_single_row_is_kaczmarz():
+    """Eq. (2): a one-row block with mu = 0 is the classical Kaczmarz step."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((5, 9))
+    b = rng.standard_normal(5)
+    x = rng.standard_normal(9)
+    i = 3
+    x1 = oracle.update_with_cholesky(_dense(A), np.array([i]), 0.0,
+                                     np.array([b[i] - A[i] @ x]), x)
+    want = x + (b[i] - A[i] @ x) / (A[i] @ A[i]) * A[i]
+    np.testing.assert_allclose(x1, want, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("mu", [1e-6, 1e-2, 3.0])
+def test_update_regularised_closed_form_and_error_map(mu):
+    """Lemma 1 / the proximal-point form: x+ = (A_B^T A_B + mu I)^{-1}
+    (A_B^T b_B + mu x); Theorem 1's proof: for b = A x*, the error map is
+    x+ - x* = mu (A_B^T A_B + mu I)^{-1} (x - x*), hence non-expansive.
+    Both closed forms are evaluated through LAPACK's SVD of A_B
+    (A_B = U S V^T), which stays accurate for small mu."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((20, 15))
+    xs = rng.standard_normal(15)
+    b = A @ xs
+    x = rng.standard_normal(15)
+    rows = np.array([2, 5, 6, 11, 17, 19])
+    sysd = _dense(A)
+    AB = A[rows]
+    U, S, Vt = np.linalg.svd(AB, full_matrices=True)
+    V = Vt.T
+    Vr = V[:, : len(S)]
+    Wm = oracle.spd_inverse(oracle.cholesky(oracle.block_gram(sysd, rows, mu)))
+    x1 = oracle.update_with_inverse(sysd, rows, Wm, b, x)
+    want = x + Vr @ ((S / (S ** 2 + mu)) * (U.T @ (b[rows] - AB @ x)))
+    np.testing.assert_allclose(x1, want, rtol=1e-10, atol=1e-11)
+    e = x - xs
+    emap = Vr @ ((mu / (S ** 2 + mu)) * (Vr.T @ e)) + (e - Vr @ (Vr.T @ e))
+    np.testing.assert_allclose(x1 - xs, emap, rtol=1e-9, atol=1e-10)
+    assert np.linalg.norm(x1 - xs) <= np.linalg.norm(e) * (1 + 1e-12)
+    x2 = oracle.update_with_cholesky(sysd, rows, mu, b[rows] - AB @ x, x)
+    np.testing.assert_allclose(x2, x1, rtol=1e-10, atol=1e-11)
+
+
+def test_update_sparse_equals_dense_storage():
+    """The same block update on CSR and dense storage of one matrix."""
+    s = W.random_sparse(40, 25, 0.15, seed=9)
+    Ad = s.to_dense()
+    x = np.random.default_rng(1).standard_normal(25)
+    rows = np.array([0, 1, 2, 3, 4, 5, 6, 7])
+    x1 = oracle.update_with_cholesky(s, rows, 1e-3, s.b[rows] - Ad[rows] @ x, x)
+    x2 = oracle.update_with_cholesky(_dense(Ad), rows, 1e-3, s.b[rows] - Ad[rows] @ x, x)
+    np.testing.assert_allclose(x1, x2, rtol=1e-13, atol=1e-14)
+
+
+# ------------------------------------------------------------ whole solver
+def test_solve_reaches_dense_lu_solution():
+    """Algorithm 1 on a tiny consistent square system converges to the
+    LU solution (scipy.linalg.lu_solve)."""
+    rng = np.random.default_rng(10)
+    n = 48
+    A = rng.standard_normal((n, n)) + n ** 0.5 * np.eye(n)
+    b = rng.standard_normal(n)
+    sysd = W.System("sq", n, n, dense=A, x_true=None, b=b, num_blocks=6, lam=1e-8, tol=1e-13)
+    res = oracle.solve(sysd, maxit=5000)
+    assert res.converged
+    x_lu = scipy.linalg.lu_solve(scipy.linalg.lu_factor(A), b)
+    np.testing.assert_allclose(res.x, x_lu, rtol=1e-9, atol=1e-10)
+
+
+def test_solve_sparse_recovers_x_true():
+    """Consistent, full-column-rank sparse system: x -> x_true."""
+    s = W.powerlaw(n=4096, num_blocks=16, seed=3, lam=1e-8, tol=1e-11)
+    res = oracle.solve(s, maxit=4000)
+    assert res.converged
+    rel = np.linalg.norm(res.x - s.x_true) / np.linalg.norm(s.x_true)
+    assert rel < 1e-7
+
+
+def test_solve_underdetermined_min_norm_and_range():
+    """Lemma 2: with x0 = 0 every iterate lies in R(A^T); for a consistent
+    m < n system the limit is the minimum-norm solution pinv(A) b."""
+    rng = np.random.default_rng(11)
+    m, n = 30, 80
+    A = rng.standard_normal((m, n))
+    b = A @ rng.standard_normal(n)
+    sysd = W.System("wide", m, n, dense=A, b=b, num_blocks=3, lam=1e-10, tol=1e-12)
+    res = oracle.solve(sysd, maxit=3000, trace_x=True)
+    assert res.converged
+    np.testing.assert_allclose(res.x, np.linalg.pinv(A) @ b, rtol=1e-9, atol=1e-10)
+    P_null = np.eye(n) - np.linalg.pinv(A) @ A
+    for xj in res.x_trace[:: max(1, res.iters // 20)]:
+        assert np.linalg.norm(P_null @ xj) <= 1e-10 * max(1.0, np.linalg.norm(xj))
+
+
+def test_solve_error_non_increasing():
+    """Theorem 1 (exact map, mu > 0): every block update is non-expansive
+    in the error, so ||x_j - x*|| never increases across iterations."""
+    s = W.random_sparse(120, 60, 0.1, seed=12, num_blocks=6, lam=1e-4)
+    res = oracle.solve(s, maxit=60, tol=0.0, trace_x=True)
+    xs = np.linalg.lstsq(s.to_dense(), s.b, rcond=None)[0]
+    err = np.linalg.norm(res.x_trace - xs, axis=1)
+    assert (np.diff(err) <= 1e-12 * err[:-1]).all()
+
+
+def test_solve_trace_consistency_and_resume():
+    """The tau trace is the sampler at (j, l); a solve stopped after 10
+    iterations and resumed with start_iter = 10 equals a 20-iteration solve
+    bit for bit (x is the whole state of Algorithm 1)."""
+    s = W.laplace2d(g=12, num_blocks=8)
+    full = oracle.solve(s, maxit=20, tol=0.0, seed=4, trace_tau=True, trace_rrn=True, trace_I=True)
+    Pbar, P, cdf = oracle.proposal(oracle.orthogonality(s, 8), s.n)
+    for j in range(20):
+        for l in range(3):
+            assert full.tau[j, l] == oracle.sample(cdf, 4, 0, j, l)
+    a = oracle.solve(s, maxit=10, tol=0.0, seed=4)
+    bb = oracle.solve(s, x0=a.x, maxit=10, tol=0.0, seed=4, start_iter=10)
+    np.testing.assert_array_equal(bb.x, full.x)
+    # the dynamic set is the top-K of the residual formed after the statics
+    assert full.I.shape == (20, s.m // 8)
+
+
+def test_solve_zero_rhs_and_immediate_convergence():
+    s = W.laplace2d(g=6, num_blocks=4)
+    res = oracle.solve(s, b=np.zeros(s.m), maxit=10)
+    assert res.converged and res.iters == 0 and not res.x.any()
+    res = oracle.solve(s, x0=s.x_true, maxit=10, tol=1e-10)
+    assert res.converged and res.iters == 1
+
+
+def test_solve_not_spd_with_zero_mu_and_dependent_rows():
+    """mu = 0 with a rank-deficient block is the case regularisation exists
+    for (Theorem 1 discussion): the Gram is singular and Cholesky fails."""
+    A = np.ones((8, 3))
+    sysd = W.System("sing", 8, 3, dense=A, b=A @ np.ones(3), num_blocks=2, lam=0.0)
+    with pytest.raises(RuntimeError):
+        oracle.solve(sysd, maxit=3)
