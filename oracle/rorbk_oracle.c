@@ -391,19 +391,21 @@ int orc_cholesky(double *G, int64_t s)
     return ORC_OK;
 }
 
-/* y = (L L^T)^{-1} r: forward z_i = (r_i - sum_{c<i} L_ic z_c)/L_ii, then
- * backward y_i = (z_i - sum_{c>i} L_ci y_c)/L_ii, sums in ascending c. */
+/* y = (L L^T)^{-1} r by two triangular solves in column (saxpy) order:
+ *   forward : y = r; for j = 0..s-1: y_j /= L_jj; y_i -= L_ij y_j (i > j);
+ *   backward: for j = s-1..0: y_j /= L_jj; y_i -= L_ji y_j (i < j).
+ * (Each y_i therefore receives its subtractions in ascending j on the way
+ * forward and in descending j on the way back.) */
 void orc_chol_solve(const double *L, int64_t s, const double *r, double *y)
 {
-    for (int64_t i = 0; i < s; ++i) {
-        double acc = r[i];
-        for (int64_t c = 0; c < i; ++c) acc -= L[i * s + c] * y[c];
-        y[i] = acc / L[i * s + i];
+    for (int64_t i = 0; i < s; ++i) y[i] = r[i];
+    for (int64_t j = 0; j < s; ++j) {
+        y[j] = y[j] / L[j * s + j];
+        for (int64_t i = j + 1; i < s; ++i) y[i] -= L[i * s + j] * y[j];
     }
-    for (int64_t i = s - 1; i >= 0; --i) {
-        double acc = y[i];
-        for (int64_t c = i + 1; c < s; ++c) acc -= L[c * s + i] * y[c];
-        y[i] = acc / L[i * s + i];
+    for (int64_t j = s - 1; j >= 0; --j) {
+        y[j] = y[j] / L[j * s + j];
+        for (int64_t i = 0; i < j; ++i) y[i] -= L[j * s + i] * y[j];
     }
 }
 
