@@ -1,0 +1,232 @@
+/*
+ * rorbk.h -- C ABI of the GB300 ROR-BK solver.
+ *
+ * ROR-BK (Regularized Orthogonality and Residual based Block-Kaczmarz) solves a
+ * consistent linear system A x = b, A in R^{m x n}, square, over- or
+ * under-determined (Kar & Venkatapathi, arXiv 2510.02156, Section 1 Eq. (1)
+ * and Section 2).  Algorithm 1 of the paper is the method:
+ *
+ *   setup   (Algorithm 1, steps 1-4; Section 2; Section 3.1)
+ *     - split the rows into k contiguous blocks of >= floor(m/k) rows;
+ *     - centroids Abar_t = sum of block t's rows;
+ *       C(i,j) = |<Abar_i,Abar_j>| / (|Abar_i| |Abar_j|);
+ *     - Pbar_t = exp(-2 sum_j C(t,j) / n),  P = Pbar / sum(Pbar);
+ *     - for each block, W_t = (A_t A_t^T + mu I)^{-1}, formed once and stored
+ *       (Section 3.1), here through a Cholesky factor L_t: W_t = L_t^-T L_t^-1.
+ *   iteration j (Algorithm 1, the loop body)
+ *     - 3 times: draw tau ~ P; x += A_tau^T W_tau (b_tau - A_tau x);
+ *     - r = b - A x; stop if ||r|| / ||b|| <= tol;
+ *     - I = the floor(m/k) rows with the largest r_i^2;
+ *       x += A_I^T (A_I A_I^T + mu I)^{-1} r_I   (Gram + Cholesky per call).
+ *
+ * All arithmetic runs in CUDA kernels compiled for sm_103a; nothing falls back
+ * to the CPU.  Every call returns an rorbk_status; on failure
+ * rorbk_last_error(h) holds a message.  A handle is not thread-safe: use one
+ * host thread per handle.
+ *
+ * Readings of points the paper leaves open (block remainder placement, the
+ * random stream, tie-breaking, zero centroids, zero right-hand side) are
+ * listed beside each entry point below.
+ */
+#ifndef RORBK_H
+#define RORBK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rorbk_ctx *rorbk_handle;
+
+typedef enum {
+    RORBK_OK = 0,                 /* converged (solve) or success            */
+    RORBK_NOT_CONVERGED = 1,      /* non-fatal: maxit reached; x holds the last iterate */
+    RORBK_ERR_INVALID_ARG = -1,   /* bad pointer, size, partition or CSR structure */
+    RORBK_ERR_CUDA = -2,          /* a CUDA runtime call failed               */
+    RORBK_ERR_OOM = -3,           /* device allocation failed                 */
+    RORBK_ERR_NOT_SPD = -4,       /* a block Gram lost positive definiteness (only reachable with lambda = 0) */
+    RORBK_ERR_NUMERIC = -5,       /* NaN/Inf in A, b or the residual          */
+    RORBK_ERR_BOUNDS = -6,        /* an index escaped its range on the device */
+    RORBK_ERR_UNSUPPORTED = -7    /* a mode this build does not provide       */
+} rorbk_status;
+
+enum { RORBK_FORMAT_CSR = 0, RORBK_FORMAT_DENSE = 1 };
+enum { RORBK_F64 = 0, RORBK_F32 = 1 };
+
+/* Arithmetic of the iteration.
+ *   FP64  : the plain method, every step in FP64 (values stored as FP32 are
+ *           widened exactly).
+ *   MIXED : FP64 iterative refinement around FP32 ROR-BK: r = b - A x in
+ *           FP64, an FP32 ROR-BK solve of A d = r to a relative residual of
+ *           inner_tol (or inner_maxit iterations), x += d in FP64, repeated
+ *           until ||b - A x|| / ||b|| <= tol.  The block operators W_t and the
+ *           dynamic block's Cholesky are formed in FP64 and applied in FP32. */
+enum { RORBK_PREC_FP64 = 0, RORBK_PREC_MIXED = 1 };
+
+/* Matrix description for rorbk_setup.
+ *   CSR  : row_ptr[m+1] (int32, row_ptr[0] = 0, non-decreasing, nnz < 2^31),
+ *          col_idx[nnz] (int32, strictly ascending inside each row, in [0,n)),
+ *          values[nnz] (dtype).
+ *   DENSE: values is row-major m x n with leading dimension ld >= n.
+ * Pointers are host memory unless on_device != 0 (then CUDA device memory of
+ * the current device).  rorbk_setup copies A into memory the handle owns; the
+ * caller may free its arrays when setup returns. */
+typedef struct {
+    int32_t format;
+    int32_t dtype;
+    int64_t m, n, nnz;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const void *values;
+    int64_t ld;
+    int32_t on_device;
+    int32_t reserved_;
+} rorbk_matrix;
+
+/* Row partition.  num_blocks = k >= 1.  offsets == NULL selects the uniform
+ * contiguous split of Algorithm 1 step 1: block t holds rows
+ * [t*floor(m/k) + min(t, m mod k), (t+1)*floor(m/k) + min(t+1, m mod k)),
+ * so the first (m mod k) blocks carry one extra row (the paper only asks for
+ * at least floor(m/k) rows per block).  A caller-supplied offsets[k+1]
+ * (host, strictly increasing, 0 .. m) gives any other contiguous split.
+ * Blocks may hold at most 1024 rows. */
+typedef struct {
+    int32_t num_blocks;
+    int32_t reserved_;
+    const int64_t *offsets;
+} rorbk_partition;
+
+/* Optional per-iteration record (device pointers; each may be NULL).
+ *   tau [capacity * n_static] int64 : sampled blocks
+ *   rrn [capacity]            double: ||b - A x|| / ||b|| after the statics
+ *   I   [capacity * K]        int32 : dynamic index set, ascending (K = floor(m/k))
+ *   x   [capacity * n]        double: x at the end of the iteration (after the
+ *                                     dynamic update; on the converging
+ *                                     iteration, after the static updates)
+ * Iterations beyond capacity are not recorded.  FP64 mode only. */
+typedef struct {
+    int64_t capacity;
+    int64_t *tau;
+    double *rrn;
+    int32_t *I;
+    double *x;
+} rorbk_trace;
+
+/* Options (NULL = defaults). */
+typedef struct {
+    uint64_t seed;          /* Philox key word 0                       (0)    */
+    uint64_t system_id;     /* Philox key word 1                       (0)    */
+    int32_t n_static;       /* sampled updates per iteration, l       (3)    */
+    int32_t precision;      /* RORBK_PREC_*                            (FP64) */
+    int64_t start_iter;     /* counter of the first iteration (resume) (0)    */
+    double inner_tol;       /* MIXED: inner relative residual target   (1e-4) */
+    int64_t inner_maxit;    /* MIXED: inner iteration cap per refinement (2000000) */
+    rorbk_trace *trace;     /* FP64 only                               (NULL) */
+    void *stream;           /* cudaStream_t for all work               (0 = legacy default) */
+} rorbk_options;
+
+typedef struct {
+    int64_t iters;          /* ROR-BK iterations executed (MIXED: inner iterations summed) */
+    double rrn;             /* final ||b - A x|| / ||b|| (FP64)                  */
+    int32_t converged;      /* 1 if rrn <= tol                                   */
+    int32_t status;         /* same as the call's return value                   */
+    int64_t refinements;    /* MIXED: outer refinement steps                     */
+    double time_ms;         /* device time of the iteration loop (CUDA events)   */
+} rorbk_result;
+
+typedef struct {
+    int64_t m, n, nnz;
+    int32_t num_blocks;     /* k                                                 */
+    int32_t dyn_rows;       /* K = floor(m/k), rows of the dynamic block         */
+    int32_t max_block_rows; /* largest static block                              */
+    int32_t format;
+    double lambda;          /* mu                                                */
+    int64_t device_bytes;   /* device memory the handle owns                     */
+} rorbk_info;
+
+/* Fills *opt with the defaults listed above. */
+void rorbk_default_options(rorbk_options *opt);
+
+/* Setup (Algorithm 1 steps 1-4 and Section 3.1): validates and copies A,
+ * builds the partition, the centroids, C's row sums, P and its running sum
+ * (cdf, summed sequentially in FP64), and the static operators W_t.
+ *   lambda : mu, added to the diagonal of every block Gram; lambda < 0 selects
+ *            the paper's default mu = 1e-6 * floor(m/k) (Section 2, after
+ *            Theorem 1; Section 3.1).  lambda = 0 is allowed and may fail with
+ *            RORBK_ERR_NOT_SPD on rank-deficient blocks.
+ *   opt    : only opt->precision (which operator copies to keep) and
+ *            opt->stream are read; NULL = defaults.
+ *   *out   : the new handle, or NULL on failure.
+ * Zero centroids: C(t,t) = 1 and C(t,j) = 0 (j != t) when either centroid is 0. */
+rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part,
+                         double lambda, const rorbk_options *opt,
+                         rorbk_handle *out);
+
+/* Solve (Algorithm 1's iteration) from x0 until ||b - A x|| / ||b|| <= tol or
+ * maxit iterations.
+ *   b  : device, m doubles.   x0 : device, n doubles, or NULL for x0 = 0.
+ *   x  : device, n doubles (may alias x0); receives the last iterate.
+ *   The random stream: iteration j's l-th draw uses Philox4x64-10 with key
+ *   (seed, system_id) and counter (start_iter + j, l, 0, 0); u = (word0 >> 11)
+ *   * 2^-53 and tau = min{t : u * cdf[k-1] < cdf[t]}.
+ *   Convergence is tested after the static updates, before the dynamic one;
+ *   ||b|| = 0 returns x = 0 with iters = 0.  Top-K ties go to the lower row.
+ * Returns RORBK_OK, RORBK_NOT_CONVERGED or an error.  res may be NULL.  The
+ * call returns after the device work finished (it synchronises the stream). */
+rorbk_status rorbk_solve(rorbk_handle h, const double *b, const double *x0,
+                         double *x, double tol, int64_t maxit,
+                         const rorbk_options *opt, rorbk_result *res);
+
+/* rorbk_solve with host buffers: b_host (m), x0_host (n or NULL), x_host (n).
+ * The host<->device copies are part of the call. */
+rorbk_status rorbk_solve_host(rorbk_handle h, const double *b_host,
+                              const double *x0_host, double *x_host, double tol,
+                              int64_t maxit, const rorbk_options *opt,
+                              rorbk_result *res);
+
+void rorbk_free(rorbk_handle h);                    /* NULL-safe */
+const char *rorbk_last_error(rorbk_handle h);       /* never NULL */
+rorbk_status rorbk_get_info(rorbk_handle h, rorbk_info *info);
+
+/* ---- single steps of the iteration (parity tests, tracing, custom loops) --
+ * All pointers are device memory of the handle's device; each call finishes
+ * its device work before returning. */
+
+/* Setup products to host: cdf[k] (running sum of Pbar) and C's row sums[k];
+ * either may be NULL. */
+rorbk_status rorbk_get_proposal(rorbk_handle h, double *cdf_host,
+                                double *c_rowsum_host);
+
+/* Static operator W_t = (A_t A_t^T + mu I)^{-1} of block t as a dense s_t x s_t
+ * row-major host array (s_t = rows of block t). */
+rorbk_status rorbk_get_static_operator(rorbk_handle h, int64_t t, double *W_host);
+
+/* The device sampler: tau for (iteration counter it, draw l). */
+rorbk_status rorbk_sample(rorbk_handle h, uint64_t seed, uint64_t system_id,
+                          int64_t it, int64_t l, int64_t *tau_host);
+
+/* One static update with block tau: x += A_tau^T W_tau (b_tau - A_tau x). */
+rorbk_status rorbk_static_update(rorbk_handle h, int64_t tau, const double *b,
+                                 double *x);
+
+/* r = b - A x (device r, m doubles) and ||r||^2 to *rr_host.  With
+ * rr_host == NULL the call only enqueues the kernel on the handle's stream and
+ * returns without waiting (for back-to-back timing). */
+rorbk_status rorbk_residual(rorbk_handle h, const double *b, const double *x,
+                            double *r, double *rr_host);
+
+/* I[K] (device int32): the K = floor(m/k) rows with the largest |r_i|, ties to
+ * the lower index, ascending. */
+rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);
+
+/* Dynamic update for the ascending row set I[K] (device) with the residual r
+ * (device, m doubles, read at I): x += A_I^T (A_I A_I^T + mu I)^{-1} r_I. */
+rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
+                                  const double *r, double *x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RORBK_H */

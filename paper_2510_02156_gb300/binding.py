@@ -1,0 +1,258 @@
+"""ctypes binding of the C ABI in include/rorbk.h (argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``_build/librorbk.so``; this
+module converts numpy arrays and torch CUDA tensors to pointers, calls the
+entry point of the same name and turns a non-OK status into an exception.
+There is no CPU fallback: if the library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+RORBK_OK, RORBK_NOT_CONVERGED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_INVALID_ARG", -2: "ERR_CUDA",
+                -3: "ERR_OOM", -4: "ERR_NOT_SPD", -5: "ERR_NUMERIC", -6: "ERR_BOUNDS",
+                -7: "ERR_UNSUPPORTED"}
+FORMAT_CSR, FORMAT_DENSE = 0, 1
+F64, F32 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class RorbkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rorbk status {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Matrix(C.Structure):
+    _fields_ = [("format", C.c_int32), ("dtype", C.c_int32), ("m", C.c_int64),
+                ("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("values", C.c_void_p), ("ld", C.c_int64),
+                ("on_device", C.c_int32), ("reserved_", C.c_int32)]
+
+
+class Partition(C.Structure):
+    _fields_ = [("num_blocks", C.c_int32), ("reserved_", C.c_int32), ("offsets", C.c_void_p)]
+
+
+class Trace(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("tau", C.c_void_p), ("rrn", C.c_void_p),
+                ("I", C.c_void_p), ("x", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("system_id", C.c_uint64), ("n_static", C.c_int32),
+                ("precision", C.c_int32), ("start_iter", C.c_int64), ("inner_tol", C.c_double),
+                ("inner_maxit", C.c_int64), ("trace", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("rrn", C.c_double), ("converged", C.c_int32),
+                ("status", C.c_int32), ("refinements", C.c_int64), ("time_ms", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64),
+                ("num_blocks", C.c_int32), ("dyn_rows", C.c_int32),
+                ("max_block_rows", C.c_int32), ("format", C.c_int32), ("lambda_", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+# the entry points declared in include/rorbk.h, with their ctypes signatures
+_P, _I64, _U64, _D = C.c_void_p, C.c_int64, C.c_uint64, C.c_double
+SIGNATURES = {
+    "rorbk_default_options": (None, [_P]),
+    "rorbk_setup": (C.c_int, [_P, _P, _D, _P, _P]),
+    "rorbk_solve": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P]),
+    "rorbk_solve_host": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P]),
+    "rorbk_free": (None, [_P]),
+    "rorbk_last_error": (C.c_char_p, [_P]),
+    "rorbk_get_info": (C.c_int, [_P, _P]),
+    "rorbk_get_proposal": (C.c_int, [_P, _P, _P]),
+    "rorbk_get_static_operator": (C.c_int, [_P, _I64, _P]),
+    "rorbk_sample": (C.c_int, [_P, _U64, _U64, _I64, _I64, _P]),
+    "rorbk_static_update": (C.c_int, [_P, _I64, _P, _P]),
+    "rorbk_residual": (C.c_int, [_P, _P, _P, _P, _P]),
+    "rorbk_topk": (C.c_int, [_P, _P, _P]),
+    "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build: bool = True):
+    """Load the CUDA library (building it first if its sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library missing: {path} (run __graft_entry__.build())")
+            L = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st, h=None):
+    if st < 0:
+        msg = lib().rorbk_last_error(h)
+        raise RorbkError(st, msg.decode() if msg else "")
+    return st
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(C.c_void_p)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().rorbk_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream)
+
+
+class Handle:
+    """Owns one rorbk_handle (rorbk_setup ... rorbk_free)."""
+
+    def __init__(self, row_ptr, col_idx, values, m, n, num_blocks, lam, precision=PREC_FP64,
+                 offsets=None, stream=None):
+        self._keep = []
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        vals = np.ascontiguousarray(values)
+        if vals.dtype == np.float32:
+            dt = F32
+        else:
+            vals = np.ascontiguousarray(vals, dtype=np.float64)
+            dt = F64
+        self._keep += [rp, ci, vals]
+        A = Matrix(FORMAT_CSR, dt, m, n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data,
+                   vals.ctypes.data, 0, 0, 0)
+        offs = None
+        if offsets is not None:
+            offs = np.ascontiguousarray(offsets, dtype=np.int64)
+            self._keep.append(offs)
+        part = Partition(num_blocks, 0, None if offs is None else offs.ctypes.data)
+        opt = default_options(precision=precision, stream=_stream_ptr(stream))
+        h = C.c_void_p()
+        st = lib().rorbk_setup(C.byref(A), C.byref(part), lam, C.byref(opt), C.byref(h))
+        _check(st, None)
+        self.h = h
+        self.info = Info()
+        _check(lib().rorbk_get_info(self.h, C.byref(self.info)), self.h)
+
+    @classmethod
+    def from_system(cls, system, lam=None, precision=PREC_FP64, **kw):
+        return cls(system.row_ptr, system.col_idx, system.values, system.m, system.n,
+                   system.num_blocks, system.lam if lam is None else lam, precision, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rorbk_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- whole solve --------------------------------------------------------
+    def solve(self, b, x, x0=None, tol=1e-8, maxit=1000, seed=0, system_id=0, n_static=3,
+              start_iter=0, precision=PREC_FP64, trace=None, stream=None, inner_tol=1e-4,
+              inner_maxit=2000000):
+        """rorbk_solve on device tensors b (m), x (n), x0 (n or None)."""
+        opt = default_options(seed=seed, system_id=system_id, n_static=n_static,
+                              start_iter=start_iter, precision=precision,
+                              stream=_stream_ptr(stream), inner_tol=inner_tol,
+                              inner_maxit=inner_maxit)
+        if trace is not None:
+            opt.trace = C.cast(C.pointer(trace), C.c_void_p)
+        res = Result()
+        st = lib().rorbk_solve(self.h, _ptr(b), _ptr(x0), _ptr(x), tol, maxit, C.byref(opt),
+                               C.byref(res))
+        _check(st, self.h)
+        return res
+
+    def solve_host(self, b, x, x0=None, tol=1e-8, maxit=1000, seed=0, system_id=0,
+                   n_static=3, start_iter=0, precision=PREC_FP64, stream=None,
+                   inner_tol=1e-4, inner_maxit=2000000):
+        """rorbk_solve_host on host (numpy float64) arrays."""
+        opt = default_options(seed=seed, system_id=system_id, n_static=n_static,
+                              start_iter=start_iter, precision=precision,
+                              stream=_stream_ptr(stream), inner_tol=inner_tol,
+                              inner_maxit=inner_maxit)
+        res = Result()
+        st = lib().rorbk_solve_host(self.h, _ptr(b), _ptr(x0), _ptr(x), tol, maxit,
+                                    C.byref(opt), C.byref(res))
+        _check(st, self.h)
+        return res
+
+    # -- setup products and single steps -----------------------------------
+    def proposal(self):
+        k = self.info.num_blocks
+        cdf, rs = np.zeros(k), np.zeros(k)
+        _check(lib().rorbk_get_proposal(self.h, _ptr(cdf), _ptr(rs)), self.h)
+        return cdf, rs
+
+    def static_operator(self, t, s):
+        W = np.zeros((s, s))
+        _check(lib().rorbk_get_static_operator(self.h, t, _ptr(W)), self.h)
+        return W
+
+    def sample(self, seed, system_id, it, l):
+        tau = C.c_int64()
+        _check(lib().rorbk_sample(self.h, seed, system_id, it, l, C.byref(tau)), self.h)
+        return tau.value
+
+    def static_update(self, tau, b, x):
+        _check(lib().rorbk_static_update(self.h, tau, _ptr(b), _ptr(x)), self.h)
+
+    def residual(self, b, x, r):
+        rr = C.c_double()
+        _check(lib().rorbk_residual(self.h, _ptr(b), _ptr(x), _ptr(r), C.byref(rr)), self.h)
+        return rr.value
+
+    def residual_async(self, b, x, r):
+        """Enqueue r = b - A x on the handle's stream without waiting."""
+        _check(lib().rorbk_residual(self.h, _ptr(b), _ptr(x), _ptr(r), None), self.h)
+
+    def topk(self, r, I):
+        _check(lib().rorbk_topk(self.h, _ptr(r), _ptr(I)), self.h)
+
+    def dynamic_update(self, I, r, x):
+        _check(lib().rorbk_dynamic_update(self.h, _ptr(I), _ptr(r), _ptr(x)), self.h)

@@ -1,0 +1,211 @@
+// common.cuh -- small device helpers for the ROR-BK kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rorbk {
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// (X0,X1,X2,X3) -> (hi(M1 X2)^X1^K0, lo(M1 X2), hi(M0 X0)^X3^K1, lo(M0 X0)),
+// the key advanced by the Weyl increments between rounds.
+__device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                              uint64_t c3, uint64_t k0, uint64_t k1,
+                                              uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Block draw of Algorithm 1: u from word 0 of the Philox block at counter
+// (it, l, 0, 0), key (seed, sysid); tau = min{t : u * cdf[k-1] < cdf[t]}.
+__device__ __forceinline__ int sample_block(const double *cdf, int k, uint64_t seed,
+                                            uint64_t sysid, uint64_t it, uint64_t l) {
+    uint64_t w[4];
+    philox4x64_10(it, l, 0, 0, seed, sysid, w);
+    double u = (double)(w[0] >> 11) * 0x1.0p-53;
+    double target = u * cdf[k - 1];
+    int lo = 0, hi = k;               // first t with cdf[t] > target
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (cdf[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    return lo < k ? lo : k - 1;
+}
+
+// Order-preserving key of |v| (non-negative doubles compare as uint64).
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+    return (unsigned long long)__double_as_longlong(fabs(v));
+}
+__device__ __forceinline__ unsigned long long abs_key(float v) {
+    return abs_key((double)v);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed tree for a fixed blockDim); result valid in
+// thread 0.  scratch: >= 32 elements of shared memory.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *scratch) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    T s = 0;
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        s = lane < nw ? scratch[lane] : T(0);
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+// Exclusive block scan of one int per thread; returns the prefix, *total gets
+// the block total.  scratch: >= 33 ints of shared memory.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *scratch, int *total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) scratch[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        int w = lane < nw ? scratch[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) scratch[lane] = w;     // inclusive warp totals
+        if (lane == nw - 1) scratch[32] = w;
+    }
+    __syncthreads();
+    int prefix = x - v + (wid > 0 ? scratch[wid - 1] : 0);
+    *total = scratch[32];
+    __syncthreads();
+    return prefix;
+}
+
+// Bitonic sort of n (power of two) 64-bit keys, ascending, by one block.
+__device__ __forceinline__ void block_bitonic_sort(unsigned long long *keys, int n) {
+    for (int kk = 2; kk <= n; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    unsigned long long a = keys[i], b = keys[ixj];
+                    bool up = (i & kk) == 0;
+                    if ((a > b) == up) { keys[i] = b; keys[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Bitonic sort of (key, idx) pairs so that larger keys come first and equal
+// keys keep ascending idx (the top-K order of Algorithm 1 with ties to the
+// lower row).  n is a power of two; padding uses key 0 / idx INT_MAX.
+__device__ __forceinline__ bool topk_before(unsigned long long ka, int ia,
+                                            unsigned long long kb, int ib) {
+    return ka > kb || (ka == kb && ia < ib);
+}
+__device__ __forceinline__ void block_bitonic_sort_desc(unsigned long long *keys, int *idx,
+                                                        int n) {
+    for (int kk = 2; kk <= n; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    unsigned long long a = keys[i], b = keys[ixj];
+                    int ia = idx[i], ib = idx[ixj];
+                    bool up = (i & kk) == 0;
+                    // "up" segments end with a before b in topk order
+                    bool swap = up ? topk_before(b, ib, a, ia) : topk_before(a, ia, b, ib);
+                    if (swap) { keys[i] = b; keys[ixj] = a; idx[i] = ib; idx[ixj] = ia; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+__device__ __forceinline__ void set_status(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------- dense SPD helpers
+// Cholesky G = L L^T of an nS x nS row-major array in place (right-looking,
+// zero multipliers skipped), one block of threads.  Returns false if a pivot
+// is not positive (the factorisation continues with pivot 1 so that every
+// thread leaves the loop).
+__device__ __forceinline__ bool block_cholesky(double *G, int ld, int nS, int *bad) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < nS; ++j) {
+        if (threadIdx.x == 0) {
+            double d = G[(long long)j * ld + j];
+            if (!(d > 0.0)) { *bad = 1; d = 1.0; }
+            G[(long long)j * ld + j] = sqrt(d);
+        }
+        __syncthreads();
+        double l = G[(long long)j * ld + j];
+        for (int i = j + 1 + threadIdx.x; i < nS; i += blockDim.x)
+            G[(long long)i * ld + j] = G[(long long)i * ld + j] / l;
+        __syncthreads();
+        for (int a = j + 1 + wid; a < nS; a += nw) {
+            double la = G[(long long)a * ld + j];
+            if (la == 0.0) continue;
+            for (int b = j + 1 + lane; b <= a; b += 32) {
+                double lb = G[(long long)b * ld + j];
+                if (lb != 0.0)
+                    G[(long long)a * ld + b] = __dsub_rn(G[(long long)a * ld + b], __dmul_rn(la, lb));
+            }
+        }
+        __syncthreads();
+    }
+    for (int a = threadIdx.x; a < nS; a += blockDim.x)
+        for (int b = a + 1; b < nS; ++b) G[(long long)a * ld + b] = 0.0;
+    __syncthreads();
+    return true;
+}
+
+// <row a, row b> over ascending columns (merge of two sorted CSR rows).
+template <typename V>
+__device__ __forceinline__ double row_merge_dot(const int *col, const V *val, int p, int pe,
+                                                int q, int qe) {
+    double s = 0.0;
+    while (p < pe && q < qe) {
+        int cp = col[p], cq = col[q];
+        if (cp == cq) { s = __dadd_rn(s, __dmul_rn((double)val[p], (double)val[q])); ++p; ++q; }
+        else if (cp < cq) ++p;
+        else ++q;
+    }
+    return s;
+}
+
+}  // namespace rorbk

@@ -1,0 +1,156 @@
+// internal.cuh -- device helpers and the handle layout shared by the CUDA
+// translation units of the ROR-BK library.  Nothing here is part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rorbk.h"
+
+namespace rorbk {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxBlockRows = 1024;     // static block rows (one thread per row)
+constexpr int kMaxDynRows = 1024;       // K = floor(m/k)
+constexpr int kTileRows = 256;          // residual tile: rows ...
+constexpr int kTileNnz = 2048;          // ... and nonzeros per tile
+constexpr int kHistBins = 2048;         // 11-bit radix digits of |r| keys
+constexpr int kEqCap = 4096;            // top-K candidates sorted in one CTA
+constexpr int kSortCapSmem = 4096;      // entries sorted in shared memory
+constexpr int kCholSmemMax = 96;        // coupled-set size factored in smem
+
+// device error codes (ctl->status)
+constexpr int kDevOk = 0;
+constexpr int kDevNotSpd = 1;
+constexpr int kDevBounds = 2;
+constexpr int kDevNumeric = 3;
+
+// ----------------------------------------------------- device-side state
+// Loop state of one solve, kept in device memory so that the whole iteration
+// loop runs without the host.
+struct Ctl {
+    long long iter;        // iterations completed in this solve
+    long long maxit;
+    long long iter_base;   // Philox counter of iteration 0 (start_iter)
+    unsigned long long seed, sysid;
+    double tol, bnorm, rr, rrn;
+    int done;              // set when rrn <= tol (or ||b|| = 0)
+    int status;            // kDev* error word (first error wins)
+    int n_static;
+    unsigned ticket;       // last-block election of grid-wide kernels
+    // radix select of the top-K keys
+    int sel1, above1, prefix, above, n_in, n_eq;
+    // trace (device pointers, FP64 mode)
+    long long trace_cap;
+    long long *tr_tau;
+    double *tr_rrn;
+    int *tr_I;
+    double *tr_x;
+    // mixed precision outer loop
+    long long outer, inner_maxit, inner_total;
+    double inner_tol, outer_rrn;
+    int outer_done;
+    int has_x0;
+};
+
+// Sparse operator of one static block t (Section 3.1's stored inverse
+// W_t = (A_t A_t^T + mu I)^{-1}).  Rows of the block that share no column
+// with another row of the block ("uncoupled") make W_t diagonal there:
+// W_ii = 1 / L_ii^2; the coupled rows S_t carry a dense |S_t| x |S_t| block.
+struct StaticOps {
+    int *s_ptr = nullptr;       // [k+1] offsets into s_idx
+    uint16_t *s_idx = nullptr;  // coupled local rows, ascending
+    long long *w_ptr = nullptr; // [k+1] offsets into w_ss
+    double *w_ss = nullptr;     // dense W on S_t, row-major
+    double *w_diag = nullptr;   // [m] W_ii for uncoupled rows
+    int *s_pos = nullptr;       // [m] position of a row in its S_t, or -1
+    float *w_ss32 = nullptr, *w_diag32 = nullptr;  // FP32 copies (mixed)
+};
+
+// Per-block column-sorted copy of the block's nonzeros, used for the
+// deterministic scatter x += A_t^T y.  Entries of block t occupy the same
+// positions as the block's CSR range, sorted by (column, row).
+struct BlockT {
+    int *col = nullptr;
+    uint16_t *row = nullptr;    // local row in the block
+    double *val = nullptr;
+    float *val32 = nullptr;
+    int *seg = nullptr;         // segment (distinct column) start positions
+    int *seg_ptr = nullptr;     // [k] segment count of block t; its segments
+                                // start at seg[row_ptr[off[t]] ...]
+};
+
+}  // namespace rorbk
+
+struct rorbk_ctx {
+    int device = 0;
+    cudaStream_t stream = 0;
+    std::string err;
+    int64_t m = 0, n = 0, nnz = 0;
+    int format = RORBK_FORMAT_CSR, vdtype = RORBK_F64;
+    int k = 0, K = 0, smax = 0;
+    double mu = 0;
+    int precision_built = 0;
+    int num_sms = 0;
+    int64_t bytes = 0;
+    std::vector<void *> allocs;
+    // matrix (CSR)
+    int *rowptr = nullptr, *col = nullptr;
+    double *val = nullptr;      // FP64 values (exact widening if given FP32)
+    float *val32 = nullptr;     // FP32 values (mixed precision)
+    // partition
+    std::vector<int64_t> h_off;
+    int *off = nullptr;
+    // proposal
+    double *cdf = nullptr, *crowsum = nullptr;
+    rorbk::StaticOps ops;
+    rorbk::BlockT bt;
+    // residual tiles
+    int ntiles = 0;
+    int *tile_row0 = nullptr;
+    int grid_res = 0;
+    // workspace
+    double *r = nullptr, *xb = nullptr, *bb = nullptr, *x64 = nullptr;
+    float *r32 = nullptr, *b32 = nullptr, *d32 = nullptr;
+    double *partials = nullptr;
+    unsigned *hist1 = nullptr, *hist2 = nullptr;
+    int *in_list = nullptr, *eq_list = nullptr, *dynI = nullptr;
+    double *dyn_g = nullptr;           // K*K FP64 fallback for a large coupled set
+    unsigned long long *dyn_keys = nullptr;  // fallback sort space
+    int *dyn_ecol = nullptr; double *dyn_eval = nullptr; uint16_t *dyn_erow = nullptr;
+    int64_t dyn_ecap = 0;
+    rorbk::Ctl *ctl = nullptr;
+    // graphs
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+    cudaGraphExec_t exec_fp64 = nullptr, exec_mixed = nullptr;
+    std::vector<void *> tmp;
+};
+
+namespace rorbk {
+
+// host helpers implemented in rorbk.cu
+rorbk_status fail(rorbk_ctx *h, rorbk_status st, const std::string &msg);
+rorbk_status cuda_check(rorbk_ctx *h, cudaError_t e, const char *what);
+void *dev_alloc(rorbk_ctx *h, size_t bytes);
+
+// setup (kernels_setup.cu)
+rorbk_status build_setup(rorbk_ctx *h);
+void widen_values(rorbk_ctx *h, int dtype);   // FP32 <-> FP64 value copies
+
+// iteration launches (kernels_iter.cu); all enqueue on h->stream
+void configure_kernels();
+void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
+                  unsigned long long hcond);
+void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
+                      unsigned long long hcond);
+void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x);
+void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r);
+void launch_topk_only(rorbk_ctx *h, const double *r, int *I);
+void launch_dynamic_given(rorbk_ctx *h, const int *I, const double *r, double *x);
+void launch_sample_probe(rorbk_ctx *h, uint64_t seed, uint64_t sysid, int64_t it, int64_t l,
+                         long long *out);
+
+}  // namespace rorbk

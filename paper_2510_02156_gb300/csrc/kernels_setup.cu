@@ -1,0 +1,527 @@
+// kernels_setup.cu -- setup of ROR-BK (Algorithm 1 steps 1-4, Section 3.1).
+//
+//   k_validate_csr        structure and finiteness checks of the copied A
+//   k_block_transpose     per static block: nonzeros sorted by (column, row),
+//                         distinct-column segments, coupled rows
+//   k_centroid_*          centroids Abar_t (sum of the block's rows), the Gram
+//                         Abar Abar^T one row per warp, C's row sums
+//   k_proposal            Pbar_t = exp(-2 sum_j C(t,j) / n) and its running sum
+//   k_static_ops          W_t = (A_t A_t^T + mu I)^{-1} per block through a
+//                         Cholesky factor, on the block's coupled rows only
+//
+// The "coupled" rows of a row set are those sharing at least one column with
+// another row of the set.  The Gram A_t A_t^T is diagonal outside the
+// coupled rows, so the Cholesky factor, its inverse and W_t are too; the dense
+// work is restricted to the coupled rows, which gives the same numbers as the
+// dense factorisation (zero multipliers contribute exact zeros).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace rorbk {
+
+// ------------------------------------------------------------------ checks
+__global__ void k_validate_csr(const int *__restrict__ rowptr, const int *__restrict__ col,
+                               const double *__restrict__ val, int m, int n, int *flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        int p0 = rowptr[i], p1 = rowptr[i + 1];
+        if (p1 < p0) { atomicOr(flags, 1); continue; }
+        int prev = -1;
+        for (int p = p0; p < p1; ++p) {
+            int c = col[p];
+            if (c < 0 || c >= n || c <= prev) { atomicOr(flags, 1); break; }
+            prev = c;
+            if (!isfinite(val[p])) atomicOr(flags, 2);
+        }
+    }
+}
+
+__global__ void k_widen(const float *__restrict__ in, double *__restrict__ out, long long nn) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+__global__ void k_narrow(const double *__restrict__ in, float *__restrict__ out, long long nn) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+// ---------------------------------------------------------- block transpose
+// One block of threads per static block t.  Entry p of the block's CSR range
+// lands at rank(p) = #entries with a smaller column + #entries in earlier
+// rows with the same column, found by binary searches in every row of the
+// block (rows hold ascending columns).
+__device__ __forceinline__ int lower_bound_col(const int *col, int lo, int hi, int c) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (col[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_block_transpose(const int *__restrict__ rowptr, const int *__restrict__ col,
+                                  const double *__restrict__ val, const int *__restrict__ off,
+                                  int *__restrict__ bt_col, uint16_t *__restrict__ bt_row,
+                                  double *__restrict__ bt_val, int *__restrict__ bt_seg,
+                                  int *__restrict__ nseg_out, unsigned char *__restrict__ coupled,
+                                  int *__restrict__ ncoupled_out) {
+    __shared__ int scan_scratch[33];
+    __shared__ unsigned char flag[kMaxBlockRows];
+    const int t = blockIdx.x;
+    const int r0 = off[t], r1 = off[t + 1], s = r1 - r0;
+    const int p0 = rowptr[r0], E = rowptr[r1] - p0;
+    for (int a = threadIdx.x; a < s; a += blockDim.x) flag[a] = 0;
+
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        int p = p0 + e;
+        int c = col[p];
+        int lo = r0, hi = r1;                    // row of entry p: last i with rowptr[i] <= p
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (rowptr[mid] <= p) lo = mid; else hi = mid;
+        }
+        int a = lo - r0;
+        int rank = 0;
+        for (int b = 0; b < s; ++b) {
+            int q0 = rowptr[r0 + b], q1 = rowptr[r0 + b + 1];
+            int lb = lower_bound_col(col, q0, q1, c);
+            rank += lb - q0;
+            if (b < a && lb < q1 && col[lb] == c) rank += 1;
+        }
+        int dst = p0 + rank;
+        bt_col[dst] = c;
+        bt_row[dst] = (uint16_t)a;
+        bt_val[dst] = val[p];
+    }
+    __syncthreads();
+
+    int nseg = 0;
+    for (int base = 0; base < E; base += blockDim.x) {
+        int q = base + threadIdx.x;
+        int head = 0;
+        if (q < E) head = (q == 0) || (bt_col[p0 + q] != bt_col[p0 + q - 1]);
+        int total;
+        int pre = block_exclusive_scan(head, scan_scratch, &total);
+        if (head) {
+            bt_seg[p0 + nseg + pre] = p0 + q;
+            int c = bt_col[p0 + q];
+            int e = q + 1;
+            while (e < E && bt_col[p0 + e] == c) ++e;
+            if (e - q > 1)
+                for (int u = q; u < e; ++u) flag[bt_row[p0 + u]] = 1;
+        }
+        nseg += total;
+    }
+    __syncthreads();
+    int cnt = 0;
+    for (int a = threadIdx.x; a < s; a += blockDim.x) {
+        coupled[r0 + a] = flag[a];
+        cnt += flag[a];
+    }
+    int tot = block_sum(cnt, scan_scratch);
+    if (threadIdx.x == 0) {
+        nseg_out[t] = nseg;
+        ncoupled_out[t] = tot;
+    }
+}
+
+// ------------------------------------------------------------ device scans
+// Exclusive scan of n ints in place (n < 2^31), three launches.
+__global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out,
+                             int *__restrict__ tile_sums, long long n) {
+    __shared__ int sc[33];
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int v = i < n ? in[i] : 0;
+    int total;
+    int pre = block_exclusive_scan(v, sc, &total);
+    if (i < n) out[i] = pre;
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+__global__ void k_scan_sums(int *tile_sums, int ntiles, int *grand_total) {
+    __shared__ int sc[33];
+    int carry = 0;
+    for (int base = 0; base < ntiles; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < ntiles ? tile_sums[i] : 0;
+        int total;
+        int pre = block_exclusive_scan(v, sc, &total);
+        if (i < ntiles) tile_sums[i] = carry + pre;
+        carry += total;
+    }
+    if (threadIdx.x == 0) *grand_total = carry;
+}
+__global__ void k_scan_add(int *out, const int *tile_sums, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tile_sums[blockIdx.x];
+}
+
+// ------------------------------------------------------- centroids and C
+// Centroid entry of block t at segment g: column bt_col[seg], value = sum of
+// the segment's values in ascending row order (the rows are added in order).
+__global__ void k_centroid_count(const int *__restrict__ rowptr, const int *__restrict__ off,
+                                 const int *__restrict__ bt_col, const int *__restrict__ bt_seg,
+                                 const int *__restrict__ nseg, int k, int *__restrict__ colcnt) {
+    for (int t = blockIdx.x; t < k; t += gridDim.x) {
+        int p0 = rowptr[off[t]];
+        for (int g = threadIdx.x; g < nseg[t]; g += blockDim.x)
+            atomicAdd(&colcnt[bt_col[bt_seg[p0 + g]]], 1);
+    }
+}
+
+__device__ __forceinline__ double segment_sum(const double *bt_val, const int *bt_col,
+                                              int q, int qend) {
+    int c = bt_col[q];
+    double v = 0.0;
+    for (int u = q; u < qend && bt_col[u] == c; ++u) v = __dadd_rn(v, bt_val[u]);
+    return v;
+}
+
+__global__ void k_centroid_fill(const int *__restrict__ rowptr, const int *__restrict__ off,
+                                const int *__restrict__ bt_col, const double *__restrict__ bt_val,
+                                const int *__restrict__ bt_seg, const int *__restrict__ nseg, int k,
+                                const int *__restrict__ colptr, int *__restrict__ fill,
+                                int *__restrict__ cb, double *__restrict__ cv) {
+    for (int t = blockIdx.x; t < k; t += gridDim.x) {
+        int p0 = rowptr[off[t]], pend = rowptr[off[t + 1]];
+        for (int g = threadIdx.x; g < nseg[t]; g += blockDim.x) {
+            int q = bt_seg[p0 + g];
+            int c = bt_col[q];
+            double v = segment_sum(bt_val, bt_col, q, pend);
+            int pos = colptr[c] + atomicAdd(&fill[c], 1);
+            cb[pos] = t;
+            cv[pos] = v;
+        }
+    }
+}
+
+// Row t of G = Abar Abar^T, one warp per block t: columns c of Abar_t in
+// ascending order, G(t, j) += Abar_tc * Abar_jc over the blocks j of column c
+// (distinct j inside one column, so the lanes never collide).
+__global__ void k_centroid_gram(const int *__restrict__ rowptr, const int *__restrict__ off,
+                                const int *__restrict__ bt_col, const double *__restrict__ bt_val,
+                                const int *__restrict__ bt_seg, const int *__restrict__ nseg,
+                                int k, const int *__restrict__ colptr,
+                                const int *__restrict__ cb, const double *__restrict__ cv,
+                                double *__restrict__ G) {
+    int lane = threadIdx.x & 31;
+    int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= k) return;
+    int p0 = rowptr[off[t]], pend = rowptr[off[t + 1]];
+    double *Gt = G + (long long)t * k;
+    for (int g = 0; g < nseg[t]; ++g) {
+        int q = bt_seg[p0 + g];
+        int c = bt_col[q];
+        double v = segment_sum(bt_val, bt_col, q, pend);
+        for (int e = colptr[c] + lane; e < colptr[c + 1]; e += 32) {
+            int j = cb[e];
+            Gt[j] = __dadd_rn(Gt[j], __dmul_rn(v, cv[e]));
+        }
+        __syncwarp();
+    }
+}
+
+// Dense centroids: Abar (k x n) row t = sum of the block's rows in order.
+__global__ void k_centroid_dense(const double *__restrict__ A, long long ld,
+                                 const int *__restrict__ off, int k, int n,
+                                 double *__restrict__ Abar) {
+    for (int t = blockIdx.y; t < k; t += gridDim.y)
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+            double v = 0.0;
+            for (int i = off[t]; i < off[t + 1]; ++i) v = __dadd_rn(v, A[(long long)i * ld + c]);
+            Abar[(long long)t * n + c] = v;
+        }
+}
+
+// G = Abar Abar^T for dense centroids: one thread per (t, j), ascending c.
+__global__ void k_centroid_gram_dense(const double *__restrict__ Abar, int k, int n,
+                                      double *__restrict__ G) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = blockIdx.y;
+    if (j >= k) return;
+    const double *a = Abar + (long long)t * n, *b = Abar + (long long)j * n;
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s = __dadd_rn(s, __dmul_rn(a[c], b[c]));
+    G[(long long)t * k + j] = s;
+}
+
+// sum_j C(t, j), C(t,t) = 1, C(t,j) = 0 when either centroid is zero.
+__global__ void k_crowsum(const double *__restrict__ G, int k, double *__restrict__ rowsum) {
+    int lane = threadIdx.x & 31;
+    int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= k) return;
+    double nt = sqrt(G[(long long)t * k + t]);
+    double s = 0.0;
+    for (int j = lane; j < k; j += 32) {
+        double nj = sqrt(G[(long long)j * k + j]);
+        double cij;
+        if (j == t) cij = 1.0;
+        else if (nt == 0.0 || nj == 0.0) cij = 0.0;
+        else cij = fabs(G[(long long)t * k + j]) / (nt * nj);
+        s += cij;
+    }
+    s = warp_sum(s);
+    if (lane == 0) rowsum[t] = s;
+}
+
+// Pbar_t = exp(-2 rowsum_t / n); cdf_t = Pbar_0 + ... + Pbar_t summed in
+// order by one thread (the normalisation of P is folded into the sampler).
+__global__ void k_proposal(const double *__restrict__ rowsum, int k, double n,
+                           double *__restrict__ cdf) {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) cdf[t] = exp(-2.0 * rowsum[t] / n);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int t = 0; t < k; ++t) {
+            s += cdf[t];
+            cdf[t] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------ static ops
+// One block of threads per static block t.  Inputs: the block's coupled
+// flags and S offsets; outputs W on S (row-major |S|^2 at w_ss + w_ptr[t]),
+// W_ii for uncoupled rows, and s_idx / s_pos.  Linv scratch has the layout of
+// w_ss.
+__global__ void k_static_ops(const int *__restrict__ rowptr, const int *__restrict__ col,
+                             const double *__restrict__ val, const int *__restrict__ off,
+                             double mu, const unsigned char *__restrict__ coupled,
+                             const int *__restrict__ s_ptr, const long long *__restrict__ w_ptr,
+                             uint16_t *__restrict__ s_idx, int *__restrict__ s_pos,
+                             double *__restrict__ w_ss, double *__restrict__ w_diag,
+                             double *__restrict__ linv, int *__restrict__ status) {
+    __shared__ int scan_scratch[33];
+    __shared__ int bad;
+    __shared__ double gdiag[kMaxBlockRows];
+    const int t = blockIdx.x;
+    const int r0 = off[t], s = off[t + 1] - r0;
+    const int sb = s_ptr[t], nS = s_ptr[t + 1] - sb;
+    double *G = w_ss + w_ptr[t];
+    double *Li = linv + w_ptr[t];
+    if (threadIdx.x == 0) bad = 0;
+
+    // coupled rows in ascending order; diagonal of the Gram for every row
+    int cnt = 0;
+    for (int base = 0; base < s; base += blockDim.x) {
+        int a = base + threadIdx.x;
+        int f = a < s ? coupled[r0 + a] : 0;
+        int total;
+        int pre = block_exclusive_scan(f, scan_scratch, &total);
+        if (a < s) {
+            s_pos[r0 + a] = f ? cnt + pre : -1;
+            if (f) s_idx[sb + cnt + pre] = (uint16_t)a;
+            int p0 = rowptr[r0 + a], p1 = rowptr[r0 + a + 1];
+            double g = 0.0;
+            for (int p = p0; p < p1; ++p) g = __dadd_rn(g, __dmul_rn(val[p], val[p]));
+            g = __dadd_rn(g, mu);
+            gdiag[a] = g;
+            if (!f) {
+                if (!(g > 0.0)) { bad = 1; g = 1.0; }
+                double li = 1.0 / sqrt(g);
+                w_diag[r0 + a] = __dmul_rn(li, li);
+            } else {
+                w_diag[r0 + a] = 0.0;
+            }
+        }
+        cnt += total;
+    }
+    __syncthreads();
+    if (nS > 0) {
+        // G on S: merges of the coupled rows (lower triangle + diagonal)
+        long long pairs = (long long)nS * (nS + 1) / 2;
+        for (long long idx = threadIdx.x; idx < pairs; idx += blockDim.x) {
+            int i = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+            while ((long long)(i + 1) * (i + 2) / 2 <= idx) ++i;
+            while ((long long)i * (i + 1) / 2 > idx) --i;
+            int j = (int)(idx - (long long)i * (i + 1) / 2);
+            int a = s_idx[sb + i], b = s_idx[sb + j];
+            double g;
+            if (i == j) g = gdiag[a];
+            else g = row_merge_dot(col, val, rowptr[r0 + a], rowptr[r0 + a + 1],
+                                   rowptr[r0 + b], rowptr[r0 + b + 1]);
+            G[(long long)i * nS + j] = g;
+        }
+        __syncthreads();
+        block_cholesky(G, nS, nS, &bad);
+        // Linv column by column: Linv_jj = 1/L_jj, Linv_ij = -(sum_{c=j}^{i-1}
+        // L_ic Linv_cj) / L_ii, c ascending.
+        for (int j = threadIdx.x; j < nS; j += blockDim.x) {
+            for (int i = 0; i < j; ++i) Li[(long long)i * nS + j] = 0.0;
+            Li[(long long)j * nS + j] = 1.0 / G[(long long)j * nS + j];
+            for (int i = j + 1; i < nS; ++i) {
+                double acc = 0.0;
+                for (int c = j; c < i; ++c)
+                    acc = __dadd_rn(acc, __dmul_rn(G[(long long)i * nS + c], Li[(long long)c * nS + j]));
+                Li[(long long)i * nS + j] = -acc / G[(long long)i * nS + i];
+            }
+        }
+        __syncthreads();
+        // W_ij = sum_{c >= max(i,j)} Linv_ci Linv_cj (c ascending), written
+        // over the factor.
+        for (long long idx = threadIdx.x; idx < (long long)nS * nS; idx += blockDim.x) {
+            int i = (int)(idx / nS), j = (int)(idx % nS);
+            if (j > i) continue;
+            double acc = 0.0;
+            for (int c = i; c < nS; ++c)
+                acc = __dadd_rn(acc, __dmul_rn(Li[(long long)c * nS + i], Li[(long long)c * nS + j]));
+            // the factor's (i, j) is read by nobody after the Linv pass
+            G[(long long)i * nS + j] = acc;
+        }
+        __syncthreads();
+        for (long long idx = threadIdx.x; idx < (long long)nS * nS; idx += blockDim.x) {
+            int i = (int)(idx / nS), j = (int)(idx % nS);
+            if (j > i) G[(long long)i * nS + j] = G[(long long)j * nS + i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && bad) set_status(status, kDevNotSpd);
+}
+
+// FP64 working copy of FP32-stored values (exact), or FP32 copy of FP64
+// values for the mixed-precision inner solve.
+void widen_values(rorbk_ctx *h, int dtype) {
+    const int gs = std::max(1, std::min(8 * h->num_sms, (int)((h->nnz + 255) / 256)));
+    if (h->nnz == 0) return;
+    if (dtype == RORBK_F32) k_widen<<<gs, 256, 0, h->stream>>>(h->val32, h->val, h->nnz);
+    else if (h->val32) k_narrow<<<gs, 256, 0, h->stream>>>(h->val, h->val32, h->nnz);
+}
+
+// ---------------------------------------------------------------- driver
+static rorbk_status scan_device(rorbk_ctx *h, int *d, long long n, int *grand_total_host) {
+    const int nt = 256;
+    long long tiles = (n + nt - 1) / nt;
+    int *sums = (int *)dev_alloc(h, (size_t)(tiles + 1) * sizeof(int));
+    int *tot = (int *)dev_alloc(h, sizeof(int));
+    if (!sums || !tot) return fail(h, RORBK_ERR_OOM, "scan workspace");
+    k_scan_tiles<<<(unsigned)tiles, nt, 0, h->stream>>>(d, d, sums, n);
+    k_scan_sums<<<1, 1024, 0, h->stream>>>(sums, (int)tiles, tot);
+    k_scan_add<<<(unsigned)tiles, nt, 0, h->stream>>>(d, sums, n);
+    rorbk_status st = cuda_check(h, cudaMemcpyAsync(grand_total_host, tot, sizeof(int),
+                                                    cudaMemcpyDeviceToHost, h->stream), "scan total");
+    if (st) return st;
+    return cuda_check(h, cudaStreamSynchronize(h->stream), "scan");
+}
+
+rorbk_status build_setup(rorbk_ctx *h) {
+    cudaStream_t s = h->stream;
+    const int m = (int)h->m, n = (int)h->n, k = h->k;
+    rorbk_status st;
+    int *flags = (int *)dev_alloc(h, 2 * sizeof(int));
+    if (!flags) return fail(h, RORBK_ERR_OOM, "flags");
+    cudaMemsetAsync(flags, 0, 2 * sizeof(int), s);
+    int gs = std::max(1, std::min(4 * h->num_sms, (m + 255) / 256));
+    k_validate_csr<<<gs, 256, 0, s>>>(h->rowptr, h->col, h->val, m, n, flags);
+    int hf[2] = {0, 0};
+    if ((st = cuda_check(h, cudaMemcpyAsync(hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s), "validate")))
+        return st;
+    if ((st = cuda_check(h, cudaStreamSynchronize(s), "validate"))) return st;
+    if (hf[0] & 1)
+        return fail(h, RORBK_ERR_INVALID_ARG,
+                    "CSR structure: row_ptr must be non-decreasing and columns strictly ascending in [0,n)");
+    if (hf[0] & 2) return fail(h, RORBK_ERR_NUMERIC, "A holds NaN or Inf");
+
+    // block transpose, coupled rows
+    const long long nnz = h->nnz;
+    h->bt.col = (int *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(int));
+    h->bt.row = (uint16_t *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(uint16_t));
+    h->bt.val = (double *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(double));
+    h->bt.seg = (int *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(int));
+    h->bt.seg_ptr = (int *)dev_alloc(h, (size_t)k * sizeof(int));   // segment counts
+    unsigned char *coupled = (unsigned char *)dev_alloc(h, (size_t)m);
+    int *ncoupled = (int *)dev_alloc(h, (size_t)(k + 1) * sizeof(int));
+    if (!h->bt.col || !h->bt.row || !h->bt.val || !h->bt.seg || !h->bt.seg_ptr || !coupled ||
+        !ncoupled)
+        return fail(h, RORBK_ERR_OOM, "block transpose");
+    k_block_transpose<<<k, 256, 0, s>>>(h->rowptr, h->col, h->val, h->off, h->bt.col, h->bt.row,
+                                        h->bt.val, h->bt.seg, h->bt.seg_ptr, coupled, ncoupled);
+    if ((st = cuda_check(h, cudaGetLastError(), "block transpose"))) return st;
+
+    // centroids, C row sums, proposal
+    {
+        int *colcnt = (int *)dev_alloc(h, (size_t)(n + 1) * sizeof(int));
+        int *fill = (int *)dev_alloc(h, (size_t)(n + 1) * sizeof(int));
+        if (!colcnt || !fill) return fail(h, RORBK_ERR_OOM, "centroid columns");
+        cudaMemsetAsync(colcnt, 0, (size_t)(n + 1) * sizeof(int), s);
+        cudaMemsetAsync(fill, 0, (size_t)(n + 1) * sizeof(int), s);
+        int gk = std::min(k, 8 * h->num_sms);
+        k_centroid_count<<<gk, 128, 0, s>>>(h->rowptr, h->off, h->bt.col, h->bt.seg, h->bt.seg_ptr,
+                                           k, colcnt);
+        int total = 0;
+        if ((st = scan_device(h, colcnt, (long long)n + 1, &total))) return st;
+        int *cb = (int *)dev_alloc(h, (size_t)std::max(1, total) * sizeof(int));
+        double *cv = (double *)dev_alloc(h, (size_t)std::max(1, total) * sizeof(double));
+        double *G = (double *)dev_alloc(h, (size_t)k * k * sizeof(double));
+        if (!cb || !cv || !G) return fail(h, RORBK_ERR_OOM, "centroid Gram");
+        k_centroid_fill<<<gk, 128, 0, s>>>(h->rowptr, h->off, h->bt.col, h->bt.val, h->bt.seg,
+                                          h->bt.seg_ptr, k, colcnt, fill, cb, cv);
+        cudaMemsetAsync(G, 0, (size_t)k * k * sizeof(double), s);
+        k_centroid_gram<<<(k * 32 + 255) / 256, 256, 0, s>>>(h->rowptr, h->off, h->bt.col, h->bt.val,
+                                                            h->bt.seg, h->bt.seg_ptr, k, colcnt,
+                                                            cb, cv, G);
+        k_crowsum<<<(k * 32 + 255) / 256, 256, 0, s>>>(G, k, h->crowsum);
+        k_proposal<<<1, 1024, 0, s>>>(h->crowsum, k, (double)n, h->cdf);
+        if ((st = cuda_check(h, cudaGetLastError(), "proposal"))) return st;
+    }
+
+    // static operators on the coupled rows of every block
+    {
+        std::vector<int> hcnt(k + 1, 0);
+        if ((st = cuda_check(h, cudaMemcpyAsync(hcnt.data(), ncoupled, k * sizeof(int),
+                                                cudaMemcpyDeviceToHost, s), "coupled counts")))
+            return st;
+        if ((st = cuda_check(h, cudaStreamSynchronize(s), "coupled counts"))) return st;
+        std::vector<int> sptr(k + 1, 0);
+        std::vector<long long> wptr(k + 1, 0);
+        for (int t = 0; t < k; ++t) {
+            sptr[t + 1] = sptr[t] + hcnt[t];
+            wptr[t + 1] = wptr[t] + (long long)hcnt[t] * hcnt[t];
+        }
+        h->ops.s_ptr = (int *)dev_alloc(h, (size_t)(k + 1) * sizeof(int));
+        h->ops.w_ptr = (long long *)dev_alloc(h, (size_t)(k + 1) * sizeof(long long));
+        h->ops.s_idx = (uint16_t *)dev_alloc(h, (size_t)std::max(1, sptr[k]) * sizeof(uint16_t));
+        h->ops.s_pos = (int *)dev_alloc(h, (size_t)m * sizeof(int));
+        h->ops.w_ss = (double *)dev_alloc(h, (size_t)std::max(1LL, wptr[k]) * sizeof(double));
+        h->ops.w_diag = (double *)dev_alloc(h, (size_t)m * sizeof(double));
+        double *linv = nullptr;
+        if (cudaMalloc(&linv, (size_t)std::max(1LL, wptr[k]) * sizeof(double)) != cudaSuccess)
+            return fail(h, RORBK_ERR_OOM, "static operator scratch");
+        if (!h->ops.s_ptr || !h->ops.w_ptr || !h->ops.s_idx || !h->ops.s_pos || !h->ops.w_ss ||
+            !h->ops.w_diag) {
+            cudaFree(linv);
+            return fail(h, RORBK_ERR_OOM, "static operators");
+        }
+        cudaMemcpyAsync(h->ops.s_ptr, sptr.data(), (k + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(h->ops.w_ptr, wptr.data(), (k + 1) * sizeof(long long), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(flags, 0, sizeof(int), s);
+        k_static_ops<<<k, 256, 0, s>>>(h->rowptr, h->col, h->val, h->off, h->mu, coupled,
+                                       h->ops.s_ptr, h->ops.w_ptr, h->ops.s_idx, h->ops.s_pos,
+                                       h->ops.w_ss, h->ops.w_diag, linv, flags);
+        int spd = 0;
+        st = cuda_check(h, cudaMemcpyAsync(&spd, flags, sizeof(int), cudaMemcpyDeviceToHost, s), "static ops");
+        if (!st) st = cuda_check(h, cudaStreamSynchronize(s), "static ops");
+        cudaFree(linv);
+        if (st) return st;
+        if (spd) return fail(h, RORBK_ERR_NOT_SPD, "a static block Gram is not positive definite (lambda = 0 with dependent rows?)");
+        if (h->precision_built) {
+            h->ops.w_ss32 = (float *)dev_alloc(h, (size_t)std::max(1LL, wptr[k]) * sizeof(float));
+            h->ops.w_diag32 = (float *)dev_alloc(h, (size_t)m * sizeof(float));
+            h->bt.val32 = (float *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(float));
+            if (!h->ops.w_ss32 || !h->ops.w_diag32 || !h->bt.val32)
+                return fail(h, RORBK_ERR_OOM, "fp32 operators");
+            k_narrow<<<gs, 256, 0, s>>>(h->ops.w_ss, h->ops.w_ss32, std::max(1LL, wptr[k]));
+            k_narrow<<<gs, 256, 0, s>>>(h->ops.w_diag, h->ops.w_diag32, m);
+            k_narrow<<<gs, 256, 0, s>>>(h->bt.val, h->bt.val32, nnz);
+        }
+    }
+    return cuda_check(h, cudaStreamSynchronize(s), "setup");
+}
+
+}  // namespace rorbk

@@ -1,0 +1,490 @@
+// rorbk.cu -- the C ABI declared in include/rorbk.h: handle life cycle,
+// argument checks, device memory, the graph-captured iteration loop and the
+// single-step entry points.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace rorbk {
+
+static thread_local std::string g_setup_error;
+
+rorbk_status fail(rorbk_ctx *h, rorbk_status st, const std::string &msg) {
+    if (h) h->err = msg;
+    g_setup_error = msg;
+    return st;
+}
+
+rorbk_status cuda_check(rorbk_ctx *h, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return RORBK_OK;
+    cudaGetLastError();
+    return fail(h, e == cudaErrorMemoryAllocation ? RORBK_ERR_OOM : RORBK_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *dev_alloc(rorbk_ctx *h, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    h->allocs.push_back(p);
+    h->bytes += (int64_t)bytes;
+    return p;
+}
+
+static rorbk_status device_status(rorbk_ctx *h, int code) {
+    switch (code) {
+        case kDevOk: return RORBK_OK;
+        case kDevNotSpd: return fail(h, RORBK_ERR_NOT_SPD, "a block Gram is not positive definite");
+        case kDevBounds: return fail(h, RORBK_ERR_BOUNDS, "a device index or scratch bound was exceeded");
+        case kDevNumeric: return fail(h, RORBK_ERR_NUMERIC, "the residual is not finite");
+        default: return fail(h, RORBK_ERR_CUDA, "unknown device status");
+    }
+}
+
+// Greedy residual tiles: consecutive rows, at most kTileRows rows and
+// kTileNnz nonzeros, a longer row alone.
+static void build_tiles(const std::vector<int> &rp, int m, std::vector<int> &tiles) {
+    tiles.clear();
+    int r = 0;
+    while (r < m) {
+        tiles.push_back(r);
+        int nz = rp[r + 1] - rp[r];
+        if (nz > kTileNnz) { ++r; continue; }
+        int rows = 1, acc = nz;
+        ++r;
+        while (r < m && rows < kTileRows && acc + (rp[r + 1] - rp[r]) <= kTileNnz) {
+            acc += rp[r + 1] - rp[r];
+            ++rows;
+            ++r;
+        }
+    }
+    tiles.push_back(m);
+}
+
+// Capture: k_begin, then WHILE(cond) { one iteration }.
+static rorbk_status build_graph_fp64(rorbk_ctx *h) {
+    rorbk_status st;
+    cudaStream_t saved = h->stream;
+    cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2;
+    if ((st = cuda_check(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "capture")))
+        return st;
+    cudaGraph_t graph = nullptr;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphConditionalHandle hcond = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hcond, graph, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        h->stream = cs;
+        launch_begin(h, h->bb, h->xb, h->xb, 1, (unsigned long long)hcond);
+        e = cudaGetLastError();
+    }
+    cudaGraphNode_t wnode = nullptr;
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hcond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &cp);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            h->stream = cs2;
+            launch_iteration(h, h->bb, h->xb, h->r, 1, (unsigned long long)hcond);
+            cudaError_t e2 = cudaGetLastError();
+            cudaGraph_t body_out = nullptr;
+            e = cudaStreamEndCapture(cs2, &body_out);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    h->stream = saved;
+    cudaGraph_t g_out = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(cs, &g_out);
+    if (e == cudaSuccess) e = e3;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_fp64, g_out, 0);
+    if (g_out) cudaGraphDestroy(g_out);
+    return cuda_check(h, e, "building the iteration graph");
+}
+
+static rorbk_options defaults() {
+    rorbk_options o;
+    rorbk_default_options(&o);
+    return o;
+}
+
+}  // namespace rorbk
+
+using namespace rorbk;
+
+extern "C" {
+
+void rorbk_default_options(rorbk_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->n_static = 3;
+    opt->precision = RORBK_PREC_FP64;
+    opt->inner_tol = 1e-4;
+    opt->inner_maxit = 2000000;
+}
+
+const char *rorbk_last_error(rorbk_handle h) {
+    static const char none[] = "";
+    if (!h) return g_setup_error.c_str();   // the last failure on this thread
+    return h->err.empty() ? none : h->err.c_str();
+}
+
+void rorbk_free(rorbk_handle h) {
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->exec_fp64) cudaGraphExecDestroy(h->exec_fp64);
+    if (h->exec_mixed) cudaGraphExecDestroy(h->exec_mixed);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+    for (void *p : h->allocs) cudaFree(p);
+    cudaSetDevice(cur);
+    delete h;
+}
+
+rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, double lambda,
+                         const rorbk_options *opt_in, rorbk_handle *out) {
+    if (!out) return RORBK_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!A || !part) return RORBK_ERR_INVALID_ARG;
+    rorbk_options opt = opt_in ? *opt_in : defaults();
+    if (A->format != RORBK_FORMAT_CSR) return RORBK_ERR_UNSUPPORTED;
+    if (A->dtype != RORBK_F64 && A->dtype != RORBK_F32) return RORBK_ERR_INVALID_ARG;
+    if (A->m < 1 || A->n < 1 || A->m >= (1LL << 31) || A->n >= (1LL << 31) || A->nnz < 0 ||
+        A->nnz >= (1LL << 31) || !A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->values)))
+        return RORBK_ERR_INVALID_ARG;
+    const int64_t m = A->m, n = A->n, nnz = A->nnz;
+    const int k = part->num_blocks;
+    if (k < 1 || k > m || k > 65536) return RORBK_ERR_INVALID_ARG;
+
+    rorbk_ctx *h = new rorbk_ctx();
+    rorbk_status st;
+    cudaGetDevice(&h->device);
+    h->stream = (cudaStream_t)opt.stream;
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->m = m; h->n = n; h->nnz = nnz; h->k = k;
+    h->format = A->format; h->vdtype = A->dtype;
+    h->K = (int)(m / k);
+    h->precision_built = opt.precision == RORBK_PREC_MIXED ? 1 : 0;
+    auto bail = [&](rorbk_status s) {
+        std::string e = h->err.empty() ? std::string("setup failed") : h->err;
+        rorbk_free(h);
+        g_setup_error = e;
+        *out = nullptr;
+        return s;
+    };
+
+    // partition (Algorithm 1 step 1)
+    h->h_off.resize(k + 1);
+    if (part->offsets) {
+        for (int t = 0; t <= k; ++t) h->h_off[t] = part->offsets[t];
+        if (h->h_off[0] != 0 || h->h_off[k] != m) return bail(RORBK_ERR_INVALID_ARG);
+        for (int t = 0; t < k; ++t)
+            if (h->h_off[t + 1] <= h->h_off[t]) return bail(RORBK_ERR_INVALID_ARG);
+    } else {
+        const int64_t q = m / k, rem = m % k;
+        for (int t = 0; t <= k; ++t) h->h_off[t] = t * q + std::min<int64_t>(t, rem);
+    }
+    for (int t = 0; t < k; ++t) h->smax = std::max<int>(h->smax, (int)(h->h_off[t + 1] - h->h_off[t]));
+    if (h->smax > kMaxBlockRows || h->K > kMaxDynRows) return bail(RORBK_ERR_UNSUPPORTED);
+    h->mu = lambda < 0 ? 1e-6 * (double)(m / k) : lambda;
+
+    if ((st = cuda_check(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream")))
+        return bail(st);
+    if ((st = cuda_check(h, cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking), "stream")))
+        return bail(st);
+    configure_kernels();
+
+    // copy A (CSR) and a host view of row_ptr for the tiling
+    std::vector<int> hrp(m + 1);
+    const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (A->on_device) {
+        if ((st = cuda_check(h, cudaMemcpy(hrp.data(), A->row_ptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost), "row_ptr")))
+            return bail(st);
+    } else {
+        memcpy(hrp.data(), A->row_ptr, (m + 1) * sizeof(int));
+    }
+    if (hrp[0] != 0 || hrp[m] != nnz) return bail(fail(h, RORBK_ERR_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[m] = nnz"));
+    for (int64_t i = 0; i < m; ++i)
+        if (hrp[i + 1] < hrp[i]) return bail(fail(h, RORBK_ERR_INVALID_ARG, "row_ptr must be non-decreasing"));
+    int maxrow = 0;
+    for (int64_t i = 0; i < m; ++i) maxrow = std::max(maxrow, hrp[i + 1] - hrp[i]);
+
+    h->rowptr = (int *)dev_alloc(h, (m + 1) * sizeof(int));
+    h->col = (int *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(int));
+    h->val = (double *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(double));
+    h->off = (int *)dev_alloc(h, (k + 1) * sizeof(int));
+    h->cdf = (double *)dev_alloc(h, k * sizeof(double));
+    h->crowsum = (double *)dev_alloc(h, k * sizeof(double));
+    if (!h->rowptr || !h->col || !h->val || !h->off || !h->cdf || !h->crowsum) return bail(fail(h, RORBK_ERR_OOM, "matrix"));
+    cudaStream_t s = h->stream;
+    cudaMemcpyAsync(h->rowptr, A->row_ptr, (m + 1) * sizeof(int), kind, s);
+    if (nnz) cudaMemcpyAsync(h->col, A->col_idx, nnz * sizeof(int), kind, s);
+    if (A->dtype == RORBK_F64) {
+        if (nnz) cudaMemcpyAsync(h->val, A->values, nnz * sizeof(double), kind, s);
+        if (h->precision_built) {
+            h->val32 = (float *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(float));
+            if (!h->val32) return bail(fail(h, RORBK_ERR_OOM, "fp32 values"));
+        }
+    } else {
+        h->val32 = (float *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(float));
+        if (!h->val32) return bail(fail(h, RORBK_ERR_OOM, "fp32 values"));
+        if (nnz) cudaMemcpyAsync(h->val32, A->values, nnz * sizeof(float), kind, s);
+    }
+    {
+        std::vector<int> off32(k + 1);
+        for (int t = 0; t <= k; ++t) off32[t] = (int)h->h_off[t];
+        cudaMemcpyAsync(h->off, off32.data(), (k + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+        if ((st = cuda_check(h, cudaStreamSynchronize(s), "copy A"))) return bail(st);
+    }
+    widen_values(h, A->dtype);
+    if ((st = cuda_check(h, cudaGetLastError(), "value copies"))) return bail(st);
+
+    // residual tiles
+    std::vector<int> tiles;
+    build_tiles(hrp, (int)m, tiles);
+    h->ntiles = (int)tiles.size() - 1;
+    h->tile_row0 = (int *)dev_alloc(h, tiles.size() * sizeof(int));
+    h->grid_res = std::max(1, std::min(h->ntiles, 8 * h->num_sms));
+    // workspace
+    h->r = (double *)dev_alloc(h, m * sizeof(double));
+    h->xb = (double *)dev_alloc(h, n * sizeof(double));
+    h->bb = (double *)dev_alloc(h, m * sizeof(double));
+    h->partials = (double *)dev_alloc(h, std::max(h->grid_res, 4 * h->num_sms) * sizeof(double) + 64);
+    h->hist1 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
+    h->hist2 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
+    h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
+    h->eq_list = (int *)dev_alloc(h, kEqCap * sizeof(int));
+    h->ctl = (Ctl *)dev_alloc(h, sizeof(Ctl));
+    h->dyn_ecap = std::max<int64_t>(1, (int64_t)h->K * maxrow);
+    int64_t np2 = 1;
+    while (np2 < h->dyn_ecap) np2 <<= 1;
+    h->dyn_keys = (unsigned long long *)dev_alloc(h, np2 * sizeof(unsigned long long));
+    h->dyn_ecol = (int *)dev_alloc(h, h->dyn_ecap * sizeof(int));
+    h->dyn_eval = (double *)dev_alloc(h, h->dyn_ecap * sizeof(double));
+    h->dyn_erow = (uint16_t *)dev_alloc(h, h->dyn_ecap * sizeof(uint16_t));
+    h->dyn_g = (double *)dev_alloc(h, (size_t)h->K * h->K * sizeof(double));
+    if (h->precision_built) {
+        h->r32 = (float *)dev_alloc(h, m * sizeof(float));
+        h->b32 = (float *)dev_alloc(h, m * sizeof(float));
+        h->d32 = (float *)dev_alloc(h, n * sizeof(float));
+        if (!h->r32 || !h->b32 || !h->d32) return bail(fail(h, RORBK_ERR_OOM, "mixed workspace"));
+    }
+    if (!h->tile_row0 || !h->r || !h->xb || !h->bb || !h->partials || !h->hist1 || !h->hist2 ||
+        !h->in_list || !h->eq_list || !h->ctl || !h->dyn_keys || !h->dyn_ecol || !h->dyn_eval ||
+        !h->dyn_erow || !h->dyn_g)
+        return bail(fail(h, RORBK_ERR_OOM, "workspace"));
+    cudaMemcpyAsync(h->tile_row0, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(h->hist1, 0, kHistBins * sizeof(unsigned), s);
+    cudaMemsetAsync(h->hist2, 0, kHistBins * sizeof(unsigned), s);
+    cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s);
+
+    if ((st = build_setup(h))) return bail(st);
+    *out = h;
+    return RORBK_OK;
+}
+
+static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0, bool b_host,
+                               double *x, bool x_host, double tol, int64_t maxit,
+                               const rorbk_options *opt_in, rorbk_result *res) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!b || !x || maxit < 0 || !(tol >= 0)) return fail(h, RORBK_ERR_INVALID_ARG, "solve: b, x, tol >= 0, maxit >= 0");
+    rorbk_options opt = opt_in ? *opt_in : defaults();
+    if (opt.n_static < 0 || opt.n_static > 64) return fail(h, RORBK_ERR_INVALID_ARG, "n_static");
+    if (opt.precision != RORBK_PREC_FP64)
+        return fail(h, RORBK_ERR_UNSUPPORTED, "this precision mode is not built into the handle");
+    cudaSetDevice(h->device);
+    cudaStream_t s = opt.stream ? (cudaStream_t)opt.stream : h->stream;
+    const int64_t m = h->m, n = h->n;
+    rorbk_status st;
+    cudaMemcpyAsync(h->bb, b, m * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    if (x0) cudaMemcpyAsync(h->xb, x0, n * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    Ctl c;
+    memset(&c, 0, sizeof(c));
+    c.maxit = maxit;
+    c.iter_base = opt.start_iter;
+    c.seed = opt.seed;
+    c.sysid = opt.system_id;
+    c.tol = tol;
+    c.n_static = opt.n_static;
+    c.has_x0 = x0 != nullptr;
+    if (opt.trace) {
+        c.trace_cap = opt.trace->capacity;
+        c.tr_tau = (long long *)opt.trace->tau;
+        c.tr_rrn = opt.trace->rrn;
+        c.tr_I = opt.trace->I;
+        c.tr_x = opt.trace->x;
+    }
+    cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s);
+    if (!h->exec_fp64) {
+        if ((st = cuda_check(h, cudaStreamSynchronize(s), "solve prologue"))) return st;
+        if ((st = build_graph_fp64(h))) return st;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaError_t e = cudaGraphLaunch(h->exec_fp64, s);
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(x, h->xb, n * sizeof(double), x_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((st = cuda_check(h, e, "solve"))) return st;
+    st = c.status ? device_status(h, c.status) : (c.done ? RORBK_OK : RORBK_NOT_CONVERGED);
+    if (res) {
+        res->iters = c.iter;
+        res->rrn = c.rrn;
+        res->converged = c.done && c.status == 0;
+        res->status = st;
+        res->refinements = 0;
+        res->time_ms = ms;
+    }
+    return st;
+}
+
+rorbk_status rorbk_solve(rorbk_handle h, const double *b, const double *x0, double *x, double tol,
+                         int64_t maxit, const rorbk_options *opt, rorbk_result *res) {
+    return solve_impl(h, b, x0, false, x, false, tol, maxit, opt, res);
+}
+
+rorbk_status rorbk_solve_host(rorbk_handle h, const double *b_host, const double *x0_host,
+                              double *x_host, double tol, int64_t maxit, const rorbk_options *opt,
+                              rorbk_result *res) {
+    return solve_impl(h, b_host, x0_host, true, x_host, true, tol, maxit, opt, res);
+}
+
+rorbk_status rorbk_get_info(rorbk_handle h, rorbk_info *info) {
+    if (!h || !info) return RORBK_ERR_INVALID_ARG;
+    info->m = h->m; info->n = h->n; info->nnz = h->nnz;
+    info->num_blocks = h->k; info->dyn_rows = h->K; info->max_block_rows = h->smax;
+    info->format = h->format; info->lambda = h->mu; info->device_bytes = h->bytes;
+    return RORBK_OK;
+}
+
+rorbk_status rorbk_get_proposal(rorbk_handle h, double *cdf_host, double *c_rowsum_host) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    rorbk_status st = RORBK_OK;
+    if (cdf_host) st = cuda_check(h, cudaMemcpy(cdf_host, h->cdf, h->k * sizeof(double), cudaMemcpyDeviceToHost), "cdf");
+    if (!st && c_rowsum_host) st = cuda_check(h, cudaMemcpy(c_rowsum_host, h->crowsum, h->k * sizeof(double), cudaMemcpyDeviceToHost), "rowsum");
+    return st;
+}
+
+rorbk_status rorbk_get_static_operator(rorbk_handle h, int64_t t, double *W_host) {
+    if (!h || !W_host || t < 0 || t >= h->k) return RORBK_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    const int r0 = (int)h->h_off[t], s = (int)(h->h_off[t + 1] - h->h_off[t]);
+    int sp[2];
+    long long wp;
+    rorbk_status st = cuda_check(h, cudaMemcpy(sp, h->ops.s_ptr + t, 2 * sizeof(int), cudaMemcpyDeviceToHost), "W");
+    if (st) return st;
+    st = cuda_check(h, cudaMemcpy(&wp, h->ops.w_ptr + t, sizeof(long long), cudaMemcpyDeviceToHost), "W");
+    if (st) return st;
+    const int nS = sp[1] - sp[0];
+    std::vector<uint16_t> idx(std::max(1, nS));
+    std::vector<double> wss((size_t)std::max(1, nS * nS)), wd(s);
+    std::vector<int> pos(s);
+    if (nS) {
+        cudaMemcpy(idx.data(), h->ops.s_idx + sp[0], nS * sizeof(uint16_t), cudaMemcpyDeviceToHost);
+        cudaMemcpy(wss.data(), h->ops.w_ss + wp, (size_t)nS * nS * sizeof(double), cudaMemcpyDeviceToHost);
+    }
+    cudaMemcpy(wd.data(), h->ops.w_diag + r0, s * sizeof(double), cudaMemcpyDeviceToHost);
+    st = cuda_check(h, cudaMemcpy(pos.data(), h->ops.s_pos + r0, s * sizeof(int), cudaMemcpyDeviceToHost), "W");
+    if (st) return st;
+    for (int a = 0; a < s; ++a)
+        for (int b2 = 0; b2 < s; ++b2) W_host[(size_t)a * s + b2] = 0.0;
+    for (int a = 0; a < s; ++a)
+        if (pos[a] < 0) W_host[(size_t)a * s + a] = wd[a];
+    for (int i = 0; i < nS; ++i)
+        for (int j = 0; j < nS; ++j) W_host[(size_t)idx[i] * s + idx[j]] = wss[(size_t)i * nS + j];
+    return RORBK_OK;
+}
+
+rorbk_status rorbk_sample(rorbk_handle h, uint64_t seed, uint64_t system_id, int64_t it, int64_t l,
+                          int64_t *tau_host) {
+    if (!h || !tau_host) return RORBK_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    long long *d = (long long *)h->partials;
+    launch_sample_probe(h, seed, system_id, it, l, d);
+    long long v = 0;
+    rorbk_status st = cuda_check(h, cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, h->stream), "sample");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(h->stream), "sample");
+    *tau_host = v;
+    return st;
+}
+
+rorbk_status rorbk_static_update(rorbk_handle h, int64_t tau, const double *b, double *x) {
+    if (!h || !b || !x || tau < 0 || tau >= h->k) return RORBK_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    launch_static_forced(h, (int)tau, b, x);
+    rorbk_status st = cuda_check(h, cudaGetLastError(), "static update");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(h->stream), "static update");
+    return st;
+}
+
+rorbk_status rorbk_residual(rorbk_handle h, const double *b, const double *x, double *r,
+                            double *rr_host) {
+    if (!h || !b || !x || !r) return RORBK_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    launch_residual_only(h, b, x, r);
+    rorbk_status st = cuda_check(h, cudaGetLastError(), "residual");
+    if (!rr_host) return st;            // enqueue only
+    Ctl c;
+    if (!st) st = cuda_check(h, cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream), "residual");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(h->stream), "residual");
+    if (!st && rr_host) *rr_host = c.rr;
+    return st;
+}
+
+rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I) {
+    if (!h || !r || !I) return RORBK_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    launch_topk_only(h, r, I);
+    rorbk_status st = cuda_check(h, cudaGetLastError(), "top-K");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(h->stream), "top-K");
+    return st;
+}
+
+rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I, const double *r, double *x) {
+    if (!h || !I || !r || !x) return RORBK_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    cudaMemsetAsync(&h->ctl->status, 0, sizeof(int), h->stream);
+    cudaMemsetAsync(&h->ctl->done, 0, sizeof(int), h->stream);
+    launch_dynamic_given(h, I, r, x);
+    rorbk_status st = cuda_check(h, cudaGetLastError(), "dynamic update");
+    int code = 0;
+    if (!st) st = cuda_check(h, cudaMemcpyAsync(&code, &h->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "dynamic update");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(h->stream), "dynamic update");
+    if (!st && code) st = device_status(h, code);
+    return st;
+}
+
+}  // extern "C"
