@@ -40,12 +40,16 @@
  *     first use gives the same numbers);
  *   - W_t = L^{-T} L^{-1} with L = chol(A_t A_t^T + mu I).
  *
+ * Rounding: every multiply-add a*b + c is one IEEE 754 fusedMultiplyAdd
+ * (C99 fma), rounded once; plain sums and quotients round as written.
+ *
  * Fixed summation orders (so that each number has one definition):
  *   - row dot products run over a CSR row in stored (ascending column) order,
  *     a dense row in column order;
  *   - (A_B^T y)_c sums over the block's rows in ascending order into a zeroed
  *     vector delta, and then x_c += delta_c;
  *   - Gram entries G_ij = sum_c A_ic A_jc in ascending column order;
+ *   - y = W r sums over ascending columns of W;
  *   - norms are sequential sums of squares.
  */
 #include <math.h>
@@ -117,10 +121,10 @@ static double row_dot(const orc_matrix *A, int64_t i, const double *x)
     double s = 0.0;
     if (A->is_dense) {
         const double *a = A->dense + i * A->ld;
-        for (int64_t c = 0; c < A->n; ++c) s += a[c] * x[c];
+        for (int64_t c = 0; c < A->n; ++c) s = fma(a[c], x[c], s);
     } else {
         for (int64_t p = A->row_ptr[i]; p < A->row_ptr[i + 1]; ++p)
-            s += A->val[p] * x[A->col_idx[p]];
+            s = fma(A->val[p], x[A->col_idx[p]], s);
     }
     return s;
 }
@@ -131,14 +135,14 @@ static double row_row_dot(const orc_matrix *A, int64_t i, int64_t j)
     double s = 0.0;
     if (A->is_dense) {
         const double *a = A->dense + i * A->ld, *b = A->dense + j * A->ld;
-        for (int64_t c = 0; c < A->n; ++c) s += a[c] * b[c];
+        for (int64_t c = 0; c < A->n; ++c) s = fma(a[c], b[c], s);
         return s;
     }
     int64_t p = A->row_ptr[i], pe = A->row_ptr[i + 1];
     int64_t q = A->row_ptr[j], qe = A->row_ptr[j + 1];
     while (p < pe && q < qe) {
         int32_t cp = A->col_idx[p], cq = A->col_idx[q];
-        if (cp == cq) { s += A->val[p] * A->val[q]; ++p; ++q; }
+        if (cp == cq) { s = fma(A->val[p], A->val[q], s); ++p; ++q; }
         else if (cp < cq) ++p;
         else ++q;
     }
@@ -236,7 +240,7 @@ int orc_orthogonality(const orc_matrix *A, int64_t k, const int64_t *off,
     for (int64_t c = 0; c < n; ++c)
         for (int64_t a = colcnt[c]; a < colcnt[c + 1]; ++a)
             for (int64_t b2 = colcnt[c]; b2 < colcnt[c + 1]; ++b2)
-                G[(int64_t)cb[a] * k + cb[b2]] += cv[a] * cv[b2];
+                G[(int64_t)cb[a] * k + cb[b2]] = fma(cv[a], cv[b2], G[(int64_t)cb[a] * k + cb[b2]]);
 
     for (int64_t i = 0; i < k; ++i) {
         double rsum = 0.0;
@@ -293,7 +297,7 @@ double orc_residual(const orc_matrix *A, const double *b, const double *x, doubl
     double rr = 0.0;
     for (int64_t i = 0; i < A->m; ++i) {
         r[i] = b[i] - row_dot(A, i, x);
-        rr += r[i] * r[i];
+        rr = fma(r[i], r[i], rr);
     }
     return rr;
 }
@@ -383,7 +387,7 @@ int orc_cholesky(double *G, int64_t s)
         for (int64_t a = j + 1; a < s; ++a) {
             double la = G[a * s + j];
             for (int64_t b2 = j + 1; b2 <= a; ++b2)
-                G[a * s + b2] -= la * G[b2 * s + j];
+                G[a * s + b2] = fma(-la, G[b2 * s + j], G[a * s + b2]);
         }
     }
     for (int64_t a = 0; a < s; ++a)
@@ -401,11 +405,11 @@ void orc_chol_solve(const double *L, int64_t s, const double *r, double *y)
     for (int64_t i = 0; i < s; ++i) y[i] = r[i];
     for (int64_t j = 0; j < s; ++j) {
         y[j] = y[j] / L[j * s + j];
-        for (int64_t i = j + 1; i < s; ++i) y[i] -= L[i * s + j] * y[j];
+        for (int64_t i = j + 1; i < s; ++i) y[i] = fma(-L[i * s + j], y[j], y[i]);
     }
     for (int64_t j = s - 1; j >= 0; --j) {
         y[j] = y[j] / L[j * s + j];
-        for (int64_t i = 0; i < j; ++i) y[i] -= L[j * s + i] * y[j];
+        for (int64_t i = 0; i < j; ++i) y[i] = fma(-L[j * s + i], y[j], y[i]);
     }
 }
 
@@ -420,14 +424,14 @@ int orc_spd_inverse(const double *L, int64_t s, double *W)
         Li[j * s + j] = 1.0 / L[j * s + j];
         for (int64_t i = j + 1; i < s; ++i) {
             double acc = 0.0;
-            for (int64_t c = j; c < i; ++c) acc += L[i * s + c] * Li[c * s + j];
+            for (int64_t c = j; c < i; ++c) acc = fma(L[i * s + c], Li[c * s + j], acc);
             Li[i * s + j] = -acc / L[i * s + i];
         }
     }
     for (int64_t i = 0; i < s; ++i)
         for (int64_t j = 0; j <= i; ++j) {
             double acc = 0.0;
-            for (int64_t c = i; c < s; ++c) acc += Li[c * s + i] * Li[c * s + j];
+            for (int64_t c = i; c < s; ++c) acc = fma(Li[c * s + i], Li[c * s + j], acc);
             W[i * s + j] = acc;
             W[j * s + i] = acc;
         }
@@ -444,14 +448,14 @@ static void scatter_update(const orc_matrix *A, const int64_t *rows, int64_t s,
     if (A->is_dense) {
         for (int64_t a = 0; a < s; ++a) {
             const double *ar = A->dense + rows[a] * A->ld;
-            for (int64_t c = 0; c < A->n; ++c) delta[c] += ar[c] * y[a];
+            for (int64_t c = 0; c < A->n; ++c) delta[c] = fma(ar[c], y[a], delta[c]);
         }
         for (int64_t c = 0; c < A->n; ++c) { x[c] += delta[c]; delta[c] = 0.0; }
         return;
     }
     for (int64_t a = 0; a < s; ++a)
         for (int64_t p = A->row_ptr[rows[a]]; p < A->row_ptr[rows[a] + 1]; ++p)
-            delta[A->col_idx[p]] += A->val[p] * y[a];
+            delta[A->col_idx[p]] = fma(A->val[p], y[a], delta[A->col_idx[p]]);
     /* a column shared by several rows is applied on its first visit; later
      * visits add the re-zeroed delta_c = 0, which leaves x_c unchanged */
     for (int64_t a = 0; a < s; ++a)
@@ -473,7 +477,7 @@ void orc_update_with_inverse(const orc_matrix *A, const int64_t *rows, int64_t s
     for (int64_t a = 0; a < s; ++a) rB[a] = b[rows[a]] - row_dot(A, rows[a], x);
     for (int64_t a = 0; a < s; ++a) {
         double acc = 0.0;
-        for (int64_t c = 0; c < s; ++c) acc += W[a * s + c] * rB[c];
+        for (int64_t c = 0; c < s; ++c) acc = fma(W[a * s + c], rB[c], acc);
         y[a] = acc;
     }
     scatter_update(A, rows, s, y, x, scratch_n);
