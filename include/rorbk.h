@@ -105,6 +105,10 @@ typedef struct {
  *   x   [capacity * n]        double: x at the end of the iteration (after the
  *                                     dynamic update; on the converging
  *                                     iteration, after the static updates)
+ *   dyn [capacity * 4]        int32 : dynamic block structure per iteration:
+ *                                     nonzeros of A_I, nonzeros in columns
+ *                                     shared inside I, coupled rows |S|,
+ *                                     Gram contributions
  * Iterations beyond capacity are not recorded.  FP64 mode only. */
 typedef struct {
     int64_t capacity;
@@ -112,6 +116,7 @@ typedef struct {
     double *rrn;
     int32_t *I;
     double *x;
+    int32_t *dyn;
 } rorbk_trace;
 
 /* Options (NULL = defaults). */
@@ -123,6 +128,13 @@ typedef struct {
     int64_t start_iter;     /* counter of the first iteration (resume) (0)    */
     double inner_tol;       /* MIXED: inner relative residual target   (1e-4) */
     int64_t inner_maxit;    /* MIXED: inner iteration cap per refinement (2000000) */
+    int32_t host_loop;      /* 0: the whole loop runs on the device inside one
+                               CUDA graph (a conditional WHILE node);
+                               1: the host enqueues batches of `poll`
+                               iterations and reads the stop flag between
+                               batches (profilers that cannot see kernels in
+                               conditional graphs)             (0)    */
+    int32_t poll;           /* iterations per batch when host_loop = 1 (64)   */
     rorbk_trace *trace;     /* FP64 only                               (NULL) */
     void *stream;           /* cudaStream_t for all work               (0 = legacy default) */
 } rorbk_options;

@@ -43,7 +43,7 @@ __device__ __forceinline__ int sample_block(const double *cdf, int k, uint64_t s
 
 // Order-preserving key of |v| (non-negative doubles compare as uint64).
 __device__ __forceinline__ unsigned long long abs_key(double v) {
-    return (unsigned long long)__double_as_longlong(fabs(v));
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 __device__ __forceinline__ unsigned long long abs_key(float v) {
     return abs_key((double)v);
@@ -149,6 +149,25 @@ __device__ __forceinline__ void block_bitonic_sort_desc(unsigned long long *keys
     }
 }
 
+// Exact FP32 -> FP64 widening with integer operations only (the hardware
+// conversion runs on the FP64 pipe): normal numbers re-bias the exponent,
+// subnormals are normalised, zeros keep their sign, Inf/NaN keep their
+// payload.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+    const int lz = __clz(man | 1u) - 8;                  // leading zeros inside the 24-bit field
+    const unsigned long long sub_ex = (unsigned long long)(897 - lz) << 52;
+    const unsigned long long sub_man = ((unsigned long long)(man << lz) & 0x7fffffull) << 29;
+    const unsigned long long norm = ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)man << 29);
+    const unsigned long long special = (0x7ffull << 52) | ((unsigned long long)man << 29);
+    unsigned long long d = ex == 0xffu ? special : norm;
+    d = ex == 0u ? (man == 0u ? 0ull : (sub_ex | sub_man)) : d;
+    return __longlong_as_double((long long)(sign | d));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 __device__ __forceinline__ int next_pow2(int v) {
     int p = 1;
     while (p < v) p <<= 1;
@@ -183,7 +202,7 @@ __device__ __forceinline__ bool block_cholesky(double *G, int ld, int nS, int *b
             for (int b = j + 1 + lane; b <= a; b += 32) {
                 double lb = G[(long long)b * ld + j];
                 if (lb != 0.0)
-                    G[(long long)a * ld + b] = __dsub_rn(G[(long long)a * ld + b], __dmul_rn(la, lb));
+                    G[(long long)a * ld + b] = __fma_rn(-la, lb, G[(long long)a * ld + b]);
             }
         }
         __syncthreads();
@@ -201,7 +220,7 @@ __device__ __forceinline__ double row_merge_dot(const int *col, const V *val, in
     double s = 0.0;
     while (p < pe && q < qe) {
         int cp = col[p], cq = col[q];
-        if (cp == cq) { s = __dadd_rn(s, __dmul_rn((double)val[p], (double)val[q])); ++p; ++q; }
+        if (cp == cq) { s = __fma_rn((double)val[p], (double)val[q], s); ++p; ++q; }
         else if (cp < cq) ++p;
         else ++q;
     }

@@ -20,7 +20,10 @@ constexpr int kTileNnz = 2048;          // ... and nonzeros per tile
 constexpr int kHistBins = 2048;         // 11-bit radix digits of |r| keys
 constexpr int kEqCap = 4096;            // top-K candidates sorted in one CTA
 constexpr int kSortCapSmem = 4096;      // entries sorted in shared memory
-constexpr int kCholSmemMax = 96;        // coupled-set size factored in smem
+constexpr int kShCap = 2048;            // dynamic block: shared-column entries in smem
+constexpr int kPairCap = 2048;          // dynamic block: Gram contributions in smem
+constexpr int kSPackedMax = 176;        // dynamic block: coupled rows factored in smem
+constexpr int kGPack = kSPackedMax * (kSPackedMax + 1) / 2;
 
 // device error codes (ctl->status)
 constexpr int kDevOk = 0;
@@ -49,11 +52,16 @@ struct Ctl {
     double *tr_rrn;
     int *tr_I;
     double *tr_x;
+    int *tr_dyn;
     // mixed precision outer loop
     long long outer, inner_maxit, inner_total;
     double inner_tol, outer_rrn;
     int outer_done;
     int has_x0;
+    // dynamic block bookkeeping
+    int dynE, dyn_nsh, dyn_nS, dyn_npair, dyn_nraw, pad3_;
+    int halt;              // no further iteration runs (converged, error or maxit)
+    int pad2_;
 };
 
 // Sparse operator of one static block t (Section 3.1's stored inverse
@@ -108,20 +116,40 @@ struct rorbk_ctx {
     double *cdf = nullptr, *crowsum = nullptr;
     rorbk::StaticOps ops;
     rorbk::BlockT bt;
-    // residual tiles
+    // residual tiles (single-step residual on CSR) and the SELL-32 copy of A
     int ntiles = 0;
     int *tile_row0 = nullptr;
     int grid_res = 0;
+    struct {
+        int nslices = 0;
+        long long *ptr = nullptr;   // [nslices+1] first entry of slice s
+        int *len = nullptr;         // [nslices] entries per lane (the slice's longest row)
+        int *row = nullptr;         // [nslices*32] row of each lane (-1: empty lane)
+        int *rlen = nullptr;        // [nslices*32] nonzeros of that row
+        int *col = nullptr;         // [entries] column-major inside a slice
+        float *val32 = nullptr;     // FP32-stored values (FP32 systems and the mixed path)
+        double *val = nullptr;      // FP64 values (FP64 systems)
+    } sell;
     // workspace
     double *r = nullptr, *xb = nullptr, *bb = nullptr, *x64 = nullptr;
     float *r32 = nullptr, *b32 = nullptr, *d32 = nullptr;
     double *partials = nullptr;
     unsigned *hist1 = nullptr, *hist2 = nullptr;
-    int *in_list = nullptr, *eq_list = nullptr, *dynI = nullptr;
-    double *dyn_g = nullptr;           // K*K FP64 fallback for a large coupled set
-    unsigned long long *dyn_keys = nullptr;  // fallback sort space
-    int *dyn_ecol = nullptr; double *dyn_eval = nullptr; uint16_t *dyn_erow = nullptr;
-    int64_t dyn_ecap = 0;
+    int *in_list = nullptr, *eq_list = nullptr;
+    struct {
+        int *I = nullptr, *estart = nullptr;
+        double *gdiag = nullptr, *y = nullptr;
+        int *ecol = nullptr;
+        double *eval = nullptr;
+        uint16_t *erow = nullptr;
+        long long ecap = 0;
+        unsigned long long *owner = nullptr;
+        unsigned *shared = nullptr, *epoch = nullptr;
+        int *segpos = nullptr;
+        unsigned long long *raw = nullptr, *skeys = nullptr, *pkeys = nullptr;
+        long long pcap = 0;
+        double *g = nullptr;
+    } dyn;
     rorbk::Ctl *ctl = nullptr;
     // graphs
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
@@ -137,7 +165,7 @@ rorbk_status cuda_check(rorbk_ctx *h, cudaError_t e, const char *what);
 void *dev_alloc(rorbk_ctx *h, size_t bytes);
 
 // setup (kernels_setup.cu)
-rorbk_status build_setup(rorbk_ctx *h);
+rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &host_row_ptr);
 void widen_values(rorbk_ctx *h, int dtype);   // FP32 <-> FP64 value copies
 
 // iteration launches (kernels_iter.cu); all enqueue on h->stream

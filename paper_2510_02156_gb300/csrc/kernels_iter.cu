@@ -6,17 +6,22 @@
 //   k_residual     r = b - A x over nnz-balanced row tiles, ||r||^2, the
 //                  convergence test, and the first radix histogram of |r|
 //   k_topk_hist2   second 11-bit radix histogram inside the selected bin
-//   k_topk_collect the rows above the 22-bit threshold and the candidates on it
-//   k_dynamic      exact top-K, G = A_I A_I^T + mu I on the coupled rows,
-//                  Cholesky, two triangular solves, x += A_I^T y; ends the
-//                  iteration and sets the loop condition
+//   k_topk_collect rows above the 22-bit threshold and the candidates on it;
+//                  the last block completes the exact top-K set
+//   k_dyn_mark     gathers A_I, marks shared columns, Gram diagonal; the last
+//                  block factors G = A_I A_I^T + mu I on the coupled rows and
+//                  solves for y
+//   k_dyn_scatter  x += A_I^T y; ends the iteration, sets the loop condition
 //
 // Compute type T is double (the plain method) or float (the inner solve of
-// the mixed-precision form).  In FP64 every product and sum uses the
-// non-contracted __dmul_rn/__dadd_rn in the order of the oracle's
-// definitions (row dots in stored order; A^T y per column over ascending rows;
-// Gram entries over ascending columns; column-oriented triangular solves), so
-// the iterates reproduce the FP64 definition exactly.
+// the mixed-precision form).  In FP64 every multiply-add is one fused
+// multiply-add and every sum runs in the oracle's order (row dots in stored
+// order; A^T y per column over ascending rows; Gram entries over ascending
+// columns; column-ordered triangular solves), so the iterates reproduce the
+// FP64 definition exactly.  FP64 arithmetic on this part has a long latency,
+// so chains are kept short: the Cholesky of the coupled rows is scheduled
+// along its elimination tree (all columns of one tree level at once), which
+// performs the same operations on every entry in the same order.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -30,15 +35,22 @@ namespace rorbk {
 
 template <typename T> struct Ar;
 template <> struct Ar<double> {
-    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
 };
 template <> struct Ar<float> {
-    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
 };
+template <typename T> __device__ __forceinline__ T as(double v);
+template <> __device__ __forceinline__ double as<double>(double v) { return v; }
+template <> __device__ __forceinline__ float as<float>(double v) { return (float)v; }
+template <typename T> __device__ __forceinline__ T wide(float v);
+template <> __device__ __forceinline__ double wide<double>(float v) { return widen(v); }
+template <> __device__ __forceinline__ float wide<float>(float v) { return v; }
+template <typename T> __device__ __forceinline__ T wide(double v) { return (T)v; }
 
 // Matrix and operator pointers for one compute type.
 template <typename T>
@@ -64,6 +76,12 @@ struct Mat {
     int ntiles;
     double mu;
     const float *val32;         // FP32-stored values, when the system is FP32
+    // SELL-32 copy of A (the residual)
+    int nslices;
+    const long long *sptr;
+    const int *slen, *srow, *srlen, *scol;
+    const double *sval;
+    const float *sval32;
 };
 
 template <typename T>
@@ -73,25 +91,28 @@ Mat<double> make_mat<double>(rorbk_ctx *h) {
     return Mat<double>{h->rowptr, h->col, h->val, h->off, h->cdf, (int)h->m, (int)h->n, h->k, h->K,
                        h->ops.s_ptr, h->ops.s_idx, h->ops.w_ptr, h->ops.w_ss, h->ops.w_diag,
                        h->ops.s_pos, h->bt.col, h->bt.row, h->bt.val, h->bt.seg, h->bt.seg_ptr,
-                       h->tile_row0, h->ntiles, h->mu, h->val32};
+                       h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
+                       h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
+                       h->sell.val32};
 }
 template <>
 Mat<float> make_mat<float>(rorbk_ctx *h) {
     return Mat<float>{h->rowptr, h->col, h->val32, h->off, h->cdf, (int)h->m, (int)h->n, h->k, h->K,
                       h->ops.s_ptr, h->ops.s_idx, h->ops.w_ptr, h->ops.w_ss32, h->ops.w_diag32,
                       h->ops.s_pos, h->bt.col, h->bt.row, h->bt.val32, h->bt.seg, h->bt.seg_ptr,
-                      h->tile_row0, h->ntiles, h->mu, h->val32};
+                      h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
+                      h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
+                      h->sell.val32};
 }
 
 // ------------------------------------------------------------------ begin
-// ||b|| (deterministic: fixed grid, fixed trees), x = x0 or 0, loop state.
-// Launched with one block; sets the WHILE condition to (||b|| > 0 && maxit > 0).
+// ||b||, x = x0 or 0, loop state.  One block; sets the WHILE condition.
 __global__ void k_begin(const double *__restrict__ b, int m, const double *__restrict__ x0,
                         double *__restrict__ x, int n, Ctl *ctl, int use_cond,
                         cudaGraphConditionalHandle hcond) {
     __shared__ double red[32];
     double s = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s += b[i] * b[i];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s = __fma_rn(b[i], b[i], s);
     s = block_sum(s, red);
     __shared__ double bn;
     if (threadIdx.x == 0) bn = sqrt(s);
@@ -104,72 +125,85 @@ __global__ void k_begin(const double *__restrict__ b, int m, const double *__res
         ctl->rr = 0.0;
         ctl->rrn = bn == 0.0 ? 0.0 : 1.0;
         ctl->done = bn == 0.0;
+        ctl->halt = !(bn > 0.0 && ctl->maxit > 0);
         ctl->status = 0;
         ctl->ticket = 0;
         ctl->n_in = 0;
         ctl->n_eq = 0;
-        if (use_cond) cudaGraphSetConditional(hcond, (bn > 0.0 && ctl->maxit > 0) ? 1u : 0u);
+        if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
     }
 }
 
 // ----------------------------------------------------------------- static
 // One block of threads runs the n_static sampled updates of an iteration in
-// sequence (Algorithm 1, the inner loop over l).  force_tau >= 0 replaces the
-// draw by that block (single-step API).  Uses the stored W_tau (Section 3.1).
+// sequence (Algorithm 1, the inner loop over l); the draws do not depend on
+// x and are taken up front.  force_tau >= 0 replaces the draw by that block
+// (single-step API).  Uses the stored W_tau (Section 3.1).  The local
+// residual streams the block's nonzeros and gathered x through shared memory
+// in chunks; each row is a fused multiply-add chain in stored order.
+constexpr int kStaticChunk = 1536;
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__ b, T *x,
                                                  Ctl *ctl, int force_tau) {
     __shared__ T rloc[kMaxBlockRows];
     __shared__ T y[kMaxBlockRows];
-    __shared__ int tau_s;
-    if (force_tau < 0 && ctl->done) return;
-    const long long it = ctl->iter_base + ctl->iter;
+    __shared__ T sv[kStaticChunk];
+    __shared__ T sx[kStaticChunk];
+    __shared__ int taus[64];
+    if (force_tau < 0 && (ctl->done || ctl->halt)) return;
     const int nst = force_tau >= 0 ? 1 : ctl->n_static;
+    const int a = threadIdx.x;
+    if (a < nst) {
+        const long long it = ctl->iter_base + ctl->iter;
+        const int tau = force_tau >= 0 ? force_tau
+                                       : sample_block(A.cdf, A.k, ctl->seed, ctl->sysid,
+                                                      (uint64_t)it, (uint64_t)a);
+        taus[a] = tau;
+        if (force_tau < 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
+            ctl->tr_tau[ctl->iter * nst + a] = tau;
+    }
+    __syncthreads();
     for (int l = 0; l < nst; ++l) {
-        if (threadIdx.x == 0) {
-            int tau = force_tau >= 0 ? force_tau
-                                     : sample_block(A.cdf, A.k, ctl->seed, ctl->sysid,
-                                                    (uint64_t)it, (uint64_t)l);
-            tau_s = tau;
-            if (force_tau < 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
-                ctl->tr_tau[ctl->iter * nst + l] = tau;
-        }
-        __syncthreads();
-        const int tau = tau_s;
+        const int tau = taus[l];
         const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
-        for (int a = threadIdx.x; a < s; a += blockDim.x) {
-            const int i = r0 + a;
-            T acc = T(0);
-            for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p)
-                acc = Ar<T>::add(acc, Ar<T>::mul(A.val[p], x[A.col[p]]));
-            rloc[a] = Ar<T>::sub(b[i], acc);
+        const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
+        const int q0 = a < s ? A.rowptr[r0 + a] : 0, q1 = a < s ? A.rowptr[r0 + a + 1] : 0;
+        T acc = T(0);
+        for (int c0 = p0; c0 < pend; c0 += kStaticChunk) {
+            const int c1 = min(pend, c0 + kStaticChunk);
+            for (int p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
+                sv[p - c0] = A.val[p];
+                sx[p - c0] = x[A.col[p]];
+            }
+            __syncthreads();
+            for (int p = max(q0, c0); p < min(q1, c1); ++p) acc = Ar<T>::fma(sv[p - c0], sx[p - c0], acc);
+            __syncthreads();
         }
+        if (a < s) rloc[a] = Ar<T>::sub(b[r0 + a], acc);
         __syncthreads();
         const int sb = A.s_ptr[tau], nS = A.s_ptr[tau + 1] - sb;
         const T *W = A.w_ss + A.w_ptr[tau];
-        for (int a = threadIdx.x; a < s; a += blockDim.x) {
+        if (a < s) {
             const int i = r0 + a;
             const int pos = A.s_pos[i];
             if (pos < 0) {
-                y[a] = Ar<T>::mul(A.w_diag[i], rloc[a]);
+                y[a] = Ar<T>::fma(A.w_diag[i], rloc[a], T(0));
             } else {
                 const T *Wr = W + (long long)pos * nS;
-                T acc = T(0);
-                for (int q = 0; q < nS; ++q)
-                    acc = Ar<T>::add(acc, Ar<T>::mul(Wr[q], rloc[A.s_idx[sb + q]]));
-                y[a] = acc;
+                T acc2 = T(0);
+                for (int q = 0; q < nS; ++q) acc2 = Ar<T>::fma(Wr[q], rloc[A.s_idx[sb + q]], acc2);
+                y[a] = acc2;
             }
         }
         __syncthreads();
-        const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
         const int ns = A.nseg[tau];
         for (int g = threadIdx.x; g < ns; g += blockDim.x) {
             int q = A.bt_seg[p0 + g];
             const int c = A.bt_col[q];
-            T acc = T(0);
-            for (; q < pend && A.bt_col[q] == c; ++q)
-                acc = Ar<T>::add(acc, Ar<T>::mul(A.bt_val[q], y[A.bt_row[q]]));
-            x[c] = Ar<T>::add(x[c], acc);
+            T acc3 = T(0);
+            for (; q < pend && A.bt_col[q] == c; ++q) acc3 = Ar<T>::fma(A.bt_val[q], y[A.bt_row[q]], acc3);
+            x[c] = Ar<T>::add(x[c], acc3);
         }
         __syncthreads();
     }
@@ -203,71 +237,93 @@ __device__ void select_bin(unsigned *h, int need, int *bin_out, int *above_out) 
     *above_out = res_above;
 }
 
-// r = b - A x for the tiles of rows [tile_row0[t], tile_row0[t+1]).  Tiles
-// hold at most kTileNnz nonzeros (or a single longer row).  Products go to
-// shared memory and each row is summed in stored order by one thread.
+template <typename V, typename T>
+__device__ __forceinline__ const V *sell_values(const Mat<T> &A);
+template <>
+__device__ __forceinline__ const double *sell_values<double, double>(const Mat<double> &A) { return A.sval; }
+template <>
+__device__ __forceinline__ const float *sell_values<float, double>(const Mat<double> &A) { return A.sval32; }
+template <>
+__device__ __forceinline__ const float *sell_values<float, float>(const Mat<float> &A) { return A.sval32; }
+
+// Warp-aggregated shared-memory histogram increment.
+__device__ __forceinline__ void hist_add(unsigned *hist, unsigned bin, bool active) {
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) return;
+    const unsigned peers = __match_any_sync(mask, bin);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+}
+
+// r = b - A x on the SELL-32 copy of A: one warp per slice of 32 rows of
+// (nearly) equal length, one lane per row, so every fused multiply-add
+// instruction carries a full warp of rows; each row is one chain in stored
+// column order.  Longest slices come first.  V is the stored value type (an
+// FP32-stored system is read as FP32 and widened exactly).
 // finalize: 1 = convergence test + first radix level (iteration), 2 = ||r||^2
 // only (single-step API).
-template <typename V, typename T>
-__device__ __forceinline__ const V *stored_values(const Mat<T> &A);
-template <>
-__device__ __forceinline__ const double *stored_values<double, double>(const Mat<double> &A) { return A.val; }
-template <>
-__device__ __forceinline__ const float *stored_values<float, double>(const Mat<double> &A) { return A.val32; }
-template <>
-__device__ __forceinline__ const float *stored_values<float, float>(const Mat<float> &A) { return A.val; }
-
-// V is the stored value type (an FP32-stored system is read as FP32 and
-// widened exactly in registers).
 template <typename T, typename V>
 __global__ void __launch_bounds__(256) k_residual(Mat<T> A, const T *__restrict__ b,
                                                   const T *__restrict__ x, T *__restrict__ r,
                                                   double *partials, unsigned *hist1, Ctl *ctl,
                                                   int finalize) {
-    __shared__ T prod[kTileNnz];
     __shared__ unsigned hist[kHistBins];
     __shared__ double red[32];
     __shared__ int is_last;
-    if (finalize == 1 && ctl->done) return;
-    const V *__restrict__ val = stored_values<V, T>(A);
+    if (finalize == 1 && (ctl->done || ctl->halt)) return;
+    const V *__restrict__ val = sell_values<V, T>(A);
+    const int lane = threadIdx.x & 31;
+    const int nwb = blockDim.x >> 5;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     double rr = 0.0;
     __syncthreads();
-    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
-        const int row0 = A.tile_row0[t], row1 = A.tile_row0[t + 1];
-        const int p0 = A.rowptr[row0], p1 = A.rowptr[row1];
-        if (p1 - p0 <= kTileNnz) {
-            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x)
-                prod[p - p0] = Ar<T>::mul((T)val[p], x[A.col[p]]);
-            __syncthreads();
-            for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
-                const int q1 = A.rowptr[i + 1] - p0;
-                T s = T(0);
-                for (int q = A.rowptr[i] - p0; q < q1; ++q) s = Ar<T>::add(s, prod[q]);
-                const T ri = Ar<T>::sub(b[i], s);
-                r[i] = ri;
-                rr += (double)ri * (double)ri;
-                atomicAdd(&hist[(unsigned)(abs_key(ri) >> 52)], 1u);
-            }
-            __syncthreads();
-        } else {                                    // one long row, chunked
-            T s = T(0);
-            for (int c0 = p0; c0 < p1; c0 += kTileNnz) {
-                const int c1 = min(p1, c0 + kTileNnz);
-                for (int p = c0 + threadIdx.x; p < c1; p += blockDim.x)
-                    prod[p - c0] = Ar<T>::mul((T)val[p], x[A.col[p]]);
-                __syncthreads();
-                if (threadIdx.x == 0)
-                    for (int q = 0; q < c1 - c0; ++q) s = Ar<T>::add(s, prod[q]);
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) {
-                const T ri = Ar<T>::sub(b[row0], s);
-                r[row0] = ri;
-                rr += (double)ri * (double)ri;
-                atomicAdd(&hist[(unsigned)(abs_key(ri) >> 52)], 1u);
-            }
+    // consecutive slices go to different blocks, so the longest (first)
+    // slices spread over all SMs
+    for (int sl = blockIdx.x + gridDim.x * (threadIdx.x >> 5); sl < A.nslices; sl += gridDim.x * nwb) {
+        const long long base = A.sptr[sl] + lane;
+        const int L = A.slen[sl];
+        const int slot = sl * 32 + lane;
+        const int row = A.srow[slot], len = A.srlen[slot];
+        // software pipeline, 8 deep: the x gathers of chunk k and the index /
+        // value loads of chunk k+1 are in flight while chunk k's chain runs
+        T acc = T(0);
+        int cn[8];
+        V vn[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool in = u < len;
+            const long long d = base + 32LL * u;
+            cn[u] = in ? A.scol[d] : 0;
+            vn[u] = in ? val[d] : V(0);
         }
+        for (int c0 = 0; c0 < L; c0 += 8) {
+            T xv[8];
+            V vc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                xv[u] = c0 + u < len ? x[cn[u]] : T(0);
+                vc[u] = vn[u];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = c0 + 8 + u;
+                const bool in = j < len;
+                const long long d = base + 32LL * j;
+                cn[u] = in ? A.scol[d] : 0;
+                vn[u] = in ? val[d] : V(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < len) acc = Ar<T>::fma(wide<T>(vc[u]), xv[u], acc);
+        }
+        const bool act = row >= 0;
+        unsigned bin = 0;
+        if (act) {
+            const T ri = Ar<T>::sub(b[row], acc);
+            r[row] = ri;
+            rr = __fma_rn((double)ri, (double)ri, rr);
+            bin = (unsigned)(abs_key(ri) >> 52);
+        }
+        if (finalize == 1) hist_add(hist, bin, act);
     }
     __syncthreads();
     if (finalize == 1)
@@ -349,7 +405,7 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
                                                     unsigned *hist2, Ctl *ctl, int check_done) {
     __shared__ unsigned hist[kHistBins];
     __shared__ int is_last;
-    if (check_done && ctl->done) return;
+    if (check_done && (ctl->done || ctl->halt)) return;
     const unsigned sel1 = (unsigned)ctl->sel1;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
@@ -372,23 +428,6 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
         ctl->prefix = (int)((sel1 << 11) | (unsigned)bin);
         ctl->above = ctl->above1 + above;
         ctl->ticket = 0;
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_topk_collect(const T *__restrict__ r, int m,
-                                                      int *in_list, int *eq_list, Ctl *ctl,
-                                                      int check_done) {
-    if (check_done && ctl->done) return;
-    const unsigned long long P = (unsigned long long)(unsigned)ctl->prefix;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        unsigned long long pre = abs_key(r[i]) >> 41;
-        if (pre > P) {
-            in_list[atomicAdd(&ctl->n_in, 1)] = i;
-        } else if (pre == P) {
-            int pos = atomicAdd(&ctl->n_eq, 1);
-            if (pos < kEqCap) eq_list[pos] = i;
-        }
     }
 }
 
@@ -501,211 +540,646 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
     __syncthreads();
 }
 
+// --------------------------------------------------------- dynamic block
+// Buffers of the dynamic-block update (Algorithm 1, the residual top-K block):
+// I and its gathered nonzeros, the column owner/count marks, the Gram
+// diagonal, y, and global fallbacks for sizes above the shared-memory caps.
+struct Dyn {
+    int *I;                     // [K] ascending rows
+    int *estart;                // [K+1] entry offsets of the rows of I
+    double *gdiag;              // [K] ||A_i||^2 + mu
+    double *y;                  // [K] (A_I A_I^T + mu I)^{-1} r_I
+    int *ecol;                  // [ecap] gathered nonzeros, row order
+    double *eval;
+    uint16_t *erow;
+    long long ecap;
+    unsigned long long *owner;  // [n] (epoch << 32 | entry) of the first entry seen in a column
+    unsigned *shared;           // [n] epoch in which the column was found shared inside I
+    int *segpos;                // [n] position of a shared column in the sorted shared list
+    unsigned *epoch;            // dynamic-update counter (never reset; 0 = never)
+    unsigned long long *raw;    // [2 ecap] shared entries as found (with repeats)
+    unsigned long long *skeys;  // [pow2 >= 2 ecap] shared entries sorted by (column, entry)
+    unsigned long long *pkeys;  // [pcap] Gram contributions (fallback)
+    long long pcap;
+    double *g;                  // [K(K+1)/2] packed Gram fallback
+};
+
+__device__ __forceinline__ long long pidx(int i, int j) {     // packed lower, row-major
+    return (long long)i * (i + 1) / 2 + j;
+}
+
+// Publishes I (from shared memory) and the entry offsets of its rows.
+__device__ void publish_rows(const int *rowptr, const int *sI, int K, Dyn D, Ctl *ctl,
+                             int trace) {
+    __shared__ int sc[33];
+    int carry = 0;
+    for (int base = 0; base < K; base += blockDim.x) {
+        const int a = base + threadIdx.x;
+        const int len = a < K ? rowptr[sI[a] + 1] - rowptr[sI[a]] : 0;
+        int total;
+        const int pre = block_exclusive_scan(len, sc, &total);
+        if (a < K) {
+            D.I[a] = sI[a];
+            D.estart[a] = carry + pre;
+            if (trace && ctl->tr_I && ctl->iter < ctl->trace_cap)
+                ctl->tr_I[ctl->iter * K + a] = sI[a];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        D.estart[K] = carry;
+        ctl->dynE = carry;
+        ctl->dyn_nraw = 0;
+        *D.epoch = *D.epoch + 1u;
+    }
+}
+
+// Rows above the 22-bit threshold and the candidates on it; the last block
+// completes the exact top-K set and publishes it.
 template <typename T>
-__global__ void __launch_bounds__(512) k_topk_final(const T *__restrict__ r, int m, int K,
-                                                    const int *in_list, const int *eq_list,
-                                                    Ctl *ctl, int *I_out) {
+__global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, int m, int K,
+                                                      const int *rowptr, int *in_list,
+                                                      int *eq_list, Dyn D, Ctl *ctl,
+                                                      int check_done) {
     extern __shared__ unsigned long long dsm_u64[];
+    __shared__ int is_last;
+    if (check_done && (ctl->done || ctl->halt)) return;
+    const unsigned long long P = (unsigned long long)(unsigned)ctl->prefix;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        unsigned long long pre = abs_key(r[i]) >> 41;
+        if (pre > P) {
+            in_list[atomicAdd(&ctl->n_in, 1)] = i;
+        } else if (pre == P) {
+            int pos = atomicAdd(&ctl->n_eq, 1);
+            if (pos < kEqCap) eq_list[pos] = i;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
     unsigned long long *skey = dsm_u64;
     int *sidx = (int *)(skey + kEqCap);
     int *sI = sidx + kEqCap;
     finalize_topk<T>(r, m, K, in_list, eq_list, ctl, sI, skey, sidx);
-    for (int a = threadIdx.x; a < K; a += blockDim.x) I_out[a] = sI[a];
+    publish_rows(rowptr, sI, K, D, ctl, 1);
+    if (threadIdx.x == 0) ctl->ticket = 0;
 }
 
-// ----------------------------------------------------------------- dynamic
-// Dynamic block of Algorithm 1: x += A_I^T (A_I A_I^T + mu I)^{-1} r_I with
-// r_I read from the full residual.  One block of 512 threads.  The K rows'
-// nonzeros are gathered (in row order) and sorted by (column, position); the
-// distinct-column segments give the coupled rows S and the deterministic
-// scatter.  The Gram is diagonal outside S; on S it is factored densely.
-struct DynScratch {
-    unsigned long long *keys;   // fallback (global) when E > kSortCapSmem
-    int *ecol;
-    double *eval;
-    uint16_t *erow;
-    double *g;                  // fallback (global) when |S| > kCholSmemMax
-    long long ecap;
+// Single-step API: a given ascending I.
+__global__ void __launch_bounds__(512) k_dyn_set_rows(const int *rowptr, const int *I, int K,
+                                                      Dyn D, Ctl *ctl) {
+    __shared__ int sI[kMaxDynRows];
+    for (int a = threadIdx.x; a < K; a += blockDim.x) sI[a] = I[a];
+    __syncthreads();
+    publish_rows(rowptr, sI, K, D, ctl, 0);
+}
+
+// ---- factorisation of the coupled rows --------------------------------
+// Right-looking packed Cholesky (zero multipliers skipped: the same numbers
+// as the dense algorithm).  One block of threads.
+__device__ void packed_cholesky(double *G, int nS, int *bad) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < nS; ++j) {
+        if (threadIdx.x == 0) {
+            double d = G[pidx(j, j)];
+            if (!(d > 0.0)) { *bad = 1; d = 1.0; }
+            G[pidx(j, j)] = sqrt(d);
+        }
+        __syncthreads();
+        const double l = G[pidx(j, j)];
+        int any = 0;
+        for (int i = j + 1 + threadIdx.x; i < nS; i += blockDim.x) {
+            const double v = G[pidx(i, j)];
+            if (v != 0.0) { G[pidx(i, j)] = v / l; any = 1; }
+        }
+        if (!__syncthreads_or(any)) continue;
+        for (int a = j + 1 + wid; a < nS; a += nw) {
+            const double la = G[pidx(a, j)];
+            if (la == 0.0) continue;
+            for (int b = j + 1 + lane; b <= a; b += 32) {
+                const double lb = G[pidx(b, j)];
+                if (lb != 0.0) G[pidx(a, b)] = __fma_rn(-la, lb, G[pidx(a, b)]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Elimination tree of the coupled rows (nS <= kSymMax) from the Gram's
+// nonzero pattern, as bitsets: col[j] = rows i > j where L_ij may be
+// nonzero, row[i] = columns j < i where L_ij may be nonzero; level[j] = height
+// of j above the leaves; columns sorted by level.  Returns the cost estimates
+// (cycles) of the level-scheduled and the column-by-column factorisations.
+constexpr int kSymMax = 256;
+constexpr int kSymW = kSymMax / 32;
+
+struct Sym {
+    unsigned *col, *row;        // [kSymMax * kSymW]
+    int16_t *level, *order, *lvl_off;   // [kSymMax], [kSymMax], [kSymMax + 1]
 };
 
-template <typename T>
-__global__ void __launch_bounds__(512) k_dynamic(Mat<T> A, const T *__restrict__ r, T *x,
-                                                 const int *in_list, const int *eq_list,
-                                                 const int *I_given, DynScratch ds, Ctl *ctl,
-                                                 int use_cond, cudaGraphConditionalHandle hcond,
-                                                 int count_iter) {
-    extern __shared__ unsigned long long dsm_u64[];
-    __shared__ int sc[33];
-    __shared__ int s_E, s_nS, s_bad;
-    const int K = A.K;
-    const int tid = threadIdx.x;
-    // shared layout (sizes for K <= kMaxDynRows)
-    unsigned long long *ukeys = dsm_u64;                                   // kSortCapSmem
-    int *ucol = (int *)(ukeys + kSortCapSmem);                             // kSortCapSmem
-    double *uval = (double *)(ucol + kSortCapSmem);                        // kSortCapSmem
-    uint16_t *urow = (uint16_t *)(uval + kSortCapSmem);                    // kSortCapSmem
-    double *gss = (double *)(urow + kSortCapSmem);                         // kCholSmemMax^2
-    double *gdiag = gss + kCholSmemMax * kCholSmemMax;                     // K
-    double *z = gdiag + kMaxDynRows;                                       // K
-    double *y = z + kMaxDynRows;                                           // K
-    int *sI = (int *)(y + kMaxDynRows);                                    // K
-    int *estart = sI + kMaxDynRows;                                        // K+1
-    int16_t *spos = (int16_t *)(estart + kMaxDynRows + 1);                 // K
-    int16_t *sidx = spos + kMaxDynRows;                                    // K
-    unsigned char *flag = (unsigned char *)(sidx + kMaxDynRows);           // K
+__device__ __forceinline__ int bit_count(const unsigned *w) {
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < kSymW; ++q) c += __popc(w[q]);
+    return c;
+}
 
-    const bool skip = ctl->done;
-    if (!skip) {
-        if (I_given) {
-            for (int a = tid; a < K; a += blockDim.x) sI[a] = I_given[a];
-            __syncthreads();
-        } else {
-            finalize_topk<T>(r, A.m, K, in_list, eq_list, ctl, sI, ukeys, (int *)uval);
-            if (ctl->tr_I && ctl->iter < ctl->trace_cap)
-                for (int a = tid; a < K; a += blockDim.x) ctl->tr_I[ctl->iter * K + a] = sI[a];
-        }
-        // row extents and entry offsets
-        int len = 0;
-        for (int base = 0, carry = 0; base < K; base += blockDim.x) {
-            int a = base + tid;
-            len = a < K ? A.rowptr[sI[a] + 1] - A.rowptr[sI[a]] : 0;
-            int total;
-            int pre = block_exclusive_scan(len, sc, &total);
-            if (a < K) { estart[a] = carry + pre; flag[a] = 0; }
-            carry += total;
-            if (base + (int)blockDim.x >= K && tid == 0) { estart[K] = carry; s_E = carry; }
-        }
-        if (tid == 0) s_bad = 0;
-        __syncthreads();
-        const int E = s_E;
-        const bool big = E > kSortCapSmem;
-        unsigned long long *keys = big ? ds.keys : ukeys;
-        int *ecol = big ? ds.ecol : ucol;
-        double *eval = big ? ds.eval : uval;
-        uint16_t *erow = big ? ds.erow : urow;
-        if (big && E > ds.ecap) { if (tid == 0) set_status(&ctl->status, kDevBounds); }
-        else {
-            // gather (row order), Gram diagonal, sort keys
-            for (int a = tid; a < K; a += blockDim.x) {
-                const int i = sI[a];
-                int e = estart[a];
-                double g = 0.0;
-                for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p, ++e) {
-                    const double v = (double)A.val[p];
-                    ecol[e] = A.col[p];
-                    eval[e] = v;
-                    erow[e] = (uint16_t)a;
-                    g = __dadd_rn(g, __dmul_rn(v, v));
+__device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use_levels) {
+    __shared__ int s_cnt[kSymMax + 1];
+    __shared__ long long s_cost_lvl, s_cost_col;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int q = tid; q < kSymMax * kSymW; q += blockDim.x) { S.col[q] = 0u; S.row[q] = 0u; }
+    for (int j = tid; j < kSymMax; j += blockDim.x) { S.level[j] = 0; s_cnt[j] = 0; }
+    if (tid == 0) s_cnt[kSymMax] = 0;
+    __syncthreads();
+    for (long long q = tid; q < (long long)nS * (nS + 1) / 2; q += blockDim.x) {
+        int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+        while ((long long)(i + 1) * (i + 2) / 2 <= q) ++i;
+        while ((long long)i * (i + 1) / 2 > q) --i;
+        const int j = (int)(q - (long long)i * (i + 1) / 2);
+        if (j < i && G[q] != 0.0) atomicOr(&S.col[j * kSymW + (i >> 5)], 1u << (i & 31));
+    }
+    __syncthreads();
+    if (tid < 32) {                     // one warp: elimination tree and fill
+        for (int j = 0; j < nS; ++j) {
+            const unsigned w = lane < kSymW ? S.col[j * kSymW + lane] : 0u;
+            const unsigned bal = __ballot_sync(0xffffffffu, w != 0u);
+            if (bal) {
+                const int fw = __ffs(bal) - 1;
+                const unsigned wf = __shfl_sync(0xffffffffu, w, fw);
+                const int p = fw * 32 + __ffs(wf) - 1;
+                if (lane < kSymW) {
+                    unsigned add = w;
+                    if (lane == (p >> 5)) add &= ~(1u << (p & 31));
+                    S.col[p * kSymW + lane] |= add;
                 }
-                gdiag[a] = __dadd_rn(g, A.mu);
+                if (lane == 0) S.level[p] = (int16_t)max((int)S.level[p], (int)S.level[j] + 1);
             }
-            const int np = next_pow2(max(E, 1));
-            __syncthreads();
-            for (int e = tid; e < np; e += blockDim.x)
-                keys[e] = e < E ? (((unsigned long long)(unsigned)ecol[e]) << 32) | (unsigned)e : ~0ull;
-            __syncthreads();
-            block_bitonic_sort(keys, np);
-            // coupled rows: members of a segment of length >= 2
-            for (int q = tid; q < E; q += blockDim.x) {
-                const unsigned c = (unsigned)(keys[q] >> 32);
-                if (q > 0 && (unsigned)(keys[q - 1] >> 32) == c) {
-                    flag[erow[(unsigned)keys[q]]] = 1;
-                    flag[erow[(unsigned)keys[q - 1]]] = 1;
-                }
-            }
-            __syncthreads();
-            int cnt = 0;
-            for (int base = 0; base < K; base += blockDim.x) {
-                int a = base + tid;
-                int f = a < K ? flag[a] : 0;
-                int total;
-                int pre = block_exclusive_scan(f, sc, &total);
-                if (a < K) {
-                    spos[a] = f ? (int16_t)(cnt + pre) : (int16_t)-1;
-                    if (f) sidx[cnt + pre] = (int16_t)a;
-                }
-                cnt += total;
-            }
-            if (tid == 0) s_nS = cnt;
-            __syncthreads();
-            const int nS = s_nS;
-            double *G = nS > kCholSmemMax ? ds.g : gss;
-            // Gram on S (lower triangle, ascending-column merges)
-            const long long pairs = (long long)nS * (nS + 1) / 2;
-            for (long long idx = tid; idx < pairs; idx += blockDim.x) {
-                int i = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
-                while ((long long)(i + 1) * (i + 2) / 2 <= idx) ++i;
-                while ((long long)i * (i + 1) / 2 > idx) --i;
-                const int j = (int)(idx - (long long)i * (i + 1) / 2);
-                const int a = sidx[i], bb = sidx[j];
-                G[(long long)i * nS + j] =
-                    i == j ? gdiag[a]
-                           : row_merge_dot<double>(ecol, eval, estart[a], estart[a + 1], estart[bb],
-                                                   estart[bb + 1]);
-            }
-            __syncthreads();
-            block_cholesky(G, nS, nS, &s_bad);
-            // uncoupled rows: y = (r / L_aa) / L_aa; coupled: z = r_S
-            for (int a = tid; a < K; a += blockDim.x) {
-                const double ra = (double)r[sI[a]];
-                if (spos[a] < 0) {
-                    const double l = sqrt(gdiag[a]);
-                    if (!(gdiag[a] > 0.0)) s_bad = 1;
-                    y[a] = (ra / l) / l;
-                } else {
-                    z[spos[a]] = ra;
-                }
-            }
-            __syncthreads();
-            for (int j = 0; j < nS; ++j) {                 // forward, column order
-                if (tid == 0) z[j] = z[j] / G[(long long)j * nS + j];
-                __syncthreads();
-                const double zj = z[j];
-                for (int i = j + 1 + tid; i < nS; i += blockDim.x) {
-                    const double lij = G[(long long)i * nS + j];
-                    if (lij != 0.0) z[i] = __dsub_rn(z[i], __dmul_rn(lij, zj));
-                }
-                __syncthreads();
-            }
-            for (int j = nS - 1; j >= 0; --j) {            // backward, column order
-                if (tid == 0) z[j] = z[j] / G[(long long)j * nS + j];
-                __syncthreads();
-                const double zj = z[j];
-                for (int i = tid; i < j; i += blockDim.x) {
-                    const double lji = G[(long long)j * nS + i];
-                    if (lji != 0.0) z[i] = __dsub_rn(z[i], __dmul_rn(lji, zj));
-                }
-                __syncthreads();
-            }
-            for (int q = tid; q < nS; q += blockDim.x) y[sidx[q]] = z[q];
-            __syncthreads();
-            // x += A_I^T y: one thread per distinct column, rows ascending
-            for (int q = tid; q < E; q += blockDim.x) {
-                const unsigned c = (unsigned)(keys[q] >> 32);
-                if (q > 0 && (unsigned)(keys[q - 1] >> 32) == c) continue;
-                T acc = T(0);
-                for (int u = q; u < E && (unsigned)(keys[u] >> 32) == c; ++u) {
-                    const unsigned e = (unsigned)keys[u];
-                    acc = Ar<T>::add(acc, Ar<T>::mul((T)eval[e], (T)y[erow[e]]));
-                }
-                x[c] = Ar<T>::add(x[c], acc);
-            }
-            __syncthreads();
-            if (tid == 0 && s_bad) set_status(&ctl->status, kDevNotSpd);
+            __syncwarp();
         }
     }
-    if (!count_iter) return;
-    // end of iteration: trace x, advance, loop condition
-    if (ctl->tr_x && ctl->iter < ctl->trace_cap && sizeof(T) == sizeof(double))
-        for (int c = tid; c < A.n; c += blockDim.x)
-            ctl->tr_x[ctl->iter * (long long)A.n + c] = (double)x[c];
+    __syncthreads();
+    // row structures (transpose) and level counts
+    for (int q = tid; q < nS * kSymW; q += blockDim.x) {
+        const int j = q / kSymW, wd = q % kSymW;
+        unsigned w = S.col[q];
+        while (w) {
+            const int bitp = __ffs(w) - 1;
+            w &= w - 1;
+            const int i = wd * 32 + bitp;
+            atomicOr(&S.row[i * kSymW + (j >> 5)], 1u << (j & 31));
+        }
+    }
+    for (int j = tid; j < nS; j += blockDim.x) atomicAdd(&s_cnt[S.level[j]], 1);
     __syncthreads();
     if (tid == 0) {
-        const long long it = ctl->iter + 1;
-        ctl->iter = it;
-        const bool go = !ctl->done && ctl->status == 0 && it < ctl->maxit;
-        if (use_cond) cudaGraphSetConditional(hcond, go ? 1u : 0u);
+        int nl = 0, acc = 0;
+        for (int L = 0; L < kSymMax; ++L) {
+            if (s_cnt[L]) nl = L + 1;
+            const int c = s_cnt[L];
+            S.lvl_off[L] = (int16_t)acc;
+            acc += c;
+            s_cnt[L] = 0;
+        }
+        S.lvl_off[kSymMax] = (int16_t)acc;
+        *s_nlev = nl;
+        s_cost_lvl = 0;
+        s_cost_col = 0;
     }
+    __syncthreads();
+    for (int j = tid; j < nS; j += blockDim.x) {
+        const int L = S.level[j];
+        S.order[S.lvl_off[L] + atomicAdd(&s_cnt[L], 1)] = (int16_t)j;
+    }
+    __syncthreads();
+    // cost model (cycles): FP64 fma ~70, sqrt/div ~500 each, barrier ~100
+    if (tid < 32) {
+        long long lvl = 0;
+        for (int L = 0; L < *s_nlev; ++L) {
+            int mr = 0, mc = 0;
+            for (int q = S.lvl_off[L] + lane; q < S.lvl_off[L + 1]; q += 32) {
+                const int j = S.order[q];
+                mr = max(mr, bit_count(S.row + j * kSymW));
+                mc = max(mc, bit_count(S.col + j * kSymW));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+                mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+            }
+            lvl += (long long)(2 * mr + mc) * 90 + 2300;
+        }
+        if (lane == 0) {
+            s_cost_lvl = lvl;
+            s_cost_col = (long long)nS * (1300 + 2 * 800);
+            *s_use_levels = s_cost_lvl < s_cost_col;
+        }
+    }
+    __syncthreads();
+}
+
+// Left-looking Cholesky by tree levels: every column of a level at once, one
+// warp per column; entry (a, b) receives its updates L_aj L_bj over the
+// columns j of row b in ascending order (the right-looking order), then
+// L_bb = sqrt(.) and L_ab = (.) / L_bb.
+__device__ void level_cholesky(double *G, int nS, Sym S, int nlev, int *bad) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int L = 0; L < nlev; ++L) {
+        for (int q = S.lvl_off[L] + wid; q < S.lvl_off[L + 1]; q += nw) {
+            const int b = S.order[q];
+            const unsigned *rb = S.row + b * kSymW, *cb = S.col + b * kSymW;
+            double vbb = G[pidx(b, b)];
+            for (int wd = 0; wd < kSymW; ++wd)
+                for (unsigned w = rb[wd]; w; w &= w - 1) {
+                    const int j = wd * 32 + __ffs(w) - 1;
+                    const double lbj = G[pidx(b, j)];
+                    vbb = __fma_rn(-lbj, lbj, vbb);
+                }
+            if (!(vbb > 0.0)) { if (lane == 0) *bad = 1; vbb = 1.0; }
+            const double l = sqrt(vbb);
+            // entries a in col[b], lane-strided in ascending order
+            int seen = 0;
+            for (int wd = 0; wd < kSymW; ++wd) {
+                for (unsigned w = cb[wd]; w; w &= w - 1, ++seen) {
+                    if ((seen & 31) != lane) continue;
+                    const int a = wd * 32 + __ffs(w) - 1;
+                    double v = G[pidx(a, b)];
+                    for (int wr = 0; wr < kSymW; ++wr)
+                        for (unsigned u = rb[wr]; u; u &= u - 1) {
+                            const int j = wr * 32 + __ffs(u) - 1;
+                            v = __fma_rn(-G[pidx(a, j)], G[pidx(b, j)], v);
+                        }
+                    G[pidx(a, b)] = v / l;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) G[pidx(b, b)] = l;
+        }
+        __syncthreads();
+    }
+}
+
+// z <- L^{-T} L^{-1} z on the coupled rows, by tree levels (forward:
+// ascending levels, row sums over ascending columns; backward: descending
+// levels, sums over descending rows), one thread per row.
+__device__ void level_solve(const double *G, int nS, Sym S, int nlev, double *z) {
+    for (int L = 0; L < nlev; ++L) {
+        for (int q = S.lvl_off[L] + threadIdx.x; q < S.lvl_off[L + 1]; q += blockDim.x) {
+            const int b = S.order[q];
+            double v = z[b];
+            const unsigned *rb = S.row + b * kSymW;
+            for (int wd = 0; wd < kSymW; ++wd)
+                for (unsigned w = rb[wd]; w; w &= w - 1) {
+                    const int j = wd * 32 + __ffs(w) - 1;
+                    v = __fma_rn(-G[pidx(b, j)], z[j], v);
+                }
+            z[b] = v / G[pidx(b, b)];
+        }
+        __syncthreads();
+    }
+    for (int L = nlev - 1; L >= 0; --L) {
+        for (int q = S.lvl_off[L] + threadIdx.x; q < S.lvl_off[L + 1]; q += blockDim.x) {
+            const int b = S.order[q];
+            double v = z[b];
+            const unsigned *cb = S.col + b * kSymW;
+            for (int wd = kSymW - 1; wd >= 0; --wd)
+                for (unsigned w = cb[wd]; w; ) {
+                    const int hb = 31 - __clz(w);
+                    w &= ~(1u << hb);
+                    const int c = wd * 32 + hb;
+                    v = __fma_rn(-G[pidx(c, b)], z[c], v);
+                }
+            z[b] = v / G[pidx(b, b)];
+        }
+        __syncthreads();
+    }
+}
+
+// Column-by-column solves (right-looking order) with zero columns skipped.
+__device__ void column_solve(const double *G, int nS, double *z, unsigned char *cz,
+                             unsigned char *rz) {
+    const int tid = threadIdx.x;
+    for (long long q = tid; q < (long long)nS * (nS + 1) / 2; q += blockDim.x) {
+        int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+        while ((long long)(i + 1) * (i + 2) / 2 <= q) ++i;
+        while ((long long)i * (i + 1) / 2 > q) --i;
+        const int j = (int)(q - (long long)i * (i + 1) / 2);
+        if (j < i && G[q] != 0.0) { cz[j] = 1; rz[i] = 1; }
+    }
+    __syncthreads();
+    for (int j = 0; j < nS; ++j) {                       // forward
+        if (tid == 0) z[j] = z[j] / G[pidx(j, j)];
+        if (!cz[j]) continue;
+        __syncthreads();
+        const double zj = z[j];
+        for (int i = j + 1 + tid; i < nS; i += blockDim.x) {
+            const double lij = G[pidx(i, j)];
+            if (lij != 0.0) z[i] = __fma_rn(-lij, zj, z[i]);
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int j = nS - 1; j >= 0; --j) {                  // backward
+        if (tid == 0) z[j] = z[j] / G[pidx(j, j)];
+        if (!rz[j]) continue;
+        __syncthreads();
+        const double zj = z[j];
+        for (int i = tid; i < j; i += blockDim.x) {
+            const double lji = G[pidx(j, i)];
+            if (lji != 0.0) z[i] = __fma_rn(-lji, zj, z[i]);
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+}
+
+// The factor step of the dynamic update, run by the last block of
+// k_dyn_mark: coupled rows S (rows sharing a column inside I), the Gram on S
+// from the shared columns only (each entry summed over ascending columns), its
+// Cholesky, and y = (A_I A_I^T + mu I)^{-1} r_I by two triangular solves
+// (y_a = (r_a / L_aa) / L_aa outside S).
+template <typename T>
+__device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
+                           unsigned long long *dsm) {
+    __shared__ int s_nsh, s_npk, s_nS, s_bad, s_fill, s_fill2, s_nlev, s_uselev;
+    __shared__ int sc[33];
+    unsigned long long *sk = dsm;                                   // kShCap
+    unsigned long long *pk = sk + kShCap;                           // kPairCap
+    double *z = (double *)(pk + kPairCap);                          // kMaxDynRows
+    double *Gs = z + kMaxDynRows;                                   // kGPack
+    Sym S;
+    S.col = (unsigned *)(Gs + kGPack);                              // kSymMax * kSymW
+    S.row = S.col + kSymMax * kSymW;                                // kSymMax * kSymW
+    S.level = (int16_t *)(S.row + kSymMax * kSymW);                 // kSymMax
+    S.order = S.level + kSymMax;                                    // kSymMax
+    S.lvl_off = S.order + kSymMax;                                  // kSymMax + 1
+    int16_t *spos = S.lvl_off + kSymMax + 2;                        // kMaxDynRows
+    int16_t *sidx = spos + kMaxDynRows;                             // kMaxDynRows
+    unsigned char *flag = (unsigned char *)(sidx + kMaxDynRows);    // kMaxDynRows
+    unsigned char *cz = flag + kMaxDynRows;
+    unsigned char *rz = cz + kMaxDynRows;
+    const int tid = threadIdx.x;
+    const int E = ctl->dynE;
+    const int nraw = ctl->dyn_nraw;
+    for (int a = tid; a < K; a += blockDim.x) { flag[a] = 0; cz[a] = 0; rz[a] = 0; }
+    if (tid == 0) { s_nsh = 0; s_npk = 0; s_bad = 0; s_fill = 0; s_fill2 = 0; }
+    if (nraw > 2 * D.ecap || nraw >= (1 << 22)) {   // positions are packed in 22 bits
+        if (tid == 0) set_status(&ctl->status, kDevBounds);
+        return;
+    }
+    // shared entries (found with repeats by the grid pass): sort, drop repeats
+    unsigned long long *keys = nraw <= kShCap ? sk : D.skeys;
+    const int np = next_pow2(max(nraw, 1));
+    for (int q = tid; q < np; q += blockDim.x) keys[q] = q < nraw ? D.raw[q] : ~0ull;
+    __syncthreads();
+    block_bitonic_sort(keys, np);
+    int nsh_run = 0;
+    for (int base = 0; base < nraw; base += blockDim.x) {
+        const int q = base + tid;
+        unsigned long long kq = 0ull;
+        int keep = 0;
+        if (q < nraw) { kq = keys[q]; keep = q == 0 || keys[q - 1] != kq; }
+        int total;
+        const int pre = block_exclusive_scan(keep, sc, &total);
+        if (keep) {
+            keys[nsh_run + pre] = kq;                // stable compaction (target <= source)
+            flag[D.erow[(unsigned)kq]] = 1;
+        }
+        nsh_run += total;
+    }
+    const int nsh = nsh_run;
+    __syncthreads();
+    // segments: shared-list position per column, Gram contributions
+    // (pair (a_hi, a_lo) of rows, positions of both entries): 10+10+22+22 bits
+    for (int q = tid; q < nsh; q += blockDim.x) {
+        const unsigned c = (unsigned)(keys[q] >> 32);
+        if (q > 0 && (unsigned)(keys[q - 1] >> 32) == c) continue;
+        D.segpos[c] = q;
+        int qe = q + 1;
+        while (qe < nsh && (unsigned)(keys[qe] >> 32) == c) ++qe;
+        const int L = qe - q;
+        atomicAdd(&s_npk, L * (L - 1) / 2);
+    }
+    __syncthreads();
+    const int npk = s_npk;
+    unsigned long long *pkeys = npk <= kPairCap ? pk : D.pkeys;
+    if (npk > kPairCap && npk > D.pcap) {
+        if (tid == 0) set_status(&ctl->status, kDevBounds);
+        return;
+    }
+    for (int q = tid; q < nsh; q += blockDim.x) {
+        const unsigned c = (unsigned)(keys[q] >> 32);
+        if (q > 0 && (unsigned)(keys[q - 1] >> 32) == c) continue;
+        int qe = q + 1;
+        while (qe < nsh && (unsigned)(keys[qe] >> 32) == c) ++qe;
+        for (int u = q; u < qe; ++u)
+            for (int w = u + 1; w < qe; ++w) {
+                const unsigned a_lo = D.erow[(unsigned)keys[u]], a_hi = D.erow[(unsigned)keys[w]];
+                pkeys[atomicAdd(&s_fill2, 1)] = ((unsigned long long)a_hi << 54) |
+                                                ((unsigned long long)a_lo << 44) |
+                                                ((unsigned long long)u << 22) | (unsigned long long)w;
+            }
+    }
+    const int npp = next_pow2(max(npk, 1));
+    __syncthreads();
+    for (int q = npk + tid; q < npp; q += blockDim.x) pkeys[q] = ~0ull;
+    __syncthreads();
+    block_bitonic_sort(pkeys, npp);
+    // coupled set S in ascending row order
+    int cnt = 0;
+    for (int base = 0; base < K; base += blockDim.x) {
+        const int a = base + tid;
+        const int f = a < K ? flag[a] : 0;
+        int total;
+        const int pre = block_exclusive_scan(f, sc, &total);
+        if (a < K) {
+            spos[a] = f ? (int16_t)(cnt + pre) : (int16_t)-1;
+            if (f) sidx[cnt + pre] = (int16_t)a;
+        }
+        cnt += total;
+    }
+    if (tid == 0) s_nS = cnt;
+    __syncthreads();
+    const int nS = s_nS;
+    double *G = nS <= kSPackedMax ? Gs : D.g;
+    for (long long q = tid; q < (long long)nS * (nS + 1) / 2; q += blockDim.x) G[q] = 0.0;
+    __syncthreads();
+    for (int i = tid; i < nS; i += blockDim.x) G[pidx(i, i)] = D.gdiag[sidx[i]];
+    // off-diagonal Gram entries: fused sums over the pair's shared columns, ascending
+    for (int q = tid; q < npk; q += blockDim.x) {
+        const unsigned long long pr = pkeys[q] >> 44;
+        if (q > 0 && (pkeys[q - 1] >> 44) == pr) continue;
+        double acc = 0.0;
+        for (int u = q; u < npk && (pkeys[u] >> 44) == pr; ++u) {
+            const unsigned qa = (unsigned)((pkeys[u] >> 22) & 0x3FFFFF), qb = (unsigned)(pkeys[u] & 0x3FFFFF);
+            acc = __fma_rn(D.eval[(unsigned)keys[qb]], D.eval[(unsigned)keys[qa]], acc);
+        }
+        const int a_hi = (int)(pr >> 10), a_lo = (int)(pr & 1023);
+        G[pidx(spos[a_hi], spos[a_lo])] = acc;
+    }
+    __syncthreads();
+    for (int a = tid; a < K; a += blockDim.x) {
+        const double ra = (double)r[D.I[a]];
+        if (spos[a] < 0) {
+            const double g = D.gdiag[a];
+            if (!(g > 0.0)) s_bad = 1;
+            const double l = sqrt(g);
+            D.y[a] = (ra / l) / l;
+        } else {
+            z[spos[a]] = ra;
+        }
+    }
+    __syncthreads();
+    if (nS > 0) {
+        if (nS <= kSymMax) symbolic(G, nS, S, &s_nlev, &s_uselev);
+        else if (tid == 0) s_uselev = 0;
+        __syncthreads();
+        if (s_uselev) {
+            level_cholesky(G, nS, S, s_nlev, &s_bad);
+            level_solve(G, nS, S, s_nlev, z);
+        } else {
+            packed_cholesky(G, nS, &s_bad);
+            column_solve(G, nS, z, cz, rz);
+        }
+    }
+    for (int q = tid; q < nS; q += blockDim.x) D.y[sidx[q]] = z[q];
+    if (keys != D.skeys)
+        for (int q = tid; q < nsh; q += blockDim.x) D.skeys[q] = keys[q];
+    if (tid == 0) {
+        ctl->dyn_nsh = nsh;
+        ctl->dyn_nS = nS;
+        ctl->dyn_npair = npk;
+        if (ctl->tr_dyn && ctl->iter < ctl->trace_cap) {
+            int *t = ctl->tr_dyn + 4 * ctl->iter;
+            t[0] = E; t[1] = nsh; t[2] = nS; t[3] = nS > 0 && nS <= kSymMax && s_uselev ? s_nlev : -1;
+        }
+        if (s_bad) set_status(&ctl->status, kDevNotSpd);
+    }
+}
+
+// Gathers the nonzeros of A_I (row order), marks each column's lowest entry
+// and entry count, forms ||A_i||^2 + mu; the last block factors.
+template <typename T>
+__global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict__ r, Dyn D,
+                                                  Ctl *ctl, int check_done) {
+    extern __shared__ unsigned long long dsm_u64[];
+    __shared__ int is_last;
+    if (check_done && (ctl->done || ctl->halt)) return;
+    const int K = A.K;
+    const int E = ctl->dynE;
+    if (E > D.ecap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&ctl->status, kDevBounds);
+        return;
+    }
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    const unsigned ep = *D.epoch;
+    for (int a = gt; a < K; a += gs) {
+        const int i = D.I[a];
+        double g = 0.0;
+        for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p) {
+            const double v = (double)A.val[p];
+            g = __fma_rn(v, v, g);
+        }
+        D.gdiag[a] = __dadd_rn(g, A.mu);
+    }
+    for (int e = gt; e < E; e += gs) {
+        int lo = 0, hi = K;                          // last a with estart[a] <= e
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (D.estart[mid] <= e) lo = mid; else hi = mid;
+        }
+        const int p = A.rowptr[D.I[lo]] + (e - D.estart[lo]);
+        const int c = A.col[p];
+        D.ecol[e] = c;
+        D.eval[e] = (double)A.val[p];
+        D.erow[e] = (uint16_t)lo;
+        // first entry of a column this epoch owns it; any later entry marks the
+        // column shared and records itself and the owner
+        const unsigned long long mine = ((unsigned long long)ep << 32) | (unsigned)e;
+        unsigned long long old = D.owner[c];
+        for (;;) {
+            if ((unsigned)(old >> 32) == ep) {
+                D.shared[c] = ep;
+                const int pos = atomicAdd(&ctl->dyn_nraw, 2);
+                if (pos + 1 < 2 * D.ecap) {
+                    D.raw[pos] = ((unsigned long long)(unsigned)c << 32) | (old & 0xffffffffull);
+                    D.raw[pos + 1] = ((unsigned long long)(unsigned)c << 32) | (unsigned)e;
+                }
+                break;
+            }
+            const unsigned long long prev = atomicCAS(&D.owner[c], old, mine);
+            if (prev == old) break;
+            old = prev;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    dyn_factor<T>(r, K, D, ctl, dsm_u64);
+    if (threadIdx.x == 0) ctl->ticket = 0;
+}
+
+// End of an iteration: trace x, advance, loop condition (one block).
+template <typename T>
+__device__ void end_iteration(const T *x, int n, Ctl *ctl, int use_cond,
+                              cudaGraphConditionalHandle hcond) {
+    if (ctl->tr_x && ctl->iter < ctl->trace_cap && sizeof(T) == sizeof(double))
+        for (int c = threadIdx.x; c < n; c += blockDim.x)
+            ctl->tr_x[ctl->iter * (long long)n + c] = (double)x[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!ctl->halt) {
+            const long long it = ctl->iter + 1;
+            ctl->iter = it;
+            if (ctl->done || ctl->status != 0 || it >= ctl->maxit) ctl->halt = 1;
+        }
+        if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
+    }
+}
+
+// x += A_I^T y: a column used by one row of I takes its single product; a
+// shared column is summed over its rows in ascending order by the entry that
+// owns it.  The last block clears the column marks and ends the iteration.
+template <typename T>
+__global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ctl, int count_iter,
+                                                     int use_cond,
+                                                     cudaGraphConditionalHandle hcond) {
+    __shared__ int is_last;
+    if (ctl->done || ctl->status || ctl->halt) {
+        if (count_iter && blockIdx.x == 0) end_iteration<T>(x, n, ctl, use_cond, hcond);
+        return;
+    }
+    const int E = ctl->dynE, nsh = ctl->dyn_nsh;
+    const unsigned ep = *D.epoch;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    for (int e = gt; e < E; e += gs) {
+        const int c = D.ecol[e];
+        if (D.shared[c] != ep) {
+            x[c] = Ar<T>::add(x[c], Ar<T>::fma(as<T>(D.eval[e]), as<T>(D.y[D.erow[e]]), T(0)));
+        } else if ((unsigned)D.skeys[D.segpos[c]] == (unsigned)e) {
+            T acc = T(0);
+            for (int u = D.segpos[c]; u < nsh && (int)(D.skeys[u] >> 32) == c; ++u) {
+                const unsigned e2 = (unsigned)D.skeys[u];
+                acc = Ar<T>::fma(as<T>(D.eval[e2]), as<T>(D.y[D.erow[e2]]), acc);
+            }
+            x[c] = Ar<T>::add(x[c], acc);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) ctl->ticket = 0;
+    __syncthreads();
+    if (count_iter) end_iteration<T>(x, n, ctl, use_cond, hcond);
 }
 
 // Sampler probe (single-step API).
@@ -715,14 +1189,17 @@ __global__ void k_sample_probe(const double *cdf, int k, uint64_t seed, uint64_t
 }
 
 // ------------------------------------------------------------- launchers
-static size_t dyn_smem_bytes() {
-    return (size_t)kSortCapSmem * (8 + 4 + 8 + 2) + (size_t)kCholSmemMax * kCholSmemMax * 8 +
-           (size_t)kMaxDynRows * (8 * 3 + 4 + 4 + 2 + 2 + 1) + 8 + 64;
+static size_t collect_smem_bytes() { return (size_t)kEqCap * (8 + 4) + (size_t)kMaxDynRows * 4; }
+static size_t factor_smem_bytes() {
+    return (size_t)(kShCap + kPairCap) * 8 + (size_t)kMaxDynRows * 8 + (size_t)kGPack * 8 +
+           (size_t)2 * kSymMax * kSymW * 4 + (size_t)(3 * kSymMax + 2) * 2 +
+           (size_t)kMaxDynRows * (2 + 2 + 1 + 1 + 1) + 64;
 }
-static size_t topk_final_smem_bytes() { return (size_t)kEqCap * (8 + 4) + (size_t)kMaxDynRows * 4; }
 
-static DynScratch dyn_scratch(rorbk_ctx *h) {
-    return DynScratch{h->dyn_keys, h->dyn_ecol, h->dyn_eval, h->dyn_erow, h->dyn_g, h->dyn_ecap};
+static Dyn dyn_bufs(rorbk_ctx *h) {
+    return Dyn{h->dyn.I, h->dyn.estart, h->dyn.gdiag, h->dyn.y, h->dyn.ecol, h->dyn.eval,
+               h->dyn.erow, h->dyn.ecap, h->dyn.owner, h->dyn.shared, h->dyn.segpos,
+               h->dyn.epoch, h->dyn.raw, h->dyn.skeys, h->dyn.pkeys, h->dyn.pcap, h->dyn.g};
 }
 
 static int grid_stream(rorbk_ctx *h, int m) {
@@ -730,20 +1207,31 @@ static int grid_stream(rorbk_ctx *h, int m) {
 }
 
 void configure_kernels() {
-    cudaFuncSetAttribute(k_dynamic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)dyn_smem_bytes());
-    cudaFuncSetAttribute(k_dynamic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)dyn_smem_bytes());
-    cudaFuncSetAttribute(k_topk_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)topk_final_smem_bytes());
-    cudaFuncSetAttribute(k_topk_final<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)topk_final_smem_bytes());
+    cudaFuncSetAttribute(k_topk_collect<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)collect_smem_bytes());
+    cudaFuncSetAttribute(k_topk_collect<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)collect_smem_bytes());
+    cudaFuncSetAttribute(k_dyn_mark<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)factor_smem_bytes());
+    cudaFuncSetAttribute(k_dyn_mark<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)factor_smem_bytes());
 }
 
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
                   unsigned long long hcond) {
     k_begin<<<1, 1024, 0, h->stream>>>(b, (int)h->m, x0, x, (int)h->n, h->ctl, use_cond,
                                        (cudaGraphConditionalHandle)hcond);
+}
+
+template <typename T>
+static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int check_done,
+                                int count_iter, int use_cond, unsigned long long hcond) {
+    Mat<T> A = make_mat<T>(h);
+    k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
+                                                                        check_done);
+    k_dyn_scatter<T><<<2 * h->num_sms, 512, 0, h->stream>>>(x, (int)h->n, dyn_bufs(h), ctl,
+                                                           count_iter, use_cond,
+                                                           (cudaGraphConditionalHandle)hcond);
 }
 
 template <typename T>
@@ -757,10 +1245,9 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
         k_residual<T, double><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
     const int g = grid_stream(h, (int)h->m);
     k_topk_hist2<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1);
-    k_topk_collect<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->in_list, h->eq_list, ctl, 1);
-    k_dynamic<T><<<1, 512, dyn_smem_bytes(), h->stream>>>(A, r, x, h->in_list, h->eq_list, nullptr,
-                                                          dyn_scratch(h), ctl, use_cond,
-                                                          (cudaGraphConditionalHandle)hcond, 1);
+    k_topk_collect<T><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
+        r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1);
+    launch_dynamic_tail<T>(h, r, x, ctl, 1, 1, use_cond, hcond);
 }
 
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
@@ -785,14 +1272,14 @@ void launch_topk_only(rorbk_ctx *h, const double *r, int *I) {
     const int g = grid_stream(h, (int)h->m);
     k_topk_hist1<double><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist1, h->ctl);
     k_topk_hist2<double><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, h->ctl, 0);
-    k_topk_collect<double><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->in_list, h->eq_list, h->ctl, 0);
-    k_topk_final<double><<<1, 512, topk_final_smem_bytes(), h->stream>>>(
-        r, (int)h->m, h->K, h->in_list, h->eq_list, h->ctl, I);
+    k_topk_collect<double><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
+        r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), h->ctl, 0);
+    cudaMemcpyAsync(I, h->dyn.I, h->K * sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
 }
 
 void launch_dynamic_given(rorbk_ctx *h, const int *I, const double *r, double *x) {
-    k_dynamic<double><<<1, 512, dyn_smem_bytes(), h->stream>>>(
-        make_mat<double>(h), r, x, h->in_list, h->eq_list, I, dyn_scratch(h), h->ctl, 0, 0, 0);
+    k_dyn_set_rows<<<1, 512, 0, h->stream>>>(h->rowptr, I, h->K, dyn_bufs(h), h->ctl);
+    launch_dynamic_tail<double>(h, r, x, h->ctl, 0, 0, 0, 0);
 }
 
 void launch_sample_probe(rorbk_ctx *h, uint64_t seed, uint64_t sysid, int64_t it, int64_t l,

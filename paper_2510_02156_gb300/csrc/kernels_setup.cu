@@ -222,7 +222,7 @@ __global__ void k_centroid_gram(const int *__restrict__ rowptr, const int *__res
         double v = segment_sum(bt_val, bt_col, q, pend);
         for (int e = colptr[c] + lane; e < colptr[c + 1]; e += 32) {
             int j = cb[e];
-            Gt[j] = __dadd_rn(Gt[j], __dmul_rn(v, cv[e]));
+            Gt[j] = __fma_rn(v, cv[e], Gt[j]);
         }
         __syncwarp();
     }
@@ -248,7 +248,7 @@ __global__ void k_centroid_gram_dense(const double *__restrict__ Abar, int k, in
     if (j >= k) return;
     const double *a = Abar + (long long)t * n, *b = Abar + (long long)j * n;
     double s = 0.0;
-    for (int c = 0; c < n; ++c) s = __dadd_rn(s, __dmul_rn(a[c], b[c]));
+    for (int c = 0; c < n; ++c) s = __fma_rn(a[c], b[c], s);
     G[(long long)t * k + j] = s;
 }
 
@@ -320,7 +320,7 @@ __global__ void k_static_ops(const int *__restrict__ rowptr, const int *__restri
             if (f) s_idx[sb + cnt + pre] = (uint16_t)a;
             int p0 = rowptr[r0 + a], p1 = rowptr[r0 + a + 1];
             double g = 0.0;
-            for (int p = p0; p < p1; ++p) g = __dadd_rn(g, __dmul_rn(val[p], val[p]));
+            for (int p = p0; p < p1; ++p) g = __fma_rn(val[p], val[p], g);
             g = __dadd_rn(g, mu);
             gdiag[a] = g;
             if (!f) {
@@ -359,7 +359,7 @@ __global__ void k_static_ops(const int *__restrict__ rowptr, const int *__restri
             for (int i = j + 1; i < nS; ++i) {
                 double acc = 0.0;
                 for (int c = j; c < i; ++c)
-                    acc = __dadd_rn(acc, __dmul_rn(G[(long long)i * nS + c], Li[(long long)c * nS + j]));
+                    acc = __fma_rn(G[(long long)i * nS + c], Li[(long long)c * nS + j], acc);
                 Li[(long long)i * nS + j] = -acc / G[(long long)i * nS + i];
             }
         }
@@ -371,7 +371,7 @@ __global__ void k_static_ops(const int *__restrict__ rowptr, const int *__restri
             if (j > i) continue;
             double acc = 0.0;
             for (int c = i; c < nS; ++c)
-                acc = __dadd_rn(acc, __dmul_rn(Li[(long long)c * nS + i], Li[(long long)c * nS + j]));
+                acc = __fma_rn(Li[(long long)c * nS + i], Li[(long long)c * nS + j], acc);
             // the factor's (i, j) is read by nobody after the Linv pass
             G[(long long)i * nS + j] = acc;
         }
@@ -394,6 +394,29 @@ void widen_values(rorbk_ctx *h, int dtype) {
     else if (h->val32) k_narrow<<<gs, 256, 0, h->stream>>>(h->val, h->val32, h->nnz);
 }
 
+// SELL-32 copy of A: lane l of slice s holds row sell_row[32 s + l]; entry j
+// of that lane sits at ptr[s] + 32 j + l.
+__global__ void k_sell_fill(const int *__restrict__ rowptr, const int *__restrict__ col,
+                            const double *__restrict__ val, const float *__restrict__ val32,
+                            int nslices, const long long *__restrict__ ptr,
+                            const int *__restrict__ srow, const int *__restrict__ srlen,
+                            int *__restrict__ scol, double *__restrict__ sval,
+                            float *__restrict__ sval32) {
+    const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (slot >= (long long)nslices * 32) return;
+    const int s = (int)(slot >> 5), lane = (int)(slot & 31);
+    const int r = srow[slot], len = srlen[slot];
+    const long long base = ptr[s] + lane;
+    const int p0 = r >= 0 ? rowptr[r] : 0;
+    for (int j = 0; j < (int)((ptr[s + 1] - ptr[s]) >> 5); ++j) {
+        const long long d = base + 32LL * j;
+        const bool in = j < len;
+        scol[d] = in ? col[p0 + j] : 0;
+        if (sval) sval[d] = in ? val[p0 + j] : 0.0;
+        if (sval32) sval32[d] = in ? val32[p0 + j] : 0.0f;
+    }
+}
+
 // ---------------------------------------------------------------- driver
 static rorbk_status scan_device(rorbk_ctx *h, int *d, long long n, int *grand_total_host) {
     const int nt = 256;
@@ -410,7 +433,57 @@ static rorbk_status scan_device(rorbk_ctx *h, int *d, long long n, int *grand_to
     return cuda_check(h, cudaStreamSynchronize(h->stream), "scan");
 }
 
-rorbk_status build_setup(rorbk_ctx *h) {
+// Rows sorted by length (longest first, ties by row) into slices of 32.
+static rorbk_status build_sell(rorbk_ctx *h, const std::vector<int> &hrp) {
+    const int m = (int)h->m;
+    int maxlen = 0;
+    for (int i = 0; i < m; ++i) maxlen = std::max(maxlen, hrp[i + 1] - hrp[i]);
+    std::vector<int> cnt(maxlen + 2, 0);
+    for (int i = 0; i < m; ++i) cnt[hrp[i + 1] - hrp[i]]++;
+    std::vector<int> start(maxlen + 2, 0);      // descending length order
+    for (int L = maxlen, acc = 0; L >= 0; --L) { start[L] = acc; acc += cnt[L]; }
+    std::vector<int> order(m);
+    for (int i = 0; i < m; ++i) order[start[hrp[i + 1] - hrp[i]]++] = i;
+    const int ns = (m + 31) / 32;
+    std::vector<long long> ptr(ns + 1, 0);
+    std::vector<int> len(ns), row((size_t)ns * 32, -1), rlen((size_t)ns * 32, 0);
+    for (int sl = 0; sl < ns; ++sl) {
+        int L = 0;
+        for (int l = 0; l < 32; ++l) {
+            const int q = sl * 32 + l;
+            if (q < m) {
+                row[q] = order[q];
+                rlen[q] = hrp[order[q] + 1] - hrp[order[q]];
+                L = std::max(L, rlen[q]);
+            }
+        }
+        len[sl] = L;
+        ptr[sl + 1] = ptr[sl] + 32LL * L;
+    }
+    auto &S = h->sell;
+    S.nslices = ns;
+    S.ptr = (long long *)dev_alloc(h, (ns + 1) * sizeof(long long));
+    S.len = (int *)dev_alloc(h, ns * sizeof(int));
+    S.row = (int *)dev_alloc(h, (size_t)ns * 32 * sizeof(int));
+    S.rlen = (int *)dev_alloc(h, (size_t)ns * 32 * sizeof(int));
+    const long long ent = std::max(1LL, ptr[ns]);
+    S.col = (int *)dev_alloc(h, ent * sizeof(int));
+    if (h->vdtype == RORBK_F64) S.val = (double *)dev_alloc(h, ent * sizeof(double));
+    if (h->val32) S.val32 = (float *)dev_alloc(h, ent * sizeof(float));
+    if (!S.ptr || !S.len || !S.row || !S.rlen || !S.col || (h->vdtype == RORBK_F64 && !S.val) ||
+        (h->val32 && !S.val32))
+        return fail(h, RORBK_ERR_OOM, "SELL copy of A");
+    cudaStream_t st = h->stream;
+    cudaMemcpyAsync(S.ptr, ptr.data(), (ns + 1) * sizeof(long long), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(S.len, len.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(S.row, row.data(), (size_t)ns * 32 * sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(S.rlen, rlen.data(), (size_t)ns * 32 * sizeof(int), cudaMemcpyHostToDevice, st);
+    k_sell_fill<<<(unsigned)((ns * 32LL + 255) / 256), 256, 0, st>>>(
+        h->rowptr, h->col, h->val, h->val32, ns, S.ptr, S.row, S.rlen, S.col, S.val, S.val32);
+    return cuda_check(h, cudaStreamSynchronize(st), "SELL copy of A");
+}
+
+rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
     cudaStream_t s = h->stream;
     const int m = (int)h->m, n = (int)h->n, k = h->k;
     rorbk_status st;
@@ -427,6 +500,7 @@ rorbk_status build_setup(rorbk_ctx *h) {
         return fail(h, RORBK_ERR_INVALID_ARG,
                     "CSR structure: row_ptr must be non-decreasing and columns strictly ascending in [0,n)");
     if (hf[0] & 2) return fail(h, RORBK_ERR_NUMERIC, "A holds NaN or Inf");
+    if ((st = build_sell(h, hrp))) return st;
 
     // block transpose, coupled rows
     const long long nnz = h->nnz;

@@ -142,6 +142,8 @@ void rorbk_default_options(rorbk_options *opt) {
     opt->precision = RORBK_PREC_FP64;
     opt->inner_tol = 1e-4;
     opt->inner_maxit = 2000000;
+    opt->host_loop = 0;
+    opt->poll = 64;
 }
 
 const char *rorbk_last_error(rorbk_handle h) {
@@ -268,7 +270,7 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     build_tiles(hrp, (int)m, tiles);
     h->ntiles = (int)tiles.size() - 1;
     h->tile_row0 = (int *)dev_alloc(h, tiles.size() * sizeof(int));
-    h->grid_res = std::max(1, std::min(h->ntiles, 8 * h->num_sms));
+    h->grid_res = 8 * h->num_sms;
     // workspace
     h->r = (double *)dev_alloc(h, m * sizeof(double));
     h->xb = (double *)dev_alloc(h, n * sizeof(double));
@@ -279,14 +281,35 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
     h->eq_list = (int *)dev_alloc(h, kEqCap * sizeof(int));
     h->ctl = (Ctl *)dev_alloc(h, sizeof(Ctl));
-    h->dyn_ecap = std::max<int64_t>(1, (int64_t)h->K * maxrow);
-    int64_t np2 = 1;
-    while (np2 < h->dyn_ecap) np2 <<= 1;
-    h->dyn_keys = (unsigned long long *)dev_alloc(h, np2 * sizeof(unsigned long long));
-    h->dyn_ecol = (int *)dev_alloc(h, h->dyn_ecap * sizeof(int));
-    h->dyn_eval = (double *)dev_alloc(h, h->dyn_ecap * sizeof(double));
-    h->dyn_erow = (uint16_t *)dev_alloc(h, h->dyn_ecap * sizeof(uint16_t));
-    h->dyn_g = (double *)dev_alloc(h, (size_t)h->K * h->K * sizeof(double));
+    {
+        auto &D = h->dyn;
+        D.ecap = std::max<int64_t>(1, (int64_t)h->K * maxrow);
+        int64_t np2 = 1;
+        while (np2 < 2 * D.ecap) np2 <<= 1;
+        D.pcap = 1;
+        while (D.pcap < std::max<int64_t>(16 * D.ecap, 1 << 16)) D.pcap <<= 1;
+        D.I = (int *)dev_alloc(h, h->K * sizeof(int));
+        D.estart = (int *)dev_alloc(h, (h->K + 1) * sizeof(int));
+        D.gdiag = (double *)dev_alloc(h, h->K * sizeof(double));
+        D.y = (double *)dev_alloc(h, h->K * sizeof(double));
+        D.ecol = (int *)dev_alloc(h, D.ecap * sizeof(int));
+        D.eval = (double *)dev_alloc(h, D.ecap * sizeof(double));
+        D.erow = (uint16_t *)dev_alloc(h, D.ecap * sizeof(uint16_t));
+        D.owner = (unsigned long long *)dev_alloc(h, n * sizeof(unsigned long long));
+        D.shared = (unsigned *)dev_alloc(h, n * sizeof(unsigned));
+        D.epoch = (unsigned *)dev_alloc(h, sizeof(unsigned));
+        D.segpos = (int *)dev_alloc(h, n * sizeof(int));
+        D.raw = (unsigned long long *)dev_alloc(h, 2 * D.ecap * sizeof(unsigned long long));
+        D.skeys = (unsigned long long *)dev_alloc(h, np2 * sizeof(unsigned long long));
+        D.pkeys = (unsigned long long *)dev_alloc(h, D.pcap * sizeof(unsigned long long));
+        D.g = (double *)dev_alloc(h, ((size_t)h->K * (h->K + 1) / 2) * sizeof(double));
+        if (!D.I || !D.estart || !D.gdiag || !D.y || !D.ecol || !D.eval || !D.erow || !D.owner ||
+            !D.shared || !D.epoch || !D.segpos || !D.raw || !D.skeys || !D.pkeys || !D.g)
+            return bail(fail(h, RORBK_ERR_OOM, "dynamic-block workspace"));
+        cudaMemsetAsync(D.owner, 0, n * sizeof(unsigned long long), s);   // epoch 0: never
+        cudaMemsetAsync(D.shared, 0, n * sizeof(unsigned), s);
+        cudaMemsetAsync(D.epoch, 0, sizeof(unsigned), s);
+    }
     if (h->precision_built) {
         h->r32 = (float *)dev_alloc(h, m * sizeof(float));
         h->b32 = (float *)dev_alloc(h, m * sizeof(float));
@@ -294,15 +317,14 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
         if (!h->r32 || !h->b32 || !h->d32) return bail(fail(h, RORBK_ERR_OOM, "mixed workspace"));
     }
     if (!h->tile_row0 || !h->r || !h->xb || !h->bb || !h->partials || !h->hist1 || !h->hist2 ||
-        !h->in_list || !h->eq_list || !h->ctl || !h->dyn_keys || !h->dyn_ecol || !h->dyn_eval ||
-        !h->dyn_erow || !h->dyn_g)
+        !h->in_list || !h->eq_list || !h->ctl)
         return bail(fail(h, RORBK_ERR_OOM, "workspace"));
     cudaMemcpyAsync(h->tile_row0, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(h->hist1, 0, kHistBins * sizeof(unsigned), s);
     cudaMemsetAsync(h->hist2, 0, kHistBins * sizeof(unsigned), s);
     cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s);
 
-    if ((st = build_setup(h))) return bail(st);
+    if ((st = build_setup(h, hrp))) return bail(st);
     *out = h;
     return RORBK_OK;
 }
@@ -337,9 +359,10 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
         c.tr_rrn = opt.trace->rrn;
         c.tr_I = opt.trace->I;
         c.tr_x = opt.trace->x;
+        c.tr_dyn = opt.trace->dyn;
     }
     cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s);
-    if (!h->exec_fp64) {
+    if (!opt.host_loop && !h->exec_fp64) {
         if ((st = cuda_check(h, cudaStreamSynchronize(s), "solve prologue"))) return st;
         if ((st = build_graph_fp64(h))) return st;
     }
@@ -347,7 +370,26 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    cudaError_t e = cudaGraphLaunch(h->exec_fp64, s);
+    cudaError_t e = cudaSuccess;
+    if (!opt.host_loop) {
+        e = cudaGraphLaunch(h->exec_fp64, s);
+    } else {
+        // host-driven: batches of `poll` iterations, stop flag read between them
+        const int poll = std::max(1, opt.poll);
+        cudaStream_t saved = h->stream;
+        h->stream = s;
+        launch_begin(h, h->bb, h->xb, h->xb, 0, 0);
+        int halt = 0;
+        int64_t launched = 0;
+        while (e == cudaSuccess && !halt && launched < maxit) {
+            for (int q = 0; q < poll && launched < maxit; ++q, ++launched)
+                launch_iteration(h, h->bb, h->xb, h->r, 0, 0);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        h->stream = saved;
+    }
     cudaEventRecord(e1, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(x, h->xb, n * sizeof(double), x_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);

@@ -250,3 +250,46 @@ def test_full_size_powerlaw_iterations_and_residual(cuda_ok):
         h.solve(dev(s.b), x, tol=0.0, maxit=3, seed=1)
     o = oracle.solve(s, maxit=3, tol=0.0, seed=1)
     assert rel(x.cpu().numpy(), o.x) <= REL
+
+
+def test_host_loop_equals_graph_loop(cuda_ok):
+    """The host-driven loop (profiling mode) and the device-side graph loop
+    run the same iterations and give the same x."""
+    s = W.powerlaw(n=1 << 13, num_blocks=32, seed=4, lam=1e-8, tol=1e-6)
+    with B.Handle.from_system(s) as h:
+        x1 = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        x2 = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        r1 = h.solve(dev(s.b), x1, tol=s.tol, maxit=3000, seed=6)
+        r2 = h.solve(dev(s.b), x2, tol=s.tol, maxit=3000, seed=6, host_loop=1, poll=7)
+    assert r1.iters == r2.iters and r1.converged and r2.converged
+    assert torch.equal(x1, x2)
+
+
+def test_dense_coupling_takes_both_factor_schedules(cuda_ok):
+    """A matrix whose dynamic rows couple densely (every row shares columns
+    with every other) exercises the column-by-column factorisation; the
+    power-law system exercises the tree-level one.  Both agree with the
+    oracle."""
+    s = W.random_sparse(400, 120, 0.3, seed=13, num_blocks=8, lam=1e-6)
+    o = oracle.solve(s, maxit=20, tol=0.0, seed=2)
+    with B.Handle.from_system(s) as h:
+        x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        h.solve(dev(s.b), x, tol=0.0, maxit=20, seed=2)
+    assert rel(x.cpu().numpy(), o.x) <= REL
+
+
+def test_residual_fp32_subnormal_and_signed_zero_values(cuda_ok):
+    """FP32-stored values are widened exactly (normal, subnormal, +-0): the
+    FP64 residual still equals the oracle's bit for bit."""
+    s = W.random_sparse(500, 300, 0.05, seed=21, num_blocks=5)
+    v = s.values.copy()
+    rng = np.random.default_rng(0)
+    pick = rng.choice(len(v), len(v) // 3, replace=False)
+    v[pick[: len(pick) // 2]] *= 1e-41                  # FP32 subnormals
+    v[pick[len(pick) // 2:][:5]] = -0.0
+    s.values = v.astype(np.float32)
+    x = rng.standard_normal(s.n) * 1e30
+    with B.Handle.from_system(s) as h:
+        r = torch.empty(s.m, dtype=torch.float64, device="cuda")
+        h.residual(dev(s.b), dev(x), r)
+    np.testing.assert_array_equal(r.cpu().numpy(), oracle.residual(s, s.b, x)[0])
