@@ -18,7 +18,7 @@ from . import _build
 RORBK_OK, RORBK_NOT_CONVERGED = 0, 1
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_INVALID_ARG", -2: "ERR_CUDA",
                 -3: "ERR_OOM", -4: "ERR_NOT_SPD", -5: "ERR_NUMERIC", -6: "ERR_BOUNDS",
-                -7: "ERR_UNSUPPORTED"}
+                -7: "ERR_UNSUPPORTED", -8: "ERR_DEVICE_TIMEOUT"}
 FORMAT_CSR, FORMAT_DENSE = 0, 1
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1

@@ -30,6 +30,7 @@ constexpr int kDevOk = 0;
 constexpr int kDevNotSpd = 1;
 constexpr int kDevBounds = 2;
 constexpr int kDevNumeric = 3;
+constexpr int kDevTimeout = 4;   // a bounded device wait gave up
 
 // ----------------------------------------------------- device-side state
 // Loop state of one solve, kept in device memory so that the whole iteration
@@ -71,6 +72,7 @@ struct Ctl {
 struct StaticOps {
     int *s_ptr = nullptr;       // [k+1] offsets into s_idx
     uint16_t *s_idx = nullptr;  // coupled local rows, ascending
+    uint16_t *bperm = nullptr;  // [m] local rows of each block, longest first
     long long *w_ptr = nullptr; // [k+1] offsets into w_ss
     double *w_ss = nullptr;     // dense W on S_t, row-major
     double *w_diag = nullptr;   // [m] W_ii for uncoupled rows
@@ -151,8 +153,9 @@ struct rorbk_ctx {
         double *g = nullptr;
     } dyn;
     rorbk::Ctl *ctl = nullptr;
+    rorbk::Ctl *ctl_in = nullptr;       // inner (FP32) loop state of the mixed form
     // graphs
-    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr, cap_stream3 = nullptr;
     cudaGraphExec_t exec_fp64 = nullptr, exec_mixed = nullptr;
     std::vector<void *> tmp;
 };
@@ -170,11 +173,15 @@ void widen_values(rorbk_ctx *h, int dtype);   // FP32 <-> FP64 value copies
 
 // iteration launches (kernels_iter.cu); all enqueue on h->stream
 void configure_kernels();
+int residual_grid(rorbk_ctx *h);   // one resident wave of the residual kernel
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
                   unsigned long long hcond);
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
                       unsigned long long hcond);
 void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x);
+void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner);
+void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner);
+void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_outer);
 void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r);
 void launch_topk_only(rorbk_ctx *h, const double *r, int *I);
 void launch_dynamic_given(rorbk_ctx *h, const int *I, const double *r, double *x);

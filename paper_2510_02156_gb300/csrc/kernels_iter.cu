@@ -66,6 +66,7 @@ struct Mat {
     const long long *w_ptr;
     const T *w_ss, *w_diag;
     const int *s_pos;
+    const uint16_t *bperm;
     // block transpose
     const int *bt_col;
     const uint16_t *bt_row;
@@ -90,7 +91,7 @@ template <>
 Mat<double> make_mat<double>(rorbk_ctx *h) {
     return Mat<double>{h->rowptr, h->col, h->val, h->off, h->cdf, (int)h->m, (int)h->n, h->k, h->K,
                        h->ops.s_ptr, h->ops.s_idx, h->ops.w_ptr, h->ops.w_ss, h->ops.w_diag,
-                       h->ops.s_pos, h->bt.col, h->bt.row, h->bt.val, h->bt.seg, h->bt.seg_ptr,
+                       h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val, h->bt.seg, h->bt.seg_ptr,
                        h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                        h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
                        h->sell.val32};
@@ -99,7 +100,7 @@ template <>
 Mat<float> make_mat<float>(rorbk_ctx *h) {
     return Mat<float>{h->rowptr, h->col, h->val32, h->off, h->cdf, (int)h->m, (int)h->n, h->k, h->K,
                       h->ops.s_ptr, h->ops.s_idx, h->ops.w_ptr, h->ops.w_ss32, h->ops.w_diag32,
-                      h->ops.s_pos, h->bt.col, h->bt.row, h->bt.val32, h->bt.seg, h->bt.seg_ptr,
+                      h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val32, h->bt.seg, h->bt.seg_ptr,
                       h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                       h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
                       h->sell.val32};
@@ -130,6 +131,7 @@ __global__ void k_begin(const double *__restrict__ b, int m, const double *__res
         ctl->ticket = 0;
         ctl->n_in = 0;
         ctl->n_eq = 0;
+        ctl->outer = 0;
         if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
     }
 }
@@ -137,23 +139,85 @@ __global__ void k_begin(const double *__restrict__ b, int m, const double *__res
 // ----------------------------------------------------------------- static
 // One block of threads runs the n_static sampled updates of an iteration in
 // sequence (Algorithm 1, the inner loop over l); the draws do not depend on
-// x and are taken up front.  force_tau >= 0 replaces the draw by that block
-// (single-step API).  Uses the stored W_tau (Section 3.1).  The local
-// residual streams the block's nonzeros and gathered x through shared memory
-// in chunks; each row is a fused multiply-add chain in stored order.
-constexpr int kStaticChunk = 1536;
+// x and are taken up front.  Uses the stored W_tau (Section 3.1).
+//
+// Data movement: the CSR range of a sampled block and its column-sorted copy
+// (columns, local rows, values) do not depend on x, so they are brought into
+// shared memory by TMA bulk copies two blocks ahead (two stages, one mbarrier
+// each), while the current update runs.  Each update then needs two
+// dependent global round trips only: the gather of x at the block's columns
+// and the update of x.  Blocks larger than a stage take the direct path
+// (chunked loads from global memory), with the same arithmetic.
+// force_tau >= 0 replaces the draw by that block (single-step API, direct
+// path only).
+constexpr int kStaticChunk = 1536;   // direct path
+constexpr int kStageCap = 3072;      // entries of one block held by a stage
+constexpr int kStageC = kStageCap + 16;
+constexpr long long kWaitTries = 1LL << 24;
+
+template <typename T>
+__host__ __device__ constexpr size_t static_stage_bytes() {
+    return (size_t)kStageC * (2 * sizeof(T) + 4 + 4 + 2);
+}
+template <typename T>
+__host__ __device__ constexpr size_t static_smem_bytes() {
+    return 64 + 2 * static_stage_bytes<T>() + (size_t)kStageC * sizeof(T);
+}
+
+template <typename T>
+struct Stage {
+    T *val, *btval;
+    int *col, *btcol;
+    uint16_t *btrow;
+};
+template <typename T>
+__device__ __forceinline__ Stage<T> stage_at(unsigned char *base) {
+    Stage<T> st;
+    st.val = (T *)base;
+    st.btval = st.val + kStageC;
+    st.col = (int *)(st.btval + kStageC);
+    st.btcol = st.col + kStageC;
+    st.btrow = (uint16_t *)(st.btcol + kStageC);
+    return st;
+}
+
+// Issues the bulk copies of block tau into a stage (thread 0).  Returns the
+// aligned first entry a0, or -1 when the block does not fit a stage.
+template <typename T>
+__device__ int stage_issue(const Mat<T> &A, int tau, Stage<T> st, unsigned long long *bar) {
+    const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
+    const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
+    if (pend <= p0) return -2;                        // no nonzeros: nothing to stage
+    const int a0 = p0 & ~7, a1 = (pend + 7) & ~7;     // 16-byte aligned for every array
+    const int n = a1 - a0;
+    if (n > kStageC) return -1;
+    const unsigned bytes = (unsigned)n * (2u * sizeof(T) + 4u + 4u + 2u);
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(st.val, A.val + a0, n * sizeof(T), bar);
+    bulk_g2s(st.btval, A.bt_val + a0, n * sizeof(T), bar);
+    bulk_g2s(st.col, A.col + a0, n * 4, bar);
+    bulk_g2s(st.btcol, A.bt_col + a0, n * 4, bar);
+    bulk_g2s(st.btrow, A.bt_row + a0, n * 2, bar);
+    return a0;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__ b, T *x,
-                                                 Ctl *ctl, int force_tau) {
+                                                 Ctl *ctl, int force_tau, int use_stages) {
+    extern __shared__ unsigned long long dsm_u64[];
     __shared__ T rloc[kMaxBlockRows];
     __shared__ T y[kMaxBlockRows];
-    __shared__ T sv[kStaticChunk];
-    __shared__ T sx[kStaticChunk];
     __shared__ int taus[64];
+    __shared__ int s_a0[2];
+    __shared__ int s_fail;
     if (force_tau < 0 && (ctl->done || ctl->halt)) return;
     const int nst = force_tau >= 0 ? 1 : ctl->n_static;
     const int a = threadIdx.x;
+    unsigned long long *bar = dsm_u64;                // two mbarriers
+    unsigned char *sbase = (unsigned char *)(dsm_u64 + 8);
+    Stage<T> stg[2] = {stage_at<T>(sbase), stage_at<T>(sbase + static_stage_bytes<T>())};
+    T *sx = (T *)(sbase + 2 * static_stage_bytes<T>());
     if (a < nst) {
         const long long it = ctl->iter_base + ctl->iter;
         const int tau = force_tau >= 0 ? force_tau
@@ -163,49 +227,110 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         if (force_tau < 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
             ctl->tr_tau[ctl->iter * nst + a] = tau;
     }
+    if (a == 0) {
+        s_fail = 0;
+        s_a0[0] = s_a0[1] = -1;
+        if (use_stages) { mbar_init(&bar[0], 1); mbar_init(&bar[1], 1); }
+    }
     __syncthreads();
+    if (use_stages && a == 0) {
+        if (nst > 0) s_a0[0] = stage_issue<T>(A, taus[0], stg[0], &bar[0]);
+        if (nst > 1) s_a0[1] = stage_issue<T>(A, taus[1], stg[1], &bar[1]);
+    }
+    unsigned phase[2] = {0u, 0u};
     for (int l = 0; l < nst; ++l) {
         const int tau = taus[l];
+        const int sidx = l & 1;
         const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
         const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
-        const int q0 = a < s ? A.rowptr[r0 + a] : 0, q1 = a < s ? A.rowptr[r0 + a + 1] : 0;
-        T acc = T(0);
-        for (int c0 = p0; c0 < pend; c0 += kStaticChunk) {
-            const int c1 = min(pend, c0 + kStaticChunk);
-            for (int p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
-                sv[p - c0] = A.val[p];
-                sx[p - c0] = x[A.col[p]];
-            }
-            __syncthreads();
-            for (int p = max(q0, c0); p < min(q1, c1); ++p) acc = Ar<T>::fma(sv[p - c0], sx[p - c0], acc);
-            __syncthreads();
-        }
-        if (a < s) rloc[a] = Ar<T>::sub(b[r0 + a], acc);
-        __syncthreads();
-        const int sb = A.s_ptr[tau], nS = A.s_ptr[tau + 1] - sb;
-        const T *W = A.w_ss + A.w_ptr[tau];
+        // x-independent per-row data, loaded before anything waits; thread a
+        // takes the a-th longest row la of the block
+        int q0 = 0, q1 = 0, pos = -1, la = 0;
+        T bi = T(0), wd = T(0);
         if (a < s) {
-            const int i = r0 + a;
-            const int pos = A.s_pos[i];
+            la = A.bperm[r0 + a];
+            q0 = A.rowptr[r0 + la];
+            q1 = A.rowptr[r0 + la + 1];
+            bi = b[r0 + la];
+            pos = A.s_pos[r0 + la];
+            wd = A.w_diag[r0 + la];
+        }
+        __syncthreads();                              // s_a0 of this stage published
+        const int a0 = use_stages ? s_a0[sidx] : -1;
+        const bool staged = a0 >= 0;
+        if (staged) {
+            if (!mbar_wait_bounded(&bar[sidx], phase[sidx], kWaitTries)) atomicOr(&s_fail, 1);
+            phase[sidx] ^= 1u;
+        }
+        __syncthreads();
+        if (s_fail) {
+            if (a == 0) {
+                set_status(&ctl->status, kDevTimeout);
+                ctl->done = 1;
+                // drain whatever is still in flight before the block exits
+                mbar_wait_bounded(&bar[sidx], phase[sidx] ^ 1u, kWaitTries);
+                if (s_a0[sidx ^ 1] >= 0) mbar_wait_bounded(&bar[sidx ^ 1], phase[sidx ^ 1], kWaitTries);
+            }
+            return;
+        }
+        T acc = T(0);
+        if (staged) {
+            const Stage<T> st = stg[sidx];
+            for (int p = p0 + a; p < pend; p += blockDim.x) sx[p - p0] = x[st.col[p - a0]];
+            __syncthreads();
+            for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(st.val[p - a0], sx[p - p0], acc);
+        } else {
+            T *sv = sx, *sxx = sx + kStaticChunk;
+            for (int c0 = p0; c0 < pend; c0 += kStaticChunk) {
+                const int c1 = min(pend, c0 + kStaticChunk);
+                for (int p = c0 + a; p < c1; p += blockDim.x) {
+                    sv[p - c0] = A.val[p];
+                    sxx[p - c0] = x[A.col[p]];
+                }
+                __syncthreads();
+                for (int p = max(q0, c0); p < min(q1, c1); ++p)
+                    acc = Ar<T>::fma(sv[p - c0], sxx[p - c0], acc);
+                __syncthreads();
+            }
+        }
+        if (a < s) rloc[la] = Ar<T>::sub(bi, acc);
+        __syncthreads();
+        if (a < s) {
             if (pos < 0) {
-                y[a] = Ar<T>::fma(A.w_diag[i], rloc[a], T(0));
+                y[la] = Ar<T>::fma(wd, rloc[la], T(0));
             } else {
-                const T *Wr = W + (long long)pos * nS;
+                const int sb = A.s_ptr[tau], nS = A.s_ptr[tau + 1] - sb;
+                const T *Wr = A.w_ss + A.w_ptr[tau] + (long long)pos * nS;
                 T acc2 = T(0);
                 for (int q = 0; q < nS; ++q) acc2 = Ar<T>::fma(Wr[q], rloc[A.s_idx[sb + q]], acc2);
-                y[a] = acc2;
+                y[la] = acc2;
             }
         }
         __syncthreads();
-        const int ns = A.nseg[tau];
-        for (int g = threadIdx.x; g < ns; g += blockDim.x) {
-            int q = A.bt_seg[p0 + g];
-            const int c = A.bt_col[q];
-            T acc3 = T(0);
-            for (; q < pend && A.bt_col[q] == c; ++q) acc3 = Ar<T>::fma(A.bt_val[q], y[A.bt_row[q]], acc3);
-            x[c] = Ar<T>::add(x[c], acc3);
+        if (staged) {
+            const Stage<T> st = stg[sidx];
+            for (int q = p0 + a; q < pend; q += blockDim.x) {
+                const int c = st.btcol[q - a0];
+                if (q > p0 && st.btcol[q - 1 - a0] == c) continue;
+                T acc3 = T(0);
+                for (int u = q; u < pend && st.btcol[u - a0] == c; ++u)
+                    acc3 = Ar<T>::fma(st.btval[u - a0], y[st.btrow[u - a0]], acc3);
+                x[c] = Ar<T>::add(x[c], acc3);
+            }
+        } else {
+            const int ns = A.nseg[tau];
+            for (int g = a; g < ns; g += blockDim.x) {
+                int q = A.bt_seg[p0 + g];
+                const int c = A.bt_col[q];
+                T acc3 = T(0);
+                for (; q < pend && A.bt_col[q] == c; ++q)
+                    acc3 = Ar<T>::fma(A.bt_val[q], y[A.bt_row[q]], acc3);
+                x[c] = Ar<T>::add(x[c], acc3);
+            }
         }
         __syncthreads();
+        // this stage is free again: bring in block l + 2
+        if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stg[sidx], &bar[sidx]) : -1;
     }
 }
 
@@ -262,23 +387,28 @@ __device__ __forceinline__ void hist_add(unsigned *hist, unsigned bin, bool acti
 // finalize: 1 = convergence test + first radix level (iteration), 2 = ||r||^2
 // only (single-step API).
 template <typename T, typename V>
-__global__ void __launch_bounds__(256) k_residual(Mat<T> A, const T *__restrict__ b,
+__global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restrict__ b,
                                                   const T *__restrict__ x, T *__restrict__ r,
                                                   double *partials, unsigned *hist1, Ctl *ctl,
                                                   int finalize) {
     __shared__ unsigned hist[kHistBins];
     __shared__ double red[32];
     __shared__ int is_last;
-    if (finalize == 1 && (ctl->done || ctl->halt)) return;
+    if ((finalize == 1 || finalize == 3) && (ctl->done || ctl->halt)) return;
     const V *__restrict__ val = sell_values<V, T>(A);
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     double rr = 0.0;
     __syncthreads();
-    // consecutive slices go to different blocks, so the longest (first)
-    // slices spread over all SMs
-    for (int sl = blockIdx.x + gridDim.x * (threadIdx.x >> 5); sl < A.nslices; sl += gridDim.x * nwb) {
+    // One resident wave of blocks; slices (longest first) are dealt to the
+    // warps in snake order, warps of consecutive ids sitting on different SMs,
+    // so every warp gets a mix of long and short slices.
+    const int W = gridDim.x * nwb;
+    const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    for (int rnd = 0;; ++rnd) {
+        const int sl = rnd * W + ((rnd & 1) ? W - 1 - g : g);
+        if (sl >= A.nslices) break;
         const long long base = A.sptr[sl] + lane;
         const int L = A.slen[sl];
         const int slot = sl * 32 + lane;
@@ -347,10 +477,10 @@ __global__ void __launch_bounds__(256) k_residual(Mat<T> A, const T *__restrict_
         ctl->ticket = 0;
         ctl->rr = tot;
         stop = 0;
-        if (finalize == 1) {
+        if (finalize == 1 || finalize == 3) {
             const double rrn = sqrt(tot) / ctl->bnorm;
             ctl->rrn = rrn;
-            if (ctl->tr_rrn && ctl->iter < ctl->trace_cap) ctl->tr_rrn[ctl->iter] = rrn;
+            if (finalize == 1 && ctl->tr_rrn && ctl->iter < ctl->trace_cap) ctl->tr_rrn[ctl->iter] = rrn;
             if (!isfinite(rrn)) { set_status(&ctl->status, kDevNumeric); ctl->done = 1; }
             else if (rrn <= ctl->tol) ctl->done = 1;
             stop = ctl->done;
@@ -679,6 +809,7 @@ constexpr int kSymW = kSymMax / 32;
 struct Sym {
     unsigned *col, *row;        // [kSymMax * kSymW]
     int16_t *level, *order, *lvl_off;   // [kSymMax], [kSymMax], [kSymMax + 1]
+    int *eoff;                  // [kSymMax + 1] first off-diagonal entry of order[q]
 };
 
 __device__ __forceinline__ int bit_count(const unsigned *w) {
@@ -696,13 +827,9 @@ __device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use
     for (int j = tid; j < kSymMax; j += blockDim.x) { S.level[j] = 0; s_cnt[j] = 0; }
     if (tid == 0) s_cnt[kSymMax] = 0;
     __syncthreads();
-    for (long long q = tid; q < (long long)nS * (nS + 1) / 2; q += blockDim.x) {
-        int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
-        while ((long long)(i + 1) * (i + 2) / 2 <= q) ++i;
-        while ((long long)i * (i + 1) / 2 > q) --i;
-        const int j = (int)(q - (long long)i * (i + 1) / 2);
-        if (j < i && G[q] != 0.0) atomicOr(&S.col[j * kSymW + (i >> 5)], 1u << (i & 31));
-    }
+    for (int i = tid; i < nS; i += blockDim.x)
+        for (int j = 0; j < i; ++j)
+            if (G[pidx(i, j)] != 0.0) atomicOr(&S.col[j * kSymW + (i >> 5)], 1u << (i & 31));
     __syncthreads();
     if (tid < 32) {                     // one warp: elimination tree and fill
         for (int j = 0; j < nS; ++j) {
@@ -756,6 +883,20 @@ __device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use
         S.order[S.lvl_off[L] + atomicAdd(&s_cnt[L], 1)] = (int16_t)j;
     }
     __syncthreads();
+    {   // off-diagonal entries of each column, in level order
+        __shared__ int sc2[33];
+        int carry = 0;
+        for (int base = 0; base < nS; base += blockDim.x) {
+            const int q = base + tid;
+            const int c = q < nS ? bit_count(S.col + S.order[q] * kSymW) : 0;
+            int total;
+            const int pre = block_exclusive_scan(c, sc2, &total);
+            if (q < nS) S.eoff[q] = carry + pre;
+            carry += total;
+        }
+        if (tid == 0) S.eoff[nS] = carry;
+        __syncthreads();
+    }
     // cost model (cycles): FP64 fma ~70, sqrt/div ~500 each, barrier ~100
     if (tid < 32) {
         long long lvl = 0;
@@ -781,42 +922,55 @@ __device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use
     __syncthreads();
 }
 
-// Left-looking Cholesky by tree levels: every column of a level at once, one
-// warp per column; entry (a, b) receives its updates L_aj L_bj over the
-// columns j of row b in ascending order (the right-looking order), then
-// L_bb = sqrt(.) and L_ab = (.) / L_bb.
+// Left-looking Cholesky by tree levels: every column of a level at once.
+// Entry (a, b) receives its updates L_aj L_bj over the columns j of row b in
+// ascending order (the right-looking order).  Diagonals first (one thread per
+// column: L_bb = sqrt(.)), then the off-diagonals (one thread per entry:
+// L_ab = (.) / L_bb), so every FP64 instruction carries as many columns or
+// entries as the level has.
+__device__ __forceinline__ int kth_bit(const unsigned *w, int k) {
+    for (int wd = 0; wd < kSymW; ++wd) {
+        const int c = __popc(w[wd]);
+        if (k < c) return wd * 32 + (int)__fns(w[wd], 0, k + 1);
+        k -= c;
+    }
+    return -1;
+}
+
 __device__ void level_cholesky(double *G, int nS, Sym S, int nlev, int *bad) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int L = 0; L < nlev; ++L) {
-        for (int q = S.lvl_off[L] + wid; q < S.lvl_off[L + 1]; q += nw) {
+        const int q0 = S.lvl_off[L], q1 = S.lvl_off[L + 1];
+        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
             const int b = S.order[q];
-            const unsigned *rb = S.row + b * kSymW, *cb = S.col + b * kSymW;
-            double vbb = G[pidx(b, b)];
+            const unsigned *rb = S.row + b * kSymW;
+            double v = G[pidx(b, b)];
             for (int wd = 0; wd < kSymW; ++wd)
                 for (unsigned w = rb[wd]; w; w &= w - 1) {
                     const int j = wd * 32 + __ffs(w) - 1;
                     const double lbj = G[pidx(b, j)];
-                    vbb = __fma_rn(-lbj, lbj, vbb);
+                    v = __fma_rn(-lbj, lbj, v);
                 }
-            if (!(vbb > 0.0)) { if (lane == 0) *bad = 1; vbb = 1.0; }
-            const double l = sqrt(vbb);
-            // entries a in col[b], lane-strided in ascending order
-            int seen = 0;
-            for (int wd = 0; wd < kSymW; ++wd) {
-                for (unsigned w = cb[wd]; w; w &= w - 1, ++seen) {
-                    if ((seen & 31) != lane) continue;
-                    const int a = wd * 32 + __ffs(w) - 1;
-                    double v = G[pidx(a, b)];
-                    for (int wr = 0; wr < kSymW; ++wr)
-                        for (unsigned u = rb[wr]; u; u &= u - 1) {
-                            const int j = wr * 32 + __ffs(u) - 1;
-                            v = __fma_rn(-G[pidx(a, j)], G[pidx(b, j)], v);
-                        }
-                    G[pidx(a, b)] = v / l;
-                }
+            if (!(v > 0.0)) { *bad = 1; v = 1.0; }
+            G[pidx(b, b)] = sqrt(v);
+        }
+        __syncthreads();
+        const int e0 = S.eoff[q0], e1 = S.eoff[q1];
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            int lo = q0, hi = q1;                       // last q with eoff[q] <= e
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (S.eoff[mid] <= e) lo = mid; else hi = mid;
             }
-            __syncwarp();
-            if (lane == 0) G[pidx(b, b)] = l;
+            const int b = S.order[lo];
+            const int a = kth_bit(S.col + b * kSymW, e - S.eoff[lo]);
+            const unsigned *rb = S.row + b * kSymW;
+            double v = G[pidx(a, b)];
+            for (int wd = 0; wd < kSymW; ++wd)
+                for (unsigned w = rb[wd]; w; w &= w - 1) {
+                    const int j = wd * 32 + __ffs(w) - 1;
+                    v = __fma_rn(-G[pidx(a, j)], G[pidx(b, j)], v);
+                }
+            G[pidx(a, b)] = v / G[pidx(b, b)];
         }
         __syncthreads();
     }
@@ -862,13 +1016,9 @@ __device__ void level_solve(const double *G, int nS, Sym S, int nlev, double *z)
 __device__ void column_solve(const double *G, int nS, double *z, unsigned char *cz,
                              unsigned char *rz) {
     const int tid = threadIdx.x;
-    for (long long q = tid; q < (long long)nS * (nS + 1) / 2; q += blockDim.x) {
-        int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
-        while ((long long)(i + 1) * (i + 2) / 2 <= q) ++i;
-        while ((long long)i * (i + 1) / 2 > q) --i;
-        const int j = (int)(q - (long long)i * (i + 1) / 2);
-        if (j < i && G[q] != 0.0) { cz[j] = 1; rz[i] = 1; }
-    }
+    for (int i = tid; i < nS; i += blockDim.x)
+        for (int j = 0; j < i; ++j)
+            if (G[pidx(i, j)] != 0.0) { cz[j] = 1; rz[i] = 1; }
     __syncthreads();
     for (int j = 0; j < nS; ++j) {                       // forward
         if (tid == 0) z[j] = z[j] / G[pidx(j, j)];
@@ -916,7 +1066,8 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
     S.level = (int16_t *)(S.row + kSymMax * kSymW);                 // kSymMax
     S.order = S.level + kSymMax;                                    // kSymMax
     S.lvl_off = S.order + kSymMax;                                  // kSymMax + 1
-    int16_t *spos = S.lvl_off + kSymMax + 2;                        // kMaxDynRows
+    S.eoff = (int *)(S.lvl_off + kSymMax + 2);                      // kSymMax + 1
+    int16_t *spos = (int16_t *)(S.eoff + kSymMax + 2);              // kMaxDynRows
     int16_t *sidx = spos + kMaxDynRows;                             // kMaxDynRows
     unsigned char *flag = (unsigned char *)(sidx + kMaxDynRows);    // kMaxDynRows
     unsigned char *cz = flag + kMaxDynRows;
@@ -1021,17 +1172,7 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
         G[pidx(spos[a_hi], spos[a_lo])] = acc;
     }
     __syncthreads();
-    for (int a = tid; a < K; a += blockDim.x) {
-        const double ra = (double)r[D.I[a]];
-        if (spos[a] < 0) {
-            const double g = D.gdiag[a];
-            if (!(g > 0.0)) s_bad = 1;
-            const double l = sqrt(g);
-            D.y[a] = (ra / l) / l;
-        } else {
-            z[spos[a]] = ra;
-        }
-    }
+    for (int q = tid; q < nS; q += blockDim.x) z[q] = (double)r[D.I[sidx[q]]];
     __syncthreads();
     if (nS > 0) {
         if (nS <= kSymMax) symbolic(G, nS, S, &s_nlev, &s_uselev);
@@ -1076,14 +1217,21 @@ __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict_
     }
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     const unsigned ep = *D.epoch;
-    for (int a = gt; a < K; a += gs) {
+    // ||A_i||^2 + mu, and y_a = (r_a / l) / l with l = sqrt(.) (the value for a
+    // row outside the coupled set; the factor step overwrites coupled rows).
+    // Rows go to different blocks so that their chains run on different SMs.
+    for (int a = blockIdx.x + gridDim.x * threadIdx.x; a < K; a += gs) {
         const int i = D.I[a];
         double g = 0.0;
         for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p) {
             const double v = (double)A.val[p];
             g = __fma_rn(v, v, g);
         }
-        D.gdiag[a] = __dadd_rn(g, A.mu);
+        g = __dadd_rn(g, A.mu);
+        D.gdiag[a] = g;
+        if (!(g > 0.0)) { set_status(&ctl->status, kDevNotSpd); g = 1.0; }
+        const double l = sqrt(g);
+        D.y[a] = ((double)r[i] / l) / l;
     }
     for (int e = gt; e < E; e += gs) {
         int lo = 0, hi = K;                          // last a with estart[a] <= e
@@ -1188,11 +1336,105 @@ __global__ void k_sample_probe(const double *cdf, int k, uint64_t seed, uint64_t
     *out = sample_block(cdf, k, seed, sysid, (uint64_t)it, (uint64_t)l);
 }
 
+// -------------------------------------------------- mixed precision
+// Iterative refinement around the FP32 form of the iteration (the loop state
+// of the FP64 outer loop is `out`, of the FP32 inner solve `in`):
+//   r = b - A x in FP64 (k_residual, finalize 3: the convergence test only);
+//   k_inner_prep: b32 = fl32(r), d32 = 0, the inner loop state;
+//   inner ROR-BK iterations on A d = b32 in FP32 until ||b32 - A d|| <=
+//     inner_tol ||b32|| or the inner cap (the block Gram Cholesky stays FP64);
+//   k_outer_update: x += d in FP64.
+// The Philox counter runs on across refinements (inner iteration t of the
+// refinement that starts after T inner iterations in total uses counter
+// start_iter + T + t).
+__global__ void __launch_bounds__(256) k_inner_prep(const double *__restrict__ r64, int m,
+                                                    float *__restrict__ b32, float *__restrict__ d32,
+                                                    int n, double *partials, Ctl *out, Ctl *in,
+                                                    int use_cond, cudaGraphConditionalHandle hcond) {
+    __shared__ double red[32];
+    __shared__ int is_last;
+    if (out->done || out->status || out->halt) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hcond, 0u);
+        return;
+    }
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const float v = (float)r64[i];
+        b32[i] = v;
+        acc = __fma_rn((double)v, (double)v, acc);
+    }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) d32[c] = 0.f;
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = acc;
+        __threadfence();
+        is_last = atomicAdd(&out->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double tot = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += partials[i];
+    tot = block_sum(tot, red);
+    if (threadIdx.x == 0) {
+        out->ticket = 0;
+        const double bn = sqrt(tot);
+        const long long left = out->maxit - out->iter;
+        in->bnorm = bn;
+        in->iter = 0;
+        in->maxit = left < out->inner_maxit ? left : out->inner_maxit;
+        in->iter_base = out->iter_base + out->iter;
+        in->seed = out->seed;
+        in->sysid = out->sysid;
+        in->n_static = out->n_static;
+        in->tol = out->inner_tol;
+        in->rr = 0.0;
+        in->rrn = 1.0;
+        in->done = bn == 0.0;
+        in->halt = !(bn > 0.0 && in->maxit > 0);
+        in->status = 0;
+        in->ticket = 0;
+        in->n_in = 0;
+        in->n_eq = 0;
+        in->trace_cap = 0;
+        in->tr_tau = nullptr;
+        in->tr_rrn = nullptr;
+        in->tr_I = nullptr;
+        in->tr_x = nullptr;
+        in->tr_dyn = nullptr;
+        if (use_cond) cudaGraphSetConditional(hcond, in->halt ? 0u : 1u);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_outer_update(double *__restrict__ x, const float *__restrict__ d32,
+                                                      int n, Ctl *out, Ctl *in, int use_cond,
+                                                      cudaGraphConditionalHandle hcond) {
+    __shared__ int is_last;
+    const bool active = !(out->done || out->status || out->halt);
+    if (active)
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+            x[c] = __dadd_rn(x[c], (double)d32[c]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&out->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last || threadIdx.x != 0) return;
+    out->ticket = 0;
+    if (active) {
+        out->iter += in->iter;
+        out->outer += 1;
+        if (in->status) set_status(&out->status, in->status);
+        if (in->iter == 0 || out->iter >= out->maxit) out->halt = 1;
+    }
+    if (out->done || out->status) out->halt = 1;
+    if (use_cond) cudaGraphSetConditional(hcond, out->halt ? 0u : 1u);
+}
+
 // ------------------------------------------------------------- launchers
 static size_t collect_smem_bytes() { return (size_t)kEqCap * (8 + 4) + (size_t)kMaxDynRows * 4; }
 static size_t factor_smem_bytes() {
     return (size_t)(kShCap + kPairCap) * 8 + (size_t)kMaxDynRows * 8 + (size_t)kGPack * 8 +
-           (size_t)2 * kSymMax * kSymW * 4 + (size_t)(3 * kSymMax + 2) * 2 +
+           (size_t)2 * kSymMax * kSymW * 4 + (size_t)(3 * kSymMax + 2) * 2 + (size_t)(kSymMax + 2) * 4 +
            (size_t)kMaxDynRows * (2 + 2 + 1 + 1 + 1) + 64;
 }
 
@@ -1206,7 +1448,21 @@ static int grid_stream(rorbk_ctx *h, int m) {
     return std::max(1, std::min(4 * h->num_sms, (m + 255) / 256));
 }
 
+int residual_grid(rorbk_ctx *h) {
+    int per_sm = 0, per_sm32 = 0;
+    if (h->vdtype == RORBK_F32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, float>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, double>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_residual<float, float>, 256, 0);
+    return std::max(1, std::min(per_sm, per_sm32 > 0 ? per_sm32 : per_sm)) * h->num_sms;
+}
+
 void configure_kernels() {
+    cudaFuncSetAttribute(k_static<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<double>());
+    cudaFuncSetAttribute(k_static<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<float>());
     cudaFuncSetAttribute(k_topk_collect<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)collect_smem_bytes());
     cudaFuncSetAttribute(k_topk_collect<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1238,11 +1494,15 @@ template <typename T>
 void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_cond,
                         unsigned long long hcond) {
     Mat<T> A = make_mat<T>(h);
-    k_static<T><<<1, 1024, 0, h->stream>>>(A, b, x, ctl, -1);
-    if (sizeof(T) == sizeof(float) || h->vdtype == RORBK_F32)
+    k_static<T><<<1, 1024, static_smem_bytes<T>(), h->stream>>>(A, b, x, ctl, -1, 1);
+    if constexpr (sizeof(T) == sizeof(float)) {
         k_residual<T, float><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
-    else
-        k_residual<T, double><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
+    } else {
+        if (h->vdtype == RORBK_F32)
+            k_residual<T, float><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
+        else
+            k_residual<T, double><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
+    }
     const int g = grid_stream(h, (int)h->m);
     k_topk_hist2<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1);
     k_topk_collect<T><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
@@ -1255,8 +1515,33 @@ void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int u
     launch_iteration_t<double>(h, b, x, r, h->ctl, use_cond, hcond);
 }
 
+void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner) {
+    Mat<double> A = make_mat<double>(h);
+    if (h->vdtype == RORBK_F32)
+        k_residual<double, float><<<h->grid_res, 256, 0, h->stream>>>(A, h->bb, h->xb, h->r, h->partials,
+                                                                      h->hist1, h->ctl, 3);
+    else
+        k_residual<double, double><<<h->grid_res, 256, 0, h->stream>>>(A, h->bb, h->xb, h->r, h->partials,
+                                                                       h->hist1, h->ctl, 3);
+    const int g = grid_stream(h, (int)std::max(h->m, h->n));
+    k_inner_prep<<<g, 256, 0, h->stream>>>(h->r, (int)h->m, h->b32, h->d32, (int)h->n, h->partials,
+                                           h->ctl, h->ctl_in, use_cond,
+                                           (cudaGraphConditionalHandle)hcond_inner);
+}
+
+void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner) {
+    launch_iteration_t<float>(h, h->b32, h->d32, h->r32, h->ctl_in, use_cond, hcond_inner);
+}
+
+void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_outer) {
+    const int g = grid_stream(h, (int)h->n);
+    k_outer_update<<<g, 256, 0, h->stream>>>(h->xb, h->d32, (int)h->n, h->ctl, h->ctl_in, use_cond,
+                                             (cudaGraphConditionalHandle)hcond_outer);
+}
+
 void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x) {
-    k_static<double><<<1, 1024, 0, h->stream>>>(make_mat<double>(h), b, x, h->ctl, tau);
+    k_static<double><<<1, 1024, static_smem_bytes<double>(), h->stream>>>(make_mat<double>(h), b, x,
+                                                                          h->ctl, tau, 0);
 }
 
 void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r) {

@@ -483,6 +483,28 @@ static rorbk_status build_sell(rorbk_ctx *h, const std::vector<int> &hrp) {
     return cuda_check(h, cudaStreamSynchronize(st), "SELL copy of A");
 }
 
+// Local rows of every block ordered by length, longest first (ties by row):
+// the static update gives one row per thread, and a warp's fused
+// multiply-add chain is as long as its longest row.
+static rorbk_status build_block_order(rorbk_ctx *h, const std::vector<int> &hrp) {
+    const int k = h->k;
+    std::vector<uint16_t> perm(h->m);
+    std::vector<int> idx;
+    for (int t = 0; t < k; ++t) {
+        const int r0 = (int)h->h_off[t], s = (int)(h->h_off[t + 1] - h->h_off[t]);
+        idx.resize(s);
+        for (int a = 0; a < s; ++a) idx[a] = a;
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+            return hrp[r0 + x + 1] - hrp[r0 + x] > hrp[r0 + y + 1] - hrp[r0 + y];
+        });
+        for (int a = 0; a < s; ++a) perm[r0 + a] = (uint16_t)idx[a];
+    }
+    h->ops.bperm = (uint16_t *)dev_alloc(h, (size_t)h->m * sizeof(uint16_t));
+    if (!h->ops.bperm) return fail(h, RORBK_ERR_OOM, "block row order");
+    return cuda_check(h, cudaMemcpyAsync(h->ops.bperm, perm.data(), (size_t)h->m * sizeof(uint16_t),
+                                         cudaMemcpyHostToDevice, h->stream), "block row order");
+}
+
 rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
     cudaStream_t s = h->stream;
     const int m = (int)h->m, n = (int)h->n, k = h->k;
@@ -501,12 +523,13 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
                     "CSR structure: row_ptr must be non-decreasing and columns strictly ascending in [0,n)");
     if (hf[0] & 2) return fail(h, RORBK_ERR_NUMERIC, "A holds NaN or Inf");
     if ((st = build_sell(h, hrp))) return st;
+    if ((st = build_block_order(h, hrp))) return st;
 
     // block transpose, coupled rows
     const long long nnz = h->nnz;
-    h->bt.col = (int *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(int));
-    h->bt.row = (uint16_t *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(uint16_t));
-    h->bt.val = (double *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(double));
+    h->bt.col = (int *)dev_alloc(h, (size_t)(nnz + 16) * sizeof(int));
+    h->bt.row = (uint16_t *)dev_alloc(h, (size_t)(nnz + 16) * sizeof(uint16_t));
+    h->bt.val = (double *)dev_alloc(h, (size_t)(nnz + 16) * sizeof(double));
     h->bt.seg = (int *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(int));
     h->bt.seg_ptr = (int *)dev_alloc(h, (size_t)k * sizeof(int));   // segment counts
     unsigned char *coupled = (unsigned char *)dev_alloc(h, (size_t)m);
@@ -587,7 +610,7 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
         if (h->precision_built) {
             h->ops.w_ss32 = (float *)dev_alloc(h, (size_t)std::max(1LL, wptr[k]) * sizeof(float));
             h->ops.w_diag32 = (float *)dev_alloc(h, (size_t)m * sizeof(float));
-            h->bt.val32 = (float *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(float));
+            h->bt.val32 = (float *)dev_alloc(h, (size_t)(nnz + 16) * sizeof(float));
             if (!h->ops.w_ss32 || !h->ops.w_diag32 || !h->bt.val32)
                 return fail(h, RORBK_ERR_OOM, "fp32 operators");
             k_narrow<<<gs, 256, 0, s>>>(h->ops.w_ss, h->ops.w_ss32, std::max(1LL, wptr[k]));

@@ -48,6 +48,7 @@ static rorbk_status device_status(rorbk_ctx *h, int code) {
         case kDevNotSpd: return fail(h, RORBK_ERR_NOT_SPD, "a block Gram is not positive definite");
         case kDevBounds: return fail(h, RORBK_ERR_BOUNDS, "a device index or scratch bound was exceeded");
         case kDevNumeric: return fail(h, RORBK_ERR_NUMERIC, "the residual is not finite");
+        case kDevTimeout: return fail(h, RORBK_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up (asynchronous copy not completed)");
         default: return fail(h, RORBK_ERR_CUDA, "unknown device status");
     }
 }
@@ -123,6 +124,84 @@ static rorbk_status build_graph_fp64(rorbk_ctx *h) {
     return cuda_check(h, e, "building the iteration graph");
 }
 
+// Adds a WHILE node at the capture position of stream cs; returns its body.
+static cudaError_t add_while(cudaStream_t cs, cudaGraphConditionalHandle *hc, cudaGraph_t *body) {
+    cudaGraph_t graph = nullptr;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = *hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode = nullptr;
+    e = cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &cp);
+    if (e != cudaSuccess) return e;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+static cudaError_t new_handle(cudaStream_t cs, cudaGraphConditionalHandle *hc) {
+    cudaGraph_t graph = nullptr;
+    cudaStreamCaptureStatus cst;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    return cudaGraphConditionalHandleCreate(hc, graph, 0, cudaGraphCondAssignDefault);
+}
+
+// Capture: k_begin, then WHILE(outer) { FP64 residual + inner set-up,
+// WHILE(inner) { one FP32 iteration }, x += d }.
+static rorbk_status build_graph_mixed(rorbk_ctx *h) {
+    cudaStream_t saved = h->stream;
+    cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2, cs3 = h->cap_stream3;
+    cudaGraphConditionalHandle hout = 0, hin = 0;
+    cudaGraph_t body1 = nullptr, body2 = nullptr, tmp = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_check(h, e, "capture");
+    e = new_handle(cs, &hout);
+    if (e == cudaSuccess) {
+        h->stream = cs;
+        launch_begin(h, h->bb, h->xb, h->xb, 1, (unsigned long long)hout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = add_while(cs, &hout, &body1);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs2, body1, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = new_handle(cs2, &hin);
+        if (e == cudaSuccess) {
+            h->stream = cs2;
+            launch_mixed_outer(h, 1, (unsigned long long)hin);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = add_while(cs2, &hin, &body2);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs3, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            h->stream = cs3;
+            launch_mixed_inner(h, 1, (unsigned long long)hin);
+            cudaError_t e2 = cudaGetLastError();
+            e = cudaStreamEndCapture(cs3, &tmp);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) {
+            h->stream = cs2;
+            launch_mixed_update(h, 1, (unsigned long long)hout);
+            e = cudaGetLastError();
+        }
+        cudaError_t e3 = cudaStreamEndCapture(cs2, &tmp);
+        if (e == cudaSuccess) e = e3;
+    }
+    h->stream = saved;
+    cudaGraph_t g_out = nullptr;
+    cudaError_t e4 = cudaStreamEndCapture(cs, &g_out);
+    if (e == cudaSuccess) e = e4;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_mixed, g_out, 0);
+    if (g_out) cudaGraphDestroy(g_out);
+    return cuda_check(h, e, "building the mixed-precision graph");
+}
+
 static rorbk_options defaults() {
     rorbk_options o;
     rorbk_default_options(&o);
@@ -162,6 +241,7 @@ void rorbk_free(rorbk_handle h) {
     if (h->exec_mixed) cudaGraphExecDestroy(h->exec_mixed);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+    if (h->cap_stream3) cudaStreamDestroy(h->cap_stream3);
     for (void *p : h->allocs) cudaFree(p);
     cudaSetDevice(cur);
     delete h;
@@ -218,6 +298,8 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
         return bail(st);
     if ((st = cuda_check(h, cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking), "stream")))
         return bail(st);
+    if ((st = cuda_check(h, cudaStreamCreateWithFlags(&h->cap_stream3, cudaStreamNonBlocking), "stream")))
+        return bail(st);
     configure_kernels();
 
     // copy A (CSR) and a host view of row_ptr for the tiling
@@ -236,8 +318,10 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     for (int64_t i = 0; i < m; ++i) maxrow = std::max(maxrow, hrp[i + 1] - hrp[i]);
 
     h->rowptr = (int *)dev_alloc(h, (m + 1) * sizeof(int));
-    h->col = (int *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(int));
-    h->val = (double *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(double));
+    // +16 entries: the static kernel's bulk copies round block ranges up to
+    // 16-byte boundaries
+    h->col = (int *)dev_alloc(h, (nnz + 16) * sizeof(int));
+    h->val = (double *)dev_alloc(h, (nnz + 16) * sizeof(double));
     h->off = (int *)dev_alloc(h, (k + 1) * sizeof(int));
     h->cdf = (double *)dev_alloc(h, k * sizeof(double));
     h->crowsum = (double *)dev_alloc(h, k * sizeof(double));
@@ -248,11 +332,11 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     if (A->dtype == RORBK_F64) {
         if (nnz) cudaMemcpyAsync(h->val, A->values, nnz * sizeof(double), kind, s);
         if (h->precision_built) {
-            h->val32 = (float *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(float));
+            h->val32 = (float *)dev_alloc(h, (nnz + 16) * sizeof(float));
             if (!h->val32) return bail(fail(h, RORBK_ERR_OOM, "fp32 values"));
         }
     } else {
-        h->val32 = (float *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(float));
+        h->val32 = (float *)dev_alloc(h, (nnz + 16) * sizeof(float));
         if (!h->val32) return bail(fail(h, RORBK_ERR_OOM, "fp32 values"));
         if (nnz) cudaMemcpyAsync(h->val32, A->values, nnz * sizeof(float), kind, s);
     }
@@ -270,7 +354,7 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     build_tiles(hrp, (int)m, tiles);
     h->ntiles = (int)tiles.size() - 1;
     h->tile_row0 = (int *)dev_alloc(h, tiles.size() * sizeof(int));
-    h->grid_res = 8 * h->num_sms;
+    h->grid_res = residual_grid(h);
     // workspace
     h->r = (double *)dev_alloc(h, m * sizeof(double));
     h->xb = (double *)dev_alloc(h, n * sizeof(double));
@@ -281,6 +365,7 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
     h->eq_list = (int *)dev_alloc(h, kEqCap * sizeof(int));
     h->ctl = (Ctl *)dev_alloc(h, sizeof(Ctl));
+    h->ctl_in = (Ctl *)dev_alloc(h, sizeof(Ctl));
     {
         auto &D = h->dyn;
         D.ecap = std::max<int64_t>(1, (int64_t)h->K * maxrow);
@@ -317,12 +402,13 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
         if (!h->r32 || !h->b32 || !h->d32) return bail(fail(h, RORBK_ERR_OOM, "mixed workspace"));
     }
     if (!h->tile_row0 || !h->r || !h->xb || !h->bb || !h->partials || !h->hist1 || !h->hist2 ||
-        !h->in_list || !h->eq_list || !h->ctl)
+        !h->in_list || !h->eq_list || !h->ctl || !h->ctl_in)
         return bail(fail(h, RORBK_ERR_OOM, "workspace"));
     cudaMemcpyAsync(h->tile_row0, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(h->hist1, 0, kHistBins * sizeof(unsigned), s);
     cudaMemsetAsync(h->hist2, 0, kHistBins * sizeof(unsigned), s);
     cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s);
+    cudaMemsetAsync(h->ctl_in, 0, sizeof(Ctl), s);
 
     if ((st = build_setup(h, hrp))) return bail(st);
     *out = h;
@@ -336,8 +422,14 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
     if (!b || !x || maxit < 0 || !(tol >= 0)) return fail(h, RORBK_ERR_INVALID_ARG, "solve: b, x, tol >= 0, maxit >= 0");
     rorbk_options opt = opt_in ? *opt_in : defaults();
     if (opt.n_static < 0 || opt.n_static > 64) return fail(h, RORBK_ERR_INVALID_ARG, "n_static");
-    if (opt.precision != RORBK_PREC_FP64)
-        return fail(h, RORBK_ERR_UNSUPPORTED, "this precision mode is not built into the handle");
+    const bool mixed = opt.precision == RORBK_PREC_MIXED;
+    if (opt.precision != RORBK_PREC_FP64 && !mixed)
+        return fail(h, RORBK_ERR_INVALID_ARG, "unknown precision mode");
+    if (mixed && !h->precision_built)
+        return fail(h, RORBK_ERR_UNSUPPORTED,
+                    "mixed precision needs a handle set up with precision = RORBK_PREC_MIXED");
+    if (mixed && (!(opt.inner_tol > 0) || opt.inner_maxit < 1))
+        return fail(h, RORBK_ERR_INVALID_ARG, "inner_tol > 0 and inner_maxit >= 1");
     cudaSetDevice(h->device);
     cudaStream_t s = opt.stream ? (cudaStream_t)opt.stream : h->stream;
     const int64_t m = h->m, n = h->n;
@@ -353,7 +445,9 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
     c.tol = tol;
     c.n_static = opt.n_static;
     c.has_x0 = x0 != nullptr;
-    if (opt.trace) {
+    c.inner_tol = opt.inner_tol;
+    c.inner_maxit = opt.inner_maxit;
+    if (opt.trace && !mixed) {
         c.trace_cap = opt.trace->capacity;
         c.tr_tau = (long long *)opt.trace->tau;
         c.tr_rrn = opt.trace->rrn;
@@ -362,9 +456,10 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
         c.tr_dyn = opt.trace->dyn;
     }
     cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s);
-    if (!opt.host_loop && !h->exec_fp64) {
+    cudaGraphExec_t *exec = mixed ? &h->exec_mixed : &h->exec_fp64;
+    if (!opt.host_loop && !*exec) {
         if ((st = cuda_check(h, cudaStreamSynchronize(s), "solve prologue"))) return st;
-        if ((st = build_graph_fp64(h))) return st;
+        if ((st = mixed ? build_graph_mixed(h) : build_graph_fp64(h))) return st;
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -372,21 +467,44 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
     cudaEventRecord(e0, s);
     cudaError_t e = cudaSuccess;
     if (!opt.host_loop) {
-        e = cudaGraphLaunch(h->exec_fp64, s);
+        e = cudaGraphLaunch(*exec, s);
     } else {
-        // host-driven: batches of `poll` iterations, stop flag read between them
+        // host-driven: batches of `poll` iterations, stop flags read between them
         const int poll = std::max(1, opt.poll);
         cudaStream_t saved = h->stream;
         h->stream = s;
         launch_begin(h, h->bb, h->xb, h->xb, 0, 0);
         int halt = 0;
-        int64_t launched = 0;
-        while (e == cudaSuccess && !halt && launched < maxit) {
-            for (int q = 0; q < poll && launched < maxit; ++q, ++launched)
-                launch_iteration(h, h->bb, h->xb, h->r, 0, 0);
-            e = cudaGetLastError();
+        if (!mixed) {
+            int64_t launched = 0;
+            while (e == cudaSuccess && !halt && launched < maxit) {
+                for (int q = 0; q < poll && launched < maxit; ++q, ++launched)
+                    launch_iteration(h, h->bb, h->xb, h->r, 0, 0);
+                e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            }
+        } else {
             if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            while (e == cudaSuccess && !halt) {
+                launch_mixed_outer(h, 0, 0);
+                int ihalt = 0;
+                e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaMemcpyAsync(&ihalt, &h->ctl_in->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                int odone = 0;
+                if (e == cudaSuccess) e = cudaMemcpy(&odone, &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost);
+                while (e == cudaSuccess && !ihalt && !odone) {
+                    for (int q = 0; q < poll; ++q) launch_mixed_inner(h, 0, 0);
+                    e = cudaGetLastError();
+                    if (e == cudaSuccess) e = cudaMemcpyAsync(&ihalt, &h->ctl_in->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                }
+                if (e == cudaSuccess) launch_mixed_update(h, 0, 0);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            }
         }
         h->stream = saved;
     }
@@ -406,7 +524,7 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
         res->rrn = c.rrn;
         res->converged = c.done && c.status == 0;
         res->status = st;
-        res->refinements = 0;
+        res->refinements = mixed ? c.outer : 0;
         res->time_ms = ms;
     }
     return st;

@@ -293,3 +293,29 @@ def test_residual_fp32_subnormal_and_signed_zero_values(cuda_ok):
         r = torch.empty(s.m, dtype=torch.float64, device="cuda")
         h.residual(dev(s.b), dev(x), r)
     np.testing.assert_array_equal(r.cpu().numpy(), oracle.residual(s, s.b, x)[0])
+
+
+def test_mixed_precision_reaches_fp64_tolerance(cuda_ok):
+    """FP64 refinement around FP32 ROR-BK reaches ||b - A x|| / ||b|| <= tol in
+    FP64 on the power-law system; its error against the FP64 oracle's
+    solution is reported (there is no exact pin for the mixed form)."""
+    s = W.powerlaw(n=1 << 13, num_blocks=32, seed=9, lam=1e-8, tol=1e-8)
+    o = oracle.solve(s, maxit=5000, seed=2)
+    with B.Handle.from_system(s, precision=B.PREC_MIXED) as h:
+        x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        res = h.solve(dev(s.b), x, tol=s.tol, maxit=20000, seed=2, precision=B.PREC_MIXED,
+                      inner_tol=1e-4)
+        xh = np.zeros(s.n)
+        res2 = h.solve(dev(s.b), torch.zeros_like(x), tol=s.tol, maxit=20000, seed=2,
+                       precision=B.PREC_MIXED, inner_tol=1e-4, host_loop=1, poll=16)
+        x64 = torch.zeros_like(x)
+        r64 = h.solve(dev(s.b), x64, tol=s.tol, maxit=5000, seed=2)
+    xm = x.cpu().numpy()
+    r_check = np.linalg.norm(s.b - s.to_dense() @ xm) / np.linalg.norm(s.b)
+    assert res.converged and res.refinements >= 2 and r_check <= 1.001e-8, (res.iters, res.rrn, r_check)
+    assert res2.iters == res.iters and res2.refinements == res.refinements
+    assert r64.converged and r64.iters == o.iters
+    err = rel(xm, o.x)
+    print(f"mixed: {res.iters} inner iterations, {res.refinements} refinements, "
+          f"rrn {res.rrn:.2e}, rel. difference to the FP64 oracle {err:.2e}")
+    assert err < 1e-5
