@@ -1,19 +1,25 @@
 """Benchmark: time to ||Ax-b||/||b|| <= 1e-8 with ROR-BK on one GB300.
 
-Workload (default): the 2^20-row power-law CSR system (FP32-stored values,
-row nnz power law alpha=2.5 in [3,200] plus the diagonal, rows scaled
-log-uniform [1e-4,1]), 4096 contiguous row blocks, lambda=1e-8, tol=1e-8,
-x0 = 0.  One benchmark step is one whole solve from x0 = 0 to the tolerance
-(every iteration of Algorithm 1: 3 sampled static updates, the full residual,
-the top-K selection and the dynamic update).  The setup (Algorithm 1 steps
-1-4) runs once before timing and is reported separately.
+Workload: the 2^20-row power-law CSR system (FP32-stored values; row nnz a
+power law, alpha = 2.5, 3..200 off-diagonals plus the diagonal shift; rows
+scaled log-uniform in [1e-4, 1]), 4096 contiguous row blocks of 256 rows,
+lambda = 1e-8, tol = 1e-8, x0 = 0, Philox seed 1.  One benchmark step is one
+whole solve from x0 = 0 to the tolerance: every iteration of Algorithm 1
+(three sampled static block updates, the full residual, the residual top-K
+selection and the dynamic block update).  The set-up (Algorithm 1 steps 1-4)
+runs once before timing and is reported separately.
+
+Headline value: the mixed-precision form (FP64 iterative refinement around
+FP32 ROR-BK, the block Gram Cholesky in FP64); the plain FP64 form is timed on
+the same inputs beside it.
 
 Arms:
   (default)          the CUDA library through its C ABI
-  --impl reference   the FP64 CPU oracle on the host cores, a bounded sample
-                     of iterations per step, extrapolated to the same solve
+  --impl reference   the FP64 CPU oracle on the host cores: a bounded sample of
+                     iterations per step, scaled to the iterations the solve
+                     takes
 
-Prints one JSON line (rank 0).  Under torchrun every rank solves its own
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own
 system (seed = rank): weak scaling, no collective on the data path.
 """
 from __future__ import annotations
@@ -46,19 +52,21 @@ def parse():
     p.add_argument("--blocks", type=int, default=4096)
     p.add_argument("--lam", type=float, default=1e-8)
     p.add_argument("--tol", type=float, default=1e-8)
+    p.add_argument("--inner-tol", type=float, default=1e-4)
     p.add_argument("--maxit", type=int, default=2_000_000)
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "both"])
-    p.add_argument("--oracle-iters", type=int, default=40)
+    p.add_argument("--fp64-steps", type=int, default=1)
+    p.add_argument("--oracle-iters", type=int, default=60)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile", type=int, default=0,
+                   help="profiling run: N iterations of each form, the loop driven from the "
+                        "host (so that a profiler sees every kernel); prints no JSON")
     p.add_argument("--cache", default=os.path.join(ROOT, ".cache"))
     return p.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def workload(args, rank):
@@ -68,26 +76,25 @@ def workload(args, rank):
 
 
 def config(args, s, extra=None):
-    c = {"workload": f"powerlaw CSR n={s.n} nnz={s.nnz} k={s.num_blocks} blocks "
-                     f"(s=K={s.m // s.num_blocks}), FP32-stored A, lambda={s.lam:g}, "
-                     f"tol={s.tol:g}, x0=0, seed={1}",
-         "step": "one whole solve to tolerance", "l2": "flushed between timed steps"}
+    c = {"workload": (f"power-law sparse square CSR, n={s.n}, nnz={s.nnz}, FP32-stored A, "
+                      f"{s.num_blocks} row blocks of {s.m // s.num_blocks}, lambda={s.lam:g}, "
+                      f"tol={s.tol:g}, x0=0, Philox seed 1"),
+         "step": "one whole solve from x0 = 0 to the tolerance",
+         "l2": "flushed (512 MiB write) between timed steps"}
     if extra:
         c.update(extra)
     return c
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+        self.gpu, self.proc, self.lines = gpu_index, None, []
 
     def __enter__(self):
         try:
@@ -95,8 +102,7 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
         return self
@@ -134,49 +140,76 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def measured_peaks():
+def measured_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
-        d = json.load(open(p))
-        return d.get("hbm_gbs", 6800.0), "measured"
+        return float(json.load(open(p)).get("hbm_gbs", 6800.0)), "measured"
     return 6800.0, "fallback"
 
 
-def residual_bytes(s, fp32_values):
-    """Algorithmic bytes of one r = b - A x launch: the CSR arrays once,
-    x once, b read, r written (FP64 vectors)."""
-    vb = 4 if fp32_values else 8
-    return s.nnz * (vb + 4) + 4 * (s.m + 1) + 8 * s.n + 8 * s.m + 8 * s.m
+def spmv_bytes(s, vbytes, xbytes):
+    """Algorithmic bytes of one r = b - A x: A's values and column indices
+    once, x read once, b read and r written."""
+    return s.nnz * (vbytes + 4) + xbytes * s.n + 2 * xbytes * s.m
 
 
-def time_residual(h, s, torch, flush, reps=20):
-    """Average device time of the residual kernel (the same kernel and grid
-    as inside the solve), each launch after an L2 flush (cold) and back to
-    back without flush (warm, L2-resident working set)."""
-    b = torch.as_tensor(s.b, device="cuda")
-    x = torch.as_tensor(s.x_true, device="cuda") * 0.5
-    r = torch.empty(s.m, dtype=torch.float64, device="cuda")
+def time_kernel(launch, flush, torch, reps=20):
+    """Mean device time of one launch: each launch after an L2 flush (cold;
+    the kernel's HBM-bound time), and back to back (warm)."""
     st = torch.cuda.current_stream()
     for _ in range(3):
-        h.residual(b, x, r)
+        launch()
     torch.cuda.synchronize()
     cold = []
     for _ in range(reps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        h.residual_async(b, x, r)
+        launch()
         e1.record(st)
         e1.synchronize()
         cold.append(e0.elapsed_time(e1))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(reps):
-        h.residual_async(b, x, r)
+        launch()
     e1.record(st)
     e1.synchronize()
-    warm = e0.elapsed_time(e1) / reps
-    return float(np.mean(cold)), float(warm)
+    return float(np.mean(cold)), float(e0.elapsed_time(e1) / reps)
+
+
+def run_solves(h, b, x, s, args, prec, steps, warmup, flush, torch, clocks=None):
+    stream = torch.cuda.current_stream()
+    kw = dict(tol=s.tol, maxit=args.maxit, seed=1, precision=prec, inner_tol=args.inner_tol)
+    for _ in range(warmup):
+        flush.zero_()
+        h.solve(b, x, **kw)
+    torch.cuda.synchronize()
+    times, last = [], None
+    ctx = clocks if clocks is not None else _Null()
+    with ctx:
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = h.solve(b, x, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    xh = x.cpu().numpy()
+    return {"time_s": float(np.mean(times)), "times_s": times, "iters": int(last.iters),
+            "refinements": int(last.refinements), "rrn": float(last.rrn),
+            "converged": bool(last.converged),
+            "rel_err_vs_x_true": float(np.linalg.norm(xh - s.x_true) / np.linalg.norm(s.x_true))}
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
 
 
 def run_ours(args, rank, world, local):
@@ -190,170 +223,172 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl")
     s = workload(args, rank)
     t0 = time.time()
-    precs = {"fp64": [B.PREC_FP64], "mixed": [B.PREC_MIXED],
-             "both": [B.PREC_FP64, B.PREC_MIXED]}[args.precision]
-    h = B.Handle.from_system(s, precision=B.PREC_MIXED if B.PREC_MIXED in precs else B.PREC_FP64)
+    h = B.Handle.from_system(s, precision=B.PREC_MIXED)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     b = torch.as_tensor(s.b, device="cuda")
     x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    clk = ClockSampler(local)
+    mixed = run_solves(h, b, x, s, args, B.PREC_MIXED, args.steps, args.warmup, flush, torch, clk)
+    t_step = mixed["time_s"]
+    if dist:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    fp64 = run_solves(h, b, x, s, args, B.PREC_FP64, args.fp64_steps, 1, flush, torch)
 
-    results = {}
-    for prec in precs:
-        for _ in range(args.warmup):
-            flush.zero_()
-            h.solve(b, x, tol=s.tol, maxit=args.maxit, seed=1, precision=prec)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        times, iters, rrns, refs = [], [], [], []
-        with ClockSampler(local) as clk:
-            for _ in range(args.steps):
-                flush.zero_()
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                res = h.solve(b, x, tol=s.tol, maxit=args.maxit, seed=1, precision=prec)
-                e1.record(stream)
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1) / 1e3)
-                iters.append(res.iters)
-                rrns.append(res.rrn)
-                refs.append(res.refinements)
-        torch.cuda.synchronize()
-        t_step = float(np.mean(times))
-        if dist:
-            tt = torch.tensor([t_step], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_step = float(tt.item())
-        xh = x.cpu().numpy()
-        # end to end through the host-buffer entry point
-        bh = np.ascontiguousarray(s.b)
-        xo = np.zeros(s.n)
-        e2e = []
-        for _ in range(max(1, min(args.steps, 2))):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            h.solve_host(bh, xo, tol=s.tol, maxit=args.maxit, seed=1, precision=prec)
-            e2e.append(time.perf_counter() - t1)
-        results[prec] = {
-            "time_s": t_step, "iters": int(iters[-1]), "rrn": float(rrns[-1]),
-            "refinements": int(refs[-1]),
-            "rel_err_vs_x_true": float(np.linalg.norm(xh - s.x_true) / np.linalg.norm(s.x_true)),
-            "e2e_s": float(np.mean(e2e)), "clocks": clk.summary(),
-            "launches_per_step": 1 + 5 * int(iters[-1]),
-        }
+    # end to end through the host-buffer entry point (H2D of b and D2H of x
+    # inside the timed call)
+    bh = np.ascontiguousarray(s.b)
+    xo = np.zeros(s.n)
+    flush.zero_()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    h.solve_host(bh, xo, tol=s.tol, maxit=args.maxit, seed=1, precision=B.PREC_MIXED,
+                 inner_tol=args.inner_tol)
+    e2e_s = time.perf_counter() - t1
 
-    fp32_vals = s.values.dtype == np.float32
-    cold_ms, warm_ms = time_residual(h, s, torch, flush)
-    peak, peak_kind = measured_peaks()
-    nbytes = residual_bytes(s, fp32_vals)
+    # the sparse residual kernels timed alone, the same kernel and grid as in
+    # the solve: FP32 (the inner solve, every iteration) and FP64
+    x32 = (torch.as_tensor(s.x_true, device="cuda") * 0.5).float()
+    b32 = b.float()
+    r32 = torch.empty(s.m, dtype=torch.float32, device="cuda")
+    cold32, warm32 = time_kernel(lambda: h.residual32(b32, x32, r32, wait=False), flush, torch)
+    x64 = torch.as_tensor(s.x_true, device="cuda") * 0.5
+    r64 = torch.empty(s.m, dtype=torch.float64, device="cuda")
+    cold64, warm64 = time_kernel(lambda: h.residual_async(b, x64, r64), flush, torch)
     h.close()
     if rank != 0:
         if dist:
             dist.barrier()
             dist.destroy_process_group()
         return
-    head = results[B.PREC_MIXED] if B.PREC_MIXED in results else results[B.PREC_FP64]
-    ach = nbytes / (cold_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    by32 = spmv_bytes(s, 4, 4)
+    by64 = spmv_bytes(s, 4, 8)
+    ach32 = by32 / (cold32 * 1e-3) / 1e9
+    ach64 = by64 / (cold64 * 1e-3) / 1e9
+    launches = 1 + mixed["refinements"] * 3 + 6 * mixed["iters"]
     line = {
-        "metric": METRIC, "value": head["time_s"], "unit": "s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["time_s"] * 1e3,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if B.PREC_MIXED not in results else "f32+f64",
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner + f64 refinement",
         "data": "synthetic", "setup_s": setup_s,
-        "config": config(args, s, {"precision": args.precision, "solves_per_s_all_ranks": world / head["time_s"]}),
-        "fp64": _public(results.get(B.PREC_FP64)), "mixed": _public(results.get(B.PREC_MIXED)),
-        "e2e": {"value": head["e2e_s"], "unit": "s", "h2d_bytes_per_step": 8 * s.m,
+        "config": config(args, s, {"precision": "mixed (headline) and fp64",
+                                   "inner_tol": args.inner_tol,
+                                   "solves_per_s_all_ranks": world / t_step}),
+        "mixed": mixed, "fp64": fp64,
+        "speedup_mixed_vs_fp64": fp64["time_s"] / mixed["time_s"],
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * s.m,
                 "d2h_bytes_per_step": 8 * s.n},
-        "gpu_launches": head["launches_per_step"] * args.steps,
-        "clocks": head["clocks"],
-        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                     "frac": ach / peak, "traffic": None,
-                     "kernel": "k_residual (r = b - A x, FP64 accumulate, FP32-stored A)",
-                     "bytes_per_launch": nbytes, "launch_ms_cold_l2": cold_ms,
-                     "launch_ms_warm_l2": warm_ms, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk.summary(),
+        "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
+                     "frac": ach32 / peak, "traffic": None,
+                     "kernel": "k_residual<float,float>: the FP32 SELL-32 sparse residual "
+                               "r = b - A x of the inner solve (one launch per iteration)",
+                     "bytes_per_launch": by32, "launch_ms_cold_l2": cold32,
+                     "launch_ms_warm_l2": warm32,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
+        "roofline_fp64_residual": {"bound": "hbm", "achieved": ach64, "peak": peak,
+                                   "unit": "GB/s", "frac": ach64 / peak,
+                                   "bytes_per_launch": by64, "launch_ms_cold_l2": cold64,
+                                   "launch_ms_warm_l2": warm64},
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(s, args, head["iters"])
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(s, args, mixed["iters"])
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def _public(r):
-    if r is None:
-        return None
-    return {k: v for k, v in r.items() if k not in ("clocks",)}
-
-
-def cpu_baseline(s, args, iters_to_tol):
-    """The oracle, as it stands, on a bounded sample: args.oracle_iters
-    iterations of the same solve (setup excluded), scaled to the GPU run's
-    iteration count."""
+def oracle_per_iteration(s, iters):
+    """Seconds per iteration of the FP64 oracle on this solve (1 host core),
+    from a bounded run of `iters` iterations; the oracle's set-up
+    (orthogonality) is timed separately and removed."""
     import oracle
-    M = oracle.oracle.prepare(s)
     t0 = time.perf_counter()
-    res = oracle.solve(s, maxit=args.oracle_iters, tol=0.0, seed=1)
-    dt = time.perf_counter() - t0
-    # subtract the oracle's own setup (orthogonality) measured separately
+    res = oracle.solve(s, maxit=iters, tol=0.0, seed=1)
+    total = time.perf_counter() - t0
     t1 = time.perf_counter()
     oracle.orthogonality(s, s.num_blocks)
     setup = time.perf_counter() - t1
-    per_it = max(dt - setup, 1e-9) / max(1, res.iters)
-    del M
+    return max(total - setup, 1e-9) / max(1, res.iters), res.iters
+
+
+def cpu_baseline(s, args, iters_to_tol):
+    per_it, done = oracle_per_iteration(s, args.oracle_iters)
     return {"value": per_it * iters_to_tol, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"{res.iters} FP64 oracle iterations of this solve on 1 host core "
-                      f"({per_it * 1e3:.1f} ms/iteration, setup excluded), scaled to the "
-                      f"{iters_to_tol} iterations the solve takes"}
+            "sample": (f"{done} FP64 oracle iterations of this solve on 1 host core "
+                       f"({per_it * 1e3:.1f} ms/iteration, set-up excluded), scaled to the "
+                       f"{iters_to_tol} iterations the solve takes")}
+
+
+def reference_iterations(args):
+    """Iterations the FP64 oracle needs on this workload, recorded by
+    oracle/record_iterations.py (a run of the oracle alone)."""
+    p = os.path.join(ROOT, "oracle", "iterations_to_tol.json")
+    key = f"powerlaw_n{args.n}_k{args.blocks}_lam{args.lam:g}_tol{args.tol:g}_seed1"
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if key in d:
+            return int(d[key]), "recorded by oracle/record_iterations.py"
+    return None, "not recorded"
 
 
 def run_reference(args, rank, world, local):
     if rank != 0:
         return
     s = workload(args, 0)
-    import oracle
-    oracle.orthogonality(s, s.num_blocks)   # warm caches / page in
+    iters, src = reference_iterations(args)
     per = []
     for _ in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        res = oracle.solve(s, maxit=args.oracle_iters, tol=0.0, seed=1)
-        per.append((time.perf_counter() - t0) / max(1, res.iters))
+        per_it, done = oracle_per_iteration(s, args.oracle_iters)
+        per.append(per_it)
     per_it = float(np.mean(per[args.warmup:]))
-    iters = reference_iterations(args)
+    if iters is None:
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the oracle's iteration count on this workload is not "
+                                         "recorded (run oracle/record_iterations.py)"}))
+        return
     val = per_it * iters
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args, s),
             "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.oracle_iters} oracle iterations per step (setup "
-                                       f"included), {per_it * 1e3:.1f} ms/iteration, scaled to "
-                                       f"{iters} iterations to tolerance"},
+                             "sample": (f"{args.oracle_iters} oracle iterations per step, "
+                                        f"{per_it * 1e3:.1f} ms/iteration (set-up excluded), "
+                                        f"scaled to {iters} iterations to tolerance ({src})")},
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def reference_iterations(args):
-    """Iterations Algorithm 1 needs on this workload (a property of the
-    method and the seeded input, identical for every exact FP64
-    implementation), recorded by the oracle's own full run."""
-    p = os.path.join(ROOT, "oracle", "iterations_to_tol.json")
-    if os.path.exists(p):
-        d = json.load(open(p))
-        key = f"powerlaw_n{args.n}_k{args.blocks}_lam{args.lam:g}_tol{args.tol:g}_seed1"
-        if key in d:
-            return int(d[key])
-    return 1
+def run_profile(args):
+    import torch
+    from paper_2510_02156_gb300 import binding as B
+    s = workload(args, 0)
+    h = B.Handle.from_system(s, precision=B.PREC_MIXED)
+    b = torch.as_tensor(s.b, device="cuda")
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    for prec in (B.PREC_MIXED, B.PREC_FP64):
+        res = h.solve(b, x, tol=s.tol, maxit=args.profile, seed=1, precision=prec,
+                      inner_tol=args.inner_tol, host_loop=1, poll=args.profile)
+        print(f"profile run: precision {prec}: {res.iters} iterations, "
+              f"{res.time_ms / max(1, res.iters) * 1e3:.1f} us/iteration (host-driven loop)")
+    h.close()
 
 
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

@@ -231,6 +231,14 @@ rorbk_status rorbk_static_update(rorbk_handle h, int64_t tau, const double *b,
 rorbk_status rorbk_residual(rorbk_handle h, const double *b, const double *x,
                             double *r, double *rr_host);
 
+/* The FP32 form of the residual used by the mixed-precision inner solve:
+ * r = b - A x with b, x, r FP32 device vectors and A's FP32 values (handle set
+ * up with precision = RORBK_PREC_MIXED, else RORBK_ERR_UNSUPPORTED); each row
+ * is an FP32 fused multiply-add chain in stored order.  rr_host as for
+ * rorbk_residual (NULL: enqueue only). */
+rorbk_status rorbk_residual32(rorbk_handle h, const float *b, const float *x, float *r,
+                              double *rr_host);
+
 /* I[K] (device int32): the K = floor(m/k) rows with the largest |r_i|, ties to
  * the lower index, ascending. */
 rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);

@@ -80,6 +80,7 @@ SIGNATURES = {
     "rorbk_sample": (C.c_int, [_P, _U64, _U64, _I64, _I64, _P]),
     "rorbk_static_update": (C.c_int, [_P, _I64, _P, _P]),
     "rorbk_residual": (C.c_int, [_P, _P, _P, _P, _P]),
+    "rorbk_residual32": (C.c_int, [_P, _P, _P, _P, _P]),
     "rorbk_topk": (C.c_int, [_P, _P, _P]),
     "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
 }
@@ -251,6 +252,13 @@ class Handle:
     def residual_async(self, b, x, r):
         """Enqueue r = b - A x on the handle's stream without waiting."""
         _check(lib().rorbk_residual(self.h, _ptr(b), _ptr(x), _ptr(r), None), self.h)
+
+    def residual32(self, b, x, r, wait=True):
+        """FP32 residual of the mixed form (float32 device tensors)."""
+        rr = C.c_double()
+        _check(lib().rorbk_residual32(self.h, _ptr(b), _ptr(x), _ptr(r),
+                                      C.byref(rr) if wait else None), self.h)
+        return rr.value if wait else None
 
     def topk(self, r, I):
         _check(lib().rorbk_topk(self.h, _ptr(r), _ptr(I)), self.h)

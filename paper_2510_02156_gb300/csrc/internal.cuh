@@ -184,6 +184,7 @@ void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inn
 void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_outer);
 void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r);
 void launch_topk_only(rorbk_ctx *h, const double *r, int *I);
+void launch_residual32_only(rorbk_ctx *h, const float *b, const float *x, float *r);
 void launch_dynamic_given(rorbk_ctx *h, const int *I, const double *r, double *x);
 void launch_sample_probe(rorbk_ctx *h, uint64_t seed, uint64_t sysid, int64_t it, int64_t l,
                          long long *out);

@@ -1553,6 +1553,11 @@ void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double
                                                                        h->partials, h->hist1, h->ctl, 2);
 }
 
+void launch_residual32_only(rorbk_ctx *h, const float *b, const float *x, float *r) {
+    k_residual<float, float><<<h->grid_res, 256, 0, h->stream>>>(make_mat<float>(h), b, x, r, h->partials,
+                                                                 h->hist1, h->ctl, 2);
+}
+
 void launch_topk_only(rorbk_ctx *h, const double *r, int *I) {
     const int g = grid_stream(h, (int)h->m);
     k_topk_hist1<double><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist1, h->ctl);

@@ -624,6 +624,22 @@ rorbk_status rorbk_residual(rorbk_handle h, const double *b, const double *x, do
     return st;
 }
 
+rorbk_status rorbk_residual32(rorbk_handle h, const float *b, const float *x, float *r,
+                              double *rr_host) {
+    if (!h || !b || !x || !r) return RORBK_ERR_INVALID_ARG;
+    if (!h->precision_built)
+        return fail(h, RORBK_ERR_UNSUPPORTED, "the FP32 residual needs a handle set up for mixed precision");
+    cudaSetDevice(h->device);
+    launch_residual32_only(h, b, x, r);
+    rorbk_status st = cuda_check(h, cudaGetLastError(), "residual32");
+    if (!rr_host) return st;
+    Ctl c;
+    if (!st) st = cuda_check(h, cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream), "residual32");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(h->stream), "residual32");
+    if (!st) *rr_host = c.rr;
+    return st;
+}
+
 rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I) {
     if (!h || !r || !I) return RORBK_ERR_INVALID_ARG;
     cudaSetDevice(h->device);
