@@ -248,6 +248,38 @@ rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);
 rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
                                   const double *r, double *x);
 
+/* ---- a residual that allocates nothing --------------------------------
+ * (No counterpart in the paper: a service for callers that cannot allocate.)
+ * Some callers cannot call cudaMalloc where they need a residual: code that
+ * runs inside an allocator or a memory-pool callback, processes whose device
+ * memory a framework has fully reserved at start-up, and real-time loops
+ * that forbid allocation after initialisation.  This entry point computes
+ * r = b - A x and ||r||^2 for a CSR matrix in the caller's device memory
+ * without any handle and without allocating: its per-block partial sums and
+ * its completion counter live in a fixed file-scope device array.
+ *   m, n, nnz, row_ptr, col_idx, values, dtype : the CSR matrix (device
+ *       pointers; conventions as rorbk_matrix), m <= 16777216 (= 256 rows per
+ *       thread block x 65536 partial sums), n and nnz below 2^31;
+ *   b (m), x (n), r (m) : device FP64 vectors; rr_out : one device double
+ *       that receives ||r||^2;
+ *   stream : cudaStream_t (NULL = legacy default).  The call only enqueues.
+ * Each row is a fused multiply-add chain over its stored entries in order
+ * (the arithmetic of rorbk_residual), the sum of squares a fixed tree.
+ * The scratch (about 512 KiB) is held by every GPU that loads the library
+ * until the process exits.  All calls on a device share it and it keeps the
+ * last call's contents: the kernel resets the counter it consumes, so calls
+ * ordered on one stream are independent, but calls that overlap on the GPU
+ * race and give wrong results.  The first call on a device looks up the
+ * scratch's device address (once per device, with that device current);
+ * make that first call before any stream capture begins.
+ * Errors: RORBK_ERR_INVALID_ARG (message in rorbk_last_error(NULL)),
+ * RORBK_ERR_CUDA. */
+rorbk_status rorbk_csr_residual_noalloc(int64_t m, int64_t n, int64_t nnz,
+                                        const int32_t *row_ptr, const int32_t *col_idx,
+                                        const void *values, int32_t dtype, const double *b,
+                                        const double *x, double *r, double *rr_out,
+                                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

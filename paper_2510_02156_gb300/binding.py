@@ -83,6 +83,8 @@ SIGNATURES = {
     "rorbk_residual32": (C.c_int, [_P, _P, _P, _P, _P]),
     "rorbk_topk": (C.c_int, [_P, _P, _P]),
     "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
+    "rorbk_csr_residual_noalloc": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, C.c_int32, _P, _P,
+                                             _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -265,3 +267,13 @@ class Handle:
 
     def dynamic_update(self, I, r, x):
         _check(lib().rorbk_dynamic_update(self.h, _ptr(I), _ptr(r), _ptr(x)), self.h)
+
+
+def csr_residual_noalloc(row_ptr, col_idx, values, m, n, b, x, r, rr_out, stream=None):
+    """rorbk_csr_residual_noalloc on device tensors (CSR arrays, b, x, r and a
+    one-element FP64 tensor rr_out); allocates no device memory."""
+    dt = F32 if str(values.dtype) == "torch.float32" else F64
+    st = lib().rorbk_csr_residual_noalloc(m, n, int(col_idx.numel()), _ptr(row_ptr), _ptr(col_idx),
+                                          _ptr(values), dt, _ptr(b), _ptr(x), _ptr(r), _ptr(rr_out),
+                                          _stream_ptr(stream))
+    _check(st, None)
