@@ -69,9 +69,26 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def replica_seed(rank):
+    """Generator seed of the system rank `rank` solves: every rank (replica)
+    solves its own independent system, so per-GPU work is fixed as N grows."""
+    return 1 + rank
+
+
+def max_over_ranks(value, dist, device):
+    """The step time of the job: the maximum over all ranks (a no-op for one
+    process).  The only collective of a replicated run besides barriers."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(args, rank):
     from paper_2510_02156_gb300 import workloads as W
-    return W.powerlaw(n=args.n, num_blocks=args.blocks, seed=1 + rank, lam=args.lam,
+    return W.powerlaw(n=args.n, num_blocks=args.blocks, seed=replica_seed(rank), lam=args.lam,
                       tol=args.tol, cache=args.cache)
 
 
@@ -260,10 +277,7 @@ def run_ours(args, rank, world, local):
     clk = ClockSampler(local)
     mixed = run_solves(h, b, x, s, args, B.PREC_MIXED, args.steps, args.warmup, flush, torch, clk)
     t_step = mixed["time_s"]
-    if dist:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(t_step, dist, "cuda")
     fp64 = run_solves(h, b, x, s, args, B.PREC_FP64, args.fp64_steps, 1, flush, torch)
 
     # end to end through the host-buffer entry point (H2D of b and D2H of x
