@@ -143,7 +143,11 @@ typedef struct {
 
 typedef struct {
     int64_t iters;          /* ROR-BK iterations executed (MIXED: inner iterations summed) */
-    double rrn;             /* final ||b - A x|| / ||b|| (FP64)                  */
+    double rrn;             /* the last ||b - A x|| / ||b|| Algorithm 1 tested:
+                               after the static updates of the last iteration.
+                               Converged: the returned x's.  After maxit the
+                               returned x also holds that iteration's dynamic
+                               update, which the paper never re-tests (FP64) */
     int32_t converged;      /* 1 if rrn <= tol                                   */
     int32_t status;         /* same as the call's return value                   */
     int64_t refinements;    /* MIXED: outer refinement steps                     */
@@ -247,6 +251,39 @@ rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);
  * (device, m doubles, read at I): x += A_I^T (A_I A_I^T + mu I)^{-1} r_I. */
 rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
                                   const double *r, double *x);
+
+/* ---- the differentiable solve ------------------------------------------
+ * (No counterpart in the paper, which never differentiates its solution.)
+ * For square non-singular A and a loss L(x) with x = A^{-1} b:
+ *   dL/db = g with A^T g = dL/dx (the adjoint system), dL/dA = -g x^T,
+ * restricted to A's stored pattern: dL/da_ij = -g_i x_j.
+ *
+ * rorbk_setup_adjoint: a new handle *out for the adjoint system, built from
+ *   h's own copy of A.  ROR-BK, like every Kaczmarz-type method, is invariant
+ *   to row scaling but not to column scaling, and A's row scaling is a column
+ *   scaling of A^T; so the handle holds At~ = A^T C^{-1} with
+ *   C = diag(||A_i||_2) (1 for a zero row): the transpose of A with its rows
+ *   normalised, in FP64 values, each row of At~ listing its columns
+ *   ascending.  It is then set up exactly as rorbk_setup would (Algorithm 1
+ *   steps 1-4 on At~).  part partitions the n rows of At~; lambda and opt as
+ *   for rorbk_setup (opt == NULL: defaults on h's stream).  Free *out with
+ *   rorbk_free.  Errors: as rorbk_setup; RORBK_ERR_INVALID_ARG for a NULL h,
+ *   part or out.
+ * rorbk_adjoint_solve: solves A^T g = y on such a handle: ROR-BK on
+ *   At~ h = y (as rorbk_solve, from h0 = 0), then g = C^{-1} h.  Because
+ *   At~ h = A^T g, res->rrn is ||y - A^T g|| / ||y||.  y (length n of A)
+ *   and g (length m of A) are device FP64 vectors; returns when g is
+ *   written.  Errors: as rorbk_solve; RORBK_ERR_INVALID_ARG if adj was not
+ *   made by rorbk_setup_adjoint.
+ * rorbk_value_grad: dvals[p] = -(g_i * x_j) for every stored entry p = (i, j)
+ *   of h's A, in the CSR order A was given in (nnz doubles).  g (m) and x (n)
+ *   are device FP64 vectors; enqueued on h's stream, not waited for.  Errors:
+ *   RORBK_ERR_INVALID_ARG for NULL pointers. */
+rorbk_status rorbk_setup_adjoint(rorbk_handle h, const rorbk_partition *part, double lambda,
+                                 const rorbk_options *opt, rorbk_handle *out);
+rorbk_status rorbk_adjoint_solve(rorbk_handle adj, const double *y, double *g, double tol,
+                                 int64_t maxit, const rorbk_options *opt, rorbk_result *res);
+rorbk_status rorbk_value_grad(rorbk_handle h, const double *g, const double *x, double *dvals);
 
 /* ---- a residual that allocates nothing --------------------------------
  * (No counterpart in the paper: a service for callers that cannot allocate.)

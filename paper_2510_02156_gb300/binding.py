@@ -83,6 +83,9 @@ SIGNATURES = {
     "rorbk_residual32": (C.c_int, [_P, _P, _P, _P, _P]),
     "rorbk_topk": (C.c_int, [_P, _P, _P]),
     "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
+    "rorbk_setup_adjoint": (C.c_int, [_P, _P, _D, _P, _P]),
+    "rorbk_adjoint_solve": (C.c_int, [_P, _P, _P, _D, _I64, _P, _P]),
+    "rorbk_value_grad": (C.c_int, [_P, _P, _P, _P]),
     "rorbk_csr_residual_noalloc": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, C.c_int32, _P, _P,
                                              _P, _P, _P]),
 }
@@ -172,6 +175,43 @@ class Handle:
         self.h = h
         self.info = Info()
         _check(lib().rorbk_get_info(self.h, C.byref(self.info)), self.h)
+
+    @classmethod
+    def _adopt(cls, raw):
+        """Wrap an rorbk_handle made by the library (rorbk_setup_adjoint)."""
+        self = cls.__new__(cls)
+        self._keep = []
+        self.h = raw
+        self.info = Info()
+        _check(lib().rorbk_get_info(self.h, C.byref(self.info)), self.h)
+        return self
+
+    def setup_adjoint(self, num_blocks, lam, precision=PREC_FP64, offsets=None, stream=None):
+        """rorbk_setup_adjoint: a Handle for A^T built from this handle's A."""
+        offs = None
+        if offsets is not None:
+            offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        part = Partition(num_blocks, 0, None if offs is None else offs.ctypes.data)
+        opt = default_options(precision=precision, stream=_stream_ptr(stream))
+        raw = C.c_void_p()
+        _check(lib().rorbk_setup_adjoint(self.h, C.byref(part), lam, C.byref(opt), C.byref(raw)),
+               self.h)
+        return Handle._adopt(raw)
+
+    def adjoint_solve(self, y, g, tol=1e-8, maxit=1000, seed=0, system_id=0, n_static=3,
+                      precision=PREC_FP64, stream=None, inner_tol=1e-4, inner_maxit=2000000):
+        """rorbk_adjoint_solve on a handle from setup_adjoint: A^T g = y."""
+        opt = default_options(seed=seed, system_id=system_id, n_static=n_static,
+                              precision=precision, stream=_stream_ptr(stream),
+                              inner_tol=inner_tol, inner_maxit=inner_maxit)
+        res = Result()
+        _check(lib().rorbk_adjoint_solve(self.h, _ptr(y), _ptr(g), tol, maxit, C.byref(opt),
+                                         C.byref(res)), self.h)
+        return res
+
+    def value_grad(self, g, x, dvals):
+        """rorbk_value_grad: dvals[p] = -g_i x_j over A's stored entries."""
+        _check(lib().rorbk_value_grad(self.h, _ptr(g), _ptr(x), _ptr(dvals)), self.h)
 
     @classmethod
     def from_system(cls, system, lam=None, precision=PREC_FP64, **kw):

@@ -132,6 +132,8 @@ struct rorbk_ctx {
         float *val32 = nullptr;     // FP32-stored values (FP32 systems and the mixed path)
         double *val = nullptr;      // FP64 values (FP64 systems)
     } sell;
+    // adjoint handles (rorbk_setup_adjoint): the row norms c_i of the primal A
+    double *adj_scale = nullptr;
     // workspace
     double *r = nullptr, *xb = nullptr, *bb = nullptr, *x64 = nullptr;
     float *r32 = nullptr, *b32 = nullptr, *d32 = nullptr;
@@ -165,6 +167,9 @@ namespace rorbk {
 // host helpers implemented in rorbk.cu
 rorbk_status fail(rorbk_ctx *h, rorbk_status st, const std::string &msg);
 rorbk_status cuda_check(rorbk_ctx *h, cudaError_t e, const char *what);
+// what rorbk_last_error(NULL) reports: the last failure on this thread that
+// left no handle
+void record_setup_error(const std::string &msg);
 void *dev_alloc(rorbk_ctx *h, size_t bytes);
 
 // setup (kernels_setup.cu)

@@ -17,6 +17,8 @@ namespace rorbk {
 
 static thread_local std::string g_setup_error;
 
+void record_setup_error(const std::string &msg) { g_setup_error = msg; }
+
 rorbk_status fail(rorbk_ctx *h, rorbk_status st, const std::string &msg) {
     if (h) h->err = msg;
     g_setup_error = msg;
