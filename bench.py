@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=1)
     p.add_argument("--oracle-iters", type=int, default=60)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autograd", action="store_true",
+                   help="skip the differentiable-solve measurement (forward + adjoint backward "
+                        "on the 262,144-unknown power-law system)")
     p.add_argument("--profile", type=int, default=0,
                    help="profiling run: N iterations of each form, the loop driven from the "
                         "host (so that a profiler sees every kernel); prints no JSON")
@@ -291,6 +294,8 @@ def run_ours(args, rank, world, local):
                  inner_tol=args.inner_tol)
     e2e_s = time.perf_counter() - t1
 
+    ag = None if args.no_autograd else autograd_measurement(args)
+
     # the sparse residual kernels timed alone, the same kernel and grid as in
     # the solve: FP32 (the inner solve, every iteration) and FP64
     x32 = (torch.as_tensor(s.x_true, device="cuda") * 0.5).float()
@@ -325,6 +330,7 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * s.m,
                 "d2h_bytes_per_step": 8 * s.n},
         "gpu_launches": launches * args.steps,
+        "autograd": ag,
         "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
                      "frac": ach32 / peak,
@@ -346,6 +352,40 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def autograd_measurement(args):
+    """Forward solve and adjoint backward of L = 0.5 ||x - x_t||^2 on the
+    262,144-unknown power-law system (1024 blocks of 256 rows), to the bench
+    tolerance, through the torch.autograd.Function.  Wall times include the
+    handles' set-up (the adjoint handle's transpose and equilibration); the
+    solve times are the device loops'."""
+    import torch
+    from paper_2510_02156_gb300 import autograd as AG
+    from paper_2510_02156_gb300 import workloads as W
+    s = W.powerlaw(n=1 << 18, num_blocks=1024, seed=1, lam=args.lam, tol=args.tol,
+                   cache=args.cache)
+    x_t = torch.as_tensor(np.random.default_rng(26).standard_normal(s.n), device="cuda")
+    vals = torch.tensor(s.values.astype(np.float64), requires_grad=True)
+    b = torch.tensor(s.b, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, spec = AG.solve(s.row_ptr, s.col_idx, vals, b, num_blocks=s.num_blocks, lam=s.lam,
+                       tol=s.tol, maxit=args.maxit)
+    loss = 0.5 * ((x - x_t) ** 2).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    f, a = spec.last_forward, spec.last_adjoint
+    return {"workload": f"power-law sparse square CSR, n={s.n}, nnz={s.nnz}, 1024 blocks of 256, "
+                        f"lambda={s.lam:g}, tol={s.tol:g}; L = 0.5||x - x_t||^2",
+            "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "forward_solve_s": f.time_ms / 1e3, "adjoint_solve_s": a.time_ms / 1e3,
+            "forward_iters": int(f.iters), "adjoint_iters": int(a.iters),
+            "forward_rrn": float(f.rrn), "adjoint_rrn": float(a.rrn),
+            "converged": bool(f.converged and a.converged)}
 
 
 def oracle_per_iteration(s, iters):

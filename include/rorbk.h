@@ -252,6 +252,45 @@ rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);
 rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
                                   const double *r, double *x);
 
+/* ---- many solves in one launch --------------------------------------
+ * (Beside the paper: its method solves one system; these run many ROR-BK
+ * solves at once, each exactly the solve rorbk_solve would run.)
+ *
+ * rorbk_clone: a new handle *out that shares every set-up product of src (A
+ *   and its copies, the partition, the proposal, the static operators: all
+ *   read-only during solves) and owns a fresh per-solve workspace (vectors,
+ *   loop state, dynamic-block scratch).  It solves the same system: use one
+ *   clone per right-hand side.  The shared memory is freed when the last of
+ *   src and its clones is freed (rorbk_free), in any order.  Errors:
+ *   RORBK_ERR_INVALID_ARG (NULL), RORBK_ERR_OOM, RORBK_ERR_CUDA.
+ * rorbk_batch_create: captures the whole solve loop of each of count
+ *   distinct handles (systems of any sizes, clones, or both; one device) as
+ *   independent components of one CUDA graph, for precision FP64 or MIXED
+ *   (MIXED needs handles set up for it).  The handles must outlive the batch
+ *   and must not be solved on their own while a batch solve runs.  Errors:
+ *   RORBK_ERR_INVALID_ARG (NULL or repeated handle, mixed devices, unknown
+ *   precision), RORBK_ERR_CUDA; the message is at rorbk_last_error(NULL).
+ * rorbk_batch_solve: one graph launch that runs every handle's solve to its
+ *   own stop (tolerance, maxit or error): solve i takes device vectors b[i]
+ *   (its m), x0[i] (its n; x0 == NULL or x0[i] == NULL: zero) and writes
+ *   x[i] (its n).  opt is shared (precision must be the batch's; host_loop and
+ *   trace are not available); system_ids[i] (NULL: all opt->system_id) is
+ *   solve i's Philox key word 1, so clones given the same id share the
+ *   sampled block stream.  res[count] (may be NULL) receives each solve's
+ *   result; time_ms is the whole launch.  Returns the first error of any
+ *   solve, else RORBK_NOT_CONVERGED if any solve stopped at maxit, else
+ *   RORBK_OK.
+ * rorbk_batch_free: NULL-safe; does not free the handles. */
+typedef struct rorbk_batch_ctx *rorbk_batch;
+rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out);
+rorbk_status rorbk_batch_create(const rorbk_handle *hs, int32_t count, int32_t precision,
+                                rorbk_batch *out);
+rorbk_status rorbk_batch_solve(rorbk_batch batch, const double *const *b, const double *const *x0,
+                               double *const *x, double tol, int64_t maxit,
+                               const rorbk_options *opt, const uint64_t *system_ids,
+                               rorbk_result *res);
+void rorbk_batch_free(rorbk_batch batch);
+
 /* ---- the differentiable solve ------------------------------------------
  * (No counterpart in the paper, which never differentiates its solution.)
  * For square non-singular A and a loss L(x) with x = A^{-1} b:

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_INVALID_ARG", -2: "ERR_CUD
 FORMAT_CSR, FORMAT_DENSE = 0, 1
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+OK, NOT_CONVERGED = 0, 1
 
 
 class RorbkError(RuntimeError):
@@ -83,6 +84,10 @@ SIGNATURES = {
     "rorbk_residual32": (C.c_int, [_P, _P, _P, _P, _P]),
     "rorbk_topk": (C.c_int, [_P, _P, _P]),
     "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
+    "rorbk_clone": (C.c_int, [_P, _P]),
+    "rorbk_batch_create": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
+    "rorbk_batch_solve": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P, _P]),
+    "rorbk_batch_free": (None, [_P]),
     "rorbk_setup_adjoint": (C.c_int, [_P, _P, _D, _P, _P]),
     "rorbk_adjoint_solve": (C.c_int, [_P, _P, _P, _D, _I64, _P, _P]),
     "rorbk_value_grad": (C.c_int, [_P, _P, _P, _P]),
@@ -185,6 +190,12 @@ class Handle:
         self.info = Info()
         _check(lib().rorbk_get_info(self.h, C.byref(self.info)), self.h)
         return self
+
+    def clone(self):
+        """rorbk_clone: a Handle sharing this one's set-up, with its own workspace."""
+        raw = C.c_void_p()
+        _check(lib().rorbk_clone(self.h, C.byref(raw)), self.h)
+        return Handle._adopt(raw)
 
     def setup_adjoint(self, num_blocks, lam, precision=PREC_FP64, offsets=None, stream=None):
         """rorbk_setup_adjoint: a Handle for A^T built from this handle's A."""
@@ -307,6 +318,53 @@ class Handle:
 
     def dynamic_update(self, I, r, x):
         _check(lib().rorbk_dynamic_update(self.h, _ptr(I), _ptr(r), _ptr(x)), self.h)
+
+
+class Batch:
+    """Owns one rorbk_batch: several handles' solves in one graph launch."""
+
+    def __init__(self, handles, precision=PREC_FP64):
+        self.handles = list(handles)
+        arr = (C.c_void_p * len(self.handles))(*[h.h for h in self.handles])
+        raw = C.c_void_p()
+        _check(lib().rorbk_batch_create(arr, len(self.handles), precision, C.byref(raw)), None)
+        self.b = raw
+        self.precision = precision
+
+    def solve(self, bs, xs, x0s=None, tol=1e-8, maxit=1000, seed=0, system_ids=None, n_static=3,
+              inner_tol=1e-4, inner_maxit=2000000, stream=None):
+        """rorbk_batch_solve on lists of device tensors; returns (status, results)."""
+        k = len(self.handles)
+        P = C.c_void_p * k
+        b_arr = P(*[b.data_ptr() for b in bs])
+        x_arr = P(*[x.data_ptr() for x in xs])
+        x0_arr = None if x0s is None else P(*[0 if v is None else v.data_ptr() for v in x0s])
+        ids = None if system_ids is None else (C.c_uint64 * k)(*system_ids)
+        opt = default_options(seed=seed, n_static=n_static, precision=self.precision,
+                              stream=_stream_ptr(stream), inner_tol=inner_tol,
+                              inner_maxit=inner_maxit)
+        res = (Result * k)()
+        st = lib().rorbk_batch_solve(self.b, b_arr, x0_arr, x_arr, tol, maxit, C.byref(opt), ids,
+                                     res)
+        _check(st, None)
+        return st, list(res)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().rorbk_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def csr_residual_noalloc(row_ptr, col_idx, values, m, n, b, x, r, rr_out, stream=None):

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -93,6 +94,20 @@ struct BlockT {
                                 // start at seg[row_ptr[off[t]] ...]
 };
 
+// Device memory owned jointly by a handle and its clones (rorbk_clone): the
+// set-up data.  Freed when the last of them is freed.
+struct DevBlocks {
+    int device = 0;
+    std::vector<void *> p;
+    ~DevBlocks() {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        for (void *q : p) cudaFree(q);
+        cudaSetDevice(cur);
+    }
+};
+
 }  // namespace rorbk
 
 struct rorbk_ctx {
@@ -106,7 +121,9 @@ struct rorbk_ctx {
     int precision_built = 0;
     int num_sms = 0;
     int64_t bytes = 0;
-    std::vector<void *> allocs;
+    std::vector<void *> allocs;                       // memory this handle alone owns
+    std::shared_ptr<rorbk::DevBlocks> shared_setup;   // set-up memory shared with clones
+    int maxrow = 0;                                   // longest row of A
     // matrix (CSR)
     int *rowptr = nullptr, *col = nullptr;
     double *val = nullptr;      // FP64 values (exact widening if given FP32)

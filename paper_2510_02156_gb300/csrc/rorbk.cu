@@ -75,12 +75,20 @@ static void build_tiles(const std::vector<int> &rp, int m, std::vector<int> &til
     tiles.push_back(m);
 }
 
-// Capture: k_begin, then WHILE(cond) { one iteration }.
-static rorbk_status build_graph_fp64(rorbk_ctx *h) {
+// Starts capturing on cs: into a new graph, or appended to `parent` as a new
+// independent component.
+static cudaError_t begin_capture(cudaStream_t cs, cudaGraph_t parent) {
+    if (!parent) return cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    return cudaStreamBeginCaptureToGraph(cs, parent, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+}
+
+// Capture: k_begin, then WHILE(cond) { one iteration }.  With parent == NULL
+// the graph is instantiated into h->exec_fp64, else it is appended to parent.
+static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr) {
     rorbk_status st;
     cudaStream_t saved = h->stream;
     cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2;
-    if ((st = cuda_check(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "capture")))
+    if ((st = cuda_check(h, begin_capture(cs, parent), "capture")))
         return st;
     cudaGraph_t graph = nullptr;
     cudaStreamCaptureStatus cst;
@@ -121,8 +129,10 @@ static rorbk_status build_graph_fp64(rorbk_ctx *h) {
     cudaGraph_t g_out = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(cs, &g_out);
     if (e == cudaSuccess) e = e3;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_fp64, g_out, 0);
-    if (g_out) cudaGraphDestroy(g_out);
+    if (!parent) {
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_fp64, g_out, 0);
+        if (g_out) cudaGraphDestroy(g_out);
+    }
     return cuda_check(h, e, "building the iteration graph");
 }
 
@@ -156,12 +166,12 @@ static cudaError_t new_handle(cudaStream_t cs, cudaGraphConditionalHandle *hc) {
 
 // Capture: k_begin, then WHILE(outer) { FP64 residual + inner set-up,
 // WHILE(inner) { one FP32 iteration }, x += d }.
-static rorbk_status build_graph_mixed(rorbk_ctx *h) {
+static rorbk_status build_graph_mixed(rorbk_ctx *h, cudaGraph_t parent = nullptr) {
     cudaStream_t saved = h->stream;
     cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2, cs3 = h->cap_stream3;
     cudaGraphConditionalHandle hout = 0, hin = 0;
     cudaGraph_t body1 = nullptr, body2 = nullptr, tmp = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = begin_capture(cs, parent);
     if (e != cudaSuccess) return cuda_check(h, e, "capture");
     e = new_handle(cs, &hout);
     if (e == cudaSuccess) {
@@ -199,9 +209,73 @@ static rorbk_status build_graph_mixed(rorbk_ctx *h) {
     cudaGraph_t g_out = nullptr;
     cudaError_t e4 = cudaStreamEndCapture(cs, &g_out);
     if (e == cudaSuccess) e = e4;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_mixed, g_out, 0);
-    if (g_out) cudaGraphDestroy(g_out);
+    if (!parent) {
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_mixed, g_out, 0);
+        if (g_out) cudaGraphDestroy(g_out);
+    }
     return cuda_check(h, e, "building the mixed-precision graph");
+}
+
+// Per-solve device state of a handle: vectors, reduction scratch, top-K
+// lists, the dynamic-block workspace and the loop state.  Set-up data (A and
+// its copies, the partition, the proposal, the static operators) is not part
+// of it, so clones share that and own only this.
+static rorbk_status alloc_workspace(rorbk_ctx *h) {
+    const int64_t m = h->m, n = h->n;
+    cudaStream_t s = h->stream;
+    h->r = (double *)dev_alloc(h, m * sizeof(double));
+    h->xb = (double *)dev_alloc(h, n * sizeof(double));
+    h->bb = (double *)dev_alloc(h, m * sizeof(double));
+    h->partials = (double *)dev_alloc(h, std::max(h->grid_res, 4 * h->num_sms) * sizeof(double) + 64);
+    h->hist1 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
+    h->hist2 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
+    h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
+    h->eq_list = (int *)dev_alloc(h, kEqCap * sizeof(int));
+    h->ctl = (Ctl *)dev_alloc(h, sizeof(Ctl));
+    h->ctl_in = (Ctl *)dev_alloc(h, sizeof(Ctl));
+    {
+        auto &D = h->dyn;
+        D.ecap = std::max<int64_t>(1, (int64_t)h->K * h->maxrow);
+        int64_t np2 = 1;
+        while (np2 < 2 * D.ecap) np2 <<= 1;
+        D.pcap = 1;
+        while (D.pcap < std::max<int64_t>(16 * D.ecap, 1 << 16)) D.pcap <<= 1;
+        D.I = (int *)dev_alloc(h, h->K * sizeof(int));
+        D.estart = (int *)dev_alloc(h, (h->K + 1) * sizeof(int));
+        D.gdiag = (double *)dev_alloc(h, h->K * sizeof(double));
+        D.y = (double *)dev_alloc(h, h->K * sizeof(double));
+        D.ecol = (int *)dev_alloc(h, D.ecap * sizeof(int));
+        D.eval = (double *)dev_alloc(h, D.ecap * sizeof(double));
+        D.erow = (uint16_t *)dev_alloc(h, D.ecap * sizeof(uint16_t));
+        D.owner = (unsigned long long *)dev_alloc(h, n * sizeof(unsigned long long));
+        D.shared = (unsigned *)dev_alloc(h, n * sizeof(unsigned));
+        D.epoch = (unsigned *)dev_alloc(h, sizeof(unsigned));
+        D.segpos = (int *)dev_alloc(h, n * sizeof(int));
+        D.raw = (unsigned long long *)dev_alloc(h, 2 * D.ecap * sizeof(unsigned long long));
+        D.skeys = (unsigned long long *)dev_alloc(h, np2 * sizeof(unsigned long long));
+        D.pkeys = (unsigned long long *)dev_alloc(h, D.pcap * sizeof(unsigned long long));
+        D.g = (double *)dev_alloc(h, ((size_t)h->K * (h->K + 1) / 2) * sizeof(double));
+        if (!D.I || !D.estart || !D.gdiag || !D.y || !D.ecol || !D.eval || !D.erow || !D.owner ||
+            !D.shared || !D.epoch || !D.segpos || !D.raw || !D.skeys || !D.pkeys || !D.g)
+            return fail(h, RORBK_ERR_OOM, "dynamic-block workspace");
+        cudaMemsetAsync(D.owner, 0, n * sizeof(unsigned long long), s);   // epoch 0: never
+        cudaMemsetAsync(D.shared, 0, n * sizeof(unsigned), s);
+        cudaMemsetAsync(D.epoch, 0, sizeof(unsigned), s);
+    }
+    if (h->precision_built) {
+        h->r32 = (float *)dev_alloc(h, m * sizeof(float));
+        h->b32 = (float *)dev_alloc(h, m * sizeof(float));
+        h->d32 = (float *)dev_alloc(h, n * sizeof(float));
+        if (!h->r32 || !h->b32 || !h->d32) return fail(h, RORBK_ERR_OOM, "mixed workspace");
+    }
+    if (!h->r || !h->xb || !h->bb || !h->partials || !h->hist1 || !h->hist2 || !h->in_list ||
+        !h->eq_list || !h->ctl || !h->ctl_in)
+        return fail(h, RORBK_ERR_OOM, "workspace");
+    cudaMemsetAsync(h->hist1, 0, kHistBins * sizeof(unsigned), s);
+    cudaMemsetAsync(h->hist2, 0, kHistBins * sizeof(unsigned), s);
+    cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s);
+    cudaMemsetAsync(h->ctl_in, 0, sizeof(Ctl), s);
+    return cuda_check(h, cudaGetLastError(), "workspace");
 }
 
 static rorbk_options defaults() {
@@ -357,72 +431,22 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     h->ntiles = (int)tiles.size() - 1;
     h->tile_row0 = (int *)dev_alloc(h, tiles.size() * sizeof(int));
     h->grid_res = residual_grid(h);
-    // workspace
-    h->r = (double *)dev_alloc(h, m * sizeof(double));
-    h->xb = (double *)dev_alloc(h, n * sizeof(double));
-    h->bb = (double *)dev_alloc(h, m * sizeof(double));
-    h->partials = (double *)dev_alloc(h, std::max(h->grid_res, 4 * h->num_sms) * sizeof(double) + 64);
-    h->hist1 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
-    h->hist2 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
-    h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
-    h->eq_list = (int *)dev_alloc(h, kEqCap * sizeof(int));
-    h->ctl = (Ctl *)dev_alloc(h, sizeof(Ctl));
-    h->ctl_in = (Ctl *)dev_alloc(h, sizeof(Ctl));
-    {
-        auto &D = h->dyn;
-        D.ecap = std::max<int64_t>(1, (int64_t)h->K * maxrow);
-        int64_t np2 = 1;
-        while (np2 < 2 * D.ecap) np2 <<= 1;
-        D.pcap = 1;
-        while (D.pcap < std::max<int64_t>(16 * D.ecap, 1 << 16)) D.pcap <<= 1;
-        D.I = (int *)dev_alloc(h, h->K * sizeof(int));
-        D.estart = (int *)dev_alloc(h, (h->K + 1) * sizeof(int));
-        D.gdiag = (double *)dev_alloc(h, h->K * sizeof(double));
-        D.y = (double *)dev_alloc(h, h->K * sizeof(double));
-        D.ecol = (int *)dev_alloc(h, D.ecap * sizeof(int));
-        D.eval = (double *)dev_alloc(h, D.ecap * sizeof(double));
-        D.erow = (uint16_t *)dev_alloc(h, D.ecap * sizeof(uint16_t));
-        D.owner = (unsigned long long *)dev_alloc(h, n * sizeof(unsigned long long));
-        D.shared = (unsigned *)dev_alloc(h, n * sizeof(unsigned));
-        D.epoch = (unsigned *)dev_alloc(h, sizeof(unsigned));
-        D.segpos = (int *)dev_alloc(h, n * sizeof(int));
-        D.raw = (unsigned long long *)dev_alloc(h, 2 * D.ecap * sizeof(unsigned long long));
-        D.skeys = (unsigned long long *)dev_alloc(h, np2 * sizeof(unsigned long long));
-        D.pkeys = (unsigned long long *)dev_alloc(h, D.pcap * sizeof(unsigned long long));
-        D.g = (double *)dev_alloc(h, ((size_t)h->K * (h->K + 1) / 2) * sizeof(double));
-        if (!D.I || !D.estart || !D.gdiag || !D.y || !D.ecol || !D.eval || !D.erow || !D.owner ||
-            !D.shared || !D.epoch || !D.segpos || !D.raw || !D.skeys || !D.pkeys || !D.g)
-            return bail(fail(h, RORBK_ERR_OOM, "dynamic-block workspace"));
-        cudaMemsetAsync(D.owner, 0, n * sizeof(unsigned long long), s);   // epoch 0: never
-        cudaMemsetAsync(D.shared, 0, n * sizeof(unsigned), s);
-        cudaMemsetAsync(D.epoch, 0, sizeof(unsigned), s);
-    }
-    if (h->precision_built) {
-        h->r32 = (float *)dev_alloc(h, m * sizeof(float));
-        h->b32 = (float *)dev_alloc(h, m * sizeof(float));
-        h->d32 = (float *)dev_alloc(h, n * sizeof(float));
-        if (!h->r32 || !h->b32 || !h->d32) return bail(fail(h, RORBK_ERR_OOM, "mixed workspace"));
-    }
-    if (!h->tile_row0 || !h->r || !h->xb || !h->bb || !h->partials || !h->hist1 || !h->hist2 ||
-        !h->in_list || !h->eq_list || !h->ctl || !h->ctl_in)
-        return bail(fail(h, RORBK_ERR_OOM, "workspace"));
+    h->maxrow = maxrow;
+    if (!h->tile_row0) return bail(fail(h, RORBK_ERR_OOM, "workspace"));
     cudaMemcpyAsync(h->tile_row0, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-    cudaMemsetAsync(h->hist1, 0, kHistBins * sizeof(unsigned), s);
-    cudaMemsetAsync(h->hist2, 0, kHistBins * sizeof(unsigned), s);
-    cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s);
-    cudaMemsetAsync(h->ctl_in, 0, sizeof(Ctl), s);
+    if ((st = alloc_workspace(h))) return bail(st);
 
     if ((st = build_setup(h, hrp))) return bail(st);
     *out = h;
     return RORBK_OK;
 }
 
-static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0, bool b_host,
-                               double *x, bool x_host, double tol, int64_t maxit,
-                               const rorbk_options *opt_in, rorbk_result *res) {
-    if (!h) return RORBK_ERR_INVALID_ARG;
-    if (!b || !x || maxit < 0 || !(tol >= 0)) return fail(h, RORBK_ERR_INVALID_ARG, "solve: b, x, tol >= 0, maxit >= 0");
-    rorbk_options opt = opt_in ? *opt_in : defaults();
+// Checks a solve's arguments (h, options) and enqueues on s the copies of b
+// and x0 into the handle's workspace and the initial loop state.
+static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double *x0, bool b_host,
+                                  double tol, int64_t maxit, const rorbk_options &opt,
+                                  cudaStream_t s) {
+    if (!b || maxit < 0 || !(tol >= 0)) return fail(h, RORBK_ERR_INVALID_ARG, "solve: b, tol >= 0, maxit >= 0");
     if (opt.n_static < 0 || opt.n_static > 64) return fail(h, RORBK_ERR_INVALID_ARG, "n_static");
     const bool mixed = opt.precision == RORBK_PREC_MIXED;
     if (opt.precision != RORBK_PREC_FP64 && !mixed)
@@ -432,10 +456,7 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
                     "mixed precision needs a handle set up with precision = RORBK_PREC_MIXED");
     if (mixed && (!(opt.inner_tol > 0) || opt.inner_maxit < 1))
         return fail(h, RORBK_ERR_INVALID_ARG, "inner_tol > 0 and inner_maxit >= 1");
-    cudaSetDevice(h->device);
-    cudaStream_t s = opt.stream ? (cudaStream_t)opt.stream : h->stream;
     const int64_t m = h->m, n = h->n;
-    rorbk_status st;
     cudaMemcpyAsync(h->bb, b, m * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
     if (x0) cudaMemcpyAsync(h->xb, x0, n * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
     Ctl c;
@@ -457,7 +478,46 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
         c.tr_x = opt.trace->x;
         c.tr_dyn = opt.trace->dyn;
     }
-    cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s);
+    // the pageable source is copied before cudaMemcpyAsync returns
+    return cuda_check(h, cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s), "solve prologue");
+}
+
+// Enqueues on s the copy of the solution out of the workspace and of the
+// final loop state into *c.
+static cudaError_t solve_collect(rorbk_handle h, double *x, bool x_host, cudaStream_t s, Ctl *c) {
+    cudaError_t e = cudaMemcpyAsync(x, h->xb, h->n * sizeof(double),
+                                    x_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+// Status and result of a finished solve from its final loop state.
+static rorbk_status solve_result(rorbk_handle h, const Ctl &c, bool mixed, float ms,
+                                 rorbk_result *res) {
+    const rorbk_status st = c.status ? device_status(h, c.status) : (c.done ? RORBK_OK : RORBK_NOT_CONVERGED);
+    if (res) {
+        res->iters = c.iter;
+        res->rrn = c.rrn;
+        res->converged = c.done && c.status == 0;
+        res->status = st;
+        res->refinements = mixed ? c.outer : 0;
+        res->time_ms = ms;
+    }
+    return st;
+}
+
+static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0, bool b_host,
+                               double *x, bool x_host, double tol, int64_t maxit,
+                               const rorbk_options *opt_in, rorbk_result *res) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!x) return fail(h, RORBK_ERR_INVALID_ARG, "solve: x");
+    rorbk_options opt = opt_in ? *opt_in : defaults();
+    cudaSetDevice(h->device);
+    cudaStream_t s = opt.stream ? (cudaStream_t)opt.stream : h->stream;
+    rorbk_status st;
+    if ((st = solve_prepare(h, b, x0, b_host, tol, maxit, opt, s))) return st;
+    const bool mixed = opt.precision == RORBK_PREC_MIXED;
+    Ctl c;
     cudaGraphExec_t *exec = mixed ? &h->exec_mixed : &h->exec_fp64;
     if (!opt.host_loop && !*exec) {
         if ((st = cuda_check(h, cudaStreamSynchronize(s), "solve prologue"))) return st;
@@ -511,25 +571,14 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
         h->stream = saved;
     }
     cudaEventRecord(e1, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(x, h->xb, n * sizeof(double), x_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = solve_collect(h, x, x_host, s, &c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     float ms = 0.f;
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if ((st = cuda_check(h, e, "solve"))) return st;
-    st = c.status ? device_status(h, c.status) : (c.done ? RORBK_OK : RORBK_NOT_CONVERGED);
-    if (res) {
-        res->iters = c.iter;
-        res->rrn = c.rrn;
-        res->converged = c.done && c.status == 0;
-        res->status = st;
-        res->refinements = mixed ? c.outer : 0;
-        res->time_ms = ms;
-    }
-    return st;
+    return solve_result(h, c, mixed, ms, res);
 }
 
 rorbk_status rorbk_solve(rorbk_handle h, const double *b, const double *x0, double *x, double tol,
@@ -541,6 +590,175 @@ rorbk_status rorbk_solve_host(rorbk_handle h, const double *b_host, const double
                               double *x_host, double tol, int64_t maxit, const rorbk_options *opt,
                               rorbk_result *res) {
     return solve_impl(h, b_host, x0_host, true, x_host, true, tol, maxit, opt, res);
+}
+
+rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
+    if (!out) return RORBK_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!src) return RORBK_ERR_INVALID_ARG;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(src->device);
+    rorbk_status st = cuda_check(src, cudaStreamSynchronize(src->stream), "rorbk_clone");
+    if (st) { cudaSetDevice(cur); return st; }
+    if (!src->shared_setup) {   // the source's memory becomes jointly owned
+        src->shared_setup = std::make_shared<DevBlocks>();
+        src->shared_setup->device = src->device;
+        src->shared_setup->p.swap(src->allocs);
+    }
+    rorbk_ctx *c = new rorbk_ctx(*src);
+    c->err.clear();
+    c->allocs.clear();
+    c->tmp.clear();
+    c->bytes = 0;
+    c->exec_fp64 = c->exec_mixed = nullptr;
+    c->cap_stream = c->cap_stream2 = c->cap_stream3 = nullptr;
+    auto bail = [&](rorbk_status e) {
+        record_setup_error(c->err.empty() ? std::string("rorbk_clone failed") : c->err);
+        rorbk_free(c);
+        cudaSetDevice(cur);
+        return e;
+    };
+    if ((st = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream")))
+        return bail(st);
+    if ((st = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking), "stream")))
+        return bail(st);
+    if ((st = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream3, cudaStreamNonBlocking), "stream")))
+        return bail(st);
+    if ((st = alloc_workspace(c))) return bail(st);
+    if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "rorbk_clone"))) return bail(st);
+    *out = c;
+    cudaSetDevice(cur);
+    return RORBK_OK;
+}
+
+}  // extern "C"
+
+struct rorbk_batch_ctx {
+    int device = 0;
+    int precision = RORBK_PREC_FP64;
+    std::vector<rorbk_handle> hs;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+rorbk_status rorbk_batch_create(const rorbk_handle *hs, int32_t count, int32_t precision,
+                                rorbk_batch *out) {
+    if (!out) return RORBK_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto reject = [](const char *msg) {
+        record_setup_error(msg);
+        return RORBK_ERR_INVALID_ARG;
+    };
+    if (!hs || count < 1) return reject("rorbk_batch_create: no handles");
+    if (precision != RORBK_PREC_FP64 && precision != RORBK_PREC_MIXED)
+        return reject("rorbk_batch_create: unknown precision mode");
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i]) return reject("rorbk_batch_create: NULL handle");
+        if (hs[i]->device != hs[0]->device) return reject("rorbk_batch_create: handles on different devices");
+        if (precision == RORBK_PREC_MIXED && !hs[i]->precision_built)
+            return reject("rorbk_batch_create: mixed precision needs handles set up for it");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return reject("rorbk_batch_create: a handle appears twice (clone it instead)");
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(hs[0]->device);
+    rorbk_batch_ctx *bt = new rorbk_batch_ctx();
+    bt->device = hs[0]->device;
+    bt->precision = precision;
+    bt->hs.assign(hs, hs + count);
+    cudaGraph_t parent = nullptr;
+    rorbk_status st = cuda_check(hs[0], cudaGraphCreate(&parent, 0), "rorbk_batch_create");
+    for (int i = 0; i < count && st == RORBK_OK; ++i) {
+        rorbk_ctx *h = hs[i];
+        st = cuda_check(h, cudaStreamSynchronize(h->stream), "rorbk_batch_create");
+        if (st == RORBK_OK)
+            st = precision == RORBK_PREC_MIXED ? build_graph_mixed(h, parent) : build_graph_fp64(h, parent);
+        if (st) record_setup_error(h->err);
+    }
+    if (st == RORBK_OK) {
+        st = cuda_check(hs[0], cudaGraphInstantiate(&bt->exec, parent, 0), "rorbk_batch_create");
+        if (st) record_setup_error(hs[0]->err);
+    }
+    if (parent) cudaGraphDestroy(parent);
+    cudaSetDevice(cur);
+    if (st) {
+        rorbk_batch_free(bt);
+        return st;
+    }
+    *out = bt;
+    return RORBK_OK;
+}
+
+rorbk_status rorbk_batch_solve(rorbk_batch bt, const double *const *b, const double *const *x0,
+                               double *const *x, double tol, int64_t maxit,
+                               const rorbk_options *opt_in, const uint64_t *system_ids,
+                               rorbk_result *res) {
+    auto reject = [](rorbk_status e, const char *msg) {
+        record_setup_error(msg);
+        return e;
+    };
+    if (!bt || !b || !x) return reject(RORBK_ERR_INVALID_ARG, "rorbk_batch_solve: NULL batch, b or x");
+    rorbk_options opt = opt_in ? *opt_in : defaults();
+    if (opt.precision != bt->precision)
+        return reject(RORBK_ERR_INVALID_ARG, "rorbk_batch_solve: precision differs from the batch's");
+    if (opt.host_loop || opt.trace)
+        return reject(RORBK_ERR_UNSUPPORTED, "rorbk_batch_solve: no host loop or trace in a batch");
+    const int count = (int)bt->hs.size();
+    for (int i = 0; i < count; ++i)
+        if (!b[i] || !x[i]) return reject(RORBK_ERR_INVALID_ARG, "rorbk_batch_solve: NULL b[i] or x[i]");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(bt->device);
+    cudaStream_t s = opt.stream ? (cudaStream_t)opt.stream : bt->hs[0]->stream;
+    rorbk_status st = RORBK_OK;
+    for (int i = 0; i < count && st == RORBK_OK; ++i) {
+        rorbk_options oi = opt;
+        if (system_ids) oi.system_id = system_ids[i];
+        st = solve_prepare(bt->hs[i], b[i], x0 ? x0[i] : nullptr, false, tol, maxit, oi, s);
+        if (st) record_setup_error(bt->hs[i]->err);
+    }
+    if (st) { cudaSetDevice(cur); return st; }
+    std::vector<Ctl> cs(count);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaError_t e = cudaGraphLaunch(bt->exec, s);
+    cudaEventRecord(e1, s);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) e = solve_collect(bt->hs[i], x[i], false, s, &cs[i]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        st = cuda_check(bt->hs[0], e, "rorbk_batch_solve");
+        record_setup_error(bt->hs[0]->err);
+        cudaSetDevice(cur);
+        return st;
+    }
+    const bool mixed = opt.precision == RORBK_PREC_MIXED;
+    rorbk_status worst = RORBK_OK;
+    for (int i = 0; i < count; ++i) {
+        const rorbk_status si = solve_result(bt->hs[i], cs[i], mixed, ms, res ? res + i : nullptr);
+        if (si < 0 && worst >= 0) worst = si;
+        else if (si == RORBK_NOT_CONVERGED && worst == RORBK_OK) worst = si;
+    }
+    cudaSetDevice(cur);
+    return worst;
+}
+
+void rorbk_batch_free(rorbk_batch bt) {
+    if (!bt) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(bt->device);
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    cudaSetDevice(cur);
+    delete bt;
 }
 
 rorbk_status rorbk_get_info(rorbk_handle h, rorbk_info *info) {
