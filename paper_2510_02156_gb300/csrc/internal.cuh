@@ -25,11 +25,6 @@ constexpr int kShCap = 2048;            // dynamic block: shared-column entries 
 constexpr int kPairCap = 2048;          // dynamic block: Gram contributions in smem
 constexpr int kSPackedMax = 176;        // dynamic block: coupled rows factored in smem
 constexpr int kGPack = kSPackedMax * (kSPackedMax + 1) / 2;
-// Coupled sets of kClusterMinS < |S| <= kClusterMaxS rows are factored by a
-// cluster of kClusterCTAs blocks (one SM each) instead of one block.
-constexpr int kClusterMinS = kSPackedMax;
-constexpr int kClusterMaxS = 512;
-constexpr int kClusterCTAs = 8;
 
 // device error codes (ctl->status)
 constexpr int kDevOk = 0;
@@ -66,8 +61,7 @@ struct Ctl {
     int outer_done;
     int has_x0;
     // dynamic block bookkeeping
-    int dynE, dyn_nsh, dyn_nS, dyn_npair, dyn_nraw;
-    int dyn_cluster;       // this iteration's coupled rows are factored by the cluster kernel
+    int dynE, dyn_nsh, dyn_nS, dyn_npair, dyn_nraw, pad3_;
     int halt;              // no further iteration runs (converged, error or maxit)
     int pad2_;
 };
@@ -176,7 +170,6 @@ struct rorbk_ctx {
         unsigned long long *raw = nullptr, *skeys = nullptr, *pkeys = nullptr;
         long long pcap = 0;
         double *g = nullptr;
-        int *sidx = nullptr;    // [K] local rows of the coupled set, ascending
     } dyn;
     rorbk::Ctl *ctl = nullptr;
     rorbk::Ctl *ctl_in = nullptr;       // inner (FP32) loop state of the mixed form

@@ -28,8 +28,6 @@
 
 #include <algorithm>
 
-#include <cooperative_groups.h>
-
 #include "common.cuh"
 #include "internal.cuh"
 
@@ -694,7 +692,6 @@ struct Dyn {
     unsigned long long *pkeys;  // [pcap] Gram contributions (fallback)
     long long pcap;
     double *g;                  // [K(K+1)/2] packed Gram fallback
-    int *sidx;                  // [K] coupled set (local rows), for the cluster factor
 };
 
 __device__ __forceinline__ long long pidx(int i, int j) {     // packed lower, row-major
@@ -1177,17 +1174,7 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
     __syncthreads();
     for (int q = tid; q < nS; q += blockDim.x) z[q] = (double)r[D.I[sidx[q]]];
     __syncthreads();
-    // Large coupled sets go to the cluster kernel, which runs next: it reads
-    // the packed Gram from D.g, the right-hand side from D.y at the coupled
-    // rows and the coupled set from D.sidx, and writes y there.
-    const bool clus = nS > kClusterMinS && nS <= kClusterMaxS;
-    if (clus) {
-        for (int q = tid; q < nS; q += blockDim.x) {
-            D.sidx[q] = sidx[q];
-            D.y[sidx[q]] = z[q];
-        }
-        if (tid == 0) ctl->dyn_cluster = 1;
-    } else if (nS > 0) {
+    if (nS > 0) {
         if (nS <= kSymMax) symbolic(G, nS, S, &s_nlev, &s_uselev);
         else if (tid == 0) s_uselev = 0;
         __syncthreads();
@@ -1199,8 +1186,7 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
             column_solve(G, nS, z, cz, rz);
         }
     }
-    if (!clus)
-        for (int q = tid; q < nS; q += blockDim.x) D.y[sidx[q]] = z[q];
+    for (int q = tid; q < nS; q += blockDim.x) D.y[sidx[q]] = z[q];
     if (keys != D.skeys)
         for (int q = tid; q < nsh; q += blockDim.x) D.skeys[q] = keys[q];
     if (tid == 0) {
@@ -1209,182 +1195,10 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
         ctl->dyn_npair = npk;
         if (ctl->tr_dyn && ctl->iter < ctl->trace_cap) {
             int *t = ctl->tr_dyn + 4 * ctl->iter;
-            t[0] = E; t[1] = nsh; t[2] = nS;
-            t[3] = clus ? -2 : (nS > 0 && nS <= kSymMax && s_uselev ? s_nlev : -1);
+            t[0] = E; t[1] = nsh; t[2] = nS; t[3] = nS > 0 && nS <= kSymMax && s_uselev ? s_nlev : -1;
         }
         if (s_bad) set_status(&ctl->status, kDevNotSpd);
     }
-}
-
-// ---- the cluster factor of a large coupled set ------------------------
-// Cholesky of G = (A_I A_I^T + mu I) on a coupled set of kClusterMinS <
-// nS <= kClusterMaxS rows and the two triangular solves for y, spread over a
-// cluster of kClusterCTAs blocks so that the O(nS^3) update runs on that many
-// SMs.  Column j of L lives in the shared memory of block j mod kClusterCTAs
-// (rows j..nS-1, contiguous); the others read it through distributed shared
-// memory.  Every entry receives the same fused operations in the same order
-// as the one-block right-looking factorisation and column-oriented solves
-// (zero multipliers skipped), so the result is identical to theirs.
-//
-// Per column j: its owner has applied columns 0..j-1 and finalised it
-// (sqrt, divisions); a split cluster barrier publishes it; each block copies
-// it, the owner of column j+1 first updates and finalises that column and
-// arrives for the next phase, then every block updates the rest of its own
-// columns.  Block 0 carries the forward solve as an extra column.  The
-// backward solve broadcasts y_j, computed by column j's owner, to every block,
-// which then updates the entries it owns.
-namespace {
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_arrive() {
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// generic address of `p` (a shared-memory address of this block) in block `rank`
-template <typename P>
-__device__ __forceinline__ P *cluster_map(P *p, unsigned rank) {
-    return cooperative_groups::this_cluster().map_shared_rank(p, rank);
-}
-// offset of the t-th column owned by block `rank` (columns rank, rank + C, ...)
-__device__ __forceinline__ int cl_coff(int t, int rank, int nS) {
-    return t * (nS - rank) - kClusterCTAs * t * (t - 1) / 2;
-}
-}  // namespace
-
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(512, 1)
-    k_dyn_chol_cluster(Dyn D, Ctl *ctl) {
-    extern __shared__ double csm[];
-    __shared__ int s_bad;
-    __shared__ double s_y;
-    if (!ctl->dyn_cluster || ctl->done || ctl->halt) return;   // the same for every block
-    const int nS = ctl->dyn_nS;
-    const int rank = (int)cluster_rank();
-    const int tid = threadIdx.x, nt = blockDim.x;
-    constexpr int C = kClusterCTAs;
-    const int nmine = nS > rank ? (nS - 1 - rank) / C + 1 : 0;
-    // the vectors first, at the same offsets in every block (a mapped address
-    // keeps its offset), then this block's columns
-    double *colbuf = csm;                                // [nS] column j, indexed by row
-    double *zz = colbuf + kClusterMaxS;                  // [nS] right-hand side / solution
-    double *yv = zz + kClusterMaxS;                      // [nS] y_j as broadcast
-    double *Lc = yv + kClusterMaxS;                      // own columns
-    if (tid == 0) s_bad = 0;
-    for (int t = 0; t < nmine; ++t) {
-        const int j = rank + t * C;
-        double *c = Lc + cl_coff(t, rank, nS);
-        for (int i = j + tid; i < nS; i += nt) c[i - j] = D.g[pidx(i, j)];
-    }
-    for (int q = tid; q < nS; q += nt) zz[q] = D.y[D.sidx[q]];
-    __syncthreads();
-    auto finalize = [&](int j) {                          // owner only, all threads
-        double *c = Lc + cl_coff((j - rank) / C, rank, nS);
-        if (tid == 0) {
-            double d = c[0];
-            if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
-            c[0] = sqrt(d);
-        }
-        __syncthreads();
-        const double l = c[0];
-        for (int i = j + 1 + tid; i < nS; i += nt) {
-            const double v = c[i - j];
-            if (v != 0.0) c[i - j] = v / l;
-        }
-        __syncthreads();
-    };
-    if (rank == 0 && nS > 0) finalize(0);
-    cluster_arrive();
-    for (int j = 0; j < nS; ++j) {
-        cluster_wait();                                   // column j is final
-        const int o = j % C;
-        const double *rc = cluster_map(Lc + cl_coff((j - o) / C, o, nS), (unsigned)o);
-        for (int i = j + tid; i < nS; i += nt) colbuf[i] = rc[i - j];
-        __syncthreads();
-        const int jn = j + 1;
-        if (jn < nS && jn % C == rank) {                  // the next column first
-            double *c = Lc + cl_coff((jn - rank) / C, rank, nS);
-            const double lk = colbuf[jn];
-            if (lk != 0.0)
-                for (int i = jn + tid; i < nS; i += nt) {
-                    const double li = colbuf[i];
-                    if (li != 0.0) c[i - jn] = __fma_rn(-li, lk, c[i - jn]);
-                }
-            __syncthreads();
-            finalize(jn);
-        }
-        if (jn < nS) cluster_arrive();
-        if (rank == 0) {                                  // forward solve, column j
-            if (tid == 0) zz[j] = zz[j] / colbuf[j];
-            __syncthreads();
-            const double wj = zz[j];
-            for (int i = jn + tid; i < nS; i += nt) {
-                const double li = colbuf[i];
-                if (li != 0.0) zz[i] = __fma_rn(-li, wj, zz[i]);
-            }
-        }
-        // the rest of this block's columns k > j + 1, entries i >= k
-        for (int t = (jn + 1 - rank + C - 1) / C; t < nmine; ++t) {
-            const int k = rank + t * C;
-            if (k <= jn) continue;
-            const double lk = colbuf[k];
-            if (lk == 0.0) continue;
-            double *c = Lc + cl_coff(t, rank, nS);
-            for (int i = k + tid; i < nS; i += nt) {
-                const double li = colbuf[i];
-                if (li != 0.0) c[i - k] = __fma_rn(-li, lk, c[i - k]);
-            }
-        }
-        __syncthreads();
-    }
-    // backward solve: every block takes block 0's forward result
-    cluster_arrive();
-    cluster_wait();
-    if (rank != 0) {
-        const double *z0 = cluster_map(zz, 0u);
-        for (int q = tid; q < nS; q += nt) zz[q] = z0[q];
-    }
-    cluster_arrive();                                     // block 0's copy is read before
-    cluster_wait();                                       // block 0 changes it
-    for (int j = nS - 1; j >= 0; --j) {
-        const int o = j % C;
-        if (rank == o) {
-            if (tid == 0) {
-                const double l = Lc[cl_coff((j - rank) / C, rank, nS)];
-                s_y = zz[j] / l;
-                zz[j] = s_y;
-            }
-            __syncthreads();
-            if (tid < C) *cluster_map(yv + j, (unsigned)tid) = s_y;
-        }
-        cluster_arrive();
-        cluster_wait();                                   // y_j is everywhere
-        const double yj = yv[j];
-        // own columns i < j: entry (j, i) of L updates z_i
-        for (int t = tid; t < nmine; t += nt) {
-            const int i = rank + t * C;
-            if (i >= j) break;
-            const double lji = Lc[cl_coff(t, rank, nS) + (j - i)];
-            if (lji != 0.0) zz[i] = __fma_rn(-lji, yj, zz[i]);
-        }
-        __syncthreads();
-    }
-    for (int t = tid; t < nmine; t += nt) {
-        const int i = rank + t * C;
-        D.y[D.sidx[i]] = zz[i];
-    }
-    if (tid == 0 && s_bad) set_status(&ctl->status, kDevNotSpd);
-    cluster_arrive();                                     // no block leaves while others
-    cluster_wait();                                       // may still read its memory
-}
-
-size_t cluster_smem_bytes() {
-    // the largest share of columns (block 0 at nS = kClusterMaxS) + 3 vectors
-    const int n = kClusterMaxS, t = (n - 1) / kClusterCTAs + 1;
-    return ((size_t)(t * n - kClusterCTAs * t * (t - 1) / 2) + 3 * (size_t)kClusterMaxS) * sizeof(double);
 }
 
 // Gathers the nonzeros of A_I (row order), marks each column's lowest entry
@@ -1486,7 +1300,6 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
                                                      cudaGraphConditionalHandle hcond) {
     __shared__ int is_last;
     if (ctl->done || ctl->status || ctl->halt) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->dyn_cluster = 0;
         if (count_iter && blockIdx.x == 0) end_iteration<T>(x, n, ctl, use_cond, hcond);
         return;
     }
@@ -1512,10 +1325,7 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (threadIdx.x == 0) {
-        ctl->ticket = 0;
-        ctl->dyn_cluster = 0;
-    }
+    if (threadIdx.x == 0) ctl->ticket = 0;
     __syncthreads();
     if (count_iter) end_iteration<T>(x, n, ctl, use_cond, hcond);
 }
@@ -1586,7 +1396,6 @@ __global__ void __launch_bounds__(256) k_inner_prep(const double *__restrict__ r
         in->ticket = 0;
         in->n_in = 0;
         in->n_eq = 0;
-        in->dyn_cluster = 0;
         in->trace_cap = 0;
         in->tr_tau = nullptr;
         in->tr_rrn = nullptr;
@@ -1632,8 +1441,7 @@ static size_t factor_smem_bytes() {
 static Dyn dyn_bufs(rorbk_ctx *h) {
     return Dyn{h->dyn.I, h->dyn.estart, h->dyn.gdiag, h->dyn.y, h->dyn.ecol, h->dyn.eval,
                h->dyn.erow, h->dyn.ecap, h->dyn.owner, h->dyn.shared, h->dyn.segpos,
-               h->dyn.epoch, h->dyn.raw, h->dyn.skeys, h->dyn.pkeys, h->dyn.pcap, h->dyn.g,
-               h->dyn.sidx};
+               h->dyn.epoch, h->dyn.raw, h->dyn.skeys, h->dyn.pkeys, h->dyn.pcap, h->dyn.g};
 }
 
 static int grid_stream(rorbk_ctx *h, int m) {
@@ -1663,8 +1471,6 @@ void configure_kernels() {
                          (int)factor_smem_bytes());
     cudaFuncSetAttribute(k_dyn_mark<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)factor_smem_bytes());
-    cudaFuncSetAttribute(k_dyn_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)cluster_smem_bytes());
 }
 
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
@@ -1679,8 +1485,6 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
     Mat<T> A = make_mat<T>(h);
     k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
                                                                         check_done);
-    if (h->K > kClusterMinS)   // a coupled set can exceed one block's factor
-        k_dyn_chol_cluster<<<kClusterCTAs, 512, cluster_smem_bytes(), h->stream>>>(dyn_bufs(h), ctl);
     k_dyn_scatter<T><<<2 * h->num_sms, 512, 0, h->stream>>>(x, (int)h->n, dyn_bufs(h), ctl,
                                                            count_iter, use_cond,
                                                            (cudaGraphConditionalHandle)hcond);

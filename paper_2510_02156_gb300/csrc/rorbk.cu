@@ -255,9 +255,8 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         D.skeys = (unsigned long long *)dev_alloc(h, np2 * sizeof(unsigned long long));
         D.pkeys = (unsigned long long *)dev_alloc(h, D.pcap * sizeof(unsigned long long));
         D.g = (double *)dev_alloc(h, ((size_t)h->K * (h->K + 1) / 2) * sizeof(double));
-        D.sidx = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
         if (!D.I || !D.estart || !D.gdiag || !D.y || !D.ecol || !D.eval || !D.erow || !D.owner ||
-            !D.shared || !D.epoch || !D.segpos || !D.raw || !D.skeys || !D.pkeys || !D.g || !D.sidx)
+            !D.shared || !D.epoch || !D.segpos || !D.raw || !D.skeys || !D.pkeys || !D.g)
             return fail(h, RORBK_ERR_OOM, "dynamic-block workspace");
         cudaMemsetAsync(D.owner, 0, n * sizeof(unsigned long long), s);   // epoch 0: never
         cudaMemsetAsync(D.shared, 0, n * sizeof(unsigned), s);
