@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=1)
     p.add_argument("--oracle-iters", type=int, default=60)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched measurement (16 right-hand sides of a 65,536-row "
+                        "system, and 16 systems of 5,000-200,000 rows, each in one launch)")
     p.add_argument("--no-autograd", action="store_true",
                    help="skip the differentiable-solve measurement (forward + adjoint backward "
                         "on the 262,144-unknown power-law system)")
@@ -295,6 +298,7 @@ def run_ours(args, rank, world, local):
     e2e_s = time.perf_counter() - t1
 
     ag = None if args.no_autograd else autograd_measurement(args)
+    batched = None if args.no_batched else batched_measurement(args)
 
     # the sparse residual kernels timed alone, the same kernel and grid as in
     # the solve: FP32 (the inner solve, every iteration) and FP64
@@ -331,6 +335,7 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": 8 * s.n},
         "gpu_launches": launches * args.steps,
         "autograd": ag,
+        "batched": batched,
         "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
                      "frac": ach32 / peak,
@@ -352,6 +357,79 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _timed(fn, torch):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, out
+
+
+def _batch_vs_sequential(handles, bs, tol, maxit, precision, torch, B, system_ids):
+    """One batched launch against the same solves one after another (each
+    solve's own graph); returns the two wall times and the batch's results."""
+    xs = [torch.empty(h.info.n, dtype=torch.float64, device="cuda") for h in handles]
+    with B.Batch(handles, precision=precision) as bt:
+        bt.solve(bs, xs, tol=tol, maxit=maxit, seed=1, system_ids=system_ids)     # warm-up
+        t_b, (st, res) = _timed(lambda: bt.solve(bs, xs, tol=tol, maxit=maxit, seed=1,
+                                                 system_ids=system_ids), torch)
+    for h, b, x, sid in zip(handles, bs, xs, system_ids):
+        h.solve(b, x, tol=tol, maxit=maxit, seed=1, system_id=sid, precision=precision)
+    t_s, seq = _timed(lambda: [h.solve(b, x, tol=tol, maxit=maxit, seed=1, system_id=sid,
+                                       precision=precision)
+                               for h, b, x, sid in zip(handles, bs, xs, system_ids)], torch)
+    same = all(r.iters == q.iters for r, q in zip(res, seq))
+    return {"batched_s": t_b, "sequential_s": t_s, "speedup": t_s / t_b,
+            "iters": [int(r.iters) for r in res],
+            "all_converged": bool(all(r.converged for r in res)),
+            "same_iterations_as_single_solves": bool(same)}
+
+
+def batched_measurement(args):
+    """The batched form: (a) 16 right-hand sides of one power-law system
+    (n = 65,536, 256 blocks of 256 rows; the source handle and 15 clones, one
+    shared sampled block stream); (b) 16 power-law systems with n drawn
+    uniformly from [5,000, 200,000] and 3-50 off-diagonals per row, blocks of
+    256 rows, one right-hand side each.  Each form runs as one graph launch
+    and, for comparison, as the same solves one after another; mixed
+    precision and FP64."""
+    import torch
+    import scipy.sparse as sp
+    from paper_2510_02156_gb300 import binding as B
+    from paper_2510_02156_gb300 import workloads as W
+    out = {}
+    s = W.powerlaw(n=1 << 16, num_blocks=256, seed=5, lam=args.lam, tol=args.tol,
+                   cache=args.cache)
+    A = sp.csr_matrix((s.values.astype(np.float64), s.col_idx, s.row_ptr), shape=(s.m, s.n))
+    rng = np.random.default_rng(41)
+    bs = [torch.as_tensor(A @ rng.standard_normal(s.n), device="cuda") for _ in range(16)]
+    h0 = B.Handle.from_system(s, precision=B.PREC_MIXED)
+    hs = [h0] + [h0.clone() for _ in range(15)]
+    rhs = {"workload": f"16 right-hand sides, power-law CSR n={s.n}, nnz={s.nnz}, 256 blocks of 256, "
+                       f"lambda={s.lam:g}, tol={s.tol:g}"}
+    for name, prec in (("mixed", B.PREC_MIXED), ("fp64", B.PREC_FP64)):
+        rhs[name] = _batch_vs_sequential(hs, bs, s.tol, args.maxit, prec, torch, B, [0] * 16)
+    for h in hs:
+        h.close()
+    out["multi_rhs"] = rhs
+    sizes = np.random.default_rng(42).integers(5000, 200001, 16)
+    systems = [W.powerlaw(n=int(n), num_blocks=max(1, int(n) // 256), seed=100 + i, dmax=50,
+                          lam=args.lam, tol=args.tol, cache=args.cache)
+               for i, n in enumerate(sizes)]
+    hs = [B.Handle.from_system(q, precision=B.PREC_MIXED) for q in systems]
+    bs = [torch.as_tensor(q.b, device="cuda") for q in systems]
+    ms = {"workload": (f"16 power-law CSR systems, n in [5000, 200000] (total {int(sizes.sum())} rows, "
+                       f"{sum(q.nnz for q in systems)} nnz), 3-50 off-diagonals per row, blocks of "
+                       f"256 rows, lambda={args.lam:g}, tol={args.tol:g}")}
+    for name, prec in (("mixed", B.PREC_MIXED), ("fp64", B.PREC_FP64)):
+        ms[name] = _batch_vs_sequential(hs, bs, args.tol, args.maxit, prec, torch, B,
+                                        list(range(16)))
+    for h in hs:
+        h.close()
+    out["multi_system"] = ms
+    return out
 
 
 def autograd_measurement(args):
