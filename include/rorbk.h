@@ -64,14 +64,24 @@ enum { RORBK_F64 = 0, RORBK_F32 = 1 };
  *           FP64, an FP32 ROR-BK solve of A d = r to a relative residual of
  *           inner_tol (or inner_maxit iterations), x += d in FP64, repeated
  *           until ||b - A x|| / ||b|| <= tol.  The block operators W_t and the
- *           dynamic block's Cholesky are formed in FP64 and applied in FP32. */
+ *           dynamic block's Cholesky are formed in FP64 and applied in FP32.
+ *           MIXED needs every block to have at most as many rows as A has
+ *           columns (s <= n): with s > n, A_t A_t^T is singular, W_t carries
+ *           1/mu on its null space, and FP32 rounding there is amplified
+ *           until the inner solve diverges; such solves return
+ *           RORBK_ERR_UNSUPPORTED. */
 enum { RORBK_PREC_FP64 = 0, RORBK_PREC_MIXED = 1 };
 
 /* Matrix description for rorbk_setup.
  *   CSR  : row_ptr[m+1] (int32, row_ptr[0] = 0, non-decreasing, nnz < 2^31),
  *          col_idx[nnz] (int32, strictly ascending inside each row, in [0,n)),
  *          values[nnz] (dtype).
- *   DENSE: values is row-major m x n with leading dimension ld >= n.
+ *   DENSE: values is row-major m x n with leading dimension ld >= n
+ *          (row_ptr, col_idx and nnz are ignored; m * n < 2^31).  The handle
+ *          keeps it as CSR with all m * n entries stored, so every step runs
+ *          the same arithmetic as for a sparse A, except the dynamic block:
+ *          all of its rows share all columns, and its Gram, Cholesky and
+ *          A_I^T y run as dense kernels.
  * Pointers are host memory unless on_device != 0 (then CUDA device memory of
  * the current device).  rorbk_setup copies A into memory the handle owns; the
  * caller may free its arrays when setup returns. */

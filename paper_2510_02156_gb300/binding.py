@@ -157,17 +157,23 @@ class Handle:
     def __init__(self, row_ptr, col_idx, values, m, n, num_blocks, lam, precision=PREC_FP64,
                  offsets=None, stream=None):
         self._keep = []
-        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
-        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
         vals = np.ascontiguousarray(values)
         if vals.dtype == np.float32:
             dt = F32
         else:
             vals = np.ascontiguousarray(vals, dtype=np.float64)
             dt = F64
-        self._keep += [rp, ci, vals]
-        A = Matrix(FORMAT_CSR, dt, m, n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data,
-                   vals.ctypes.data, 0, 0, 0)
+        if row_ptr is None:            # dense row-major m x n
+            if vals.shape != (m, n):
+                raise ValueError("dense values must have shape (m, n)")
+            self._keep.append(vals)
+            A = Matrix(FORMAT_DENSE, dt, m, n, m * n, None, None, vals.ctypes.data, n, 0, 0)
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+            self._keep += [rp, ci, vals]
+            A = Matrix(FORMAT_CSR, dt, m, n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data,
+                       vals.ctypes.data, 0, 0, 0)
         offs = None
         if offsets is not None:
             offs = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -226,8 +232,12 @@ class Handle:
 
     @classmethod
     def from_system(cls, system, lam=None, precision=PREC_FP64, **kw):
+        lam = system.lam if lam is None else lam
+        if system.is_dense:
+            return cls(None, None, system.dense, system.m, system.n, system.num_blocks, lam,
+                       precision, **kw)
         return cls(system.row_ptr, system.col_idx, system.values, system.m, system.n,
-                   system.num_blocks, system.lam if lam is None else lam, precision, **kw)
+                   system.num_blocks, lam, precision, **kw)
 
     def close(self):
         if getattr(self, "h", None):

@@ -192,6 +192,7 @@ void *dev_alloc(rorbk_ctx *h, size_t bytes);
 // setup (kernels_setup.cu)
 rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &host_row_ptr);
 void widen_values(rorbk_ctx *h, int dtype);   // FP32 <-> FP64 value copies
+void fill_dense_columns(rorbk_ctx *h);        // column indices of a dense A held as CSR
 
 // iteration launches (kernels_iter.cu); all enqueue on h->stream
 void configure_kernels();

@@ -1330,6 +1330,101 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
     if (count_iter) end_iteration<T>(x, n, ctl, use_cond, hcond);
 }
 
+// ---- the dynamic update of a dense A -------------------------------------
+// Every row of I holds every column, so all of I is coupled and the Gram is
+// dense: G = A_I A_I^T + mu I (packed lower, D.g), each entry one fused chain
+// over ascending columns as in the definition; one block factors it and
+// solves (the same right-looking Cholesky and column-oriented solves as the
+// sparse coupled set); x += A_I^T y, each column summed over ascending rows
+// of I, then added.
+constexpr int kGT = 16;         // Gram tile: kGT x kGT entries per block
+constexpr int kGC = 64;         // columns staged per step
+
+__global__ void __launch_bounds__(kGT * kGT) k_dyn_dense_gram(const double *__restrict__ val, int n,
+                                                              int K, double mu, Dyn D, Ctl *ctl) {
+    __shared__ double sa[kGT][kGC + 1], sb[kGT][kGC + 1];
+    if (ctl->done || ctl->status || ctl->halt) return;
+    int t = blockIdx.x, ti = 0;                 // tile (ti, tj), tj <= ti
+    while (t > ti) { t -= ti + 1; ++ti; }
+    const int tj = t, tid = threadIdx.x;
+    const int ta = tid / kGT, tb = tid % kGT;
+    const int a = ti * kGT + ta, b = tj * kGT + tb;
+    double acc = 0.0;
+    for (int c0 = 0; c0 < n; c0 += kGC) {
+        const int w = min(kGC, n - c0);
+        for (int q = tid; q < kGT * kGC; q += blockDim.x) {
+            const int rr = q / kGC, cc = q % kGC;
+            const int ra = ti * kGT + rr, rb = tj * kGT + rr;
+            sa[rr][cc] = (ra < K && cc < w) ? val[(long long)D.I[ra] * n + c0 + cc] : 0.0;
+            sb[rr][cc] = (rb < K && cc < w) ? val[(long long)D.I[rb] * n + c0 + cc] : 0.0;
+        }
+        __syncthreads();
+        if (a < K && b <= a)
+            for (int cc = 0; cc < w; ++cc) acc = __fma_rn(sa[ta][cc], sb[tb][cc], acc);
+        __syncthreads();
+    }
+    if (a < K && b <= a) D.g[pidx(a, b)] = a == b ? __dadd_rn(acc, mu) : acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_dyn_dense_factor(const T *__restrict__ r, int K, Dyn D,
+                                                           Ctl *ctl) {
+    __shared__ double z[kMaxDynRows];
+    __shared__ unsigned char cz[kMaxDynRows], rz[kMaxDynRows];
+    __shared__ int s_bad;
+    if (ctl->done || ctl->status || ctl->halt) return;
+    for (int q = threadIdx.x; q < K; q += blockDim.x) {
+        z[q] = (double)r[D.I[q]];
+        cz[q] = 0;
+        rz[q] = 0;
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    packed_cholesky(D.g, K, &s_bad);
+    column_solve(D.g, K, z, cz, rz);
+    for (int q = threadIdx.x; q < K; q += blockDim.x) D.y[q] = z[q];
+    if (threadIdx.x == 0 && s_bad) set_status(&ctl->status, kDevNotSpd);
+}
+
+template <typename T>
+__device__ __forceinline__ T dense_value(const double *v64, const float *v32, long long p);
+template <>
+__device__ __forceinline__ double dense_value<double>(const double *v64, const float *, long long p) {
+    return v64[p];
+}
+template <>
+__device__ __forceinline__ float dense_value<float>(const double *, const float *v32, long long p) {
+    return v32[p];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dyn_dense_scatter(const double *__restrict__ v64,
+                                                           const float *__restrict__ v32, T *x, int n,
+                                                           int K, Dyn D, Ctl *ctl, int count_iter,
+                                                           int use_cond,
+                                                           cudaGraphConditionalHandle hcond) {
+    __shared__ int is_last;
+    if (ctl->done || ctl->status || ctl->halt) {
+        if (count_iter && blockIdx.x == 0) end_iteration<T>(x, n, ctl, use_cond, hcond);
+        return;
+    }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        T acc = T(0);
+        for (int a = 0; a < K; ++a)
+            acc = Ar<T>::fma(dense_value<T>(v64, v32, (long long)D.I[a] * n + c), as<T>(D.y[a]), acc);
+        x[c] = Ar<T>::add(x[c], acc);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) ctl->ticket = 0;
+    __syncthreads();
+    if (count_iter) end_iteration<T>(x, n, ctl, use_cond, hcond);
+}
+
 // Sampler probe (single-step API).
 __global__ void k_sample_probe(const double *cdf, int k, uint64_t seed, uint64_t sysid,
                                long long it, long long l, long long *out) {
@@ -1482,6 +1577,17 @@ void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, in
 template <typename T>
 static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int check_done,
                                 int count_iter, int use_cond, unsigned long long hcond) {
+    if (h->format == RORBK_FORMAT_DENSE) {
+        const int K = h->K, T16 = (K + kGT - 1) / kGT;
+        k_dyn_dense_gram<<<T16 * (T16 + 1) / 2, kGT * kGT, 0, h->stream>>>(h->val, (int)h->n, K, h->mu,
+                                                                          dyn_bufs(h), ctl);
+        k_dyn_dense_factor<T><<<1, 1024, 0, h->stream>>>(r, K, dyn_bufs(h), ctl);
+        const int g = std::max(1, std::min(4 * h->num_sms, (int)((h->n + 255) / 256)));
+        k_dyn_dense_scatter<T><<<g, 256, 0, h->stream>>>(h->val, h->val32, x, (int)h->n, K, dyn_bufs(h),
+                                                          ctl, count_iter, use_cond,
+                                                          (cudaGraphConditionalHandle)hcond);
+        return;
+    }
     Mat<T> A = make_mat<T>(h);
     k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
                                                                         check_done);

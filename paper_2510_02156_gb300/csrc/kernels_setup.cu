@@ -417,6 +417,18 @@ __global__ void k_sell_fill(const int *__restrict__ rowptr, const int *__restric
     }
 }
 
+// A dense A held as CSR: entry p = i*n + c has column c.
+__global__ void k_dense_cols(int *__restrict__ col, long long nnz, int n) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nnz;
+         p += (long long)gridDim.x * blockDim.x)
+        col[p] = (int)(p % n);
+}
+
+void fill_dense_columns(rorbk_ctx *h) {
+    const int g = std::max(1, std::min(8 * h->num_sms, (int)((h->nnz + 255) / 256)));
+    k_dense_cols<<<g, 256, 0, h->stream>>>(h->col, h->nnz, (int)h->n);
+}
+
 // ---------------------------------------------------------------- driver
 static rorbk_status scan_device(rorbk_ctx *h, int *d, long long n, int *grand_total_host) {
     const int nt = 256;

@@ -329,12 +329,18 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     *out = nullptr;
     if (!A || !part) return RORBK_ERR_INVALID_ARG;
     rorbk_options opt = opt_in ? *opt_in : defaults();
-    if (A->format != RORBK_FORMAT_CSR) return RORBK_ERR_UNSUPPORTED;
+    if (A->format != RORBK_FORMAT_CSR && A->format != RORBK_FORMAT_DENSE) return RORBK_ERR_UNSUPPORTED;
     if (A->dtype != RORBK_F64 && A->dtype != RORBK_F32) return RORBK_ERR_INVALID_ARG;
-    if (A->m < 1 || A->n < 1 || A->m >= (1LL << 31) || A->n >= (1LL << 31) || A->nnz < 0 ||
-        A->nnz >= (1LL << 31) || !A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->values)))
+    const bool dense = A->format == RORBK_FORMAT_DENSE;
+    if (A->m < 1 || A->n < 1 || A->m >= (1LL << 31) || A->n >= (1LL << 31)) return RORBK_ERR_INVALID_ARG;
+    if (dense) {
+        // every entry is stored: the matrix is held as CSR with all m*n entries
+        if (!A->values || A->ld < A->n || A->m * A->n >= (1LL << 31)) return RORBK_ERR_INVALID_ARG;
+    } else if (A->nnz < 0 || A->nnz >= (1LL << 31) || !A->row_ptr ||
+               (A->nnz > 0 && (!A->col_idx || !A->values))) {
         return RORBK_ERR_INVALID_ARG;
-    const int64_t m = A->m, n = A->n, nnz = A->nnz;
+    }
+    const int64_t m = A->m, n = A->n, nnz = dense ? A->m * A->n : A->nnz;
     const int k = part->num_blocks;
     if (k < 1 || k > m || k > 65536) return RORBK_ERR_INVALID_ARG;
 
@@ -381,7 +387,9 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     // copy A (CSR) and a host view of row_ptr for the tiling
     std::vector<int> hrp(m + 1);
     const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (A->on_device) {
+    if (dense) {
+        for (int64_t i = 0; i <= m; ++i) hrp[i] = (int)(i * n);
+    } else if (A->on_device) {
         if ((st = cuda_check(h, cudaMemcpy(hrp.data(), A->row_ptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost), "row_ptr")))
             return bail(st);
     } else {
@@ -403,10 +411,22 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     h->crowsum = (double *)dev_alloc(h, k * sizeof(double));
     if (!h->rowptr || !h->col || !h->val || !h->off || !h->cdf || !h->crowsum) return bail(fail(h, RORBK_ERR_OOM, "matrix"));
     cudaStream_t s = h->stream;
-    cudaMemcpyAsync(h->rowptr, A->row_ptr, (m + 1) * sizeof(int), kind, s);
-    if (nnz) cudaMemcpyAsync(h->col, A->col_idx, nnz * sizeof(int), kind, s);
+    // rows of a dense A are copied from its leading dimension into n-entry rows
+    const size_t esz = A->dtype == RORBK_F64 ? sizeof(double) : sizeof(float);
+    auto copy_values = [&](void *dst) {
+        if (!nnz) return;
+        if (dense) cudaMemcpy2DAsync(dst, n * esz, A->values, A->ld * esz, n * esz, m, kind, s);
+        else cudaMemcpyAsync(dst, A->values, nnz * esz, kind, s);
+    };
+    if (dense) {
+        cudaMemcpyAsync(h->rowptr, hrp.data(), (m + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+        fill_dense_columns(h);
+    } else {
+        cudaMemcpyAsync(h->rowptr, A->row_ptr, (m + 1) * sizeof(int), kind, s);
+        if (nnz) cudaMemcpyAsync(h->col, A->col_idx, nnz * sizeof(int), kind, s);
+    }
     if (A->dtype == RORBK_F64) {
-        if (nnz) cudaMemcpyAsync(h->val, A->values, nnz * sizeof(double), kind, s);
+        copy_values(h->val);
         if (h->precision_built) {
             h->val32 = (float *)dev_alloc(h, (nnz + 16) * sizeof(float));
             if (!h->val32) return bail(fail(h, RORBK_ERR_OOM, "fp32 values"));
@@ -414,7 +434,7 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     } else {
         h->val32 = (float *)dev_alloc(h, (nnz + 16) * sizeof(float));
         if (!h->val32) return bail(fail(h, RORBK_ERR_OOM, "fp32 values"));
-        if (nnz) cudaMemcpyAsync(h->val32, A->values, nnz * sizeof(float), kind, s);
+        copy_values(h->val32);
     }
     {
         std::vector<int> off32(k + 1);
@@ -456,6 +476,11 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
                     "mixed precision needs a handle set up with precision = RORBK_PREC_MIXED");
     if (mixed && (!(opt.inner_tol > 0) || opt.inner_maxit < 1))
         return fail(h, RORBK_ERR_INVALID_ARG, "inner_tol > 0 and inner_maxit >= 1");
+    if (mixed && h->smax > h->n)
+        return fail(h, RORBK_ERR_UNSUPPORTED,
+                    "mixed precision needs blocks of at most n rows: with s > n the stored "
+                    "inverse scales the null space of A_t A_t^T by 1/mu, which FP32 cannot "
+                    "carry (the s >= n form of Lemma 1 is not built)");
     const int64_t m = h->m, n = h->n;
     cudaMemcpyAsync(h->bb, b, m * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
     if (x0) cudaMemcpyAsync(h->xb, x0, n * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
@@ -874,6 +899,7 @@ rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I, const double
     cudaSetDevice(h->device);
     cudaMemsetAsync(&h->ctl->status, 0, sizeof(int), h->stream);
     cudaMemsetAsync(&h->ctl->done, 0, sizeof(int), h->stream);
+    cudaMemsetAsync(&h->ctl->halt, 0, sizeof(int), h->stream);
     launch_dynamic_given(h, I, r, x);
     rorbk_status st = cuda_check(h, cudaGetLastError(), "dynamic update");
     int code = 0;
