@@ -57,6 +57,10 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=1)
     p.add_argument("--oracle-iters", type=int, default=60)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-dense", action="store_true",
+                   help="skip the dense measurement (A = U diag(s) V^T, 200,000 x 2,048, "
+                        "781 blocks of 256 rows; a fixed number of iterations)")
+    p.add_argument("--dense-iters", type=int, default=100)
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched measurement (16 right-hand sides of a 65,536-row "
                         "system, and 16 systems of 5,000-200,000 rows, each in one launch)")
@@ -299,6 +303,7 @@ def run_ours(args, rank, world, local):
 
     ag = None if args.no_autograd else autograd_measurement(args)
     batched = None if args.no_batched else batched_measurement(args)
+    dense = None if args.no_dense else dense_measurement(args, flush)
 
     # the sparse residual kernels timed alone, the same kernel and grid as in
     # the solve: FP32 (the inner solve, every iteration) and FP64
@@ -336,6 +341,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches * args.steps,
         "autograd": ag,
         "batched": batched,
+        "dense": dense,
         "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
                      "frac": ach32 / peak,
@@ -385,6 +391,61 @@ def _batch_vs_sequential(handles, bs, tol, maxit, precision, torch, B, system_id
             "iters": [int(r.iters) for r in res],
             "all_converged": bool(all(r.converged for r in res)),
             "same_iterations_as_single_solves": bool(same)}
+
+
+def dense_measurement(args, flush):
+    """The dense least-squares form: A = U diag(s) V^T, m = 200,000, n = 2,048,
+    s_i geometric from 1 to 1e-8, 781 blocks of 256 rows, mu = 1e-6 * 256.
+    Its condition number (1e8) puts RRN = 1e-8 out of reach of any row-action
+    method in a practical number of iterations, so a fixed number of
+    iterations is timed (FP64 and mixed) and the RRN reached is reported, with
+    the dense residual kernel timed alone against the HBM roofline."""
+    import torch
+    from paper_2510_02156_gb300 import binding as B
+    from paper_2510_02156_gb300 import workloads as W
+    s = W.dense_usv_cuda(200_000, 2048, seed=2, block_rows=256, lam=2.56e-4, tol=args.tol)
+    t0 = time.time()
+    h = B.Handle.from_system(s, precision=B.PREC_MIXED)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    b = torch.as_tensor(s.b, device="cuda")
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    out = {"workload": (f"dense A = U diag(s) V^T, m={s.m}, n={s.n}, s geometric 1..1e-8, "
+                        f"{s.num_blocks} blocks of 256 rows (781 = floor(m/256)), lambda=2.56e-4, "
+                        f"x0=0, Philox seed 1"),
+           "setup_s": setup_s, "iterations": args.dense_iters}
+    for name, prec in (("fp64", B.PREC_FP64), ("mixed", B.PREC_MIXED)):
+        h.solve(b, x, tol=0.0, maxit=5, seed=1, precision=prec)            # warm-up
+        flush.zero_()
+        torch.cuda.synchronize()
+        r = h.solve(b, x, tol=0.0, maxit=args.dense_iters, seed=1, precision=prec)
+        xh = x.cpu().numpy()
+        out[name] = {"ms_per_iteration": r.time_ms / max(1, r.iters), "iters": int(r.iters),
+                     "rrn": float(np.linalg.norm(s.dense @ xh - s.b) / np.linalg.norm(s.b)),
+                     "refinements": int(r.refinements)}
+    # the residual over the dense A (its CSR form) timed alone, cold L2
+    x64 = torch.as_tensor(s.x_true, device="cuda") * 0.5
+    r64 = torch.empty(s.m, dtype=torch.float64, device="cuda")
+    cold64, warm64 = time_kernel(lambda: h.residual_async(b, x64, r64), flush, torch, reps=10)
+    b32, x32 = b.float(), x64.float()
+    r32 = torch.empty(s.m, dtype=torch.float32, device="cuda")
+    cold32, warm32 = time_kernel(lambda: h.residual32(b32, x32, r32, wait=False), flush, torch,
+                                 reps=10)
+    peak, kind = measured_hbm_peak()
+    mn = s.m * s.n
+    by64 = mn * 8 + 8 * (s.n + 2 * s.m)       # a dense GEMV: A once, x, b, r
+    by32 = mn * 4 + 4 * (s.n + 2 * s.m)
+    out["residual_fp64"] = {"bound": "hbm", "launch_ms_cold_l2": cold64, "launch_ms_warm_l2": warm64,
+                            "bytes_per_launch": by64, "achieved": by64 / (cold64 * 1e-3) / 1e9,
+                            "peak": peak, "unit": "GB/s", "frac": by64 / (cold64 * 1e-3) / 1e9 / peak,
+                            "note": "algorithmic bytes of a dense GEMV; the CSR form also reads "
+                                    "4 bytes of column index per entry"}
+    out["residual_fp32"] = {"bound": "hbm", "launch_ms_cold_l2": cold32, "launch_ms_warm_l2": warm32,
+                            "bytes_per_launch": by32, "achieved": by32 / (cold32 * 1e-3) / 1e9,
+                            "peak": peak, "unit": "GB/s", "frac": by32 / (cold32 * 1e-3) / 1e9 / peak}
+    h.close()
+    del s
+    return out
 
 
 def batched_measurement(args):

@@ -210,6 +210,32 @@ def dense_usv(m: int, n: int, seed: int = 2, smin: float = 1e-8,
                   num_blocks=k, lam=lam, tol=tol)
 
 
+def dense_usv_cuda(m: int, n: int, seed: int = 2, smin: float = 1e-8,
+                   block_rows: int = 256, lam: float = 1e-6, tol: float = 1e-8) -> System:
+    """The dense_usv recipe at sizes where host QR is slow: U (m x r) and
+    V (n x r) are the Q factors of seeded N(0,1) matrices drawn and factored on
+    the current CUDA device with torch (input generation only), A = U diag(s)
+    V^T in FP64, x_true ~ N(0,1), b = A x_true.  Returned as host arrays.  The
+    stream differs from dense_usv's (another generator), not the recipe."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    r = min(m, n)
+    U, _ = torch.linalg.qr(torch.randn(m, r, generator=g, device="cuda", dtype=torch.float64))
+    V, _ = torch.linalg.qr(torch.randn(n, r, generator=g, device="cuda", dtype=torch.float64))
+    sv = smin ** (torch.arange(r, device="cuda", dtype=torch.float64) / max(r - 1, 1))
+    A = (U * sv) @ V.T
+    del U
+    x_true = torch.randn(n, generator=g, device="cuda", dtype=torch.float64)
+    b = A @ x_true
+    A_h = A.cpu().numpy()
+    del A
+    torch.cuda.empty_cache()
+    k = max(1, m // block_rows)
+    return System(f"dense_usv_{m}x{n}", m, n, dense=np.ascontiguousarray(A_h),
+                  x_true=x_true.cpu().numpy(), b=b.cpu().numpy(), num_blocks=k, lam=lam, tol=tol)
+
+
 def gaussian_dense(m: int, n: int, seed: int = 3, num_blocks: int = 4,
                    lam: float = 1e-6, tol: float = 1e-8) -> System:
     """Dense N(0,1) matrix with a consistent right-hand side (small tests)."""
