@@ -146,11 +146,11 @@ __global__ void k_begin(const double *__restrict__ b, int m, const double *__res
 // shared memory by TMA bulk copies two blocks ahead (two stages, one mbarrier
 // each), while the current update runs.  Each update then needs two
 // dependent global round trips only: the gather of x at the block's columns
-// and the update of x.  Blocks larger than a stage take the direct path
-// (chunked loads from global memory), with the same arithmetic.
+// and the update of x.  Blocks larger than a stage (long or dense rows) take
+// the direct path (each row read from global memory by its thread), with the
+// same arithmetic.
 // force_tau >= 0 replaces the draw by that block (single-step API, direct
 // path only).
-constexpr int kStaticChunk = 1536;   // direct path
 constexpr int kStageCap = 3072;      // entries of one block held by a stage
 constexpr int kStageC = kStageCap + 16;
 constexpr long long kWaitTries = 1LL << 24;
@@ -280,18 +280,11 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
             __syncthreads();
             for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(st.val[p - a0], sx[p - p0], acc);
         } else {
-            T *sv = sx, *sxx = sx + kStaticChunk;
-            for (int c0 = p0; c0 < pend; c0 += kStaticChunk) {
-                const int c1 = min(pend, c0 + kStaticChunk);
-                for (int p = c0 + a; p < c1; p += blockDim.x) {
-                    sv[p - c0] = A.val[p];
-                    sxx[p - c0] = x[A.col[p]];
-                }
-                __syncthreads();
-                for (int p = max(q0, c0); p < min(q1, c1); ++p)
-                    acc = Ar<T>::fma(sv[p - c0], sxx[p - c0], acc);
-                __syncthreads();
-            }
+            // a block too large for a stage: every thread runs its own row
+            // straight from global memory (loads unrolled ahead of the chain),
+            // so the rows proceed side by side however long they are
+#pragma unroll 8
+            for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(A.val[p], x[A.col[p]], acc);
         }
         if (a < s) rloc[la] = Ar<T>::sub(bi, acc);
         __syncthreads();
