@@ -153,6 +153,7 @@ struct rorbk_ctx {
     double *adj_scale = nullptr;
     // workspace
     double *r = nullptr, *xb = nullptr, *bb = nullptr, *x64 = nullptr;
+    double *sd_scratch = nullptr;   // [2 kMaxBlockRows] r_tau and y of the dense static updates
     float *r32 = nullptr, *b32 = nullptr, *d32 = nullptr;
     double *partials = nullptr;
     unsigned *hist1 = nullptr, *hist2 = nullptr;

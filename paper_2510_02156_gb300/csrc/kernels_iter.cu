@@ -204,7 +204,8 @@ __device__ int stage_issue(const Mat<T> &A, int tau, Stage<T> st, unsigned long 
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__ b, T *x,
-                                                 Ctl *ctl, int force_tau, int use_stages) {
+                                                 Ctl *ctl, int force_tau, int use_stages,
+                                                 int l_begin) {
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ T rloc[kMaxBlockRows];
     __shared__ T y[kMaxBlockRows];
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         if (nst > 1) s_a0[1] = stage_issue<T>(A, taus[1], stg[1], &bar[1]);
     }
     unsigned phase[2] = {0u, 0u};
-    for (int l = 0; l < nst; ++l) {
+    for (int l = l_begin; l < nst; ++l) {
         const int tau = taus[l];
         const int sidx = l & 1;
         const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
@@ -1323,6 +1324,73 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
     if (count_iter) end_iteration<T>(x, n, ctl, use_cond, hcond);
 }
 
+// ---- the static updates of a dense A --------------------------------------
+// A block of a dense A (s rows of n entries) is far larger than a stage, and
+// one block of threads reading it row by row runs short of loads in flight.
+// Each of the first kDenseStatic updates of an iteration therefore runs as
+// three grid launches with the arithmetic of k_static's direct path: the
+// block's residual (one lane per row, the row's chain in column order),
+// y = W_tau r_tau, and x += A_tau^T y (one thread per column segment, rows
+// ascending).  Every launch draws the same tau from the Philox stream.
+constexpr int kDenseStatic = 3;
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_sd_rows(Mat<T> A, const T *__restrict__ b,
+                                               const T *__restrict__ x, T *rloc, Ctl *ctl, int l) {
+    if (ctl->done || ctl->halt || l >= ctl->n_static) return;
+    const long long it = ctl->iter_base + ctl->iter;
+    const int tau = sample_block(A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
+        ctl->tr_tau[ctl->iter * ctl->n_static + l] = tau;
+    const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
+    const int a = blockIdx.x * 32 + threadIdx.x;
+    if (a >= s) return;
+    const int q0 = A.rowptr[r0 + a], q1 = A.rowptr[r0 + a + 1];
+    T acc = T(0);
+#pragma unroll 8
+    for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(A.val[p], x[A.col[p]], acc);
+    rloc[a] = Ar<T>::sub(b[r0 + a], acc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_sd_apply(Mat<T> A, const T *__restrict__ rloc, T *y,
+                                                   Ctl *ctl, int l) {
+    if (ctl->done || ctl->halt || l >= ctl->n_static) return;
+    const long long it = ctl->iter_base + ctl->iter;
+    const int tau = sample_block(A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
+    const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
+    const int a = threadIdx.x;
+    if (a >= s) return;
+    const int pos = A.s_pos[r0 + a];
+    if (pos < 0) {
+        y[a] = Ar<T>::fma(A.w_diag[r0 + a], rloc[a], T(0));
+    } else {
+        const int sb = A.s_ptr[tau], nS = A.s_ptr[tau + 1] - sb;
+        const T *Wr = A.w_ss + A.w_ptr[tau] + (long long)pos * nS;
+        T acc2 = T(0);
+        for (int q = 0; q < nS; ++q) acc2 = Ar<T>::fma(Wr[q], rloc[A.s_idx[sb + q]], acc2);
+        y[a] = acc2;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sd_scatter(Mat<T> A, const T *__restrict__ y, T *x,
+                                                    Ctl *ctl, int l) {
+    if (ctl->done || ctl->halt || l >= ctl->n_static) return;
+    const long long it = ctl->iter_base + ctl->iter;
+    const int tau = sample_block(A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
+    const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
+    const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
+    const int ns = A.nseg[tau];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ns; g += gridDim.x * blockDim.x) {
+        int q = A.bt_seg[p0 + g];
+        const int c = A.bt_col[q];
+        T acc3 = T(0);
+        for (; q < pend && A.bt_col[q] == c; ++q) acc3 = Ar<T>::fma(A.bt_val[q], y[A.bt_row[q]], acc3);
+        x[c] = Ar<T>::add(x[c], acc3);
+    }
+}
+
 // ---- the dynamic update of a dense A -------------------------------------
 // Every row of I holds every column, so all of I is coupled and the Gram is
 // dense: G = A_I A_I^T + mu I (packed lower, D.g), each entry one fused chain
@@ -1377,6 +1445,121 @@ __global__ void __launch_bounds__(1024) k_dyn_dense_factor(const T *__restrict__
     column_solve(D.g, K, z, cz, rz);
     for (int q = threadIdx.x; q < K; q += blockDim.x) D.y[q] = z[q];
     if (threadIdx.x == 0 && s_bad) set_status(&ctl->status, kDevNotSpd);
+}
+
+// Blocked factor of the dense Gram (K <= kDenseCholMaxK): panels of kPW
+// columns.  The panel kernel (one block) factors the panel's columns in
+// shared memory, right-looking inside the panel, and carries the forward
+// solve for them (z is the panel's extra column); the trailing kernel (many
+// blocks) applies the panel's columns to every later entry, in ascending
+// column order; the backward solve runs last in one block.  Every entry sees
+// the operations of the one-block right-looking factor and column-oriented
+// solves in the same order (zero multipliers skipped alike).
+constexpr int kPW = 32;
+constexpr int kDenseCholMaxK = 768;
+
+size_t dchol_panel_smem(int K) { return ((size_t)K * (kPW + 1) + (size_t)K) * sizeof(double); }
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_dchol_panel(const T *__restrict__ r, int K, int j0, Dyn D,
+                                                      Ctl *ctl) {
+    extern __shared__ double dps[];
+    __shared__ int s_bad;
+    if (ctl->done || ctl->status || ctl->halt) return;
+    const int w = min(kPW, K - j0), nr = K - j0, tid = threadIdx.x;
+    double *Pm = dps;                        // [nr][kPW + 1]: rows j0.., panel columns
+    double *zz = dps + (size_t)nr * (kPW + 1);
+    for (int q = tid; q < nr * w; q += blockDim.x) {
+        const int i = q / w, jj = q % w;      // row j0 + i, column j0 + jj
+        Pm[i * (kPW + 1) + jj] = i >= jj ? D.g[pidx(j0 + i, j0 + jj)] : 0.0;
+    }
+    for (int i = tid; i < nr; i += blockDim.x)
+        zz[i] = j0 == 0 ? (double)r[D.I[i]] : D.y[j0 + i];
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int jj = 0; jj < w; ++jj) {
+        double *cj = Pm + jj;                 // column jj: cj[i * (kPW + 1)]
+        if (tid == 0) {
+            double d = cj[jj * (kPW + 1)];
+            if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
+            cj[jj * (kPW + 1)] = sqrt(d);
+        }
+        __syncthreads();
+        const double l = cj[jj * (kPW + 1)];
+        for (int i = jj + 1 + tid; i < nr; i += blockDim.x) {
+            const double v = cj[i * (kPW + 1)];
+            if (v != 0.0) cj[i * (kPW + 1)] = v / l;
+        }
+        if (tid == 0) zz[jj] = zz[jj] / l;    // forward solve: w_j
+        __syncthreads();
+        const double wj = zz[jj];
+        // the panel's later columns jj2, rows i >= jj2
+        for (int q = tid; q < (w - jj - 1) * nr; q += blockDim.x) {
+            const int jj2 = jj + 1 + q / nr, i = q % nr;
+            if (i < jj2) continue;
+            const double la = cj[i * (kPW + 1)], lb = cj[jj2 * (kPW + 1)];
+            if (la != 0.0 && lb != 0.0)
+                Pm[i * (kPW + 1) + jj2] = __fma_rn(-la, lb, Pm[i * (kPW + 1) + jj2]);
+        }
+        for (int i = jj + 1 + tid; i < nr; i += blockDim.x) {
+            const double lij = cj[i * (kPW + 1)];
+            if (lij != 0.0) zz[i] = __fma_rn(-lij, wj, zz[i]);
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < nr * w; q += blockDim.x) {
+        const int i = q / w, jj = q % w;
+        if (i >= jj) D.g[pidx(j0 + i, j0 + jj)] = Pm[i * (kPW + 1) + jj];
+    }
+    for (int i = tid; i < nr; i += blockDim.x) D.y[j0 + i] = zz[i];
+    if (tid == 0 && s_bad) set_status(&ctl->status, kDevNotSpd);
+}
+
+// G[a][b] -= L[a][j] L[b][j] for the panel's columns j (ascending), over the
+// trailing entries j1 <= b <= a < K, in 16 x 16 tiles.
+__global__ void __launch_bounds__(256) k_dchol_trail(int K, int j0, Dyn D, Ctl *ctl) {
+    __shared__ double La[16][kPW + 1], Lb[16][kPW + 1];
+    if (ctl->done || ctl->status || ctl->halt) return;
+    const int w = min(kPW, K - j0), j1 = j0 + w;
+    int t = blockIdx.x, ti = 0;
+    while (t > ti) { t -= ti + 1; ++ti; }
+    const int tj = t, tid = threadIdx.x;
+    for (int q = tid; q < 16 * w; q += blockDim.x) {
+        const int rr = q / w, jj = q % w;
+        const int a = j1 + ti * 16 + rr, b = j1 + tj * 16 + rr;
+        La[rr][jj] = a < K ? D.g[pidx(a, j0 + jj)] : 0.0;
+        Lb[rr][jj] = b < K ? D.g[pidx(b, j0 + jj)] : 0.0;
+    }
+    __syncthreads();
+    const int ta = tid / 16, tb = tid % 16;
+    const int a = j1 + ti * 16 + ta, b = j1 + tj * 16 + tb;
+    if (a >= K || b > a) return;
+    double g = D.g[pidx(a, b)];
+    for (int jj = 0; jj < w; ++jj) {
+        const double la = La[ta][jj], lb = Lb[tb][jj];
+        if (la != 0.0 && lb != 0.0) g = __fma_rn(-la, lb, g);
+    }
+    D.g[pidx(a, b)] = g;
+}
+
+// y = L^{-T} w (column-oriented, columns descending; row j of L is contiguous).
+__global__ void __launch_bounds__(1024) k_dchol_back(int K, Dyn D, Ctl *ctl) {
+    __shared__ double z[kMaxDynRows];
+    if (ctl->done || ctl->status || ctl->halt) return;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < K; q += blockDim.x) z[q] = D.y[q];
+    __syncthreads();
+    for (int j = K - 1; j >= 0; --j) {
+        if (tid == 0) z[j] = z[j] / D.g[pidx(j, j)];
+        __syncthreads();
+        const double zj = z[j];
+        for (int i = tid; i < j; i += blockDim.x) {
+            const double lji = D.g[pidx(j, i)];
+            if (lji != 0.0) z[i] = __fma_rn(-lji, zj, z[i]);
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < K; q += blockDim.x) D.y[q] = z[q];
 }
 
 template <typename T>
@@ -1559,6 +1742,10 @@ void configure_kernels() {
                          (int)factor_smem_bytes());
     cudaFuncSetAttribute(k_dyn_mark<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)factor_smem_bytes());
+    cudaFuncSetAttribute(k_dchol_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)dchol_panel_smem(kDenseCholMaxK));
+    cudaFuncSetAttribute(k_dchol_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)dchol_panel_smem(kDenseCholMaxK));
 }
 
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
@@ -1574,7 +1761,17 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
         const int K = h->K, T16 = (K + kGT - 1) / kGT;
         k_dyn_dense_gram<<<T16 * (T16 + 1) / 2, kGT * kGT, 0, h->stream>>>(h->val, (int)h->n, K, h->mu,
                                                                           dyn_bufs(h), ctl);
-        k_dyn_dense_factor<T><<<1, 1024, 0, h->stream>>>(r, K, dyn_bufs(h), ctl);
+        if (K <= kDenseCholMaxK) {
+            for (int j0 = 0; j0 < K; j0 += kPW) {
+                k_dchol_panel<T><<<1, 1024, dchol_panel_smem(K - j0), h->stream>>>(r, K, j0, dyn_bufs(h), ctl);
+                const int rest = K - std::min(K, j0 + kPW), tt = (rest + 15) / 16;
+                if (rest > 0)
+                    k_dchol_trail<<<tt * (tt + 1) / 2, 256, 0, h->stream>>>(K, j0, dyn_bufs(h), ctl);
+            }
+            k_dchol_back<<<1, 1024, 0, h->stream>>>(K, dyn_bufs(h), ctl);
+        } else {
+            k_dyn_dense_factor<T><<<1, 1024, 0, h->stream>>>(r, K, dyn_bufs(h), ctl);
+        }
         const int g = std::max(1, std::min(4 * h->num_sms, (int)((h->n + 255) / 256)));
         k_dyn_dense_scatter<T><<<g, 256, 0, h->stream>>>(h->val, h->val32, x, (int)h->n, K, dyn_bufs(h),
                                                           ctl, count_iter, use_cond,
@@ -1593,7 +1790,20 @@ template <typename T>
 void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_cond,
                         unsigned long long hcond) {
     Mat<T> A = make_mat<T>(h);
-    k_static<T><<<1, 1024, static_smem_bytes<T>(), h->stream>>>(A, b, x, ctl, -1, 1);
+    if (h->format == RORBK_FORMAT_DENSE) {
+        T *rl = (T *)h->sd_scratch, *yy = rl + kMaxBlockRows;
+        const int gr = (h->smax + 31) / 32;
+        const int gs = std::max(1, std::min(4 * h->num_sms, (int)((h->n + 255) / 256)));
+        for (int l = 0; l < kDenseStatic; ++l) {
+            k_sd_rows<T><<<gr, 32, 0, h->stream>>>(A, b, x, rl, ctl, l);
+            k_sd_apply<T><<<1, 1024, 0, h->stream>>>(A, rl, yy, ctl, l);
+            k_sd_scatter<T><<<gs, 256, 0, h->stream>>>(A, yy, x, ctl, l);
+        }
+        // updates beyond kDenseStatic (n_static > 3), if any
+        k_static<T><<<1, 1024, static_smem_bytes<T>(), h->stream>>>(A, b, x, ctl, -1, 0, kDenseStatic);
+    } else {
+        k_static<T><<<1, 1024, static_smem_bytes<T>(), h->stream>>>(A, b, x, ctl, -1, 1, 0);
+    }
     if constexpr (sizeof(T) == sizeof(float)) {
         k_residual<T, float><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
     } else {
@@ -1640,7 +1850,7 @@ void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_ou
 
 void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x) {
     k_static<double><<<1, 1024, static_smem_bytes<double>(), h->stream>>>(make_mat<double>(h), b, x,
-                                                                          h->ctl, tau, 0);
+                                                                          h->ctl, tau, 0, 0);
 }
 
 void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r) {

@@ -227,6 +227,7 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
     h->xb = (double *)dev_alloc(h, n * sizeof(double));
     h->bb = (double *)dev_alloc(h, m * sizeof(double));
     h->partials = (double *)dev_alloc(h, std::max(h->grid_res, 4 * h->num_sms) * sizeof(double) + 64);
+    h->sd_scratch = (double *)dev_alloc(h, 2 * kMaxBlockRows * sizeof(double));
     h->hist1 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
     h->hist2 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
     h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
@@ -268,7 +269,7 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         h->d32 = (float *)dev_alloc(h, n * sizeof(float));
         if (!h->r32 || !h->b32 || !h->d32) return fail(h, RORBK_ERR_OOM, "mixed workspace");
     }
-    if (!h->r || !h->xb || !h->bb || !h->partials || !h->hist1 || !h->hist2 || !h->in_list ||
+    if (!h->r || !h->xb || !h->bb || !h->partials || !h->sd_scratch || !h->hist1 || !h->hist2 || !h->in_list ||
         !h->eq_list || !h->ctl || !h->ctl_in)
         return fail(h, RORBK_ERR_OOM, "workspace");
     cudaMemsetAsync(h->hist1, 0, kHistBins * sizeof(unsigned), s);
