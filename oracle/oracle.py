@@ -67,8 +67,10 @@ def lib():
                 "orc_update_with_inverse": (None, [_P, _P, _I64, _P, _P, _P, _P, _P]),
                 "orc_update_with_cholesky": (C.c_int, [_P, _P, _I64, _D, _P, _P, _P]),
                 "orc_solve": (C.c_int, [_P, _I64, _D, _P, _P, _P, _D, _I64,
-                                        C.c_uint64, C.c_uint64, _I64, _I64,
+                                        C.c_uint64, C.c_uint64, _I64, _I64, C.c_int,
                                         _P, _P, _P, _P, _P, _P]),
+                "orc_block_norms": (None, [_P, _P, _I64, _P]),
+                "orc_weighted_cdf": (_D, [_P, _P, _I64, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -249,11 +251,16 @@ class SolveResult:
         return self.status == ORC_OK
 
 
+PAPER, RESIDUAL_WEIGHTED = 0, 1
+
+
 def solve(system, b=None, x0=None, *, k=None, mu=None, tol=None, maxit=100,
           seed=0, sysid=0, n_static=3, start_iter=0, trace_tau=False,
-          trace_rrn=False, trace_I=False, trace_x=False):
+          trace_rrn=False, trace_I=False, trace_x=False, dist_mode=PAPER):
     """Algorithm 1 on one right-hand side.  ``system`` is a workloads.System
-    (or its prepared matrix); b defaults to system.b."""
+    (or its prepared matrix); b defaults to system.b.  dist_mode=RESIDUAL_WEIGHTED
+    draws the static blocks with weights Pbar_t * ||r_{B_t}||^2 from the
+    previous iteration's residual (not in the paper)."""
     M = _mat(system)
     k = system.num_blocks if k is None else k
     mu = system.lam if mu is None else mu
@@ -270,7 +277,7 @@ def solve(system, b=None, x0=None, *, k=None, mu=None, tol=None, maxit=100,
     rrn = C.c_double(0.0)
     st = lib().orc_solve(M.ref, k, mu, _ptr(b), _ptr(x0), _ptr(x), tol, maxit,
                          C.c_uint64(seed), C.c_uint64(sysid), n_static, start_iter,
-                         C.byref(iters), C.byref(rrn), _ptr(tr_tau), _ptr(tr_rrn),
+                         int(dist_mode), C.byref(iters), C.byref(rrn), _ptr(tr_tau), _ptr(tr_rrn),
                          _ptr(tr_I), _ptr(tr_x))
     if st < 0:
         raise RuntimeError(f"oracle solve failed with status {st}")
@@ -282,6 +289,24 @@ def solve(system, b=None, x0=None, *, k=None, mu=None, tol=None, maxit=100,
         I=None if tr_I is None else tr_I[: it * K].reshape(it, K),
         x_trace=None if tr_x is None else tr_x[: it * M.n].reshape(it, M.n),
     )
+
+
+def block_norms(r, off):
+    """rho_t = sum of r_i^2 over block t's rows (fused, rows ascending)."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    rho = np.zeros(off.size - 1)
+    lib().orc_block_norms(_ptr(r), _ptr(off), off.size - 1, _ptr(rho))
+    return rho
+
+
+def weighted_cdf(Pbar, rho):
+    """Running sum of Pbar_t * rho_t in 64-block chunks; returns the cdf."""
+    Pbar = np.ascontiguousarray(Pbar, dtype=np.float64)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    cdf = np.zeros(Pbar.size)
+    lib().orc_weighted_cdf(_ptr(Pbar), _ptr(rho), Pbar.size, _ptr(cdf))
+    return cdf
 
 
 def prepare(system):

@@ -532,9 +532,47 @@ int orc_static_operator(const orc_matrix *A, const int64_t *off, int64_t t,
  *                                dynamic update; on the converging iteration,
  *                                x after the static updates)
  * Returns ORC_OK when converged, ORC_NOT_CONVERGED at maxit, or an error. */
+/* ------------------------------------------------------------------------ */
+/* The residual-weighted proposal (not in the paper: its P is static, Algorithm 1
+ * step 3).  Block t is drawn with weight w_t = Pbar_t * rho_t, where rho_t is
+ * the squared norm of the residual on block t's rows: one fused chain over the
+ * rows in ascending order.  The running sum of the weights is formed in chunks
+ * of ORC_WCHUNK blocks: each chunk's running sum from zero, then the chunks'
+ * totals summed in chunk order, and each entry offset by the total of the
+ * chunks before it. */
+#define ORC_WCHUNK 64
+
+void orc_block_norms(const double *r, const int64_t *off, int64_t k, double *rho)
+{
+    for (int64_t t = 0; t < k; ++t) {
+        double s = 0.0;
+        for (int64_t i = off[t]; i < off[t + 1]; ++i) s = fma(r[i], r[i], s);
+        rho[t] = s;
+    }
+}
+
+/* Returns the total weight (cdf[k-1]). */
+double orc_weighted_cdf(const double *Pbar, const double *rho, int64_t k, double *cdf)
+{
+    int64_t nc = (k + ORC_WCHUNK - 1) / ORC_WCHUNK;
+    double off = 0.0;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t t0 = c * ORC_WCHUNK, t1 = t0 + ORC_WCHUNK < k ? t0 + ORC_WCHUNK : k;
+        double s = 0.0;
+        for (int64_t t = t0; t < t1; ++t) {
+            s = s + Pbar[t] * rho[t];
+            cdf[t] = s;
+        }
+        for (int64_t t = t0; t < t1; ++t) cdf[t] = off + cdf[t];
+        off = off + s;
+    }
+    return cdf[k - 1];
+}
+
 int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
               const double *x0, double *x, double tol, int64_t maxit,
               uint64_t seed, uint64_t sysid, int64_t n_static, int64_t start_iter,
+              int dist_mode,
               int64_t *iters, double *rrn_out,
               int64_t *tr_tau, double *tr_rrn, int64_t *tr_I, double *tr_x)
 {
@@ -553,9 +591,13 @@ int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
     int64_t smax = m / k + 1;
     int64_t *rows = (int64_t *)malloc((size_t)smax * sizeof(int64_t));
     double *work = (double *)malloc((size_t)(2 * smax) * sizeof(double));
+    double *rho = (double *)malloc((size_t)k * sizeof(double));
+    double *wcdf = (double *)malloc((size_t)k * sizeof(double));
+    const double *dcdf = NULL;      /* the cdf the next draws use */
     int st = ORC_OK;
     if (!off || !rs || !Pbar || !cdf || !r || !delta || !Wcache || !I || !rI ||
-        !rows || !work) { st = ORC_ERR_OOM; goto done; }
+        !rows || !work || !rho || !wcdf) { st = ORC_ERR_OOM; goto done; }
+    if (dist_mode != 0 && dist_mode != 1) { st = ORC_ERR_ARG; goto done; }
 
     orc_partition(m, k, off);
     st = orc_orthogonality(A, k, off, NULL, rs);
@@ -574,9 +616,15 @@ int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
         goto done;
     }
     st = ORC_NOT_CONVERGED;
+    dcdf = cdf;
+    if (dist_mode == 1) {               /* weights from r = b - A x0 */
+        orc_residual(A, b, x, r);
+        orc_block_norms(r, off, k, rho);
+        if (orc_weighted_cdf(Pbar, rho, k, wcdf) > 0.0) dcdf = wcdf;
+    }
     for (int64_t j = 0; j < maxit; ++j) {
         for (int64_t l = 0; l < n_static; ++l) {
-            int64_t tau = orc_sample(cdf, k, seed, sysid, start_iter + j, l);
+            int64_t tau = orc_sample(dcdf, k, seed, sysid, start_iter + j, l);
             if (tr_tau) tr_tau[j * n_static + l] = tau;
             int64_t s = off[tau + 1] - off[tau];
             if (!Wcache[tau]) {
@@ -590,6 +638,10 @@ int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
         }
         double rr = orc_residual(A, b, x, r);
         double rrn = sqrt(rr) / bnorm;
+        if (dist_mode == 1) {           /* weights of the next iteration */
+            orc_block_norms(r, off, k, rho);
+            dcdf = orc_weighted_cdf(Pbar, rho, k, wcdf) > 0.0 ? wcdf : cdf;
+        }
         if (tr_rrn) tr_rrn[j] = rrn;
         *iters = j + 1;
         *rrn_out = rrn;
@@ -608,6 +660,6 @@ int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
 done:
     if (Wcache) for (int64_t t = 0; t < k; ++t) free(Wcache[t]);
     free(Wcache); free(off); free(rs); free(Pbar); free(cdf); free(r); free(delta);
-    free(I); free(rI); free(rows); free(work);
+    free(I); free(rI); free(rows); free(work); free(rho); free(wcdf);
     return st;
 }

@@ -389,3 +389,69 @@ def test_solve_not_spd_with_zero_mu_and_dependent_rows():
     sysd = W.System("sing", 8, 3, dense=A, b=A @ np.ones(3), num_blocks=2, lam=0.0)
     with pytest.raises(RuntimeError):
         oracle.solve(sysd, maxit=3)
+
+
+# ------------------------------------------- residual-weighted proposal
+# (not in the paper, whose P is static: the weighted variant draws block t with
+# weight Pbar_t * ||r_{B_t}||^2 from the previous iteration's residual.)
+def test_weighted_cdf_is_a_running_sum_of_the_weights():
+    """The chunked running sum equals the running sum numpy forms (to
+    rounding), for sizes that end inside and on a chunk boundary."""
+    rng = np.random.default_rng(51)
+    for k in (1, 63, 64, 65, 300, 4096):
+        Pbar = rng.uniform(0.9, 1.0, k)
+        rho = rng.uniform(0.0, 5.0, k) ** 3
+        cdf = oracle.weighted_cdf(Pbar, rho)
+        ref = np.cumsum(Pbar * rho)
+        np.testing.assert_allclose(cdf, ref, rtol=1e-13, atol=0)
+        assert np.all(np.diff(cdf) >= 0)
+
+
+def test_block_norms_are_squared_block_residuals():
+    rng = np.random.default_rng(52)
+    r = rng.standard_normal(1000)
+    off = np.array([0, 1, 300, 301, 700, 1000])
+    rho = oracle.block_norms(r, off)
+    ref = np.array([np.linalg.norm(r[off[t]:off[t + 1]]) ** 2 for t in range(5)])
+    np.testing.assert_allclose(rho, ref, rtol=1e-13)
+
+
+def test_weighted_draws_follow_the_weights():
+    """Chi-square of 200k draws through the oracle's sampler on the weighted
+    cdf against the normalised weights Pbar_t * rho_t."""
+    import scipy.stats
+    Pbar = np.array([0.9, 1.0, 0.95, 0.8, 1.0, 0.85, 0.9, 1.0])
+    rho = np.array([4.0, 0.5, 2.0, 9.0, 0.25, 1.0, 3.0, 0.0])
+    cdf = oracle.weighted_cdf(Pbar, rho)
+    lib = oracle.lib()
+    counts = np.zeros(8)
+    for it in range(100_000):
+        for l in range(2):
+            counts[lib.orc_sample(cdf.ctypes.data, 8, 5, 1, it, l)] += 1
+    w = Pbar * rho
+    assert counts[7] == 0                         # zero residual: never drawn
+    expected = w[:7] / w.sum() * counts.sum()
+    chi2 = ((counts[:7] - expected) ** 2 / expected).sum()
+    assert scipy.stats.chi2.sf(chi2, 6) > 1e-4
+
+
+def test_weighted_first_draws_avoid_blocks_without_residual():
+    """With x0 = 0 the first iteration's weights are Pbar_t ||b_{B_t}||^2, so a
+    block whose right-hand side is zero is never drawn there."""
+    s = W.random_sparse(400, 120, 0.3, seed=13, num_blocks=8, lam=1e-6)
+    b = s.b.copy()
+    b[0:50] = 0.0                                  # block 0 (50 rows)
+    b[150:200] = 0.0                               # block 3
+    for seed in range(40):
+        res = oracle.solve(s, b=b, maxit=1, tol=0.0, seed=seed, trace_tau=True,
+                           dist_mode=oracle.RESIDUAL_WEIGHTED)
+        assert not set(res.tau[0]) & {0, 3}
+
+
+def test_weighted_solve_recovers_x_true():
+    """The weighting changes which blocks are drawn, not the fixed point: a
+    consistent well-conditioned system still converges to x_true."""
+    s = W.powerlaw(n=1 << 10, num_blocks=8, seed=3, lam=1e-8, tol=1e-10)
+    res = oracle.solve(s, maxit=5000, seed=1, dist_mode=oracle.RESIDUAL_WEIGHTED)
+    assert res.converged
+    assert np.linalg.norm(res.x - s.x_true) / np.linalg.norm(s.x_true) < 1e-6
