@@ -149,7 +149,23 @@ typedef struct {
     int32_t poll;           /* iterations per batch when host_loop = 1 (64)   */
     rorbk_trace *trace;     /* FP64 only                               (NULL) */
     void *stream;           /* cudaStream_t for all work               (0 = legacy default) */
+    int32_t dist_mode;      /* RORBK_DIST_*: how the static blocks are drawn (PAPER) */
+    int32_t reserved_;
 } rorbk_options;
+
+/* Distribution of the static blocks (rorbk_options.dist_mode).
+ *   PAPER             : tau ~ P, P_t proportional to Pbar_t (Algorithm 1 step 3;
+ *                       static over the solve).
+ *   RESIDUAL_WEIGHTED : not in the paper.  Iteration j draws block t with
+ *                       weight Pbar_t * rho_t, rho_t = sum of r_i^2 over the
+ *                       block's rows (one fused chain, rows ascending) of the
+ *                       residual r of iteration j-1 (r = b - A x0 for j = 0).
+ *                       The running sum of the weights is formed in chunks of
+ *                       64 blocks (each chunk from zero, the chunk totals in
+ *                       order, each entry offset by the totals before its
+ *                       chunk); if every weight is zero the draws use P.
+ *                       FP64 precision, single solves (not batched). */
+enum { RORBK_DIST_PAPER = 0, RORBK_DIST_RESIDUAL_WEIGHTED = 1 };
 
 typedef struct {
     int64_t iters;          /* ROR-BK iterations executed (MIXED: inner iterations summed) */

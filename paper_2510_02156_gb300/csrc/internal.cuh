@@ -63,6 +63,8 @@ struct Ctl {
     // dynamic block bookkeeping
     int dynE, dyn_nsh, dyn_nS, dyn_npair, dyn_nraw, pad3_;
     int halt;              // no further iteration runs (converged, error or maxit)
+    int weighted;          // residual-weighted draws (RORBK_DIST_RESIDUAL_WEIGHTED)
+    const double *scdf;    // the running sum the static draws use (P's, or the weighted one)
     int pad2_;
 };
 
@@ -133,6 +135,7 @@ struct rorbk_ctx {
     int *off = nullptr;
     // proposal
     double *cdf = nullptr, *crowsum = nullptr;
+    double *pbar = nullptr;             // [k] Pbar_t (the weights before the running sum)
     rorbk::StaticOps ops;
     rorbk::BlockT bt;
     // residual tiles (single-step residual on CSR) and the SELL-32 copy of A
@@ -154,6 +157,8 @@ struct rorbk_ctx {
     // workspace
     double *r = nullptr, *xb = nullptr, *bb = nullptr, *x64 = nullptr;
     double *sd_scratch = nullptr;   // [2 kMaxBlockRows] r_tau and y of the dense static updates
+    double *wgt = nullptr, *wcdf = nullptr;   // [k] residual-weighted draws: weights, running sum
+    cudaGraphExec_t exec_fp64_w = nullptr;   // the FP64 loop with residual-weighted draws
     float *r32 = nullptr, *b32 = nullptr, *d32 = nullptr;
     double *partials = nullptr;
     unsigned *hist1 = nullptr, *hist2 = nullptr;
@@ -201,7 +206,8 @@ int residual_grid(rorbk_ctx *h);   // one resident wave of the residual kernel
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
                   unsigned long long hcond);
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
-                      unsigned long long hcond);
+                      unsigned long long hcond, int weighted = 0);
+void launch_weights(rorbk_ctx *h, const double *r);   // residual-weighted running sum from r
 void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x);
 void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner);
 void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner);

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
     if (a < nst) {
         const long long it = ctl->iter_base + ctl->iter;
         const int tau = force_tau >= 0 ? force_tau
-                                       : sample_block(A.cdf, A.k, ctl->seed, ctl->sysid,
+                                       : sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid,
                                                       (uint64_t)it, (uint64_t)a);
         taus[a] = tau;
         if (force_tau < 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
@@ -1324,6 +1324,59 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
     if (count_iter) end_iteration<T>(x, n, ctl, use_cond, hcond);
 }
 
+// ---- residual-weighted draws (not in the paper) -----------------------------
+// Block t's weight is Pbar_t * rho_t, rho_t = sum of r_i^2 over its rows (one
+// fused chain, rows ascending); the running sum is formed in chunks of
+// kWChunk blocks (each chunk from zero, the chunk totals in order, each entry
+// offset by the totals before its chunk).  The next static draws use it, or
+// P's running sum if every weight is zero.
+constexpr int kWChunk = 64;
+
+__global__ void __launch_bounds__(256) k_wweights(const double *__restrict__ r,
+                                                  const int *__restrict__ off, int k,
+                                                  const double *__restrict__ pbar,
+                                                  double *__restrict__ w, Ctl *ctl) {
+    if (ctl->done || ctl->halt) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = off[t]; i < off[t + 1]; ++i) s = __fma_rn(r[i], r[i], s);
+        w[t] = __dmul_rn(pbar[t], s);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_wcdf(const double *__restrict__ w, int k,
+                                               double *__restrict__ wcdf,
+                                               const double *__restrict__ cdf, Ctl *ctl) {
+    __shared__ double tot[1024];
+    if (ctl->done || ctl->halt) return;
+    const int nc = (k + kWChunk - 1) / kWChunk;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int t1 = min(k, (c + 1) * kWChunk);
+        double s = 0.0;
+        for (int t = c * kWChunk; t < t1; ++t) {
+            s = __dadd_rn(s, w[t]);
+            wcdf[t] = s;
+        }
+        tot[c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {                       // chunk offsets, in chunk order
+        double off = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            const double sc = tot[c];
+            tot[c] = off;
+            off = __dadd_rn(off, sc);
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int t1 = min(k, (c + 1) * kWChunk);
+        for (int t = c * kWChunk; t < t1; ++t) wcdf[t] = __dadd_rn(tot[c], wcdf[t]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ctl->scdf = wcdf[k - 1] > 0.0 ? wcdf : cdf;
+}
+
 // ---- the static updates of a dense A --------------------------------------
 // A block of a dense A (s rows of n entries) is far larger than a stage, and
 // one block of threads reading it row by row runs short of loads in flight.
@@ -1339,7 +1392,7 @@ __global__ void __launch_bounds__(32) k_sd_rows(Mat<T> A, const T *__restrict__ 
                                                const T *__restrict__ x, T *rloc, Ctl *ctl, int l) {
     if (ctl->done || ctl->halt || l >= ctl->n_static) return;
     const long long it = ctl->iter_base + ctl->iter;
-    const int tau = sample_block(A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
+    const int tau = sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
     if (blockIdx.x == 0 && threadIdx.x == 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
         ctl->tr_tau[ctl->iter * ctl->n_static + l] = tau;
     const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
@@ -1357,7 +1410,7 @@ __global__ void __launch_bounds__(1024) k_sd_apply(Mat<T> A, const T *__restrict
                                                    Ctl *ctl, int l) {
     if (ctl->done || ctl->halt || l >= ctl->n_static) return;
     const long long it = ctl->iter_base + ctl->iter;
-    const int tau = sample_block(A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
+    const int tau = sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
     const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
     const int a = threadIdx.x;
     if (a >= s) return;
@@ -1378,7 +1431,7 @@ __global__ void __launch_bounds__(256) k_sd_scatter(Mat<T> A, const T *__restric
                                                     Ctl *ctl, int l) {
     if (ctl->done || ctl->halt || l >= ctl->n_static) return;
     const long long it = ctl->iter_base + ctl->iter;
-    const int tau = sample_block(A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
+    const int tau = sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
     const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
     const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
     const int ns = A.nseg[tau];
@@ -1788,7 +1841,7 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
 
 template <typename T>
 void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_cond,
-                        unsigned long long hcond) {
+                        unsigned long long hcond, int weighted = 0) {
     Mat<T> A = make_mat<T>(h);
     if (h->format == RORBK_FORMAT_DENSE) {
         T *rl = (T *)h->sd_scratch, *yy = rl + kMaxBlockRows;
@@ -1812,6 +1865,8 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
         else
             k_residual<T, double><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
     }
+    if constexpr (sizeof(T) == sizeof(double))
+        if (weighted) launch_weights(h, r);      // the draws of the next iteration
     const int g = grid_stream(h, (int)h->m);
     k_topk_hist2<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1);
     k_topk_collect<T><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
@@ -1819,9 +1874,15 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
     launch_dynamic_tail<T>(h, r, x, ctl, 1, 1, use_cond, hcond);
 }
 
+void launch_weights(rorbk_ctx *h, const double *r) {
+    k_wweights<<<std::max(1, std::min(4 * h->num_sms, (h->k + 255) / 256)), 256, 0, h->stream>>>(
+        r, h->off, h->k, h->pbar, h->wgt, h->ctl);
+    k_wcdf<<<1, 1024, 0, h->stream>>>(h->wgt, h->k, h->wcdf, h->cdf, h->ctl);
+}
+
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
-                      unsigned long long hcond) {
-    launch_iteration_t<double>(h, b, x, r, h->ctl, use_cond, hcond);
+                      unsigned long long hcond, int weighted) {
+    launch_iteration_t<double>(h, b, x, r, h->ctl, use_cond, hcond, weighted);
 }
 
 void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner) {

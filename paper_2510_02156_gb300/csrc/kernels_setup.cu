@@ -274,8 +274,12 @@ __global__ void k_crowsum(const double *__restrict__ G, int k, double *__restric
 // Pbar_t = exp(-2 rowsum_t / n); cdf_t = Pbar_0 + ... + Pbar_t summed in
 // order by one thread (the normalisation of P is folded into the sampler).
 __global__ void k_proposal(const double *__restrict__ rowsum, int k, double n,
-                           double *__restrict__ cdf) {
-    for (int t = threadIdx.x; t < k; t += blockDim.x) cdf[t] = exp(-2.0 * rowsum[t] / n);
+                           double *__restrict__ cdf, double *__restrict__ pbar) {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        const double v = exp(-2.0 * rowsum[t] / n);
+        cdf[t] = v;
+        pbar[t] = v;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -576,7 +580,7 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
                                                             h->bt.seg, h->bt.seg_ptr, k, colcnt,
                                                             cb, cv, G);
         k_crowsum<<<(k * 32 + 255) / 256, 256, 0, s>>>(G, k, h->crowsum);
-        k_proposal<<<1, 1024, 0, s>>>(h->crowsum, k, (double)n, h->cdf);
+        k_proposal<<<1, 1024, 0, s>>>(h->crowsum, k, (double)n, h->cdf, h->pbar);
         if ((st = cuda_check(h, cudaGetLastError(), "proposal"))) return st;
     }
 

@@ -84,7 +84,7 @@ static cudaError_t begin_capture(cudaStream_t cs, cudaGraph_t parent) {
 
 // Capture: k_begin, then WHILE(cond) { one iteration }.  With parent == NULL
 // the graph is instantiated into h->exec_fp64, else it is appended to parent.
-static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr) {
+static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr, int weighted = 0) {
     rorbk_status st;
     cudaStream_t saved = h->stream;
     cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2;
@@ -100,6 +100,10 @@ static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr)
     if (e == cudaSuccess) {
         h->stream = cs;
         launch_begin(h, h->bb, h->xb, h->xb, 1, (unsigned long long)hcond);
+        if (weighted) {                 // the first draws' weights: r = b - A x0
+            launch_residual_only(h, h->bb, h->xb, h->r);
+            launch_weights(h, h->r);
+        }
         e = cudaGetLastError();
     }
     cudaGraphNode_t wnode = nullptr;
@@ -118,7 +122,7 @@ static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr)
         e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             h->stream = cs2;
-            launch_iteration(h, h->bb, h->xb, h->r, 1, (unsigned long long)hcond);
+            launch_iteration(h, h->bb, h->xb, h->r, 1, (unsigned long long)hcond, weighted);
             cudaError_t e2 = cudaGetLastError();
             cudaGraph_t body_out = nullptr;
             e = cudaStreamEndCapture(cs2, &body_out);
@@ -130,7 +134,7 @@ static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr)
     cudaError_t e3 = cudaStreamEndCapture(cs, &g_out);
     if (e == cudaSuccess) e = e3;
     if (!parent) {
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_fp64, g_out, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(weighted ? &h->exec_fp64_w : &h->exec_fp64, g_out, 0);
         if (g_out) cudaGraphDestroy(g_out);
     }
     return cuda_check(h, e, "building the iteration graph");
@@ -228,6 +232,8 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
     h->bb = (double *)dev_alloc(h, m * sizeof(double));
     h->partials = (double *)dev_alloc(h, std::max(h->grid_res, 4 * h->num_sms) * sizeof(double) + 64);
     h->sd_scratch = (double *)dev_alloc(h, 2 * kMaxBlockRows * sizeof(double));
+    h->wgt = (double *)dev_alloc(h, h->k * sizeof(double));
+    h->wcdf = (double *)dev_alloc(h, h->k * sizeof(double));
     h->hist1 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
     h->hist2 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
     h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
@@ -269,7 +275,8 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         h->d32 = (float *)dev_alloc(h, n * sizeof(float));
         if (!h->r32 || !h->b32 || !h->d32) return fail(h, RORBK_ERR_OOM, "mixed workspace");
     }
-    if (!h->r || !h->xb || !h->bb || !h->partials || !h->sd_scratch || !h->hist1 || !h->hist2 || !h->in_list ||
+    if (!h->r || !h->xb || !h->bb || !h->partials || !h->sd_scratch || !h->wgt || !h->wcdf ||
+        !h->hist1 || !h->hist2 || !h->in_list ||
         !h->eq_list || !h->ctl || !h->ctl_in)
         return fail(h, RORBK_ERR_OOM, "workspace");
     cudaMemsetAsync(h->hist1, 0, kHistBins * sizeof(unsigned), s);
@@ -316,6 +323,7 @@ void rorbk_free(rorbk_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->exec_fp64) cudaGraphExecDestroy(h->exec_fp64);
     if (h->exec_mixed) cudaGraphExecDestroy(h->exec_mixed);
+    if (h->exec_fp64_w) cudaGraphExecDestroy(h->exec_fp64_w);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
     if (h->cap_stream3) cudaStreamDestroy(h->cap_stream3);
@@ -410,7 +418,9 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     h->off = (int *)dev_alloc(h, (k + 1) * sizeof(int));
     h->cdf = (double *)dev_alloc(h, k * sizeof(double));
     h->crowsum = (double *)dev_alloc(h, k * sizeof(double));
-    if (!h->rowptr || !h->col || !h->val || !h->off || !h->cdf || !h->crowsum) return bail(fail(h, RORBK_ERR_OOM, "matrix"));
+    h->pbar = (double *)dev_alloc(h, k * sizeof(double));
+    if (!h->rowptr || !h->col || !h->val || !h->off || !h->cdf || !h->crowsum || !h->pbar)
+        return bail(fail(h, RORBK_ERR_OOM, "matrix"));
     cudaStream_t s = h->stream;
     // rows of a dense A are copied from its leading dimension into n-entry rows
     const size_t esz = A->dtype == RORBK_F64 ? sizeof(double) : sizeof(float);
@@ -477,6 +487,10 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
                     "mixed precision needs a handle set up with precision = RORBK_PREC_MIXED");
     if (mixed && (!(opt.inner_tol > 0) || opt.inner_maxit < 1))
         return fail(h, RORBK_ERR_INVALID_ARG, "inner_tol > 0 and inner_maxit >= 1");
+    if (opt.dist_mode != RORBK_DIST_PAPER && opt.dist_mode != RORBK_DIST_RESIDUAL_WEIGHTED)
+        return fail(h, RORBK_ERR_INVALID_ARG, "unknown dist_mode");
+    if (mixed && opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED)
+        return fail(h, RORBK_ERR_UNSUPPORTED, "residual-weighted draws are available in FP64 precision");
     if (mixed && h->smax > h->n)
         return fail(h, RORBK_ERR_UNSUPPORTED,
                     "mixed precision needs blocks of at most n rows: with s > n the stored "
@@ -496,6 +510,8 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
     c.has_x0 = x0 != nullptr;
     c.inner_tol = opt.inner_tol;
     c.inner_maxit = opt.inner_maxit;
+    c.weighted = opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED;
+    c.scdf = nullptr;                   // P's running sum until weights replace it
     if (opt.trace && !mixed) {
         c.trace_cap = opt.trace->capacity;
         c.tr_tau = (long long *)opt.trace->tau;
@@ -544,10 +560,11 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
     if ((st = solve_prepare(h, b, x0, b_host, tol, maxit, opt, s))) return st;
     const bool mixed = opt.precision == RORBK_PREC_MIXED;
     Ctl c;
-    cudaGraphExec_t *exec = mixed ? &h->exec_mixed : &h->exec_fp64;
+    const int weighted = opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED;
+    cudaGraphExec_t *exec = mixed ? &h->exec_mixed : (weighted ? &h->exec_fp64_w : &h->exec_fp64);
     if (!opt.host_loop && !*exec) {
         if ((st = cuda_check(h, cudaStreamSynchronize(s), "solve prologue"))) return st;
-        if ((st = mixed ? build_graph_mixed(h) : build_graph_fp64(h))) return st;
+        if ((st = mixed ? build_graph_mixed(h) : build_graph_fp64(h, nullptr, weighted))) return st;
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -564,10 +581,14 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
         launch_begin(h, h->bb, h->xb, h->xb, 0, 0);
         int halt = 0;
         if (!mixed) {
+            if (weighted) {
+                launch_residual_only(h, h->bb, h->xb, h->r);
+                launch_weights(h, h->r);
+            }
             int64_t launched = 0;
             while (e == cudaSuccess && !halt && launched < maxit) {
                 for (int q = 0; q < poll && launched < maxit; ++q, ++launched)
-                    launch_iteration(h, h->bb, h->xb, h->r, 0, 0);
+                    launch_iteration(h, h->bb, h->xb, h->r, 0, 0, weighted);
                 e = cudaGetLastError();
                 if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -637,7 +658,7 @@ rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
     c->allocs.clear();
     c->tmp.clear();
     c->bytes = 0;
-    c->exec_fp64 = c->exec_mixed = nullptr;
+    c->exec_fp64 = c->exec_mixed = c->exec_fp64_w = nullptr;
     c->cap_stream = c->cap_stream2 = c->cap_stream3 = nullptr;
     auto bail = [&](rorbk_status e) {
         record_setup_error(c->err.empty() ? std::string("rorbk_clone failed") : c->err);
@@ -730,8 +751,9 @@ rorbk_status rorbk_batch_solve(rorbk_batch bt, const double *const *b, const dou
     rorbk_options opt = opt_in ? *opt_in : defaults();
     if (opt.precision != bt->precision)
         return reject(RORBK_ERR_INVALID_ARG, "rorbk_batch_solve: precision differs from the batch's");
-    if (opt.host_loop || opt.trace)
-        return reject(RORBK_ERR_UNSUPPORTED, "rorbk_batch_solve: no host loop or trace in a batch");
+    if (opt.host_loop || opt.trace || opt.dist_mode != RORBK_DIST_PAPER)
+        return reject(RORBK_ERR_UNSUPPORTED,
+                      "rorbk_batch_solve: no host loop, trace or residual-weighted draws in a batch");
     const int count = (int)bt->hs.size();
     for (int i = 0; i < count; ++i)
         if (!b[i] || !x[i]) return reject(RORBK_ERR_INVALID_ARG, "rorbk_batch_solve: NULL b[i] or x[i]");
