@@ -61,6 +61,9 @@ def parse():
                    help="skip the dense measurement (A = U diag(s) V^T, 200,000 x 2,048, "
                         "781 blocks of 256 rows; a fixed number of iterations)")
     p.add_argument("--dense-iters", type=int, default=100)
+    p.add_argument("--no-weighted", action="store_true",
+                   help="skip the comparison of the residual-weighted draws with the paper's "
+                        "(FP64 to tolerance on the 262,144-unknown power-law system)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched measurement (16 right-hand sides of a 65,536-row "
                         "system, and 16 systems of 5,000-200,000 rows, each in one launch)")
@@ -302,6 +305,7 @@ def run_ours(args, rank, world, local):
     e2e_s = time.perf_counter() - t1
 
     ag = None if args.no_autograd else autograd_measurement(args)
+    weighted = None if args.no_weighted else weighted_measurement(args)
     batched = None if args.no_batched else batched_measurement(args)
     dense = None if args.no_dense else dense_measurement(args, flush)
 
@@ -341,6 +345,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches * args.steps,
         "autograd": ag,
         "batched": batched,
+        "residual_weighted": weighted,
         "dense": dense,
         "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
@@ -501,6 +506,30 @@ def dense_measurement(args, flush):
                             "peak": peak, "unit": "GB/s", "frac": by32 / (cold32 * 1e-3) / 1e9 / peak}
     h.close()
     del s
+    return out
+
+
+def weighted_measurement(args):
+    """Iterations and time to tolerance of the FP64 solve with the paper's
+    static proposal and with residual-weighted draws (not in the paper), on
+    the 262,144-unknown power-law system (1024 blocks of 256 rows)."""
+    import torch
+    from paper_2510_02156_gb300 import binding as B
+    from paper_2510_02156_gb300 import workloads as W
+    s = W.powerlaw(n=1 << 18, num_blocks=1024, seed=1, lam=args.lam, tol=args.tol,
+                   cache=args.cache)
+    h = B.Handle.from_system(s)
+    b = torch.as_tensor(s.b, device="cuda")
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    out = {"workload": f"power-law sparse square CSR, n={s.n}, nnz={s.nnz}, 1024 blocks of 256, "
+                       f"lambda={s.lam:g}, tol={s.tol:g}, FP64, seed 1"}
+    for name, mode in (("paper", B.DIST_PAPER), ("residual_weighted", B.DIST_RESIDUAL_WEIGHTED)):
+        h.solve(b, x, tol=s.tol, maxit=20, seed=1, dist_mode=mode)           # builds the graph
+        r = h.solve(b, x, tol=s.tol, maxit=args.maxit, seed=1, dist_mode=mode)
+        out[name] = {"iters": int(r.iters), "time_s": r.time_ms / 1e3,
+                     "us_per_iteration": r.time_ms / max(1, r.iters) * 1e3,
+                     "rrn": float(r.rrn), "converged": bool(r.converged)}
+    h.close()
     return out
 
 

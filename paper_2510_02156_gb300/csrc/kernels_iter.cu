@@ -1339,6 +1339,7 @@ __global__ void __launch_bounds__(256) k_wweights(const double *__restrict__ r,
     if (ctl->done || ctl->halt) return;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
         double s = 0.0;
+#pragma unroll 8
         for (int i = off[t]; i < off[t + 1]; ++i) s = __fma_rn(r[i], r[i], s);
         w[t] = __dmul_rn(pbar[t], s);
     }
