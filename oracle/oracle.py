@@ -70,6 +70,7 @@ def lib():
                                         C.c_uint64, C.c_uint64, _I64, _I64, C.c_int,
                                         _P, _P, _P, _P, _P, _P]),
                 "orc_block_norms": (None, [_P, _P, _I64, _P]),
+                "orc_initial_solution": (C.c_int, [_P, _I64, _I64, _P, _P]),
                 "orc_weighted_cdf": (_D, [_P, _P, _I64, _P]),
             }
             for name, (res, args) in sig.items():
@@ -289,6 +290,18 @@ def solve(system, b=None, x0=None, *, k=None, mu=None, tol=None, maxit=100,
         I=None if tr_I is None else tr_I[: it * K].reshape(it, K),
         x_trace=None if tr_x is None else tr_x[: it * M.n].reshape(it, M.n),
     )
+
+
+def initial_solution(system, first, count, b=None):
+    """Algorithm 2: x0 = (<b, A y> / ||A y||^2) y, y = sum of rows first ..
+    first + count - 1."""
+    M = _mat(system)
+    b = np.ascontiguousarray(system.b if b is None else b, dtype=np.float64)
+    x0 = np.zeros(M.n)
+    st = lib().orc_initial_solution(M.ref, first, count, _ptr(b), _ptr(x0))
+    if st != 0:
+        raise ValueError(f"oracle initial solution status {st}")
+    return x0
 
 
 def block_norms(r, off):

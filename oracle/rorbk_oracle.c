@@ -533,6 +533,45 @@ int orc_static_operator(const orc_matrix *A, const int64_t *off, int64_t t,
  *                                x after the static updates)
  * Returns ORC_OK when converged, ORC_NOT_CONVERGED at maxit, or an error. */
 /* ------------------------------------------------------------------------ */
+/* Algorithm 2 (Appendix, initial solution): y = the sum of a set of rows of A
+ * (here rows first .. first+count-1, each column summed over the rows in
+ * ascending order), b~ = A y, x0 = (<b, b~> / ||b~||^2) y.  x0 lies in
+ * range(A^T) and ||b - A x0|| <= ||b|| (the Remark after Algorithm 2).  The
+ * two inner products are summed in index order.  Returns ORC_ERR_ARG for an
+ * empty or out-of-range set or b~ = 0. */
+int orc_initial_solution(const orc_matrix *A, int64_t first, int64_t count,
+                         const double *b, double *x0)
+{
+    int64_t m = A->m, n = A->n;
+    if (count < 1 || first < 0 || first + count > m) return ORC_ERR_ARG;
+    double *bt = (double *)malloc((size_t)m * sizeof(double));
+    double *zero = (double *)calloc((size_t)m, sizeof(double));
+    if (!bt || !zero) { free(bt); free(zero); return ORC_ERR_OOM; }
+    for (int64_t c = 0; c < n; ++c) x0[c] = 0.0;
+    for (int64_t i = first; i < first + count; ++i) {
+        if (A->is_dense) {
+            const double *a = A->dense + i * A->ld;
+            for (int64_t c = 0; c < n; ++c) x0[c] = x0[c] + a[c];
+        } else {
+            for (int64_t p = A->row_ptr[i]; p < A->row_ptr[i + 1]; ++p)
+                x0[A->col_idx[p]] = x0[A->col_idx[p]] + A->val[p];
+        }
+    }
+    orc_residual(A, zero, x0, bt);              /* bt = 0 - A y */
+    double bb = 0.0, tt = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double v = -bt[i];                       /* b~ = A y */
+        bb = fma(b[i], v, bb);
+        tt = fma(v, v, tt);
+    }
+    free(bt); free(zero);
+    if (!(tt > 0.0)) return ORC_ERR_ARG;
+    double alpha = bb / tt;
+    for (int64_t c = 0; c < n; ++c) x0[c] = alpha * x0[c];
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The residual-weighted proposal (not in the paper: its P is static, Algorithm 1
  * step 3).  Block t is drawn with weight w_t = Pbar_t * rho_t, where rho_t is
  * the squared norm of the residual on block t's rows: one fused chain over the

@@ -455,3 +455,32 @@ def test_weighted_solve_recovers_x_true():
     res = oracle.solve(s, maxit=5000, seed=1, dist_mode=oracle.RESIDUAL_WEIGHTED)
     assert res.converged
     assert np.linalg.norm(res.x - s.x_true) / np.linalg.norm(s.x_true) < 1e-6
+
+
+# --------------------------------------------- Algorithm 2: initial solution
+def test_initial_solution_satisfies_the_remark():
+    """The Remark after Algorithm 2: x0 = alpha y lies in range(A^T) (y is a
+    sum of rows) and ||b - A x0|| <= ||b||.  Its proof fixes more: b - A x0 is
+    orthogonal to b~ = A y, so ||b - A x0||^2 = ||b||^2 - <b, b~>^2/||b~||^2, and
+    alpha minimises ||b - alpha A y|| (a least-squares fit in one unknown)."""
+    for s, first, count in ((W.random_sparse(400, 120, 0.3, seed=13, num_blocks=8), 50, 50),
+                            (W.gaussian_dense(300, 80, seed=4), 0, 300),
+                            (W.laplace2d(g=12, num_blocks=4), 36, 36)):
+        x0 = oracle.initial_solution(s, first, count)
+        A = s.to_dense()
+        y = A[first:first + count].sum(axis=0)
+        bt = A @ y
+        alpha = np.linalg.lstsq(bt[:, None], s.b, rcond=None)[0][0]
+        np.testing.assert_allclose(x0, alpha * y, rtol=1e-12, atol=1e-14 * np.abs(alpha * y).max())
+        r0 = s.b - A @ x0
+        assert np.linalg.norm(r0) <= np.linalg.norm(s.b)
+        assert abs(r0 @ bt) <= 1e-10 * np.linalg.norm(r0) * np.linalg.norm(bt) + 1e-300
+        lhs = np.linalg.norm(r0) ** 2
+        rhs = np.linalg.norm(s.b) ** 2 - (s.b @ bt) ** 2 / (bt @ bt)
+        assert lhs == pytest.approx(rhs, rel=1e-9, abs=1e-12 * np.linalg.norm(s.b) ** 2)
+
+
+def test_initial_solution_rejects_an_empty_set():
+    s = W.random_sparse(40, 12, 0.3, seed=3, num_blocks=2)
+    with pytest.raises(ValueError):
+        oracle.initial_solution(s, 10, 0)
