@@ -278,6 +278,16 @@ rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);
 rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
                                   const double *r, double *x);
 
+/* ---- the initial solution of Algorithm 2 (Appendix) -----------------------
+ * x0 = (<b, b~> / ||b~||^2) y, y = the sum of the rows of static block
+ * `block` (each column summed over the block's rows in ascending order),
+ * b~ = A y.  x0 lies in range(A^T) and ||b - A x0|| <= ||b|| (the Remark after
+ * Algorithm 2); pass it as x0 to rorbk_solve.  b (m) and x0 (n) are device
+ * FP64 vectors; the call uses the handle's workspace and returns when x0 is
+ * written.  Errors: RORBK_ERR_INVALID_ARG for a NULL pointer, a block outside
+ * [0, k), or A y = 0. */
+rorbk_status rorbk_initial_solution(rorbk_handle h, int64_t block, const double *b, double *x0);
+
 /* ---- many solves in one launch --------------------------------------
  * (Beside the paper: its method solves one system; these run many ROR-BK
  * solves at once, each exactly the solve rorbk_solve would run.)

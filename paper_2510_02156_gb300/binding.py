@@ -86,6 +86,7 @@ SIGNATURES = {
     "rorbk_residual32": (C.c_int, [_P, _P, _P, _P, _P]),
     "rorbk_topk": (C.c_int, [_P, _P, _P]),
     "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
+    "rorbk_initial_solution": (C.c_int, [_P, _I64, _P, _P]),
     "rorbk_clone": (C.c_int, [_P, _P]),
     "rorbk_batch_create": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "rorbk_batch_solve": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P, _P]),
@@ -198,6 +199,10 @@ class Handle:
         self.info = Info()
         _check(lib().rorbk_get_info(self.h, C.byref(self.info)), self.h)
         return self
+
+    def initial_solution(self, b, x0, block=0):
+        """rorbk_initial_solution (Algorithm 2) on device tensors b (m), x0 (n)."""
+        _check(lib().rorbk_initial_solution(self.h, block, _ptr(b), _ptr(x0)), self.h)
 
     def clone(self):
         """rorbk_clone: a Handle sharing this one's set-up, with its own workspace."""
