@@ -12,5 +12,5 @@ from .oracle import (  # noqa: F401
     build, lib, OracleMatrix, philox4x64_10, partition, orthogonality,
     proposal, sample, residual, topk, block_gram, cholesky, chol_solve,
     spd_inverse, static_operator, update_with_inverse, update_with_cholesky,
-    solve, SolveResult, initial_solution, block_norms, weighted_cdf, PAPER, RESIDUAL_WEIGHTED,
+    solve, SolveResult, initial_solution, fabgmres, block_norms, weighted_cdf, PAPER, RESIDUAL_WEIGHTED,
 )

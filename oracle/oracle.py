@@ -71,6 +71,8 @@ def lib():
                                         _P, _P, _P, _P, _P, _P]),
                 "orc_block_norms": (None, [_P, _P, _I64, _P]),
                 "orc_initial_solution": (C.c_int, [_P, _I64, _I64, _P, _P]),
+                "orc_fabgmres": (C.c_int, [_P, _I64, _D, _P, _P, _P, _D, _I64, _D, _I64,
+                                           C.c_uint64, C.c_uint64, _I64, _P, _P, _P, _P]),
                 "orc_weighted_cdf": (_D, [_P, _P, _I64, _P]),
             }
             for name, (res, args) in sig.items():
@@ -290,6 +292,25 @@ def solve(system, b=None, x0=None, *, k=None, mu=None, tol=None, maxit=100,
         I=None if tr_I is None else tr_I[: it * K].reshape(it, K),
         x_trace=None if tr_x is None else tr_x[: it * M.n].reshape(it, M.n),
     )
+
+
+def fabgmres(system, b=None, x0=None, *, tol=None, maxit=50, eta=1e-2, lmax=100, seed=0,
+             sysid=0, n_static=3):
+    """Algorithm 3: flexible AB-GMRES with ROR-BK inner solves.  Returns
+    (x, outer, inner, rrn, estimates, status)."""
+    M = _mat(system)
+    b = np.ascontiguousarray(system.b if b is None else b, dtype=np.float64)
+    x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+    tol = system.tol if tol is None else tol
+    x = np.zeros(M.n)
+    est = np.full(maxit, np.nan)
+    outer, inner, rrn = C.c_int64(0), C.c_int64(0), C.c_double(0.0)
+    st = lib().orc_fabgmres(M.ref, system.num_blocks, system.lam, _ptr(b), _ptr(x0), _ptr(x), tol,
+                            maxit, eta, lmax, C.c_uint64(seed), C.c_uint64(sysid), n_static,
+                            C.byref(outer), C.byref(inner), C.byref(rrn), _ptr(est))
+    if st < 0:
+        raise RuntimeError(f"oracle FAB-GMRES status {st}")
+    return x, outer.value, inner.value, rrn.value, est[: outer.value], st
 
 
 def initial_solution(system, first, count, b=None):

@@ -702,3 +702,104 @@ done:
     free(I); free(rI); free(rows); free(work); free(rho); free(wcdf);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3 (Appendix): flexible AB-GMRES with ROR-BK as the right
+ * preconditioner.  x = x0 (0 if NULL), r0 = b - A x, beta = ||r0||,
+ * v_1 = r0 / beta.  Outer step j: z_j = ROR-BK on A z = v_j from z = 0 until
+ * ||v_j - A z|| <= eta ||v_j|| or lmax iterations (the Philox counter runs on
+ * across the inner solves); w = A z_j; modified Gram-Schmidt against
+ * v_1..v_j (h_ij = <w, v_i>, w -= h_ij v_i); h_{j+1,j} = ||w||,
+ * v_{j+1} = w / h_{j+1,j}; Givens rotations keep the least-squares problem
+ * min ||beta e1 - H y|| triangular, and |g_{j+1}| is its residual norm.  Stops
+ * when |g_{j+1}| <= tol ||b||, at breakdown (h_{j+1,j} = 0) or after maxit
+ * outer steps; then y from the triangle, x += Z y.  Inner products and norms
+ * are fused chains in index order.  Outputs: outer and inner iteration counts,
+ * the final ||b - A x|| / ||b||, the residual estimate after each outer step. */
+static double dotv(const double *a, const double *b, int64_t m)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s = fma(a[i], b[i], s);
+    return s;
+}
+
+int orc_fabgmres(const orc_matrix *A, int64_t k, double mu, const double *b,
+                 const double *x0, double *x, double tol, int64_t maxit, double eta,
+                 int64_t lmax, uint64_t seed, uint64_t sysid, int64_t n_static,
+                 int64_t *outer_out, int64_t *inner_out, double *rrn_out, double *est_hist)
+{
+    int64_t m = A->m, n = A->n;
+    if (maxit < 1 || lmax < 0 || !(eta >= 0) || !(tol >= 0)) return ORC_ERR_ARG;
+    double *V = (double *)malloc((size_t)(maxit + 1) * m * sizeof(double));
+    double *Z = (double *)malloc((size_t)maxit * n * sizeof(double));
+    double *H = (double *)calloc((size_t)(maxit + 1) * maxit, sizeof(double));
+    double *cs = (double *)malloc((size_t)maxit * sizeof(double));
+    double *sn = (double *)malloc((size_t)maxit * sizeof(double));
+    double *g = (double *)calloc((size_t)(maxit + 1), sizeof(double));
+    double *y = (double *)malloc((size_t)maxit * sizeof(double));
+    double *w = (double *)malloc((size_t)m * sizeof(double));
+    double *zero = (double *)calloc((size_t)m, sizeof(double));
+    int st = ORC_OK;
+    if (!V || !Z || !H || !cs || !sn || !g || !y || !w || !zero) { st = ORC_ERR_OOM; goto done; }
+    for (int64_t c = 0; c < n; ++c) x[c] = x0 ? x0[c] : 0.0;
+    double bnorm = sqrt(dotv(b, b, m));
+    *outer_out = 0; *inner_out = 0; *rrn_out = 0.0;
+    if (bnorm == 0.0) { for (int64_t c = 0; c < n; ++c) x[c] = 0.0; goto done; }
+    double beta = sqrt(orc_residual(A, b, x, w));
+    if (beta == 0.0) goto done;
+    for (int64_t i = 0; i < m; ++i) V[i] = w[i] / beta;
+    g[0] = beta;
+    int64_t J = 0, inner = 0;
+    for (int64_t j = 0; j < maxit; ++j) {
+        double *vj = V + j * m, *zj = Z + j * n;
+        int64_t it = 0;
+        double rr = 0.0;
+        int e = orc_solve(A, k, mu, vj, NULL, zj, eta, lmax, seed, sysid, n_static, inner, 0,
+                          &it, &rr, NULL, NULL, NULL, NULL);
+        if (e < 0) { st = e; goto done; }
+        inner += it;
+        orc_residual(A, zero, zj, w);            /* w = -A z_j */
+        for (int64_t i = 0; i < m; ++i) w[i] = -w[i];
+        for (int64_t i = 0; i <= j; ++i) {
+            const double *vi = V + i * m;
+            double h = dotv(w, vi, m);
+            H[i * maxit + j] = h;
+            for (int64_t t = 0; t < m; ++t) w[t] = fma(-h, vi[t], w[t]);
+        }
+        double hn = sqrt(dotv(w, w, m));
+        H[(j + 1) * maxit + j] = hn;
+        if (hn > 0.0) for (int64_t t = 0; t < m; ++t) V[(j + 1) * m + t] = w[t] / hn;
+        for (int64_t i = 0; i < j; ++i) {        /* earlier rotations on column j */
+            double a0 = H[i * maxit + j], a1 = H[(i + 1) * maxit + j];
+            H[i * maxit + j] = cs[i] * a0 + sn[i] * a1;
+            H[(i + 1) * maxit + j] = -sn[i] * a0 + cs[i] * a1;
+        }
+        double a0 = H[j * maxit + j], a1 = H[(j + 1) * maxit + j];
+        double d = sqrt(a0 * a0 + a1 * a1);
+        cs[j] = a0 / d; sn[j] = a1 / d;
+        H[j * maxit + j] = d; H[(j + 1) * maxit + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        J = j + 1;
+        double est = fabs(g[j + 1]) / bnorm;
+        if (est_hist) est_hist[j] = est;
+        if (est <= tol || hn == 0.0) break;
+    }
+    for (int64_t i = J - 1; i >= 0; --i) {       /* R y = g */
+        double s = g[i];
+        for (int64_t l = i + 1; l < J; ++l) s = fma(-H[i * maxit + l], y[l], s);
+        y[i] = s / H[i * maxit + i];
+    }
+    for (int64_t c = 0; c < n; ++c) {
+        double u = 0.0;
+        for (int64_t j = 0; j < J; ++j) u = fma(y[j], Z[j * n + c], u);
+        x[c] = x[c] + u;
+    }
+    *outer_out = J;
+    *inner_out = inner;
+    *rrn_out = sqrt(orc_residual(A, b, x, w)) / bnorm;
+    st = *rrn_out <= tol ? ORC_OK : ORC_NOT_CONVERGED;
+done:
+    free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y); free(w); free(zero);
+    return st;
+}

@@ -484,3 +484,39 @@ def test_initial_solution_rejects_an_empty_set():
     s = W.random_sparse(40, 12, 0.3, seed=3, num_blocks=2)
     with pytest.raises(ValueError):
         oracle.initial_solution(s, 10, 0)
+
+
+# --------------------------------- Algorithm 3: FAB-GMRES with ROR-BK inside
+def test_fabgmres_with_exact_inner_solves_reaches_lu_solution():
+    """When the inner ROR-BK solve is (nearly) exact, B ~ A^{-1}, so A z_1 =
+    v_1 and the first outer step already holds the solution."""
+    s = W.random_sparse(60, 60, 0.25, seed=21, num_blocks=3, lam=1e-12, tol=1e-12)
+    A = s.to_dense() + 6.0 * np.eye(60)
+    S = W.System("diag", 60, 60, dense=A, b=A @ s.x_true, x_true=s.x_true, num_blocks=3,
+                 lam=1e-12, tol=1e-12)
+    x, outer, inner, rrn, est, st = oracle.fabgmres(S, tol=1e-10, maxit=10, eta=1e-13,
+                                                    lmax=200000)
+    assert outer <= 2 and rrn <= 1e-10
+    np.testing.assert_allclose(x, np.linalg.solve(A, S.b), rtol=1e-8, atol=1e-10)
+
+
+def test_fabgmres_estimates_are_monotone_and_exact_at_the_end():
+    """GMRES minimises the residual over a growing space: the estimates never
+    increase, and the last equals ||b - A x|| / ||b|| of the returned x."""
+    s = W.laplace2d(g=12, num_blocks=4)
+    x, outer, inner, rrn, est, st = oracle.fabgmres(s, tol=1e-10, maxit=60, eta=1e-1, lmax=50)
+    assert st == 0 and outer >= 3
+    assert np.all(np.diff(est) <= 1e-14)
+    true = np.linalg.norm(s.b - s.to_dense() @ x) / np.linalg.norm(s.b)
+    assert true == pytest.approx(rrn, rel=1e-12)
+    assert abs(est[-1] - rrn) <= 1e-3 * rrn + 1e-14
+
+
+def test_fabgmres_wide_system_gives_min_norm_solution():
+    """With x0 and the inner starts in range(A^T), the solution lies in
+    range(A^T): on a wide system it is the minimum-norm solution."""
+    s = W.gaussian_dense(80, 200, seed=6, num_blocks=4, lam=1e-10)
+    x, outer, inner, rrn, est, st = oracle.fabgmres(s, tol=1e-11, maxit=40, eta=1e-2, lmax=200)
+    assert st == 0
+    x_mn = np.linalg.lstsq(s.dense, s.b, rcond=None)[0]
+    assert np.linalg.norm(x - x_mn) / np.linalg.norm(x_mn) <= 1e-8
