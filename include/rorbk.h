@@ -288,6 +288,25 @@ rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
  * [0, k), or A y = 0. */
 rorbk_status rorbk_initial_solution(rorbk_handle h, int64_t block, const double *b, double *x0);
 
+/* ---- Algorithm 3 (Appendix): flexible AB-GMRES with ROR-BK inside -------
+ * Solves A x = b by GMRES on A B with B = ROR-BK as a right preconditioner:
+ * x = x0 (NULL: 0), v_1 = (b - A x) / ||b - A x||; outer step j runs ROR-BK on
+ * A z = v_j from z = 0 (rorbk_solve on this handle with tolerance eta and at
+ * most lmax iterations; the Philox counter continues from opt->start_iter
+ * across the inner solves), w = A z_j, modified Gram-Schmidt against
+ * v_1..v_j (h_ij = <w, v_i>), v_{j+1} = w / ||w||, and Givens rotations on the
+ * Hessenberg matrix.  It stops when the GMRES residual estimate reaches
+ * tol * ||b||, at breakdown or after maxit (<= 4096) outer steps, then forms
+ * x += Z y.  b (m), x0 and x (n) are device FP64 vectors; opt as for
+ * rorbk_solve (FP64 or MIXED inner solves; no host loop, trace or weighted
+ * draws).  res->iters = outer steps, res->refinements = inner ROR-BK
+ * iterations in total, res->rrn = ||b - A x|| / ||b|| of the returned x.
+ * The Krylov basis ((maxit + 1) m + maxit n doubles) is allocated for the
+ * call.  Returns RORBK_OK or RORBK_NOT_CONVERGED; errors as rorbk_solve. */
+rorbk_status rorbk_fabgmres(rorbk_handle h, const double *b, const double *x0, double *x,
+                            double tol, int64_t maxit, double eta, int64_t lmax,
+                            const rorbk_options *opt, rorbk_result *res);
+
 /* ---- many solves in one launch --------------------------------------
  * (Beside the paper: its method solves one system; these run many ROR-BK
  * solves at once, each exactly the solve rorbk_solve would run.)

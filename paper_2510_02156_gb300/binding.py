@@ -87,6 +87,7 @@ SIGNATURES = {
     "rorbk_topk": (C.c_int, [_P, _P, _P]),
     "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
     "rorbk_initial_solution": (C.c_int, [_P, _I64, _P, _P]),
+    "rorbk_fabgmres": (C.c_int, [_P, _P, _P, _P, _D, _I64, _D, _I64, _P, _P]),
     "rorbk_clone": (C.c_int, [_P, _P]),
     "rorbk_batch_create": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "rorbk_batch_solve": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P, _P]),
@@ -199,6 +200,18 @@ class Handle:
         self.info = Info()
         _check(lib().rorbk_get_info(self.h, C.byref(self.info)), self.h)
         return self
+
+    def fabgmres(self, b, x, x0=None, tol=1e-8, maxit=50, eta=1e-2, lmax=100, seed=0,
+                 system_id=0, n_static=3, start_iter=0, precision=PREC_FP64, stream=None):
+        """rorbk_fabgmres (Algorithm 3) on device tensors; returns the Result
+        (iters = outer steps, refinements = inner iterations in total)."""
+        opt = default_options(seed=seed, system_id=system_id, n_static=n_static,
+                              start_iter=start_iter, precision=precision,
+                              stream=_stream_ptr(stream))
+        res = Result()
+        _check(lib().rorbk_fabgmres(self.h, _ptr(b), _ptr(x0), _ptr(x), tol, maxit, eta, lmax,
+                                    C.byref(opt), C.byref(res)), self.h)
+        return res
 
     def initial_solution(self, b, x0, block=0):
         """rorbk_initial_solution (Algorithm 2) on device tensors b (m), x0 (n)."""
