@@ -61,6 +61,8 @@ def parse():
                    help="skip the dense measurement (A = U diag(s) V^T, 200,000 x 2,048, "
                         "781 blocks of 256 rows; a fixed number of iterations)")
     p.add_argument("--dense-iters", type=int, default=100)
+    p.add_argument("--no-fabgmres", action="store_true",
+                   help="skip FAB-GMRES with ROR-BK inner solves (Algorithm 3) on the main workload")
     p.add_argument("--no-weighted", action="store_true",
                    help="skip the comparison of the residual-weighted draws with the paper's "
                         "(FP64 to tolerance on the 262,144-unknown power-law system)")
@@ -304,6 +306,7 @@ def run_ours(args, rank, world, local):
                  inner_tol=args.inner_tol)
     e2e_s = time.perf_counter() - t1
 
+    fg = None if args.no_fabgmres else fabgmres_measurement(args, s, h, b, x, flush)
     ag = None if args.no_autograd else autograd_measurement(args)
     weighted = None if args.no_weighted else weighted_measurement(args)
     batched = None if args.no_batched else batched_measurement(args)
@@ -346,6 +349,7 @@ def run_ours(args, rank, world, local):
         "autograd": ag,
         "batched": batched,
         "residual_weighted": weighted,
+        "fabgmres": fg,
         "dense": dense,
         "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
@@ -506,6 +510,26 @@ def dense_measurement(args, flush):
                             "peak": peak, "unit": "GB/s", "frac": by32 / (cold32 * 1e-3) / 1e9 / peak}
     h.close()
     del s
+    return out
+
+
+def fabgmres_measurement(args, s, h, b, x, flush):
+    """Algorithm 3 on the main workload: flexible AB-GMRES whose preconditioner
+    is a ROR-BK solve of at most 200 iterations to a relative residual of 0.1,
+    to the same tolerance, with FP64 and with mixed inner solves."""
+    import torch
+    from paper_2510_02156_gb300 import binding as B
+    out = {"algorithm": "Algorithm 3 (flexible AB-GMRES, ROR-BK inner solves)",
+           "eta": 0.1, "lmax": 200, "max_outer": 400}
+    for name, prec in (("mixed", B.PREC_MIXED), ("fp64", B.PREC_FP64)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = h.fabgmres(b, x, tol=s.tol, maxit=400, eta=0.1, lmax=200, seed=1, precision=prec)
+        torch.cuda.synchronize()
+        out[name] = {"time_s": time.perf_counter() - t0, "outer": int(r.iters),
+                     "inner_iterations": int(r.refinements), "rrn": float(r.rrn),
+                     "converged": bool(r.converged)}
     return out
 
 
