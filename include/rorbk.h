@@ -150,8 +150,30 @@ typedef struct {
     rorbk_trace *trace;     /* FP64 only                               (NULL) */
     void *stream;           /* cudaStream_t for all work               (0 = legacy default) */
     int32_t dist_mode;      /* RORBK_DIST_*: how the static blocks are drawn (PAPER) */
+    int32_t residual_mode;  /* RORBK_RESIDUAL_*: how r = b - A x is formed   (EXACT) */
+    int32_t refresh;        /* INCREMENTAL: an exact residual every `refresh`
+                               iterations (0: 50)                          (0)    */
     int32_t reserved_;
 } rorbk_options;
+
+/* How the full residual of each iteration is formed (rorbk_options.residual_mode).
+ *   EXACT       : r = b - A x over all of A (Algorithm 1).
+ *   INCREMENTAL : a cheaper evaluation of the same residual, which Section
+ *                 3.1's cost discussion leaves open (there the O(mn) residual
+ *                 dominates an iteration): every x += dx of
+ *                 the iteration is logged as (column, increment) pairs and
+ *                 r -= A dx is applied through a CSC copy of A (built at the
+ *                 first such solve, 16 bytes per nonzero) with atomic adds, so
+ *                 r carries rounding drift and the order of the adds varies
+ *                 from run to run.  An exact residual is formed in the first
+ *                 iteration, every `refresh` iterations, when the log
+ *                 overflows, and whenever the incremental residual reaches the
+ *                 tolerance: the solve stops only on an exact residual.
+ *                 Sparse (CSR) systems, FP64 or MIXED; not with
+ *                 residual-weighted draws; single solves (not batched);
+ *                 RORBK_ERR_UNSUPPORTED otherwise.  `refresh` < 0 is
+ *                 RORBK_ERR_INVALID_ARG. */
+enum { RORBK_RESIDUAL_EXACT = 0, RORBK_RESIDUAL_INCREMENTAL = 1 };
 
 /* Distribution of the static blocks (rorbk_options.dist_mode).
  *   PAPER             : tau ~ P, P_t proportional to Pbar_t (Algorithm 1 step 3;

@@ -24,6 +24,7 @@ F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 OK, NOT_CONVERGED = 0, 1
 DIST_PAPER, DIST_RESIDUAL_WEIGHTED = 0, 1
+RESIDUAL_EXACT, RESIDUAL_INCREMENTAL = 0, 1
 
 
 class RorbkError(RuntimeError):
@@ -53,7 +54,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("start_iter", C.c_int64), ("inner_tol", C.c_double),
                 ("inner_maxit", C.c_int64), ("host_loop", C.c_int32), ("poll", C.c_int32),
                 ("trace", C.c_void_p), ("stream", C.c_void_p), ("dist_mode", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("residual_mode", C.c_int32), ("refresh", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -279,13 +280,15 @@ class Handle:
     # -- whole solve --------------------------------------------------------
     def solve(self, b, x, x0=None, tol=1e-8, maxit=1000, seed=0, system_id=0, n_static=3,
               start_iter=0, precision=PREC_FP64, trace=None, stream=None, inner_tol=1e-4,
-              inner_maxit=2000000, host_loop=0, poll=64, dist_mode=DIST_PAPER):
+              inner_maxit=2000000, host_loop=0, poll=64, dist_mode=DIST_PAPER,
+              residual_mode=RESIDUAL_EXACT, refresh=0):
         """rorbk_solve on device tensors b (m), x (n), x0 (n or None)."""
         opt = default_options(seed=seed, system_id=system_id, n_static=n_static,
                               start_iter=start_iter, precision=precision,
                               stream=_stream_ptr(stream), inner_tol=inner_tol,
                               inner_maxit=inner_maxit, host_loop=host_loop, poll=poll,
-                              dist_mode=dist_mode)
+                              dist_mode=dist_mode, residual_mode=residual_mode,
+                              refresh=refresh)
         if trace is not None:
             opt.trace = C.cast(C.pointer(trace), C.c_void_p)
         res = Result()

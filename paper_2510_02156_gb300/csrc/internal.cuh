@@ -64,6 +64,14 @@ struct Ctl {
     int dynE, dyn_nsh, dyn_nS, dyn_npair, dyn_nraw, pad3_;
     int halt;              // no further iteration runs (converged, error or maxit)
     int weighted;          // residual-weighted draws (RORBK_DIST_RESIDUAL_WEIGHTED)
+    // incremental residual (RORBK_RESIDUAL_INCREMENTAL): the scatters log
+    // (column, increment) pairs, r -= A dx is applied from the log, and an
+    // exact residual is formed when inc_full is set (first iteration, every
+    // inc_refresh iterations, a full log, or to confirm convergence)
+    int inc, inc_full, inc_count, inc_refresh;
+    int nlog, log_full, log_cap, pad4_;
+    int *log_col;          // [log_cap] changed columns
+    double *log_val;       // [log_cap] their increments
     const double *scdf;    // the running sum the static draws use (P's, or the weighted one)
     int pad2_;
 };
@@ -158,6 +166,15 @@ struct rorbk_ctx {
     double *r = nullptr, *xb = nullptr, *bb = nullptr, *x64 = nullptr;
     double *sd_scratch = nullptr;   // [2 kMaxBlockRows] r_tau and y of the dense static updates
     double *wgt = nullptr, *wcdf = nullptr;   // [k] residual-weighted draws: weights, running sum
+    // incremental residual: CSC copy of A (built at the first such solve) and
+    // the log of (column, increment) pairs
+    int *csc_ptr = nullptr, *csc_row = nullptr;
+    double *csc_val = nullptr;
+    float *csc_val32 = nullptr;
+    int *ilog_col = nullptr;
+    double *ilog_val = nullptr;
+    int ilog_cap = 0;
+    cudaGraphExec_t exec_fp64_inc = nullptr, exec_mixed_inc = nullptr;
     cudaGraphExec_t exec_fp64_w = nullptr;   // the FP64 loop with residual-weighted draws
     float *r32 = nullptr, *b32 = nullptr, *d32 = nullptr;
     double *partials = nullptr;
@@ -190,6 +207,9 @@ namespace rorbk {
 // host helpers implemented in rorbk.cu
 rorbk_status fail(rorbk_ctx *h, rorbk_status st, const std::string &msg);
 rorbk_status cuda_check(rorbk_ctx *h, cudaError_t e, const char *what);
+// incremental residual: CSC copy of A and the change log, built once (incremental.cu)
+rorbk_status ensure_incremental(rorbk_ctx *h);
+constexpr int kIncRefreshDefault = 50;
 // what rorbk_last_error(NULL) reports: the last failure on this thread that
 // left no handle
 void record_setup_error(const std::string &msg);
@@ -206,11 +226,11 @@ int residual_grid(rorbk_ctx *h);   // one resident wave of the residual kernel
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
                   unsigned long long hcond);
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
-                      unsigned long long hcond, int weighted = 0);
+                      unsigned long long hcond, int weighted = 0, int inc = 0);
+void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner, int inc = 0);
 void launch_weights(rorbk_ctx *h, const double *r);   // residual-weighted running sum from r
 void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x);
 void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner);
-void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner);
 void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_outer);
 void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r);
 void launch_topk_only(rorbk_ctx *h, const double *r, int *I);

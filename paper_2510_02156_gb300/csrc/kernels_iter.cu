@@ -106,6 +106,26 @@ Mat<float> make_mat<float>(rorbk_ctx *h) {
                       h->sell.val32};
 }
 
+// ---------------------------------------------------- incremental residual
+// Appends (c, v) for an update x_c += v to the iteration's change log.  The
+// calling lanes of a warp take consecutive slots from one atomic; entries past
+// the capacity set log_full, which makes the next residual exact.
+__device__ __forceinline__ void inc_log(Ctl *ctl, int c, double v) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&ctl->nlog, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    const int idx = base + __popc(mask & ((1u << lane) - 1u));
+    if (idx < ctl->log_cap) {
+        ctl->log_col[idx] = c;
+        ctl->log_val[idx] = v;
+    } else {
+        ctl->log_full = 1;
+    }
+}
+
 // ------------------------------------------------------------------ begin
 // ||b||, x = x0 or 0, loop state.  One block; sets the WHILE condition.
 __global__ void k_begin(const double *__restrict__ b, int m, const double *__restrict__ x0,
@@ -132,6 +152,10 @@ __global__ void k_begin(const double *__restrict__ b, int m, const double *__res
         ctl->n_in = 0;
         ctl->n_eq = 0;
         ctl->outer = 0;
+        ctl->inc_full = 1;         // the first residual of a solve is exact
+        ctl->inc_count = 0;
+        ctl->nlog = 0;
+        ctl->log_full = 0;
         if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
     }
 }
@@ -202,7 +226,8 @@ __device__ int stage_issue(const Mat<T> &A, int tau, Stage<T> st, unsigned long 
     return a0;
 }
 
-template <typename T>
+// LOG: the incremental residual's variant, which logs every change of x.
+template <typename T, bool LOG = false>
 __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__ b, T *x,
                                                  Ctl *ctl, int force_tau, int use_stages,
                                                  int l_begin) {
@@ -213,6 +238,7 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
     __shared__ int s_a0[2];
     __shared__ int s_fail;
     if (force_tau < 0 && (ctl->done || ctl->halt)) return;
+    const bool lg = LOG && force_tau < 0;            // log x's changes
     const int nst = force_tau >= 0 ? 1 : ctl->n_static;
     const int a = threadIdx.x;
     unsigned long long *bar = dsm_u64;                // two mbarriers
@@ -310,6 +336,7 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
                 for (int u = q; u < pend && st.btcol[u - a0] == c; ++u)
                     acc3 = Ar<T>::fma(st.btval[u - a0], y[st.btrow[u - a0]], acc3);
                 x[c] = Ar<T>::add(x[c], acc3);
+                if (lg) inc_log(ctl, c, (double)acc3);
             }
         } else {
             const int ns = A.nseg[tau];
@@ -320,12 +347,17 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
                 for (; q < pend && A.bt_col[q] == c; ++q)
                     acc3 = Ar<T>::fma(A.bt_val[q], y[A.bt_row[q]], acc3);
                 x[c] = Ar<T>::add(x[c], acc3);
+                if (lg) inc_log(ctl, c, (double)acc3);
             }
         }
         __syncthreads();
         // this stage is free again: bring in block l + 2
         if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stg[sidx], &bar[sidx]) : -1;
     }
+    // incremental residual: this iteration's residual is exact after a full
+    // log or every inc_refresh iterations
+    if (lg && a == 0 && !ctl->inc_full)
+        if (ctl->log_full || ++ctl->inc_count >= ctl->inc_refresh) ctl->inc_full = 1;
 }
 
 // ---------------------------------------------------------------- residual
@@ -389,6 +421,7 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
     __shared__ double red[32];
     __shared__ int is_last;
     if ((finalize == 1 || finalize == 3) && (ctl->done || ctl->halt)) return;
+    if (finalize == 1 && ctl->inc && !ctl->inc_full) return;   // r came from the change log
     const V *__restrict__ val = sell_values<V, T>(A);
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
@@ -481,6 +514,12 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
             ctl->n_in = 0;
             ctl->n_eq = 0;
         }
+        if (finalize == 1 && ctl->inc) {   // the log so far is folded into this r
+            ctl->nlog = 0;
+            ctl->log_full = 0;
+            ctl->inc_full = 0;
+            ctl->inc_count = 0;
+        }
     }
     __syncthreads();
     if (finalize == 1) {
@@ -491,6 +530,94 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
         } else {
             for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist1[i] = 0u;
         }
+    }
+}
+
+// Incremental residual, step 1: r -= A dx from the iteration's change log,
+// through the CSC copy of A.  A group of kIncLanes lanes takes one logged
+// column and subtracts a_ic * dx_c from r_i for its entries (atomic adds, so
+// the order of the additions into r_i varies from run to run).  Does nothing
+// when this iteration's residual is exact.
+constexpr int kIncLanes = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inc_apply(const int *__restrict__ cptr,
+                                                   const int *__restrict__ crow,
+                                                   const T *__restrict__ cval, T *r, Ctl *ctl) {
+    if (ctl->done || ctl->halt || ctl->inc_full) return;
+    const int nlog = min(ctl->nlog, ctl->log_cap);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = t % kIncLanes, ng = gridDim.x * blockDim.x / kIncLanes;
+    for (int e = t / kIncLanes; e < nlog; e += ng) {
+        const int c = ctl->log_col[e];
+        const T d = (T)ctl->log_val[e];
+        const int p1 = cptr[c + 1];
+        for (int p = cptr[c] + sub; p < p1; p += kIncLanes) atomicAdd(&r[crow[p]], -(cval[p] * d));
+    }
+}
+
+// Incremental residual, step 2: ||r||^2, the first radix level of the top-K
+// select and the stopping test on the updated r.  A relative residual at or
+// below the tolerance (or not finite) is not trusted: it sets inc_full, and
+// the exact residual kernel that follows decides in the same iteration.
+template <typename T>
+__global__ void __launch_bounds__(256) k_inc_finish(const T *__restrict__ r, int m, int K,
+                                                    double *partials, unsigned *hist1, Ctl *ctl) {
+    __shared__ unsigned hist[kHistBins];
+    __shared__ double red[32];
+    __shared__ int is_last, stop;
+    if (ctl->done || ctl->halt || ctl->inc_full) return;
+    for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    double rr = 0.0;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < m; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool act = i < m;
+        unsigned bin = 0;
+        if (act) {
+            const T ri = r[i];
+            rr = __fma_rn((double)ri, (double)ri, rr);
+            bin = (unsigned)(abs_key(ri) >> 52);
+        }
+        hist_add(hist, bin, act);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
+        if (hist[i]) atomicAdd(&hist1[i], hist[i]);
+    rr = block_sum(rr, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = rr;
+        __threadfence();
+        is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double tot = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += partials[i];
+    tot = block_sum(tot, red);
+    if (threadIdx.x == 0) {
+        ctl->ticket = 0;
+        ctl->n_in = 0;
+        ctl->n_eq = 0;
+        ctl->nlog = 0;
+        const double rrn = sqrt(tot) / ctl->bnorm;
+        stop = !(rrn > ctl->tol);
+        if (stop) {
+            ctl->inc_full = 1;
+        } else {
+            ctl->rr = tot;
+            ctl->rrn = rrn;
+            if (ctl->tr_rrn && ctl->iter < ctl->trace_cap) ctl->tr_rrn[ctl->iter] = rrn;
+        }
+    }
+    __syncthreads();
+    if (!stop) {
+        int bin, above;
+        select_bin(hist1, K, &bin, &above);
+        if (threadIdx.x == 0) { ctl->sel1 = bin; ctl->above1 = above; }
+    } else {
+        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist1[i] = 0u;
     }
 }
 
@@ -1288,7 +1415,7 @@ __device__ void end_iteration(const T *x, int n, Ctl *ctl, int use_cond,
 // x += A_I^T y: a column used by one row of I takes its single product; a
 // shared column is summed over its rows in ascending order by the entry that
 // owns it.  The last block clears the column marks and ends the iteration.
-template <typename T>
+template <typename T, bool LOG = false>
 __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ctl, int count_iter,
                                                      int use_cond,
                                                      cudaGraphConditionalHandle hcond) {
@@ -1298,12 +1425,15 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
         return;
     }
     const int E = ctl->dynE, nsh = ctl->dyn_nsh;
+    const bool lg = LOG && count_iter;               // log x's changes
     const unsigned ep = *D.epoch;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     for (int e = gt; e < E; e += gs) {
         const int c = D.ecol[e];
         if (D.shared[c] != ep) {
-            x[c] = Ar<T>::add(x[c], Ar<T>::fma(as<T>(D.eval[e]), as<T>(D.y[D.erow[e]]), T(0)));
+            const T d = Ar<T>::fma(as<T>(D.eval[e]), as<T>(D.y[D.erow[e]]), T(0));
+            x[c] = Ar<T>::add(x[c], d);
+            if (lg) inc_log(ctl, c, (double)d);
         } else if ((unsigned)D.skeys[D.segpos[c]] == (unsigned)e) {
             T acc = T(0);
             for (int u = D.segpos[c]; u < nsh && (int)(D.skeys[u] >> 32) == c; ++u) {
@@ -1311,6 +1441,7 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
                 acc = Ar<T>::fma(as<T>(D.eval[e2]), as<T>(D.y[D.erow[e2]]), acc);
             }
             x[c] = Ar<T>::add(x[c], acc);
+            if (lg) inc_log(ctl, c, (double)acc);
         }
     }
     __threadfence();
@@ -1727,6 +1858,15 @@ __global__ void __launch_bounds__(256) k_inner_prep(const double *__restrict__ r
         in->tr_I = nullptr;
         in->tr_x = nullptr;
         in->tr_dyn = nullptr;
+        in->inc = out->inc;            // incremental residual: same log, exact first residual
+        in->inc_refresh = out->inc_refresh;
+        in->inc_full = 1;
+        in->inc_count = 0;
+        in->nlog = 0;
+        in->log_full = 0;
+        in->log_cap = out->log_cap;
+        in->log_col = out->log_col;
+        in->log_val = out->log_val;
         if (use_cond) cudaGraphSetConditional(hcond, in->halt ? 0u : 1u);
     }
 }
@@ -1788,6 +1928,10 @@ void configure_kernels() {
                          (int)static_smem_bytes<double>());
     cudaFuncSetAttribute(k_static<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)static_smem_bytes<float>());
+    cudaFuncSetAttribute(k_static<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<double>());
+    cudaFuncSetAttribute(k_static<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<float>());
     cudaFuncSetAttribute(k_topk_collect<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)collect_smem_bytes());
     cudaFuncSetAttribute(k_topk_collect<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1810,7 +1954,7 @@ void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, in
 
 template <typename T>
 static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int check_done,
-                                int count_iter, int use_cond, unsigned long long hcond) {
+                                int count_iter, int use_cond, unsigned long long hcond, int inc = 0) {
     if (h->format == RORBK_FORMAT_DENSE) {
         const int K = h->K, T16 = (K + kGT - 1) / kGT;
         k_dyn_dense_gram<<<T16 * (T16 + 1) / 2, kGT * kGT, 0, h->stream>>>(h->val, (int)h->n, K, h->mu,
@@ -1835,14 +1979,20 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
     Mat<T> A = make_mat<T>(h);
     k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
                                                                         check_done);
-    k_dyn_scatter<T><<<2 * h->num_sms, 512, 0, h->stream>>>(x, (int)h->n, dyn_bufs(h), ctl,
-                                                           count_iter, use_cond,
-                                                           (cudaGraphConditionalHandle)hcond);
+    (inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>)<<<2 * h->num_sms, 512, 0, h->stream>>>(
+        x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond, (cudaGraphConditionalHandle)hcond);
 }
 
 template <typename T>
+static const T *csc_values(const rorbk_ctx *h);
+template <>
+const double *csc_values<double>(const rorbk_ctx *h) { return h->csc_val; }
+template <>
+const float *csc_values<float>(const rorbk_ctx *h) { return h->csc_val32; }
+
+template <typename T>
 void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_cond,
-                        unsigned long long hcond, int weighted = 0) {
+                        unsigned long long hcond, int weighted = 0, int inc = 0) {
     Mat<T> A = make_mat<T>(h);
     if (h->format == RORBK_FORMAT_DENSE) {
         T *rl = (T *)h->sd_scratch, *yy = rl + kMaxBlockRows;
@@ -1856,7 +2006,14 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
         // updates beyond kDenseStatic (n_static > 3), if any
         k_static<T><<<1, 1024, static_smem_bytes<T>(), h->stream>>>(A, b, x, ctl, -1, 0, kDenseStatic);
     } else {
-        k_static<T><<<1, 1024, static_smem_bytes<T>(), h->stream>>>(A, b, x, ctl, -1, 1, 0);
+        (inc ? k_static<T, true> : k_static<T, false>)<<<1, 1024, static_smem_bytes<T>(), h->stream>>>(
+            A, b, x, ctl, -1, 1, 0);
+    }
+    if (inc) {   // r from the change log; the exact kernel below runs only when asked to
+        k_inc_apply<T><<<4 * h->num_sms, 256, 0, h->stream>>>(h->csc_ptr, h->csc_row, csc_values<T>(h),
+                                                              r, ctl);
+        k_inc_finish<T><<<grid_stream(h, (int)h->m), 256, 0, h->stream>>>(r, (int)h->m, h->K, h->partials,
+                                                                         h->hist1, ctl);
     }
     if constexpr (sizeof(T) == sizeof(float)) {
         k_residual<T, float><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
@@ -1872,7 +2029,7 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
     k_topk_hist2<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1);
     k_topk_collect<T><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
         r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1);
-    launch_dynamic_tail<T>(h, r, x, ctl, 1, 1, use_cond, hcond);
+    launch_dynamic_tail<T>(h, r, x, ctl, 1, 1, use_cond, hcond, inc);
 }
 
 void launch_weights(rorbk_ctx *h, const double *r) {
@@ -1882,8 +2039,8 @@ void launch_weights(rorbk_ctx *h, const double *r) {
 }
 
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
-                      unsigned long long hcond, int weighted) {
-    launch_iteration_t<double>(h, b, x, r, h->ctl, use_cond, hcond, weighted);
+                      unsigned long long hcond, int weighted, int inc) {
+    launch_iteration_t<double>(h, b, x, r, h->ctl, use_cond, hcond, weighted, inc);
 }
 
 void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner) {
@@ -1900,8 +2057,8 @@ void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inn
                                            (cudaGraphConditionalHandle)hcond_inner);
 }
 
-void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner) {
-    launch_iteration_t<float>(h, h->b32, h->d32, h->r32, h->ctl_in, use_cond, hcond_inner);
+void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner, int inc) {
+    launch_iteration_t<float>(h, h->b32, h->d32, h->r32, h->ctl_in, use_cond, hcond_inner, 0, inc);
 }
 
 void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_outer) {

@@ -84,7 +84,8 @@ static cudaError_t begin_capture(cudaStream_t cs, cudaGraph_t parent) {
 
 // Capture: k_begin, then WHILE(cond) { one iteration }.  With parent == NULL
 // the graph is instantiated into h->exec_fp64, else it is appended to parent.
-static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr, int weighted = 0) {
+static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr, int weighted = 0,
+                                     int inc = 0) {
     rorbk_status st;
     cudaStream_t saved = h->stream;
     cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2;
@@ -122,7 +123,7 @@ static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr,
         e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             h->stream = cs2;
-            launch_iteration(h, h->bb, h->xb, h->r, 1, (unsigned long long)hcond, weighted);
+            launch_iteration(h, h->bb, h->xb, h->r, 1, (unsigned long long)hcond, weighted, inc);
             cudaError_t e2 = cudaGetLastError();
             cudaGraph_t body_out = nullptr;
             e = cudaStreamEndCapture(cs2, &body_out);
@@ -134,7 +135,9 @@ static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr,
     cudaError_t e3 = cudaStreamEndCapture(cs, &g_out);
     if (e == cudaSuccess) e = e3;
     if (!parent) {
-        if (e == cudaSuccess) e = cudaGraphInstantiate(weighted ? &h->exec_fp64_w : &h->exec_fp64, g_out, 0);
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(weighted ? &h->exec_fp64_w : (inc ? &h->exec_fp64_inc : &h->exec_fp64),
+                                     g_out, 0);
         if (g_out) cudaGraphDestroy(g_out);
     }
     return cuda_check(h, e, "building the iteration graph");
@@ -170,7 +173,7 @@ static cudaError_t new_handle(cudaStream_t cs, cudaGraphConditionalHandle *hc) {
 
 // Capture: k_begin, then WHILE(outer) { FP64 residual + inner set-up,
 // WHILE(inner) { one FP32 iteration }, x += d }.
-static rorbk_status build_graph_mixed(rorbk_ctx *h, cudaGraph_t parent = nullptr) {
+static rorbk_status build_graph_mixed(rorbk_ctx *h, cudaGraph_t parent = nullptr, int inc = 0) {
     cudaStream_t saved = h->stream;
     cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2, cs3 = h->cap_stream3;
     cudaGraphConditionalHandle hout = 0, hin = 0;
@@ -196,7 +199,7 @@ static rorbk_status build_graph_mixed(rorbk_ctx *h, cudaGraph_t parent = nullptr
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs3, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             h->stream = cs3;
-            launch_mixed_inner(h, 1, (unsigned long long)hin);
+            launch_mixed_inner(h, 1, (unsigned long long)hin, inc);
             cudaError_t e2 = cudaGetLastError();
             e = cudaStreamEndCapture(cs3, &tmp);
             if (e == cudaSuccess) e = e2;
@@ -214,7 +217,7 @@ static rorbk_status build_graph_mixed(rorbk_ctx *h, cudaGraph_t parent = nullptr
     cudaError_t e4 = cudaStreamEndCapture(cs, &g_out);
     if (e == cudaSuccess) e = e4;
     if (!parent) {
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_mixed, g_out, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(inc ? &h->exec_mixed_inc : &h->exec_mixed, g_out, 0);
         if (g_out) cudaGraphDestroy(g_out);
     }
     return cuda_check(h, e, "building the mixed-precision graph");
@@ -324,6 +327,8 @@ void rorbk_free(rorbk_handle h) {
     if (h->exec_fp64) cudaGraphExecDestroy(h->exec_fp64);
     if (h->exec_mixed) cudaGraphExecDestroy(h->exec_mixed);
     if (h->exec_fp64_w) cudaGraphExecDestroy(h->exec_fp64_w);
+    if (h->exec_fp64_inc) cudaGraphExecDestroy(h->exec_fp64_inc);
+    if (h->exec_mixed_inc) cudaGraphExecDestroy(h->exec_mixed_inc);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
     if (h->cap_stream3) cudaStreamDestroy(h->cap_stream3);
@@ -491,11 +496,21 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
         return fail(h, RORBK_ERR_INVALID_ARG, "unknown dist_mode");
     if (mixed && opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED)
         return fail(h, RORBK_ERR_UNSUPPORTED, "residual-weighted draws are available in FP64 precision");
+    if (opt.residual_mode != RORBK_RESIDUAL_EXACT && opt.residual_mode != RORBK_RESIDUAL_INCREMENTAL)
+        return fail(h, RORBK_ERR_INVALID_ARG, "unknown residual_mode");
+    const bool inc = opt.residual_mode == RORBK_RESIDUAL_INCREMENTAL;
+    if (inc && opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED)
+        return fail(h, RORBK_ERR_UNSUPPORTED, "the incremental residual is not combined with residual-weighted draws");
+    if (inc && opt.refresh < 0) return fail(h, RORBK_ERR_INVALID_ARG, "refresh >= 0");
     if (mixed && h->smax > h->n)
         return fail(h, RORBK_ERR_UNSUPPORTED,
                     "mixed precision needs blocks of at most n rows: with s > n the stored "
                     "inverse scales the null space of A_t A_t^T by 1/mu, which FP32 cannot "
                     "carry (the s >= n form of Lemma 1 is not built)");
+    if (inc) {
+        rorbk_status st = ensure_incremental(h);
+        if (st) return st;
+    }
     const int64_t m = h->m, n = h->n;
     cudaMemcpyAsync(h->bb, b, m * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
     if (x0) cudaMemcpyAsync(h->xb, x0, n * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
@@ -512,6 +527,11 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
     c.inner_maxit = opt.inner_maxit;
     c.weighted = opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED;
     c.scdf = nullptr;                   // P's running sum until weights replace it
+    c.inc = inc;
+    c.inc_refresh = opt.refresh > 0 ? opt.refresh : kIncRefreshDefault;
+    c.log_cap = inc ? h->ilog_cap : 0;
+    c.log_col = inc ? h->ilog_col : nullptr;
+    c.log_val = inc ? h->ilog_val : nullptr;
     if (opt.trace && !mixed) {
         c.trace_cap = opt.trace->capacity;
         c.tr_tau = (long long *)opt.trace->tau;
@@ -561,10 +581,13 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
     const bool mixed = opt.precision == RORBK_PREC_MIXED;
     Ctl c;
     const int weighted = opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED;
-    cudaGraphExec_t *exec = mixed ? &h->exec_mixed : (weighted ? &h->exec_fp64_w : &h->exec_fp64);
+    const int inc = opt.residual_mode == RORBK_RESIDUAL_INCREMENTAL;
+    cudaGraphExec_t *exec = mixed ? (inc ? &h->exec_mixed_inc : &h->exec_mixed)
+                                  : (weighted ? &h->exec_fp64_w : (inc ? &h->exec_fp64_inc : &h->exec_fp64));
     if (!opt.host_loop && !*exec) {
         if ((st = cuda_check(h, cudaStreamSynchronize(s), "solve prologue"))) return st;
-        if ((st = mixed ? build_graph_mixed(h) : build_graph_fp64(h, nullptr, weighted))) return st;
+        if ((st = mixed ? build_graph_mixed(h, nullptr, inc) : build_graph_fp64(h, nullptr, weighted, inc)))
+            return st;
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -588,7 +611,7 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
             int64_t launched = 0;
             while (e == cudaSuccess && !halt && launched < maxit) {
                 for (int q = 0; q < poll && launched < maxit; ++q, ++launched)
-                    launch_iteration(h, h->bb, h->xb, h->r, 0, 0, weighted);
+                    launch_iteration(h, h->bb, h->xb, h->r, 0, 0, weighted, inc);
                 e = cudaGetLastError();
                 if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -605,7 +628,7 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
                 int odone = 0;
                 if (e == cudaSuccess) e = cudaMemcpy(&odone, &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost);
                 while (e == cudaSuccess && !ihalt && !odone) {
-                    for (int q = 0; q < poll; ++q) launch_mixed_inner(h, 0, 0);
+                    for (int q = 0; q < poll; ++q) launch_mixed_inner(h, 0, 0, inc);
                     e = cudaGetLastError();
                     if (e == cudaSuccess) e = cudaMemcpyAsync(&ihalt, &h->ctl_in->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
                     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -658,7 +681,15 @@ rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
     c->allocs.clear();
     c->tmp.clear();
     c->bytes = 0;
-    c->exec_fp64 = c->exec_mixed = c->exec_fp64_w = nullptr;
+    c->exec_fp64 = c->exec_mixed = c->exec_fp64_w = c->exec_fp64_inc = c->exec_mixed_inc = nullptr;
+    // the incremental residual's CSC copy and log belong to the handle that
+    // built them: a clone builds its own at its first incremental solve
+    c->csc_ptr = c->csc_row = nullptr;
+    c->csc_val = nullptr;
+    c->csc_val32 = nullptr;
+    c->ilog_col = nullptr;
+    c->ilog_val = nullptr;
+    c->ilog_cap = 0;
     c->cap_stream = c->cap_stream2 = c->cap_stream3 = nullptr;
     auto bail = [&](rorbk_status e) {
         record_setup_error(c->err.empty() ? std::string("rorbk_clone failed") : c->err);
@@ -751,9 +782,11 @@ rorbk_status rorbk_batch_solve(rorbk_batch bt, const double *const *b, const dou
     rorbk_options opt = opt_in ? *opt_in : defaults();
     if (opt.precision != bt->precision)
         return reject(RORBK_ERR_INVALID_ARG, "rorbk_batch_solve: precision differs from the batch's");
-    if (opt.host_loop || opt.trace || opt.dist_mode != RORBK_DIST_PAPER)
+    if (opt.host_loop || opt.trace || opt.dist_mode != RORBK_DIST_PAPER ||
+        opt.residual_mode != RORBK_RESIDUAL_EXACT)
         return reject(RORBK_ERR_UNSUPPORTED,
-                      "rorbk_batch_solve: no host loop, trace or residual-weighted draws in a batch");
+                      "rorbk_batch_solve: no host loop, trace, residual-weighted draws or incremental "
+                      "residual in a batch");
     const int count = (int)bt->hs.size();
     for (int i = 0; i < count; ++i)
         if (!b[i] || !x[i]) return reject(RORBK_ERR_INVALID_ARG, "rorbk_batch_solve: NULL b[i] or x[i]");
