@@ -1519,22 +1519,57 @@ __global__ void __launch_bounds__(1024) k_wcdf(const double *__restrict__ w, int
 // ascending).  Every launch draws the same tau from the Philox stream.
 constexpr int kDenseStatic = 3;
 
+// The block's residual r_tau = b_tau - A_tau x, tiled for load parallelism:
+// grid block g takes rows 32g..32g+31 of the block.  Its 256 threads copy a
+// tile of those rows' next kSdCols columns (coalesced along the columns) into
+// shared memory, transposed, while lane a of warp 0 runs row a's chain
+// acc = fma(a_aj, x_j, acc) over the previous tile, columns ascending -- the
+// operations of k_static's direct path in the same order.
+constexpr int kSdCols = 256;     // = blockDim: thread t copies column t of each row
+
 template <typename T>
-__global__ void __launch_bounds__(32) k_sd_rows(Mat<T> A, const T *__restrict__ b,
-                                               const T *__restrict__ x, T *rloc, Ctl *ctl, int l) {
+__host__ __device__ constexpr size_t sd_rows_smem() { return ((size_t)kSdCols * 33 + kSdCols) * sizeof(T); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sd_rows_tiled(Mat<T> A, const T *__restrict__ b,
+                                                      const T *__restrict__ x, T *rloc, Ctl *ctl,
+                                                      int l) {
+    extern __shared__ unsigned long long sd_dsm[];
+    T *tile = (T *)sd_dsm;                        // [kSdCols][33]: column-major tile
+    T *xs = tile + kSdCols * 33;                  // [kSdCols]
+    __shared__ long long rbase[32];
     if (ctl->done || ctl->halt || l >= ctl->n_static) return;
     const long long it = ctl->iter_base + ctl->iter;
     const int tau = sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
     if (blockIdx.x == 0 && threadIdx.x == 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
         ctl->tr_tau[ctl->iter * ctl->n_static + l] = tau;
     const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
-    const int a = blockIdx.x * 32 + threadIdx.x;
-    if (a >= s) return;
-    const int q0 = A.rowptr[r0 + a], q1 = A.rowptr[r0 + a + 1];
+    const int row0 = blockIdx.x * 32;
+    if (row0 >= s) return;
+    const int rows = min(32, s - row0), n = A.n, tid = threadIdx.x;
+    if (tid < 32) rbase[tid] = tid < rows ? (long long)A.rowptr[r0 + row0 + tid] : 0;
+    __syncthreads();
+    T pre[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) pre[u] = (u < rows && tid < n) ? A.val[rbase[u] + tid] : T(0);
     T acc = T(0);
-#pragma unroll 8
-    for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(A.val[p], x[A.col[p]], acc);
-    rloc[a] = Ar<T>::sub(b[r0 + a], acc);
+    for (int c0 = 0; c0 < n; c0 += kSdCols) {
+#pragma unroll
+        for (int u = 0; u < 32; ++u) tile[tid * 33 + u] = pre[u];
+        xs[tid] = c0 + tid < n ? x[c0 + tid] : T(0);
+        __syncthreads();
+        const int c1 = c0 + kSdCols;
+        if (c1 < n) {                             // next tile in flight during the chain
+#pragma unroll
+            for (int u = 0; u < 32; ++u) pre[u] = (u < rows && c1 + tid < n) ? A.val[rbase[u] + c1 + tid] : T(0);
+        }
+        if (tid < rows) {
+            const int jn = min(kSdCols, n - c0);
+            for (int j = 0; j < jn; ++j) acc = Ar<T>::fma(tile[j * 33 + tid], xs[j], acc);
+        }
+        __syncthreads();
+    }
+    if (tid < rows) rloc[row0 + tid] = Ar<T>::sub(b[r0 + row0 + tid], acc);
 }
 
 template <typename T>
@@ -1558,20 +1593,23 @@ __global__ void __launch_bounds__(1024) k_sd_apply(Mat<T> A, const T *__restrict
     }
 }
 
+// x_c += sum over the block's rows a (ascending) of a_ac y_a: in a dense
+// block every column holds every row, so the column-sorted copy's segment of
+// column c is the rows in ascending order, and A itself (row-major) gives the
+// same chain with loads coalesced across the threads' columns.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sd_scatter(Mat<T> A, const T *__restrict__ y, T *x,
                                                     Ctl *ctl, int l) {
+    __shared__ long long rbase[kMaxBlockRows];
     if (ctl->done || ctl->halt || l >= ctl->n_static) return;
     const long long it = ctl->iter_base + ctl->iter;
     const int tau = sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
     const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
-    const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
-    const int ns = A.nseg[tau];
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ns; g += gridDim.x * blockDim.x) {
-        int q = A.bt_seg[p0 + g];
-        const int c = A.bt_col[q];
+    for (int a = threadIdx.x; a < s; a += blockDim.x) rbase[a] = A.rowptr[r0 + a];
+    __syncthreads();
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < A.n; c += gridDim.x * blockDim.x) {
         T acc3 = T(0);
-        for (; q < pend && A.bt_col[q] == c; ++q) acc3 = Ar<T>::fma(A.bt_val[q], y[A.bt_row[q]], acc3);
+        for (int a = 0; a < s; ++a) acc3 = Ar<T>::fma(A.val[rbase[a] + c], y[a], acc3);
         x[c] = Ar<T>::add(x[c], acc3);
     }
 }
@@ -1612,92 +1650,110 @@ __global__ void __launch_bounds__(kGT * kGT) k_dyn_dense_gram(const double *__re
     if (a < K && b <= a) D.g[pidx(a, b)] = a == b ? __dadd_rn(acc, mu) : acc;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(1024) k_dyn_dense_factor(const T *__restrict__ r, int K, Dyn D,
-                                                           Ctl *ctl) {
-    __shared__ double z[kMaxDynRows];
-    __shared__ unsigned char cz[kMaxDynRows], rz[kMaxDynRows];
-    __shared__ int s_bad;
-    if (ctl->done || ctl->status || ctl->halt) return;
-    for (int q = threadIdx.x; q < K; q += blockDim.x) {
-        z[q] = (double)r[D.I[q]];
-        cz[q] = 0;
-        rz[q] = 0;
-    }
-    if (threadIdx.x == 0) s_bad = 0;
-    __syncthreads();
-    packed_cholesky(D.g, K, &s_bad);
-    column_solve(D.g, K, z, cz, rz);
-    for (int q = threadIdx.x; q < K; q += blockDim.x) D.y[q] = z[q];
-    if (threadIdx.x == 0 && s_bad) set_status(&ctl->status, kDevNotSpd);
-}
-
-// Blocked factor of the dense Gram (K <= kDenseCholMaxK): panels of kPW
-// columns.  The panel kernel (one block) factors the panel's columns in
-// shared memory, right-looking inside the panel, and carries the forward
-// solve for them (z is the panel's extra column); the trailing kernel (many
-// blocks) applies the panel's columns to every later entry, in ascending
-// column order; the backward solve runs last in one block.  Every entry sees
-// the operations of the one-block right-looking factor and column-oriented
-// solves in the same order (zero multipliers skipped alike).
+// Blocked factor of the dense Gram: panels of kPW columns.  The panel kernel
+// factors the panel's columns, right-looking inside the panel, and carries the
+// forward solve for them (z is the panel's extra column); the trailing kernel
+// (many blocks) applies the panel's columns to every later entry, in
+// ascending column order; the backward solve runs last in one block.  Every
+// entry sees the operations of the one-block right-looking factor and
+// column-oriented solves in the same order (zero multipliers skipped alike).
 constexpr int kPW = 32;
-constexpr int kDenseCholMaxK = 768;
 
-size_t dchol_panel_smem(int K) { return ((size_t)K * (kPW + 1) + (size_t)K) * sizeof(double); }
-
+// Panel j0 with its rows spread over the grid.  Every grid block factors the
+// w x w diagonal block and forward-solves its part of z in shared memory (the
+// same operations in every block); then lane t of warp 0 of block g takes row
+// i = w + 32g + t below the diagonal block and forms its w entries of L,
+// columns ascending (the multiply-adds by the earlier columns in ascending
+// order, then the division), and its z entry.  Every entry receives the
+// operations of the one-block factor in the same order.  The last block to finish
+// (ticket) writes the diagonal block back, after every block has read it.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_dchol_panel(const T *__restrict__ r, int K, int j0, Dyn D,
-                                                      Ctl *ctl) {
-    extern __shared__ double dps[];
-    __shared__ int s_bad;
+__global__ void __launch_bounds__(256) k_dchol_panel_rows(const T *__restrict__ r, int K, int j0, Dyn D,
+                                                          Ctl *ctl) {
+    __shared__ double Ld[kPW][kPW + 1];
+    __shared__ double zd[kPW];
+    __shared__ int s_bad, is_last;
     if (ctl->done || ctl->status || ctl->halt) return;
     const int w = min(kPW, K - j0), nr = K - j0, tid = threadIdx.x;
-    double *Pm = dps;                        // [nr][kPW + 1]: rows j0.., panel columns
-    double *zz = dps + (size_t)nr * (kPW + 1);
-    for (int q = tid; q < nr * w; q += blockDim.x) {
-        const int i = q / w, jj = q % w;      // row j0 + i, column j0 + jj
-        Pm[i * (kPW + 1) + jj] = i >= jj ? D.g[pidx(j0 + i, j0 + jj)] : 0.0;
+    for (int q = tid; q < w * w; q += blockDim.x) {
+        const int i = q / w, jj = q % w;
+        Ld[i][jj] = i >= jj ? D.g[pidx(j0 + i, j0 + jj)] : 0.0;
     }
-    for (int i = tid; i < nr; i += blockDim.x)
-        zz[i] = j0 == 0 ? (double)r[D.I[i]] : D.y[j0 + i];
+    for (int i = tid; i < w; i += blockDim.x) zd[i] = j0 == 0 ? (double)r[D.I[i]] : D.y[j0 + i];
+    // this block's rows below the diagonal block: read before anything is written
+    const int i = w + blockIdx.x * 32 + tid;
+    const bool own = tid < 32 && i < nr;
+    double Lr[kPW];
+#pragma unroll
+    for (int jj = 0; jj < kPW; ++jj) Lr[jj] = (own && jj < w) ? D.g[pidx(j0 + i, j0 + jj)] : 0.0;
+    double zi = own ? (j0 == 0 ? (double)r[D.I[i]] : D.y[j0 + i]) : 0.0;
     if (tid == 0) s_bad = 0;
     __syncthreads();
     for (int jj = 0; jj < w; ++jj) {
-        double *cj = Pm + jj;                 // column jj: cj[i * (kPW + 1)]
         if (tid == 0) {
-            double d = cj[jj * (kPW + 1)];
+            double d = Ld[jj][jj];
             if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
-            cj[jj * (kPW + 1)] = sqrt(d);
+            Ld[jj][jj] = sqrt(d);
         }
         __syncthreads();
-        const double l = cj[jj * (kPW + 1)];
-        for (int i = jj + 1 + tid; i < nr; i += blockDim.x) {
-            const double v = cj[i * (kPW + 1)];
-            if (v != 0.0) cj[i * (kPW + 1)] = v / l;
+        const double l = Ld[jj][jj];
+        for (int q = jj + 1 + tid; q < w; q += blockDim.x) {
+            const double v = Ld[q][jj];
+            if (v != 0.0) Ld[q][jj] = v / l;
         }
-        if (tid == 0) zz[jj] = zz[jj] / l;    // forward solve: w_j
+        if (tid == 0) zd[jj] = zd[jj] / l;
         __syncthreads();
-        const double wj = zz[jj];
-        // the panel's later columns jj2, rows i >= jj2
-        for (int q = tid; q < (w - jj - 1) * nr; q += blockDim.x) {
-            const int jj2 = jj + 1 + q / nr, i = q % nr;
-            if (i < jj2) continue;
-            const double la = cj[i * (kPW + 1)], lb = cj[jj2 * (kPW + 1)];
-            if (la != 0.0 && lb != 0.0)
-                Pm[i * (kPW + 1) + jj2] = __fma_rn(-la, lb, Pm[i * (kPW + 1) + jj2]);
+        const double wj = zd[jj];
+        for (int q = tid; q < (w - jj - 1) * w; q += blockDim.x) {
+            const int jj2 = jj + 1 + q / w, a = q % w;
+            if (a < jj2) continue;
+            const double la = Ld[a][jj], lb = Ld[jj2][jj];
+            if (la != 0.0 && lb != 0.0) Ld[a][jj2] = __fma_rn(-la, lb, Ld[a][jj2]);
         }
-        for (int i = jj + 1 + tid; i < nr; i += blockDim.x) {
-            const double lij = cj[i * (kPW + 1)];
-            if (lij != 0.0) zz[i] = __fma_rn(-lij, wj, zz[i]);
+        for (int q = jj + 1 + tid; q < w; q += blockDim.x) {
+            const double lij = Ld[q][jj];
+            if (lij != 0.0) zd[q] = __fma_rn(-lij, wj, zd[q]);
         }
         __syncthreads();
     }
-    for (int q = tid; q < nr * w; q += blockDim.x) {
-        const int i = q / w, jj = q % w;
-        if (i >= jj) D.g[pidx(j0 + i, j0 + jj)] = Pm[i * (kPW + 1) + jj];
+    if (own) {
+#pragma unroll
+        for (int jj = 0; jj < kPW; ++jj) {
+            if (jj < w) {
+                double v = Lr[jj];
+#pragma unroll
+                for (int k2 = 0; k2 < jj; ++k2) {
+                    const double a = Lr[k2], bb = Ld[jj][k2];
+                    if (a != 0.0 && bb != 0.0) v = __fma_rn(-a, bb, v);
+                }
+                if (v != 0.0) v = v / Ld[jj][jj];
+                Lr[jj] = v;
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < kPW; ++jj)
+            if (jj < w && Lr[jj] != 0.0) zi = __fma_rn(-Lr[jj], zd[jj], zi);
+#pragma unroll
+        for (int jj = 0; jj < kPW; ++jj)
+            if (jj < w) D.g[pidx(j0 + i, j0 + jj)] = Lr[jj];
+        D.y[j0 + i] = zi;
     }
-    for (int i = tid; i < nr; i += blockDim.x) D.y[j0 + i] = zz[i];
-    if (tid == 0 && s_bad) set_status(&ctl->status, kDevNotSpd);
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    for (int q = tid; q < w * w; q += blockDim.x) {
+        const int a = q / w, jj = q % w;
+        if (a >= jj) D.g[pidx(j0 + a, j0 + jj)] = Ld[a][jj];
+    }
+    for (int a = tid; a < w; a += blockDim.x) D.y[j0 + a] = zd[a];
+    if (tid == 0) {
+        ctl->ticket = 0;
+        if (s_bad) set_status(&ctl->status, kDevNotSpd);
+    }
 }
 
 // G[a][b] -= L[a][j] L[b][j] for the panel's columns j (ascending), over the
@@ -1940,10 +1996,10 @@ void configure_kernels() {
                          (int)factor_smem_bytes());
     cudaFuncSetAttribute(k_dyn_mark<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)factor_smem_bytes());
-    cudaFuncSetAttribute(k_dchol_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)dchol_panel_smem(kDenseCholMaxK));
-    cudaFuncSetAttribute(k_dchol_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)dchol_panel_smem(kDenseCholMaxK));
+    cudaFuncSetAttribute(k_sd_rows_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sd_rows_smem<double>());
+    cudaFuncSetAttribute(k_sd_rows_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sd_rows_smem<float>());
 }
 
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
@@ -1959,19 +2015,16 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
         const int K = h->K, T16 = (K + kGT - 1) / kGT;
         k_dyn_dense_gram<<<T16 * (T16 + 1) / 2, kGT * kGT, 0, h->stream>>>(h->val, (int)h->n, K, h->mu,
                                                                           dyn_bufs(h), ctl);
-        if (K <= kDenseCholMaxK) {
-            for (int j0 = 0; j0 < K; j0 += kPW) {
-                k_dchol_panel<T><<<1, 1024, dchol_panel_smem(K - j0), h->stream>>>(r, K, j0, dyn_bufs(h), ctl);
-                const int rest = K - std::min(K, j0 + kPW), tt = (rest + 15) / 16;
-                if (rest > 0)
-                    k_dchol_trail<<<tt * (tt + 1) / 2, 256, 0, h->stream>>>(K, j0, dyn_bufs(h), ctl);
-            }
-            k_dchol_back<<<1, 1024, 0, h->stream>>>(K, dyn_bufs(h), ctl);
-        } else {
-            k_dyn_dense_factor<T><<<1, 1024, 0, h->stream>>>(r, K, dyn_bufs(h), ctl);
+        for (int j0 = 0; j0 < K; j0 += kPW) {
+            const int below = K - j0 - std::min(kPW, K - j0);
+            k_dchol_panel_rows<T><<<std::max(1, (below + 31) / 32), 256, 0, h->stream>>>(r, K, j0,
+                                                                                       dyn_bufs(h), ctl);
+            const int rest = K - std::min(K, j0 + kPW), tt = (rest + 15) / 16;
+            if (rest > 0) k_dchol_trail<<<tt * (tt + 1) / 2, 256, 0, h->stream>>>(K, j0, dyn_bufs(h), ctl);
         }
-        const int g = std::max(1, std::min(4 * h->num_sms, (int)((h->n + 255) / 256)));
-        k_dyn_dense_scatter<T><<<g, 256, 0, h->stream>>>(h->val, h->val32, x, (int)h->n, K, dyn_bufs(h),
+        k_dchol_back<<<1, 1024, 0, h->stream>>>(K, dyn_bufs(h), ctl);
+        const int g = std::max(1, std::min(8 * h->num_sms, (int)((h->n + 63) / 64)));
+        k_dyn_dense_scatter<T><<<g, 64, 0, h->stream>>>(h->val, h->val32, x, (int)h->n, K, dyn_bufs(h),
                                                           ctl, count_iter, use_cond,
                                                           (cudaGraphConditionalHandle)hcond);
         return;
@@ -1997,11 +2050,13 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
     if (h->format == RORBK_FORMAT_DENSE) {
         T *rl = (T *)h->sd_scratch, *yy = rl + kMaxBlockRows;
         const int gr = (h->smax + 31) / 32;
-        const int gs = std::max(1, std::min(4 * h->num_sms, (int)((h->n + 255) / 256)));
+        // column-parallel passes in blocks of 64 threads: more SMs share the
+        // FP64 chains of a narrow system
+        const int gs = std::max(1, std::min(8 * h->num_sms, (int)((h->n + 63) / 64)));
         for (int l = 0; l < kDenseStatic; ++l) {
-            k_sd_rows<T><<<gr, 32, 0, h->stream>>>(A, b, x, rl, ctl, l);
+            k_sd_rows_tiled<T><<<gr, kSdCols, sd_rows_smem<T>(), h->stream>>>(A, b, x, rl, ctl, l);
             k_sd_apply<T><<<1, 1024, 0, h->stream>>>(A, rl, yy, ctl, l);
-            k_sd_scatter<T><<<gs, 256, 0, h->stream>>>(A, yy, x, ctl, l);
+            k_sd_scatter<T><<<gs, 64, 0, h->stream>>>(A, yy, x, ctl, l);
         }
         // updates beyond kDenseStatic (n_static > 3), if any
         k_static<T><<<1, 1024, static_smem_bytes<T>(), h->stream>>>(A, b, x, ctl, -1, 0, kDenseStatic);
