@@ -1588,6 +1588,7 @@ __global__ void __launch_bounds__(1024) k_sd_apply(Mat<T> A, const T *__restrict
         const int sb = A.s_ptr[tau], nS = A.s_ptr[tau + 1] - sb;
         const T *Wr = A.w_ss + A.w_ptr[tau] + (long long)pos * nS;
         T acc2 = T(0);
+#pragma unroll 8
         for (int q = 0; q < nS; ++q) acc2 = Ar<T>::fma(Wr[q], rloc[A.s_idx[sb + q]], acc2);
         y[a] = acc2;
     }
@@ -1661,11 +1662,13 @@ constexpr int kPW = 32;
 
 // Panel j0 with its rows spread over the grid.  Every grid block factors the
 // w x w diagonal block and forward-solves its part of z in shared memory (the
-// same operations in every block); then lane t of warp 0 of block g takes row
-// i = w + 32g + t below the diagonal block and forms its w entries of L,
-// columns ascending (the multiply-adds by the earlier columns in ascending
-// order, then the division), and its z entry.  Every entry receives the
-// operations of the one-block factor in the same order.  The last block to finish
+// same operations in every block), with warps 1..7; lane t of warp 0 of block
+// g takes row i = w + 32g + t below the diagonal block and keeps its w
+// entries of L and its z entry in registers, in step with the diagonal block:
+// at column jj the row's entry is divided by L_jj,jj and then applied to the
+// row's later entries and to z_i.  Every entry therefore receives the
+// operations of the one-block right-looking factor in the same order, while
+// the divisions of a column run side by side.  The last block to finish
 // (ticket) writes the diagonal block back, after every block has read it.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dchol_panel_rows(const T *__restrict__ r, int K, int j0, Dyn D,
@@ -1675,6 +1678,7 @@ __global__ void __launch_bounds__(256) k_dchol_panel_rows(const T *__restrict__ 
     __shared__ int s_bad, is_last;
     if (ctl->done || ctl->status || ctl->halt) return;
     const int w = min(kPW, K - j0), nr = K - j0, tid = threadIdx.x;
+    const int dt = tid - 32, dn = blockDim.x - 32;   // diagonal-block threads (warps 1..)
     for (int q = tid; q < w * w; q += blockDim.x) {
         const int i = q / w, jj = q % w;
         Ld[i][jj] = i >= jj ? D.g[pidx(j0 + i, j0 + jj)] : 0.0;
@@ -1689,50 +1693,52 @@ __global__ void __launch_bounds__(256) k_dchol_panel_rows(const T *__restrict__ 
     double zi = own ? (j0 == 0 ? (double)r[D.I[i]] : D.y[j0 + i]) : 0.0;
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    for (int jj = 0; jj < w; ++jj) {
-        if (tid == 0) {
+#pragma unroll
+    for (int jj = 0; jj < kPW; ++jj) {
+        if (jj >= w) break;
+        if (tid == 32) {
             double d = Ld[jj][jj];
             if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
             Ld[jj][jj] = sqrt(d);
         }
         __syncthreads();
         const double l = Ld[jj][jj];
-        for (int q = jj + 1 + tid; q < w; q += blockDim.x) {
-            const double v = Ld[q][jj];
-            if (v != 0.0) Ld[q][jj] = v / l;
+        double v = 0.0;
+        if (dt >= 0) {
+            for (int q = jj + 1 + dt; q < w; q += dn) {
+                const double u = Ld[q][jj];
+                if (u != 0.0) Ld[q][jj] = u / l;
+            }
+            if (dt == dn - 1) zd[jj] = zd[jj] / l;
+        } else if (own) {
+            v = Lr[jj];
+            if (v != 0.0) v = v / l;
+            Lr[jj] = v;
         }
-        if (tid == 0) zd[jj] = zd[jj] / l;
         __syncthreads();
         const double wj = zd[jj];
-        for (int q = tid; q < (w - jj - 1) * w; q += blockDim.x) {
-            const int jj2 = jj + 1 + q / w, a = q % w;
-            if (a < jj2) continue;
-            const double la = Ld[a][jj], lb = Ld[jj2][jj];
-            if (la != 0.0 && lb != 0.0) Ld[a][jj2] = __fma_rn(-la, lb, Ld[a][jj2]);
-        }
-        for (int q = jj + 1 + tid; q < w; q += blockDim.x) {
-            const double lij = Ld[q][jj];
-            if (lij != 0.0) zd[q] = __fma_rn(-lij, wj, zd[q]);
+        if (dt >= 0) {
+            for (int q = dt; q < (w - jj - 1) * w; q += dn) {
+                const int jj2 = jj + 1 + q / w, a = q % w;
+                if (a < jj2) continue;
+                const double la = Ld[a][jj], lb = Ld[jj2][jj];
+                if (la != 0.0 && lb != 0.0) Ld[a][jj2] = __fma_rn(-la, lb, Ld[a][jj2]);
+            }
+            for (int q = jj + 1 + dt; q < w; q += dn) {
+                const double lij = Ld[q][jj];
+                if (lij != 0.0) zd[q] = __fma_rn(-lij, wj, zd[q]);
+            }
+        } else if (own) {
+#pragma unroll
+            for (int j2 = jj + 1; j2 < kPW; ++j2) {
+                const double bb = Ld[j2][jj];
+                if (j2 < w && v != 0.0 && bb != 0.0) Lr[j2] = __fma_rn(-v, bb, Lr[j2]);
+            }
+            if (v != 0.0) zi = __fma_rn(-v, wj, zi);
         }
         __syncthreads();
     }
     if (own) {
-#pragma unroll
-        for (int jj = 0; jj < kPW; ++jj) {
-            if (jj < w) {
-                double v = Lr[jj];
-#pragma unroll
-                for (int k2 = 0; k2 < jj; ++k2) {
-                    const double a = Lr[k2], bb = Ld[jj][k2];
-                    if (a != 0.0 && bb != 0.0) v = __fma_rn(-a, bb, v);
-                }
-                if (v != 0.0) v = v / Ld[jj][jj];
-                Lr[jj] = v;
-            }
-        }
-#pragma unroll
-        for (int jj = 0; jj < kPW; ++jj)
-            if (jj < w && Lr[jj] != 0.0) zi = __fma_rn(-Lr[jj], zd[jj], zi);
 #pragma unroll
         for (int jj = 0; jj < kPW; ++jj)
             if (jj < w) D.g[pidx(j0 + i, j0 + jj)] = Lr[jj];
@@ -1746,10 +1752,10 @@ __global__ void __launch_bounds__(256) k_dchol_panel_rows(const T *__restrict__ 
     __syncthreads();
     if (!is_last) return;
     for (int q = tid; q < w * w; q += blockDim.x) {
-        const int a = q / w, jj = q % w;
-        if (a >= jj) D.g[pidx(j0 + a, j0 + jj)] = Ld[a][jj];
+        const int a2 = q / w, jj = q % w;
+        if (a2 >= jj) D.g[pidx(j0 + a2, j0 + jj)] = Ld[a2][jj];
     }
-    for (int a = tid; a < w; a += blockDim.x) D.y[j0 + a] = zd[a];
+    for (int a2 = tid; a2 < w; a2 += blockDim.x) D.y[j0 + a2] = zd[a2];
     if (tid == 0) {
         ctl->ticket = 0;
         if (s_bad) set_status(&ctl->status, kDevNotSpd);
@@ -1789,15 +1795,19 @@ __global__ void __launch_bounds__(1024) k_dchol_back(int K, Dyn D, Ctl *ctl) {
     if (ctl->done || ctl->status || ctl->halt) return;
     const int tid = threadIdx.x;
     for (int q = tid; q < K; q += blockDim.x) z[q] = D.y[q];
+    // row j of L for the step at hand, loaded one step ahead so that the
+    // loads are not on the chain of divisions (K <= blockDim: one entry each)
+    double lnext = tid < K - 1 ? D.g[pidx(K - 1, tid)] : 0.0;
+    double dnext = tid == 0 ? D.g[pidx(K - 1, K - 1)] : 1.0;
     __syncthreads();
     for (int j = K - 1; j >= 0; --j) {
-        if (tid == 0) z[j] = z[j] / D.g[pidx(j, j)];
+        const double lji = lnext, djj = dnext;
+        lnext = (j > 0 && tid < j - 1) ? D.g[pidx(j - 1, tid)] : 0.0;
+        dnext = (j > 0 && tid == 0) ? D.g[pidx(j - 1, j - 1)] : 1.0;
+        if (tid == 0) z[j] = z[j] / djj;
         __syncthreads();
         const double zj = z[j];
-        for (int i = tid; i < j; i += blockDim.x) {
-            const double lji = D.g[pidx(j, i)];
-            if (lji != 0.0) z[i] = __fma_rn(-lji, zj, z[i]);
-        }
+        if (tid < j && lji != 0.0) z[tid] = __fma_rn(-lji, zj, z[tid]);
         __syncthreads();
     }
     for (int q = tid; q < K; q += blockDim.x) D.y[q] = z[q];
