@@ -300,6 +300,21 @@ rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);
 rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
                                   const double *r, double *x);
 
+/* The dynamic block's Gram G = A_I A_I^T + mu I for the ascending row set I[K]
+ * (device int32) of a DENSE handle, written packed lower (row-major: entry
+ * (a, b), b <= a, at a (a + 1) / 2 + b) to G (device, K (K + 1) / 2 doubles).
+ *   precision = RORBK_PREC_FP64 : the FP64 kernel of Algorithm 1's dynamic
+ *     block update, each entry one fused chain over ascending columns.
+ *   precision = RORBK_PREC_MIXED : the kernel of the mixed-precision inner
+ *     solve: TF32 products of A's FP32 copy accumulated in FP32 on the tensor
+ *     cores (tcgen05) per 128-column chunk, the chunks added in FP64; entry
+ *     error within about 2^-10 sum_j |a_aj a_bj| (TF32 keeps 10 mantissa bits).
+ *     Needs a handle set up with precision = RORBK_PREC_MIXED.
+ * Sparse handles, an unknown precision or a mixed request on an FP64 handle:
+ * RORBK_ERR_UNSUPPORTED / RORBK_ERR_INVALID_ARG.  Enqueued on the handle's
+ * stream and waited for. */
+rorbk_status rorbk_dense_gram(rorbk_handle h, const int32_t *I, double *G, int32_t precision);
+
 /* ---- the initial solution of Algorithm 2 (Appendix) -----------------------
  * x0 = (<b, b~> / ||b~||^2) y, y = the sum of the rows of static block
  * `block` (each column summed over the block's rows in ascending order),

@@ -87,6 +87,7 @@ SIGNATURES = {
     "rorbk_residual32": (C.c_int, [_P, _P, _P, _P, _P]),
     "rorbk_topk": (C.c_int, [_P, _P, _P]),
     "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
+    "rorbk_dense_gram": (C.c_int, [_P, _P, _P, C.c_int32]),
     "rorbk_initial_solution": (C.c_int, [_P, _I64, _P, _P]),
     "rorbk_fabgmres": (C.c_int, [_P, _P, _P, _P, _D, _I64, _D, _I64, _P, _P]),
     "rorbk_clone": (C.c_int, [_P, _P]),
@@ -352,6 +353,10 @@ class Handle:
 
     def dynamic_update(self, I, r, x):
         _check(lib().rorbk_dynamic_update(self.h, _ptr(I), _ptr(r), _ptr(x)), self.h)
+
+    def dense_gram(self, I, G, precision=PREC_FP64):
+        """rorbk_dense_gram: packed lower A_I A_I^T + mu I into the device tensor G."""
+        _check(lib().rorbk_dense_gram(self.h, _ptr(I), _ptr(G), precision), self.h)
 
 
 class Batch:

@@ -271,4 +271,74 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// ------------------------------------------- 5th-generation tensor cores
+// tcgen05 (sm_100 family): the accumulator lives in tensor memory (TMEM,
+// 512 columns x 128 lanes of 32 bits per SM), allocated by one warp; one
+// thread issues the MMAs, whose operands are read from shared memory through
+// 64-bit matrix descriptors; tcgen05.commit arrives on an mbarrier when the
+// issued MMAs are done; each warp reads its 32 lanes back with tcgen05.ld.
+//
+// Operand layout used here: K-major, no swizzle, made of core matrices of 8
+// rows x 16 bytes (8 x 4 FP32/TF32 values) stored contiguously (128 bytes,
+// row r at 16 r).  Descriptor fields: start address >> 4 (bits 0-13), the
+// byte distance between core matrices adjacent along K >> 4 (bits 16-29), the
+// distance between adjacent 8-row groups >> 4 (bits 32-45), descriptor
+// version 1 (bits 46-47); base offset, LBO mode and layout type (no swizzle)
+// are zero.
+__device__ __forceinline__ unsigned long long umma_desc(unsigned saddr, unsigned k_stride,
+                                                        unsigned row8_stride) {
+    return (unsigned long long)((saddr >> 4) & 0x3FFFu) |
+           ((unsigned long long)((k_stride >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((row8_stride >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::tf32 with an FP32 accumulator, both
+// operands K-major: D format F32 (bits 4-5 = 1), A and B format TF32 (bits
+// 7-9 and 10-12 = 2), N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+__host__ __device__ constexpr unsigned idesc_tf32_f32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tmem_alloc(unsigned *slot, unsigned ncols) {   // one full warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {  // the allocating warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after_sync() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D (+)= A B^T, M = 128 lanes of TMEM from column d_tmem on; accumulate != 0
+// adds to D.
+__device__ __forceinline__ void mma_tf32(unsigned d_tmem, unsigned long long adesc, unsigned long long bdesc,
+                                         unsigned idesc, unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+// 32 consecutive 32-bit columns of this warp's 32 TMEM lanes (lane = thread).
+__device__ __forceinline__ void tmem_ld_32cols(unsigned taddr, unsigned (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 }  // namespace rorbk

@@ -168,6 +168,10 @@ struct rorbk_ctx {
     double *wgt = nullptr, *wcdf = nullptr;   // [k] residual-weighted draws: weights, running sum
     // incremental residual: CSC copy of A (built at the first such solve) and
     // the log of (column, increment) pairs
+    // mixed-precision dense dynamic Gram on the tensor cores: FP32 partial
+    // tiles [gram_tiles][gram_splits][128][128]
+    float *gram_part = nullptr;
+    int gram_tiles = 0, gram_splits = 0;
     int *csc_ptr = nullptr, *csc_row = nullptr;
     double *csc_val = nullptr;
     float *csc_val32 = nullptr;
@@ -236,6 +240,7 @@ void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double
 void launch_topk_only(rorbk_ctx *h, const double *r, int *I);
 void launch_residual32_only(rorbk_ctx *h, const float *b, const float *x, float *r);
 void launch_dynamic_given(rorbk_ctx *h, const int *I, const double *r, double *x);
+void launch_dense_gram(rorbk_ctx *h, Ctl *ctl, int tensor_cores);   // dense A: G of the rows dyn.I into dyn.g
 void launch_sample_probe(rorbk_ctx *h, uint64_t seed, uint64_t sysid, int64_t it, int64_t l,
                          long long *out);
 

@@ -1651,6 +1651,142 @@ __global__ void __launch_bounds__(kGT * kGT) k_dyn_dense_gram(const double *__re
     if (a < K && b <= a) D.g[pidx(a, b)] = a == b ? __dadd_rn(acc, mu) : acc;
 }
 
+// ---- the dynamic Gram of a dense A on the tensor cores (mixed precision) --
+// G = A_I A_I^T + mu I from the FP32 copy of A: TF32 products accumulated in
+// FP32 by tcgen05.mma, in kTcRows x kTcRows tiles of the lower triangle.  Grid
+// block (t, s) takes tile t and the s-th share of the column chunks (kTcCols
+// columns each).  Per chunk it stages the tile's rows in shared memory as core
+// matrices (see umma_desc), one thread issues the chunk's MMAs into a TMEM
+// accumulator and commits them to an mbarrier, and the block waits before it
+// stages the next chunk.  The accumulator is written as an FP32 partial tile;
+// k_dyn_gram_reduce adds a tile's partials in split order in FP64, adds mu on
+// the diagonal and writes the packed G that the FP64 Cholesky reads.
+constexpr int kTcRows = 128;                             // tile edge: M = N = 128
+constexpr int kTcCols = 128;                             // columns per chunk: 16 MMAs of K = 8
+constexpr unsigned kTcOperand = kTcRows * kTcCols * 4;   // bytes of one operand chunk
+constexpr unsigned kTcKStride = 128;                     // core matrices adjacent along K
+constexpr unsigned kTcRowStride = (kTcCols / 4) * 128;   // adjacent 8-row groups
+
+size_t gram_tc_smem() { return 2 * (size_t)kTcOperand + 1024; }
+
+// Rows r0.. r0+127 of A_I, columns c0.. c0+127, into core-matrix order: slot q
+// holds 4 consecutive values of row 8 (q / 256) + q % 8 at column group
+// (q / 8) % 32, so a warp reads 8 rows x 64 contiguous bytes and writes 512
+// contiguous bytes of shared memory.  Rows >= K and columns >= n are zero.
+__device__ __forceinline__ void tc_stage(unsigned char *dst, const float *__restrict__ v32,
+                                         const int *__restrict__ I, int K, long long n, int r0,
+                                         long long c0, bool vec) {
+    for (int q = threadIdx.x; q < kTcRows * kTcCols / 4; q += blockDim.x) {
+        const int r8 = q & 7, kg = (q >> 3) & 31, g = q >> 8;
+        const int row = r0 + g * 8 + r8;
+        const long long col = c0 + kg * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < K) {
+            const float *src = v32 + (long long)I[row] * n + col;
+            if (vec && col + 3 < n) {
+                v = *reinterpret_cast<const float4 *>(src);
+            } else {
+                if (col < n) v.x = src[0];
+                if (col + 1 < n) v.y = src[1];
+                if (col + 2 < n) v.z = src[2];
+                if (col + 3 < n) v.w = src[3];
+            }
+        }
+        *reinterpret_cast<float4 *>(dst + g * kTcRowStride + kg * kTcKStride + r8 * 16) = v;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_dyn_gram_tc(const float *__restrict__ v32, int n, int K, int S,
+                                                     int vec, Dyn D, float *__restrict__ part, Ctl *ctl) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ unsigned long long bar;
+    __shared__ unsigned tslot;
+    __shared__ int s_fail;
+    if (ctl->done || ctl->status || ctl->halt) return;
+    const int t = blockIdx.x, s = blockIdx.y;
+    int ti = 0, tj = t;
+    while (tj > ti) { tj -= ti + 1; ++ti; }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *sa = tc_smem, *sb = tc_smem + kTcOperand;
+    const bool diag = ti == tj;
+    const int nchunks = (n + kTcCols - 1) / kTcCols;
+    const int per = (nchunks + S - 1) / S, ch0 = s * per, ch1 = min(nchunks, ch0 + per);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        s_fail = 0;
+    }
+    if (warp == 0) tmem_alloc(&tslot, kTcRows);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const unsigned tmem = tslot;
+    const unsigned idesc = idesc_tf32_f32(kTcRows, kTcRows);
+    unsigned phase = 0;
+    for (int c = ch0; c < ch1; ++c) {
+        tc_stage(sa, v32, D.I, K, n, ti * kTcRows, (long long)c * kTcCols, vec != 0);
+        if (!diag) tc_stage(sb, v32, D.I, K, n, tj * kTcRows, (long long)c * kTcCols, vec != 0);
+        fence_proxy_async_smem();
+        __syncthreads();
+        tc_fence_after_sync();
+        if (tid == 0) {
+            const unsigned a0 = smem_u32(sa), b0 = smem_u32(diag ? sa : sb);
+            for (int k = 0; k < kTcCols / 8; ++k)      // K = 8 TF32 values = 2 core matrices
+                mma_tf32(tmem, umma_desc(a0 + 256u * k, kTcKStride, kTcRowStride),
+                         umma_desc(b0 + 256u * k, kTcKStride, kTcRowStride), idesc,
+                         (c > ch0 || k > 0) ? 1u : 0u);
+            mma_commit(&bar);
+        }
+        if (!mbar_wait_bounded(&bar, phase, kWaitTries)) atomicOr(&s_fail, 1);
+        phase ^= 1u;
+        __syncthreads();                               // the chunk's operands are free again
+        if (s_fail) break;
+    }
+    if (s_fail && tid == 0) mbar_wait_bounded(&bar, phase ^ 1u, kWaitTries);   // the MMAs in flight
+    tc_fence_after_sync();
+    if (!s_fail) {
+        float *P = part + ((long long)t * S + s) * kTcRows * kTcRows + (long long)(warp * 32 + lane) * kTcRows;
+        for (int c0 = 0; c0 < kTcRows; c0 += 32) {
+            unsigned v[32];
+            if (ch1 > ch0) {
+                tmem_ld_32cols(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4 *>(P + c0 + j) = make_float4(
+                    __uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                    __uint_as_float(v[j + 3]));
+        }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTcRows);
+    if (s_fail && tid == 0) set_status(&ctl->status, kDevTimeout);
+}
+
+// Packed entry q = a (a + 1) / 2 + b of G: the S partials of its tile, added
+// in split order in FP64, plus mu on the diagonal.
+__global__ void __launch_bounds__(256) k_dyn_gram_reduce(const float *__restrict__ part, int K, int S,
+                                                         double mu, Dyn D, Ctl *ctl) {
+    if (ctl->done || ctl->status || ctl->halt) return;
+    const long long total = (long long)K * (K + 1) / 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        int a = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+        while ((long long)a * (a + 1) / 2 > q) --a;
+        while ((long long)(a + 1) * (a + 2) / 2 <= q) ++a;
+        const int b = (int)(q - (long long)a * (a + 1) / 2);
+        const int ti = a / kTcRows, tj = b / kTcRows, t = ti * (ti + 1) / 2 + tj;
+        const float *P = part + (long long)t * S * kTcRows * kTcRows + (long long)(a % kTcRows) * kTcRows +
+                         (b % kTcRows);
+        double g = 0.0;
+        for (int s2 = 0; s2 < S; ++s2) g += (double)P[(long long)s2 * kTcRows * kTcRows];
+        D.g[q] = a == b ? g + mu : g;
+    }
+}
+
 // Blocked factor of the dense Gram: panels of kPW columns.  The panel kernel
 // factors the panel's columns, right-looking inside the panel, and carries the
 // forward solve for them (z is the panel's extra column); the trailing kernel
@@ -1795,19 +1931,15 @@ __global__ void __launch_bounds__(1024) k_dchol_back(int K, Dyn D, Ctl *ctl) {
     if (ctl->done || ctl->status || ctl->halt) return;
     const int tid = threadIdx.x;
     for (int q = tid; q < K; q += blockDim.x) z[q] = D.y[q];
-    // row j of L for the step at hand, loaded one step ahead so that the
-    // loads are not on the chain of divisions (K <= blockDim: one entry each)
-    double lnext = tid < K - 1 ? D.g[pidx(K - 1, tid)] : 0.0;
-    double dnext = tid == 0 ? D.g[pidx(K - 1, K - 1)] : 1.0;
     __syncthreads();
     for (int j = K - 1; j >= 0; --j) {
-        const double lji = lnext, djj = dnext;
-        lnext = (j > 0 && tid < j - 1) ? D.g[pidx(j - 1, tid)] : 0.0;
-        dnext = (j > 0 && tid == 0) ? D.g[pidx(j - 1, j - 1)] : 1.0;
-        if (tid == 0) z[j] = z[j] / djj;
+        if (tid == 0) z[j] = z[j] / D.g[pidx(j, j)];
         __syncthreads();
         const double zj = z[j];
-        if (tid < j && lji != 0.0) z[tid] = __fma_rn(-lji, zj, z[tid]);
+        for (int i = tid; i < j; i += blockDim.x) {
+            const double lji = D.g[pidx(j, i)];
+            if (lji != 0.0) z[i] = __fma_rn(-lji, zj, z[i]);
+        }
         __syncthreads();
     }
     for (int q = tid; q < K; q += blockDim.x) D.y[q] = z[q];
@@ -2006,6 +2138,7 @@ void configure_kernels() {
                          (int)factor_smem_bytes());
     cudaFuncSetAttribute(k_dyn_mark<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)factor_smem_bytes());
+    cudaFuncSetAttribute(k_dyn_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem());
     cudaFuncSetAttribute(k_sd_rows_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sd_rows_smem<double>());
     cudaFuncSetAttribute(k_sd_rows_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2018,13 +2151,30 @@ void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, in
                                        (cudaGraphConditionalHandle)hcond);
 }
 
+void launch_dense_gram(rorbk_ctx *h, Ctl *ctl, int tensor_cores) {
+    const int K = h->K;
+    if (tensor_cores) {
+        const int tiles = h->gram_tiles, S = h->gram_splits;
+        const int vec = (h->n % 4 == 0) && ((reinterpret_cast<uintptr_t>(h->val32) & 15) == 0);
+        k_dyn_gram_tc<<<dim3(tiles, S), 128, gram_tc_smem(), h->stream>>>(h->val32, (int)h->n, K, S, vec,
+                                                                       dyn_bufs(h), h->gram_part, ctl);
+        const long long np = (long long)K * (K + 1) / 2;
+        k_dyn_gram_reduce<<<(int)std::min<long long>(4LL * h->num_sms, (np + 255) / 256), 256, 0, h->stream>>>(
+            h->gram_part, K, S, h->mu, dyn_bufs(h), ctl);
+    } else {
+        const int T16 = (K + kGT - 1) / kGT;
+        k_dyn_dense_gram<<<T16 * (T16 + 1) / 2, kGT * kGT, 0, h->stream>>>(h->val, (int)h->n, K, h->mu,
+                                                                          dyn_bufs(h), ctl);
+    }
+}
+
 template <typename T>
 static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int check_done,
                                 int count_iter, int use_cond, unsigned long long hcond, int inc = 0) {
     if (h->format == RORBK_FORMAT_DENSE) {
-        const int K = h->K, T16 = (K + kGT - 1) / kGT;
-        k_dyn_dense_gram<<<T16 * (T16 + 1) / 2, kGT * kGT, 0, h->stream>>>(h->val, (int)h->n, K, h->mu,
-                                                                          dyn_bufs(h), ctl);
+        const int K = h->K;
+        // mixed precision: the TF32 tensor-core Gram (FP32 partials added in FP64)
+        launch_dense_gram(h, ctl, sizeof(T) == sizeof(float) && h->gram_part);
         for (int j0 = 0; j0 < K; j0 += kPW) {
             const int below = K - j0 - std::min(kPW, K - j0);
             k_dchol_panel_rows<T><<<std::max(1, (below + 31) / 32), 256, 0, h->stream>>>(r, K, j0,

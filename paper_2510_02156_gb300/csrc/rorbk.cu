@@ -277,6 +277,16 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         h->b32 = (float *)dev_alloc(h, m * sizeof(float));
         h->d32 = (float *)dev_alloc(h, n * sizeof(float));
         if (!h->r32 || !h->b32 || !h->d32) return fail(h, RORBK_ERR_OOM, "mixed workspace");
+        if (h->format == RORBK_FORMAT_DENSE) {
+            // tensor-core dynamic Gram: 128 x 128 lower tiles, the column chunks
+            // split so that about two blocks per SM run
+            const int64_t T = (h->K + 127) / 128, chunks = (n + 127) / 128;
+            h->gram_tiles = (int)(T * (T + 1) / 2);
+            h->gram_splits = (int)std::max<int64_t>(
+                1, std::min<int64_t>(chunks, (2 * h->num_sms + h->gram_tiles - 1) / h->gram_tiles));
+            h->gram_part = (float *)dev_alloc(h, (size_t)h->gram_tiles * h->gram_splits * 128 * 128 * sizeof(float));
+            if (!h->gram_part) return fail(h, RORBK_ERR_OOM, "tensor-core Gram workspace");
+        }
     }
     if (!h->r || !h->xb || !h->bb || !h->partials || !h->sd_scratch || !h->wgt || !h->wcdf ||
         !h->hist1 || !h->hist2 || !h->in_list ||
@@ -708,6 +718,39 @@ rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
     *out = c;
     cudaSetDevice(cur);
     return RORBK_OK;
+}
+
+rorbk_status rorbk_dense_gram(rorbk_handle h, const int32_t *I, double *G, int32_t precision) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!I || !G) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_dense_gram: NULL I or G");
+    if (h->format != RORBK_FORMAT_DENSE)
+        return fail(h, RORBK_ERR_UNSUPPORTED, "rorbk_dense_gram: dense handles only");
+    if (precision != RORBK_PREC_FP64 && precision != RORBK_PREC_MIXED)
+        return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_dense_gram: unknown precision");
+    if (precision == RORBK_PREC_MIXED && !h->gram_part)
+        return fail(h, RORBK_ERR_UNSUPPORTED,
+                    "rorbk_dense_gram: the tensor-core Gram needs a handle set up with precision = MIXED");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    cudaMemsetAsync(&h->ctl->status, 0, sizeof(int), s);
+    cudaMemsetAsync(&h->ctl->done, 0, sizeof(int), s);
+    cudaMemsetAsync(&h->ctl->halt, 0, sizeof(int), s);
+    cudaMemcpyAsync(h->dyn.I, I, (size_t)h->K * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    launch_dense_gram(h, h->ctl, precision == RORBK_PREC_MIXED);
+    rorbk_status st = cuda_check(h, cudaGetLastError(), "rorbk_dense_gram");
+    if (!st)
+        st = cuda_check(h, cudaMemcpyAsync(G, h->dyn.g, (size_t)h->K * (h->K + 1) / 2 * sizeof(double),
+                                           cudaMemcpyDeviceToDevice, s),
+                        "rorbk_dense_gram");
+    int code = 0;
+    if (!st) st = cuda_check(h, cudaMemcpyAsync(&code, &h->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s),
+                             "rorbk_dense_gram");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(s), "rorbk_dense_gram");
+    if (!st && code) st = device_status(h, code);
+    cudaSetDevice(cur);
+    return st;
 }
 
 }  // extern "C"
