@@ -6,7 +6,7 @@ scaled log-uniform in [1e-4, 1]), 4096 contiguous row blocks of 256 rows,
 lambda = 1e-8, tol = 1e-8, x0 = 0, Philox seed 1.  One benchmark step is one
 whole solve from x0 = 0 to the tolerance: every iteration of Algorithm 1
 (three sampled static block updates, the full residual, the residual top-K
-selection and the dynamic block update).  The set-up (Algorithm 1 steps 1-4)
+selection and the dynamic block update).  The set-up (Algorithm 1's partition, orthogonality weights and stored inverses)
 runs once before timing and is reported separately.
 
 Headline value: the mixed-precision form (FP64 iterative refinement around

@@ -6,7 +6,7 @@
  * under-determined (Kar & Venkatapathi, arXiv 2510.02156, Section 1 Eq. (1)
  * and Section 2).  Algorithm 1 of the paper is the method:
  *
- *   setup   (Algorithm 1, steps 1-4; Section 2; Section 3.1)
+ *   setup   (Algorithm 1's set-up; Section 2; Section 3.1)
  *     - split the rows into k contiguous blocks of >= floor(m/k) rows;
  *     - centroids Abar_t = sum of block t's rows;
  *       C(i,j) = |<Abar_i,Abar_j>| / (|Abar_i| |Abar_j|);
@@ -98,7 +98,7 @@ typedef struct {
 } rorbk_matrix;
 
 /* Row partition.  num_blocks = k >= 1.  offsets == NULL selects the uniform
- * contiguous split of Algorithm 1 step 1: block t holds rows
+ * contiguous split of Algorithm 1's partition: block t holds rows
  * [t*floor(m/k) + min(t, m mod k), (t+1)*floor(m/k) + min(t+1, m mod k)),
  * so the first (m mod k) blocks carry one extra row (the paper only asks for
  * at least floor(m/k) rows per block).  A caller-supplied offsets[k+1]
@@ -176,7 +176,7 @@ typedef struct {
 enum { RORBK_RESIDUAL_EXACT = 0, RORBK_RESIDUAL_INCREMENTAL = 1 };
 
 /* Distribution of the static blocks (rorbk_options.dist_mode).
- *   PAPER             : tau ~ P, P_t proportional to Pbar_t (Algorithm 1 step 3;
+ *   PAPER             : tau ~ P, P_t proportional to Pbar_t (Algorithm 1's proposal;
  *                       static over the solve).
  *   RESIDUAL_WEIGHTED : not in the paper.  Iteration j draws block t with
  *                       weight Pbar_t * rho_t, rho_t = sum of r_i^2 over the
@@ -215,7 +215,7 @@ typedef struct {
 /* Fills *opt with the defaults listed above. */
 void rorbk_default_options(rorbk_options *opt);
 
-/* Setup (Algorithm 1 steps 1-4 and Section 3.1): validates and copies A,
+/* Setup (Algorithm 1's set-up and Section 3.1): validates and copies A,
  * builds the partition, the centroids, C's row sums, P and its running sum
  * (cdf, summed sequentially in FP64), and the static operators W_t.
  *   lambda : mu, added to the diagonal of every block Gram; lambda < 0 selects
@@ -396,7 +396,7 @@ void rorbk_batch_free(rorbk_batch batch);
  *   C = diag(||A_i||_2) (1 for a zero row): the transpose of A with its rows
  *   normalised, in FP64 values, each row of At~ listing its columns
  *   ascending.  It is then set up exactly as rorbk_setup would (Algorithm 1
- *   steps 1-4 on At~).  part partitions the n rows of At~; lambda and opt as
+ *   set-up on At~).  part partitions the n rows of At~; lambda and opt as
  *   for rorbk_setup (opt == NULL: defaults on h's stream).  Free *out with
  *   rorbk_free.  Errors: as rorbk_setup; RORBK_ERR_INVALID_ARG for a NULL h,
  *   part or out.

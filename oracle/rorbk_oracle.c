@@ -105,7 +105,7 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 1, step 1: uniform contiguous aggregation into k blocks. */
+/* Algorithm 1, the block partition: uniform contiguous aggregation into k blocks. */
 int orc_partition(int64_t m, int64_t k, int64_t *off)
 {
     if (k < 1 || k > m) return ORC_ERR_ARG;
@@ -150,7 +150,7 @@ static double row_row_dot(const orc_matrix *A, int64_t i, int64_t j)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 1, steps 1-2 and the Section 2 definitions: centroids
+/* Algorithm 1's set-up and the Section 2 definitions: centroids
  * Abar_t = sum of the block's rows, C(i,j) = |<Abar_i,Abar_j>|/(|Abar_i||Abar_j|).
  * Outputs the row sums sum_j C(t,j) (always) and the full k x k matrix C when
  * C != NULL.  Each centroid is kept as a sorted (column, value) list; the
@@ -263,7 +263,7 @@ out:
     return st;
 }
 
-/* Algorithm 1, steps 3-4 / Section 2: Pbar_t = exp(-2 sum_j C(t,j) / n),
+/* Algorithm 1's proposal / Section 2: Pbar_t = exp(-2 sum_j C(t,j) / n),
  * P = Pbar / sum(Pbar).  Also the sequential FP64 prefix sum cdf_t. */
 void orc_proposal(const double *C_rowsum, int64_t k, int64_t n, double *Pbar,
                   double *P, double *cdf)
@@ -572,8 +572,8 @@ int orc_initial_solution(const orc_matrix *A, int64_t first, int64_t count,
 }
 
 /* ------------------------------------------------------------------------ */
-/* The residual-weighted proposal (not in the paper: its P is static, Algorithm 1
- * step 3).  Block t is drawn with weight w_t = Pbar_t * rho_t, where rho_t is
+/* The residual-weighted proposal (not in the paper: its P is static, Algorithm
+ * 1's proposal).  Block t is drawn with weight w_t = Pbar_t * rho_t, where rho_t is
  * the squared norm of the residual on block t's rows: one fused chain over the
  * rows in ascending order.  The running sum of the weights is formed in chunks
  * of ORC_WCHUNK blocks: each chunk's running sum from zero, then the chunks'

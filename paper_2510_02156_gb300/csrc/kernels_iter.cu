@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
     }
 }
 
-// Incremental residual, step 1: r -= A dx from the iteration's change log,
+// Incremental residual, first kernel: r -= A dx from the iteration's change log,
 // through the CSC copy of A.  A group of kIncLanes lanes takes one logged
 // column and subtracts a_ic * dx_c from r_i for its entries (atomic adds, so
 // the order of the additions into r_i varies from run to run).  Does nothing
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(256) k_inc_apply(const int *__restrict__ cptr,
     }
 }
 
-// Incremental residual, step 2: ||r||^2, the first radix level of the top-K
+// Incremental residual, second kernel: ||r||^2, the first radix level of the top-K
 // select and the stopping test on the updated r.  A relative residual at or
 // below the tolerance (or not finite) is not trusted: it sets inc_full, and
 // the exact residual kernel that follows decides in the same iteration.

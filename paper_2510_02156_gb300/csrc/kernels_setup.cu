@@ -1,4 +1,4 @@
-// kernels_setup.cu -- setup of ROR-BK (Algorithm 1 steps 1-4, Section 3.1).
+// kernels_setup.cu -- setup of ROR-BK (Algorithm 1's set-up, Section 3.1).
 //
 //   k_validate_csr        structure and finiteness checks of the copied A
 //   k_block_transpose     per static block: nonzeros sorted by (column, row),

@@ -385,7 +385,7 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
         return s;
     };
 
-    // partition (Algorithm 1 step 1)
+    // partition (Algorithm 1's contiguous blocks)
     h->h_off.resize(k + 1);
     if (part->offsets) {
         for (int t = 0; t <= k; ++t) h->h_off[t] = part->offsets[t];

@@ -87,7 +87,7 @@ def test_sampler_inverse_cdf_bruteforce():
 # --------------------------------------------------------------- partition
 @pytest.mark.parametrize("m,k", [(2025, 32), (100, 7), (64, 64), (10, 1), (1 << 20, 4096)])
 def test_partition_contiguous_uniform(m, k):
-    """Algorithm 1 step 1 / Section 2: k contiguous blocks, each with at
+    """Algorithm 1's partition / Section 2: k contiguous blocks, each with at
     least floor(m/k) rows, covering all rows in order."""
     off = oracle.partition(m, k)
     sizes = np.diff(off)
