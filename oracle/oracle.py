@@ -74,6 +74,10 @@ def lib():
                 "orc_fabgmres": (C.c_int, [_P, _I64, _D, _P, _P, _P, _D, _I64, _D, _I64,
                                            C.c_uint64, C.c_uint64, _I64, _P, _P, _P, _P]),
                 "orc_weighted_cdf": (_D, [_P, _P, _I64, _P]),
+                "orc_column_gram": (C.c_int, [_P, _P, _I64, _D, _P]),
+                "orc_column_operator": (C.c_int, [_P, _P, _I64, _D, _P]),
+                "orc_update_woodbury": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
+                "orc_update_woodbury_cholesky": (C.c_int, [_P, _P, _I64, _D, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -235,6 +239,53 @@ def update_with_cholesky(system, rows, mu, rI, x):
                                         _ptr(x), _ptr(scratch))
     if st != 0:
         raise np.linalg.LinAlgError(f"oracle dynamic update status {st}")
+    return x
+
+
+def column_gram(system, rows, mu):
+    """A_B^T A_B + mu I (n x n) over the listed rows (the s >= n form)."""
+    M = _mat(system)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    G = np.zeros((M.n, M.n))
+    st = lib().orc_column_gram(M.ref, _ptr(rows), len(rows), mu, _ptr(G))
+    if st != 0:
+        raise MemoryError(f"oracle column Gram status {st}")
+    return G
+
+
+def column_operator(system, k, t, mu):
+    """V_t = (A_t^T A_t + mu I)^{-1} (n x n) of static block t."""
+    M = _mat(system)
+    off = partition(M.m, k)
+    V = np.zeros((M.n, M.n))
+    st = lib().orc_column_operator(M.ref, _ptr(off), t, mu, _ptr(V))
+    if st != 0:
+        raise np.linalg.LinAlgError(f"oracle column operator status {st}")
+    return V
+
+
+def update_woodbury(system, rows, V, b, x):
+    """x + V A_B^T (b_B - A_B x); returns the updated copy of x."""
+    M = _mat(system)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.array(x, dtype=np.float64, copy=True)
+    st = lib().orc_update_woodbury(M.ref, _ptr(rows), len(rows), _ptr(V), _ptr(b), _ptr(x))
+    if st != 0:
+        raise MemoryError(f"oracle Woodbury update status {st}")
+    return x
+
+
+def update_woodbury_cholesky(system, rows, mu, rI, x):
+    """The dynamic update in the n x n form (K >= n); returns the updated copy."""
+    M = _mat(system)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    rI = np.ascontiguousarray(rI, dtype=np.float64)
+    x = np.array(x, dtype=np.float64, copy=True)
+    st = lib().orc_update_woodbury_cholesky(M.ref, _ptr(rows), len(rows), mu, _ptr(rI), _ptr(x))
+    if st != 0:
+        raise np.linalg.LinAlgError(f"oracle Woodbury dynamic update status {st}")
     return x
 
 

@@ -519,6 +519,134 @@ int orc_static_operator(const orc_matrix *A, const int64_t *off, int64_t t,
 }
 
 /* ------------------------------------------------------------------------ */
+/* The s >= n form (Lemma 1 and Section 3.1).  By Lemma 1,
+ *   x + A_B^T (A_B A_B^T + mu I)^{-1} (b_B - A_B x)
+ *     = x + (A_B^T A_B + mu I)^{-1} A_B^T (b_B - A_B x),
+ * and Section 3.1 stores the n x n inverse on the right when the block has at
+ * least as many rows as A has columns (s >= n).  The same reading is applied
+ * to the dynamic block when K >= n.  Entries that are not stored count as
+ * zero in the column sums below (a fused multiply-add by 0 leaves a finite
+ * running sum unchanged, so this equals summing over the stored entries). */
+
+/* The listed rows as a dense s x n row-major array. */
+static void dense_rows(const orc_matrix *A, const int64_t *rows, int64_t s, double *D)
+{
+    const int64_t n = A->n;
+    memset(D, 0, (size_t)(s * n) * sizeof(double));
+    for (int64_t a = 0; a < s; ++a) {
+        if (A->is_dense) {
+            memcpy(D + a * n, A->dense + rows[a] * A->ld, (size_t)n * sizeof(double));
+        } else {
+            for (int64_t p = A->row_ptr[rows[a]]; p < A->row_ptr[rows[a] + 1]; ++p)
+                D[a * n + A->col_idx[p]] = A->val[p];
+        }
+    }
+}
+
+/* G = A_B^T A_B + mu I (n x n row-major): G_cd = sum over the rows a in the
+ * listed order of a_ac a_ad, a chain of fused multiply-adds from 0, then mu
+ * added on the diagonal. */
+int orc_column_gram(const orc_matrix *A, const int64_t *rows, int64_t s, double mu, double *G)
+{
+    const int64_t n = A->n;
+    double *D = (double *)malloc((size_t)((s ? s : 1) * n) * sizeof(double));
+    if (!D) return ORC_ERR_OOM;
+    dense_rows(A, rows, s, D);
+    for (int64_t c = 0; c < n; ++c)
+        for (int64_t d = 0; d <= c; ++d) {
+            double g = 0.0;
+            for (int64_t a = 0; a < s; ++a) g = fma(D[a * n + c], D[a * n + d], g);
+            if (c == d) g += mu;
+            G[c * n + d] = g;
+            G[d * n + c] = g;
+        }
+    free(D);
+    return ORC_OK;
+}
+
+/* h = A_B^T v: h_c = sum over the rows a in the listed order of a_ac v_a (a
+ * chain of fused multiply-adds from 0). */
+static int column_sums(const orc_matrix *A, const int64_t *rows, int64_t s, const double *v, double *h)
+{
+    const int64_t n = A->n;
+    double *D = (double *)malloc((size_t)((s ? s : 1) * n) * sizeof(double));
+    if (!D) return ORC_ERR_OOM;
+    dense_rows(A, rows, s, D);
+    for (int64_t c = 0; c < n; ++c) {
+        double g = 0.0;
+        for (int64_t a = 0; a < s; ++a) g = fma(D[a * n + c], v[a], g);
+        h[c] = g;
+    }
+    free(D);
+    return ORC_OK;
+}
+
+/* V_t = (A_t^T A_t + mu I)^{-1} (n x n) for static block t: the column Gram,
+ * its Cholesky factor, then the explicit inverse as for W_t. */
+int orc_column_operator(const orc_matrix *A, const int64_t *off, int64_t t, double mu, double *V)
+{
+    const int64_t s = off[t + 1] - off[t], n = A->n;
+    int64_t *rows = (int64_t *)malloc((size_t)(s ? s : 1) * sizeof(int64_t));
+    double *G = (double *)malloc((size_t)(n * n) * sizeof(double));
+    if (!rows || !G) { free(rows); free(G); return ORC_ERR_OOM; }
+    for (int64_t a = 0; a < s; ++a) rows[a] = off[t] + a;
+    int st = orc_column_gram(A, rows, s, mu, G);
+    if (st == ORC_OK) st = orc_cholesky(G, n);
+    if (st == ORC_OK) st = orc_spd_inverse(G, n, V);
+    free(rows); free(G);
+    return st;
+}
+
+/* x += V A_B^T (b_B - A_B x) with a stored V (n x n): r_B as in the s < n
+ * form, g = A_B^T r_B (column sums above), y_c = sum over d ascending of
+ * V_cd g_d (a chain from 0), then x_c += y_c for every column c. */
+int orc_update_woodbury(const orc_matrix *A, const int64_t *rows, int64_t s, const double *V,
+                        const double *b, double *x)
+{
+    const int64_t n = A->n;
+    double *rB = (double *)malloc((size_t)(s ? s : 1) * sizeof(double));
+    double *g = (double *)malloc((size_t)n * sizeof(double));
+    double *y = (double *)malloc((size_t)n * sizeof(double));
+    int st = (rB && g && y) ? ORC_OK : ORC_ERR_OOM;
+    if (st == ORC_OK) {
+        for (int64_t a = 0; a < s; ++a) rB[a] = b[rows[a]] - row_dot(A, rows[a], x);
+        st = column_sums(A, rows, s, rB, g);
+    }
+    if (st == ORC_OK) {
+        for (int64_t c = 0; c < n; ++c) {
+            double acc = 0.0;
+            for (int64_t d = 0; d < n; ++d) acc = fma(V[c * n + d], g[d], acc);
+            y[c] = acc;
+        }
+        for (int64_t c = 0; c < n; ++c) x[c] += y[c];
+    }
+    free(rB); free(g); free(y);
+    return st;
+}
+
+/* The dynamic block when K >= n: G = A_I^T A_I + mu I, L = chol(G),
+ * h = A_I^T r_I, y = (L L^T)^{-1} h by the two triangular solves of
+ * orc_chol_solve, then x_c += y_c for every column c. */
+int orc_update_woodbury_cholesky(const orc_matrix *A, const int64_t *rows, int64_t K, double mu,
+                                 const double *rI, double *x)
+{
+    const int64_t n = A->n;
+    double *G = (double *)malloc((size_t)(n * n) * sizeof(double));
+    double *h = (double *)malloc((size_t)n * sizeof(double));
+    double *y = (double *)malloc((size_t)n * sizeof(double));
+    int st = (G && h && y) ? ORC_OK : ORC_ERR_OOM;
+    if (st == ORC_OK) st = orc_column_gram(A, rows, K, mu, G);
+    if (st == ORC_OK) st = orc_cholesky(G, n);
+    if (st == ORC_OK) st = column_sums(A, rows, K, rI, h);
+    if (st == ORC_OK) {
+        orc_chol_solve(G, n, h, y);
+        for (int64_t c = 0; c < n; ++c) x[c] += y[c];
+    }
+    free(G); free(h); free(y);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 1, the whole solve.
  *   inputs : A, k blocks (uniform partition), mu, b, x0 (NULL -> 0), tol,
  *            maxit, seed, sysid, n_static (3 in the paper), start_iter (the
@@ -666,14 +794,22 @@ int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
             int64_t tau = orc_sample(dcdf, k, seed, sysid, start_iter + j, l);
             if (tr_tau) tr_tau[j * n_static + l] = tau;
             int64_t s = off[tau + 1] - off[tau];
+            const int wood = s >= n;        /* the n x n form (Lemma 1, Section 3.1) */
             if (!Wcache[tau]) {
-                Wcache[tau] = (double *)malloc((size_t)(s * s) * sizeof(double));
+                const int64_t sz = wood ? n * n : s * s;
+                Wcache[tau] = (double *)malloc((size_t)(sz ? sz : 1) * sizeof(double));
                 if (!Wcache[tau]) { st = ORC_ERR_OOM; goto done; }
-                int e = orc_static_operator(A, off, tau, mu, Wcache[tau]);
+                int e = wood ? orc_column_operator(A, off, tau, mu, Wcache[tau])
+                             : orc_static_operator(A, off, tau, mu, Wcache[tau]);
                 if (e != ORC_OK) { st = e; goto done; }
             }
             for (int64_t a = 0; a < s; ++a) rows[a] = off[tau] + a;
-            orc_update_with_inverse(A, rows, s, Wcache[tau], b, x, delta, work);
+            if (wood) {
+                int e = orc_update_woodbury(A, rows, s, Wcache[tau], b, x);
+                if (e != ORC_OK) { st = e; goto done; }
+            } else {
+                orc_update_with_inverse(A, rows, s, Wcache[tau], b, x, delta, work);
+            }
         }
         double rr = orc_residual(A, b, x, r);
         double rrn = sqrt(rr) / bnorm;
@@ -692,7 +828,8 @@ int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
         orc_topk(r, m, K, I);
         if (tr_I) memcpy(tr_I + j * K, I, (size_t)K * sizeof(int64_t));
         for (int64_t a = 0; a < K; ++a) rI[a] = r[I[a]];
-        int e = orc_update_with_cholesky(A, I, K, mu, rI, x, delta);
+        int e = K >= n ? orc_update_woodbury_cholesky(A, I, K, mu, rI, x)
+                       : orc_update_with_cholesky(A, I, K, mu, rI, x, delta);
         if (e != ORC_OK) { st = e; break; }
         if (tr_x) memcpy(tr_x + j * n, x, (size_t)n * sizeof(double));
     }

@@ -520,3 +520,87 @@ def test_fabgmres_wide_system_gives_min_norm_solution():
     assert st == 0
     x_mn = np.linalg.lstsq(s.dense, s.b, rcond=None)[0]
     assert np.linalg.norm(x - x_mn) / np.linalg.norm(x_mn) <= 1e-8
+
+
+# ---- the s >= n form (Lemma 1, Section 3.1) ---------------------------------
+
+def _ridge(A_B, b_B, x, mu):
+    """The regularised block step in closed form: argmin ||A_B z - b_B||^2 +
+    mu ||z - x||^2 = (A_B^T A_B + mu I)^{-1} (A_B^T b_B + mu x)."""
+    n = A_B.shape[1]
+    return np.linalg.solve(A_B.T @ A_B + mu * np.eye(n), A_B.T @ b_B + mu * x)
+
+
+def _tall_sparse():
+    s = W.random_sparse(400, 40, 0.3, seed=17, num_blocks=5, lam=1e-3)
+    return s
+
+
+def test_column_operator_is_the_inverse_of_the_column_gram():
+    s = W.gaussian_dense(700, 120, seed=3, num_blocks=5, lam=1e-6)
+    V = oracle.column_operator(s, 5, 2, 1e-6)
+    A_B = s.dense[280:420]
+    ref = np.linalg.inv(A_B.T @ A_B + 1e-6 * np.eye(120))
+    assert np.max(np.abs(V - ref)) <= 1e-12 * np.max(np.abs(ref))
+    np.testing.assert_allclose(oracle.column_gram(s, np.arange(280, 420), 1e-6),
+                               A_B.T @ A_B + 1e-6 * np.eye(120), rtol=1e-13, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["dense", "sparse"])
+def test_woodbury_static_update_is_the_ridge_step_and_lemma1(kind):
+    """One static update in the n x n form equals the ridge closed form, and
+    the s < n form with W = (A_B A_B^T + mu I)^{-1} gives the same x (Lemma 1)
+    up to its own rounding: with s > n, W carries 1/mu on the null space of
+    A_B A_B^T, so that form's rounding grows like eps ||A_B||^2 / mu, which is
+    why Section 3.1 stores the n x n inverse there.  The sparse block has
+    columns that none of its rows holds."""
+    if kind == "dense":
+        s = W.gaussian_dense(700, 120, seed=3, num_blocks=5, lam=1e-6)
+        mu, k, t = 1e-6, 5, 1
+        A = s.dense
+    else:
+        s = _tall_sparse()
+        mu, k, t = 1e-3, 5, 3
+        A = s.to_dense()
+    off = oracle.partition(s.m, k)
+    rows = np.arange(off[t], off[t + 1])
+    assert len(rows) >= s.n
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(s.n)
+    b = s.b + 0.1 * rng.standard_normal(s.m)          # inconsistent block: a real step
+    V = oracle.column_operator(s, k, t, mu)
+    x_w = oracle.update_woodbury(s, rows, V, b, x)
+    x_ref = _ridge(A[rows], b[rows], x, mu)
+    assert np.linalg.norm(x_w - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    Wm = oracle.static_operator(s, k, t, mu)
+    x_s = oracle.update_with_inverse(s, rows, Wm, b, x)
+    A_B = A[rows]
+    amp = np.finfo(float).eps * np.linalg.norm(A_B, 2) ** 2 / mu
+    assert np.linalg.norm(x_s - x_ref) <= 100 * amp * np.linalg.norm(x_ref)
+    assert np.linalg.norm(x_w - x_ref) <= np.linalg.norm(x_s - x_ref) + 1e-12 * np.linalg.norm(x_ref)
+
+
+def test_woodbury_dynamic_update_is_the_ridge_step():
+    s = _tall_sparse()
+    rng = np.random.default_rng(5)
+    I = np.sort(rng.choice(s.m, 80, replace=False))
+    x = rng.standard_normal(s.n)
+    r = s.b - s.to_dense() @ x
+    x_w = oracle.update_woodbury_cholesky(s, I, 1e-3, r[I], x)
+    x_ref = _ridge(s.to_dense()[I], s.b[I], x, 1e-3)
+    assert np.linalg.norm(x_w - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    # and the K x K form agrees (Lemma 1), up to its eps ||A_I||^2 / mu rounding
+    x_k = oracle.update_with_cholesky(s, I, 1e-3, r[I], x)
+    amp = np.finfo(float).eps * np.linalg.norm(s.to_dense()[I], 2) ** 2 / 1e-3
+    assert np.linalg.norm(x_k - x_ref) <= 100 * amp * np.linalg.norm(x_ref)
+
+
+def test_tall_consistent_system_solved_by_one_full_rank_block():
+    """With s >= n and a full-column-rank block, one regularised step on a
+    consistent system lands within O(mu / sigma_min^2) of x_true."""
+    s = W.gaussian_dense(700, 120, seed=3, num_blocks=5, lam=1e-10)
+    r = oracle.solve(s, maxit=1, tol=0.0, seed=1)
+    assert np.linalg.norm(r.x - s.x_true) <= 1e-8 * np.linalg.norm(s.x_true)
+    sp = _tall_sparse()
+    r2 = oracle.solve(sp, maxit=3000, tol=1e-12, seed=2)
+    assert r2.status == 0 and r2.rrn <= 1e-12
