@@ -65,11 +65,12 @@ enum { RORBK_F64 = 0, RORBK_F32 = 1 };
  *           inner_tol (or inner_maxit iterations), x += d in FP64, repeated
  *           until ||b - A x|| / ||b|| <= tol.  The block operators W_t and the
  *           dynamic block's Cholesky are formed in FP64 and applied in FP32.
- *           MIXED needs every block to have at most as many rows as A has
- *           columns (s <= n): with s > n, A_t A_t^T is singular, W_t carries
- *           1/mu on its null space, and FP32 rounding there is amplified
- *           until the inner solve diverges; such solves return
- *           RORBK_ERR_UNSUPPORTED. */
+ *           Blocks with at least as many rows as A has columns (s >= n)
+ *           use the n x n form of Lemma 1 (Section 3.1) in both
+ *           arithmetics: V_t = (A_t^T A_t + mu I)^{-1} and, when K >= n, the
+ *           dynamic block's (A_I^T A_I + mu I)^{-1} A_I^T r_I.  The s x s
+ *           form would carry 1/mu on the null space of A_t A_t^T, which FP32
+ *           rounding cannot hold. */
 enum { RORBK_PREC_FP64 = 0, RORBK_PREC_MIXED = 1 };
 
 /* Matrix description for rorbk_setup.
@@ -266,14 +267,18 @@ rorbk_status rorbk_get_proposal(rorbk_handle h, double *cdf_host,
                                 double *c_rowsum_host);
 
 /* Static operator W_t = (A_t A_t^T + mu I)^{-1} of block t as a dense s_t x s_t
- * row-major host array (s_t = rows of block t). */
+ * row-major host array (s_t = rows of block t).  A block with s_t >= n stores
+ * V_t = (A_t^T A_t + mu I)^{-1} instead (Lemma 1 and Section 3.1: the update
+ * is then x += V_t A_t^T (b_t - A_t x)); for such a block the call writes V_t
+ * as an n x n row-major array. */
 rorbk_status rorbk_get_static_operator(rorbk_handle h, int64_t t, double *W_host);
 
 /* The device sampler: tau for (iteration counter it, draw l). */
 rorbk_status rorbk_sample(rorbk_handle h, uint64_t seed, uint64_t system_id,
                           int64_t it, int64_t l, int64_t *tau_host);
 
-/* One static update with block tau: x += A_tau^T W_tau (b_tau - A_tau x). */
+/* One static update with block tau: x += A_tau^T W_tau (b_tau - A_tau x), or
+ * x += V_tau A_tau^T (b_tau - A_tau x) for a block with s_tau >= n. */
 rorbk_status rorbk_static_update(rorbk_handle h, int64_t tau, const double *b,
                                  double *x);
 
@@ -296,7 +301,8 @@ rorbk_status rorbk_residual32(rorbk_handle h, const float *b, const float *x, fl
 rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);
 
 /* Dynamic update for the ascending row set I[K] (device) with the residual r
- * (device, m doubles, read at I): x += A_I^T (A_I A_I^T + mu I)^{-1} r_I. */
+ * (device, m doubles, read at I): x += A_I^T (A_I A_I^T + mu I)^{-1} r_I, or,
+ * when K >= n, x += (A_I^T A_I + mu I)^{-1} A_I^T r_I (Lemma 1). */
 rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
                                   const double *r, double *x);
 

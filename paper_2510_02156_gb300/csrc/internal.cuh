@@ -168,6 +168,14 @@ struct rorbk_ctx {
     double *wgt = nullptr, *wcdf = nullptr;   // [k] residual-weighted draws: weights, running sum
     // incremental residual: CSC copy of A (built at the first such solve) and
     // the log of (column, increment) pairs
+    // the s >= n form (Lemma 1, Section 3.1): V_t = (A_t^T A_t + mu I)^{-1} of
+    // the blocks with at least n rows (wood_ptr[t] >= 0, n x n row-major), and
+    // for K >= n the dynamic block's rows as a dense K x n array plus A_I^T r_I
+    long long *wood_ptr = nullptr;
+    double *wood_ss = nullptr;
+    float *wood_ss32 = nullptr;
+    int n_wood = 0;
+    double *dynw = nullptr;          // [K n + n]
     // mixed-precision dense dynamic Gram on the tensor cores: FP32 partial
     // tiles [gram_tiles][gram_splits][128][128]
     float *gram_part = nullptr;

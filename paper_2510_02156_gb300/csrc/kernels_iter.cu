@@ -83,6 +83,10 @@ struct Mat {
     const int *slen, *srow, *srlen, *scol;
     const double *sval;
     const float *sval32;
+    // the s >= n form (Lemma 1, Section 3.1): block t's V_t at wood + wood_ptr[t]
+    // (n x n row-major) when wood_ptr != nullptr and wood_ptr[t] >= 0
+    const long long *wood_ptr;
+    const T *wood;
 };
 
 template <typename T>
@@ -94,7 +98,7 @@ Mat<double> make_mat<double>(rorbk_ctx *h) {
                        h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val, h->bt.seg, h->bt.seg_ptr,
                        h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                        h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
-                       h->sell.val32};
+                       h->sell.val32, h->wood_ptr, h->wood_ss};
 }
 template <>
 Mat<float> make_mat<float>(rorbk_ctx *h) {
@@ -103,7 +107,7 @@ Mat<float> make_mat<float>(rorbk_ctx *h) {
                       h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val32, h->bt.seg, h->bt.seg_ptr,
                       h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                       h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
-                      h->sell.val32};
+                      h->sell.val32, h->wood_ptr, h->wood_ss32};
 }
 
 // ---------------------------------------------------- incremental residual
@@ -226,8 +230,40 @@ __device__ int stage_issue(const Mat<T> &A, int tau, Stage<T> st, unsigned long 
     return a0;
 }
 
+// The s >= n form of a static update (Lemma 1, Section 3.1), called by every
+// thread of k_static once r_tau is in rloc: g = A_tau^T r_tau (each column
+// over its rows ascending, 0 for the columns the block does not hold) into y,
+// then x_c += sum over d ascending of V_cd g_d for every column c.
+template <typename T>
+__device__ __forceinline__ void static_update_wood(int n, int ns, const int *bt_seg, const int *bt_col,
+                                                const uint16_t *bt_row, const T *bt_val, const T *V,
+                                                int p0, int pend, const T *rloc, T *y, T *x, Ctl *ctl,
+                                                bool lg) {
+    const int a = threadIdx.x;
+    for (int c = a; c < n; c += blockDim.x) y[c] = T(0);
+    __syncthreads();
+    for (int gq = a; gq < ns; gq += blockDim.x) {
+        int q = bt_seg[p0 + gq];
+        const int c = bt_col[q];
+        T acc3 = T(0);
+        for (; q < pend && bt_col[q] == c; ++q) acc3 = Ar<T>::fma(bt_val[q], rloc[bt_row[q]], acc3);
+        y[c] = acc3;
+    }
+    __syncthreads();
+    for (int c = a; c < n; c += blockDim.x) {
+        const T *Vr = V + (long long)c * n;
+        T acc4 = T(0);
+        for (int d = 0; d < n; ++d) acc4 = Ar<T>::fma(Vr[d], y[d], acc4);
+        x[c] = Ar<T>::add(x[c], acc4);
+        if (lg) inc_log(ctl, c, (double)acc4);
+    }
+    __syncthreads();
+}
+
 // LOG: the incremental residual's variant, which logs every change of x.
-template <typename T, bool LOG = false>
+// WOOD: the variant for handles with blocks in the s >= n form (the other
+// instances compile without that branch).
+template <typename T, bool LOG = false, bool WOOD = false>
 __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__ b, T *x,
                                                  Ctl *ctl, int force_tau, int use_stages,
                                                  int l_begin) {
@@ -315,6 +351,13 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         }
         if (a < s) rloc[la] = Ar<T>::sub(bi, acc);
         __syncthreads();
+        const long long wp = WOOD ? A.wood_ptr[tau] : -1;
+        if (WOOD && wp >= 0) {
+            static_update_wood<T>(A.n, A.nseg[tau], A.bt_seg, A.bt_col, A.bt_row, A.bt_val, A.wood + wp, p0,
+                                  pend, rloc, y, x, ctl, lg);
+            if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stg[sidx], &bar[sidx]) : -1;
+            continue;
+        }
         if (a < s) {
             if (pos < 0) {
                 y[la] = Ar<T>::fma(wd, rloc[la], T(0));
@@ -1578,6 +1621,7 @@ __global__ void __launch_bounds__(1024) k_sd_apply(Mat<T> A, const T *__restrict
     if (ctl->done || ctl->halt || l >= ctl->n_static) return;
     const long long it = ctl->iter_base + ctl->iter;
     const int tau = sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
+    if (A.wood_ptr && A.wood_ptr[tau] >= 0) return;   // the s >= n form needs no W r
     const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
     const int a = threadIdx.x;
     if (a >= s) return;
@@ -1597,9 +1641,11 @@ __global__ void __launch_bounds__(1024) k_sd_apply(Mat<T> A, const T *__restrict
 // x_c += sum over the block's rows a (ascending) of a_ac y_a: in a dense
 // block every column holds every row, so the column-sorted copy's segment of
 // column c is the rows in ascending order, and A itself (row-major) gives the
-// same chain with loads coalesced across the threads' columns.
+// same chain with loads coalesced across the threads' columns.  For a block in
+// the s >= n form it forms g_c = sum over the rows of a_ac r_a into y instead
+// (k_sd_wood applies V).
 template <typename T>
-__global__ void __launch_bounds__(256) k_sd_scatter(Mat<T> A, const T *__restrict__ y, T *x,
+__global__ void __launch_bounds__(256) k_sd_scatter(Mat<T> A, const T *__restrict__ rl, T *y, T *x,
                                                     Ctl *ctl, int l) {
     __shared__ long long rbase[kMaxBlockRows];
     if (ctl->done || ctl->halt || l >= ctl->n_static) return;
@@ -1608,10 +1654,34 @@ __global__ void __launch_bounds__(256) k_sd_scatter(Mat<T> A, const T *__restric
     const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
     for (int a = threadIdx.x; a < s; a += blockDim.x) rbase[a] = A.rowptr[r0 + a];
     __syncthreads();
+    const bool wood = A.wood_ptr && A.wood_ptr[tau] >= 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < A.n; c += gridDim.x * blockDim.x) {
         T acc3 = T(0);
-        for (int a = 0; a < s; ++a) acc3 = Ar<T>::fma(A.val[rbase[a] + c], y[a], acc3);
-        x[c] = Ar<T>::add(x[c], acc3);
+        if (wood) {
+            for (int a = 0; a < s; ++a) acc3 = Ar<T>::fma(A.val[rbase[a] + c], rl[a], acc3);
+            y[c] = acc3;
+        } else {
+            for (int a = 0; a < s; ++a) acc3 = Ar<T>::fma(A.val[rbase[a] + c], y[a], acc3);
+            x[c] = Ar<T>::add(x[c], acc3);
+        }
+    }
+}
+
+// The s >= n form of a dense block: x_c += sum over d ascending of V_cd g_d,
+// one thread per column (g from k_sd_scatter).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sd_wood(Mat<T> A, const T *__restrict__ g, T *x, Ctl *ctl, int l) {
+    if (ctl->done || ctl->halt || l >= ctl->n_static) return;
+    const long long it = ctl->iter_base + ctl->iter;
+    const int tau = sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)it, (uint64_t)l);
+    const long long wp = A.wood_ptr[tau];
+    if (wp < 0) return;
+    const T *V = A.wood + wp;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < A.n; c += gridDim.x * blockDim.x) {
+        const T *Vr = V + (long long)c * A.n;
+        T acc = T(0);
+        for (int d = 0; d < A.n; ++d) acc = Ar<T>::fma(Vr[d], g[d], acc);
+        x[c] = Ar<T>::add(x[c], acc);
     }
 }
 
@@ -1796,6 +1866,52 @@ __global__ void __launch_bounds__(256) k_dyn_gram_reduce(const float *__restrict
 // column-oriented solves in the same order (zero multipliers skipped alike).
 constexpr int kPW = 32;
 
+// ---- the dynamic block in the n x n form (K >= n; Lemma 1) ----------------
+// G = A_I^T A_I + mu I, h = A_I^T r_I, y = G^{-1} h by the blocked Cholesky and
+// its solves (size n, z starting at h), then x_c += y_c.  The rows of I are
+// first laid out as a dense K x n array (dw; unstored entries zero), so the
+// column sums run over the rows in ascending order as in the definition.
+__global__ void __launch_bounds__(256) k_dynw_rows(const int *__restrict__ rowptr, const int *__restrict__ col,
+                                                   const double *__restrict__ val, int n, int K, Dyn D,
+                                                   double *dw, Ctl *ctl) {
+    if (ctl->done || ctl->status || ctl->halt) return;
+    const int lane = threadIdx.x & 31;
+    for (int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < K; a += (gridDim.x * blockDim.x) >> 5) {
+        const int row = D.I[a];
+        for (int p = rowptr[row] + lane; p < rowptr[row + 1]; p += 32) dw[(long long)a * n + col[p]] = val[p];
+    }
+}
+
+// Packed lower entry q = c (c + 1) / 2 + d of G = A_I^T A_I + mu I: one fused
+// chain over the K rows ascending, then mu on the diagonal.
+__global__ void __launch_bounds__(256) k_dynw_gram(const double *__restrict__ dw, int n, int K, double mu, Dyn D,
+                                                   Ctl *ctl) {
+    if (ctl->done || ctl->status || ctl->halt) return;
+    const long long total = (long long)n * (n + 1) / 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        int c = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+        while ((long long)c * (c + 1) / 2 > q) --c;
+        while ((long long)(c + 1) * (c + 2) / 2 <= q) ++c;
+        const int d = (int)(q - (long long)c * (c + 1) / 2);
+        double g = 0.0;
+        for (int a = 0; a < K; ++a) g = __fma_rn(dw[(long long)a * n + c], dw[(long long)a * n + d], g);
+        D.g[q] = c == d ? __dadd_rn(g, mu) : g;
+    }
+}
+
+// h_c = sum over the K rows ascending of a_{I_a c} r_{I_a} (one fused chain).
+template <typename T>
+__global__ void __launch_bounds__(256) k_dynw_rhs(const double *__restrict__ dw, const T *__restrict__ r, int n,
+                                                  int K, Dyn D, double *hz, Ctl *ctl) {
+    if (ctl->done || ctl->status || ctl->halt) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double g = 0.0;
+        for (int a = 0; a < K; ++a) g = __fma_rn(dw[(long long)a * n + c], (double)r[D.I[a]], g);
+        hz[c] = g;
+    }
+}
+
 // Panel j0 with its rows spread over the grid.  Every grid block factors the
 // w x w diagonal block and forward-solves its part of z in shared memory (the
 // same operations in every block), with warps 1..7; lane t of warp 0 of block
@@ -1808,7 +1924,7 @@ constexpr int kPW = 32;
 // (ticket) writes the diagonal block back, after every block has read it.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dchol_panel_rows(const T *__restrict__ r, int K, int j0, Dyn D,
-                                                          Ctl *ctl) {
+                                                          Ctl *ctl, const double *__restrict__ z0) {
     __shared__ double Ld[kPW][kPW + 1];
     __shared__ double zd[kPW];
     __shared__ int s_bad, is_last;
@@ -1819,14 +1935,16 @@ __global__ void __launch_bounds__(256) k_dchol_panel_rows(const T *__restrict__ 
         const int i = q / w, jj = q % w;
         Ld[i][jj] = i >= jj ? D.g[pidx(j0 + i, j0 + jj)] : 0.0;
     }
-    for (int i = tid; i < w; i += blockDim.x) zd[i] = j0 == 0 ? (double)r[D.I[i]] : D.y[j0 + i];
+    // z starts as r_I (or as z0, the n x n form's A_I^T r_I)
+    for (int i = tid; i < w; i += blockDim.x)
+        zd[i] = j0 == 0 ? (z0 ? z0[i] : (double)r[D.I[i]]) : D.y[j0 + i];
     // this block's rows below the diagonal block: read before anything is written
     const int i = w + blockIdx.x * 32 + tid;
     const bool own = tid < 32 && i < nr;
     double Lr[kPW];
 #pragma unroll
     for (int jj = 0; jj < kPW; ++jj) Lr[jj] = (own && jj < w) ? D.g[pidx(j0 + i, j0 + jj)] : 0.0;
-    double zi = own ? (j0 == 0 ? (double)r[D.I[i]] : D.y[j0 + i]) : 0.0;
+    double zi = own ? (j0 == 0 ? (z0 ? z0[i] : (double)r[D.I[i]]) : D.y[j0 + i]) : 0.0;
     if (tid == 0) s_bad = 0;
     __syncthreads();
 #pragma unroll
@@ -1961,13 +2079,17 @@ __global__ void __launch_bounds__(256) k_dyn_dense_scatter(const double *__restr
                                                            const float *__restrict__ v32, T *x, int n,
                                                            int K, Dyn D, Ctl *ctl, int count_iter,
                                                            int use_cond,
-                                                           cudaGraphConditionalHandle hcond) {
+                                                           cudaGraphConditionalHandle hcond, int wood) {
     __shared__ int is_last;
     if (ctl->done || ctl->status || ctl->halt) {
         if (count_iter && blockIdx.x == 0) end_iteration<T>(x, n, ctl, use_cond, hcond);
         return;
     }
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        if (wood) {                           // the n x n form: x_c += y_c
+            x[c] = Ar<T>::add(x[c], as<T>(D.y[c]));
+            continue;
+        }
         T acc = T(0);
         for (int a = 0; a < K; ++a)
             acc = Ar<T>::fma(dense_value<T>(v64, v32, (long long)D.I[a] * n + c), as<T>(D.y[a]), acc);
@@ -2130,6 +2252,14 @@ void configure_kernels() {
                          (int)static_smem_bytes<double>());
     cudaFuncSetAttribute(k_static<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)static_smem_bytes<float>());
+    cudaFuncSetAttribute(k_static<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<double>());
+    cudaFuncSetAttribute(k_static<float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<float>());
+    cudaFuncSetAttribute(k_static<double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<double>());
+    cudaFuncSetAttribute(k_static<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<float>());
     cudaFuncSetAttribute(k_topk_collect<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)collect_smem_bytes());
     cudaFuncSetAttribute(k_topk_collect<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2171,6 +2301,31 @@ void launch_dense_gram(rorbk_ctx *h, Ctl *ctl, int tensor_cores) {
 template <typename T>
 static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int check_done,
                                 int count_iter, int use_cond, unsigned long long hcond, int inc = 0) {
+    if (h->K >= h->n) {
+        // the n x n form (Lemma 1): dense rows of I, G = A_I^T A_I + mu I,
+        // h = A_I^T r_I, blocked Cholesky of size n starting z at h, x += y
+        const int K = h->K, n = (int)h->n;
+        double *dw = h->dynw, *hz = h->dynw + (long long)K * n;
+        cudaMemsetAsync(dw, 0, (size_t)K * n * sizeof(double), h->stream);
+        k_dynw_rows<<<std::max(1, std::min(4 * h->num_sms, (K * 32 + 255) / 256)), 256, 0, h->stream>>>(
+            h->rowptr, h->col, h->val, n, K, dyn_bufs(h), dw, ctl);
+        const long long np = (long long)n * (n + 1) / 2;
+        k_dynw_gram<<<(int)std::max<long long>(1, std::min<long long>(8LL * h->num_sms, (np + 255) / 256)), 256, 0,
+                      h->stream>>>(dw, n, K, h->mu, dyn_bufs(h), ctl);
+        k_dynw_rhs<T><<<std::max(1, (n + 63) / 64), 64, 0, h->stream>>>(dw, r, n, K, dyn_bufs(h), hz, ctl);
+        for (int j0 = 0; j0 < n; j0 += kPW) {
+            const int below = n - j0 - std::min(kPW, n - j0);
+            k_dchol_panel_rows<T><<<std::max(1, (below + 31) / 32), 256, 0, h->stream>>>(r, n, j0, dyn_bufs(h),
+                                                                                       ctl, hz);
+            const int rest = n - std::min(n, j0 + kPW), tt = (rest + 15) / 16;
+            if (rest > 0) k_dchol_trail<<<tt * (tt + 1) / 2, 256, 0, h->stream>>>(n, j0, dyn_bufs(h), ctl);
+        }
+        k_dchol_back<<<1, 1024, 0, h->stream>>>(n, dyn_bufs(h), ctl);
+        const int g = std::max(1, std::min(8 * h->num_sms, (n + 63) / 64));
+        k_dyn_dense_scatter<T><<<g, 64, 0, h->stream>>>(h->val, h->val32, x, n, K, dyn_bufs(h), ctl, count_iter,
+                                                          use_cond, (cudaGraphConditionalHandle)hcond, 1);
+        return;
+    }
     if (h->format == RORBK_FORMAT_DENSE) {
         const int K = h->K;
         // mixed precision: the TF32 tensor-core Gram (FP32 partials added in FP64)
@@ -2178,7 +2333,8 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
         for (int j0 = 0; j0 < K; j0 += kPW) {
             const int below = K - j0 - std::min(kPW, K - j0);
             k_dchol_panel_rows<T><<<std::max(1, (below + 31) / 32), 256, 0, h->stream>>>(r, K, j0,
-                                                                                       dyn_bufs(h), ctl);
+                                                                                       dyn_bufs(h), ctl,
+                                                                                       nullptr);
             const int rest = K - std::min(K, j0 + kPW), tt = (rest + 15) / 16;
             if (rest > 0) k_dchol_trail<<<tt * (tt + 1) / 2, 256, 0, h->stream>>>(K, j0, dyn_bufs(h), ctl);
         }
@@ -2186,7 +2342,7 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
         const int g = std::max(1, std::min(8 * h->num_sms, (int)((h->n + 63) / 64)));
         k_dyn_dense_scatter<T><<<g, 64, 0, h->stream>>>(h->val, h->val32, x, (int)h->n, K, dyn_bufs(h),
                                                           ctl, count_iter, use_cond,
-                                                          (cudaGraphConditionalHandle)hcond);
+                                                          (cudaGraphConditionalHandle)hcond, 0);
         return;
     }
     Mat<T> A = make_mat<T>(h);
@@ -2216,13 +2372,18 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
         for (int l = 0; l < kDenseStatic; ++l) {
             k_sd_rows_tiled<T><<<gr, kSdCols, sd_rows_smem<T>(), h->stream>>>(A, b, x, rl, ctl, l);
             k_sd_apply<T><<<1, 1024, 0, h->stream>>>(A, rl, yy, ctl, l);
-            k_sd_scatter<T><<<gs, 64, 0, h->stream>>>(A, yy, x, ctl, l);
+            k_sd_scatter<T><<<gs, 64, 0, h->stream>>>(A, rl, yy, x, ctl, l);
+            if (h->n_wood) k_sd_wood<T><<<gs, 64, 0, h->stream>>>(A, yy, x, ctl, l);
         }
         // updates beyond kDenseStatic (n_static > 3), if any
-        k_static<T><<<1, 1024, static_smem_bytes<T>(), h->stream>>>(A, b, x, ctl, -1, 0, kDenseStatic);
+        (h->n_wood ? k_static<T, false, true> : k_static<T, false, false>)<<<1, 1024, static_smem_bytes<T>(),
+                                                                              h->stream>>>(A, b, x, ctl, -1, 0,
+                                                                                           kDenseStatic);
     } else {
-        (inc ? k_static<T, true> : k_static<T, false>)<<<1, 1024, static_smem_bytes<T>(), h->stream>>>(
-            A, b, x, ctl, -1, 1, 0);
+        const bool wd = h->n_wood > 0;
+        (inc ? (wd ? k_static<T, true, true> : k_static<T, true, false>)
+             : (wd ? k_static<T, false, true> : k_static<T, false, false>))<<<1, 1024, static_smem_bytes<T>(),
+                                                                               h->stream>>>(A, b, x, ctl, -1, 1, 0);
     }
     if (inc) {   // r from the change log; the exact kernel below runs only when asked to
         k_inc_apply<T><<<4 * h->num_sms, 256, 0, h->stream>>>(h->csc_ptr, h->csc_row, csc_values<T>(h),
@@ -2283,7 +2444,8 @@ void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_ou
 }
 
 void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x) {
-    k_static<double><<<1, 1024, static_smem_bytes<double>(), h->stream>>>(make_mat<double>(h), b, x,
+    (h->n_wood ? k_static<double, false, true> : k_static<double, false, false>)<<<
+        1, 1024, static_smem_bytes<double>(), h->stream>>>(make_mat<double>(h), b, x,
                                                                           h->ctl, tau, 0, 0);
 }
 

@@ -290,6 +290,39 @@ __global__ void k_proposal(const double *__restrict__ rowsum, int k, double n,
     }
 }
 
+// W = (L L^T)^{-1} from the Cholesky factor L in G (nS x nS row-major, lower),
+// written over G (full, symmetric); Li is nS x nS scratch.  Linv column by
+// column: Linv_jj = 1/L_jj, Linv_ij = -(sum_{c=j}^{i-1} L_ic Linv_cj) / L_ii, c
+// ascending; then W_ij = sum_{c >= max(i,j)} Linv_ci Linv_cj (c ascending).
+// All threads of the block take part.
+__device__ void spd_inverse_from_factor(double *G, double *Li, int nS) {
+    for (int j = threadIdx.x; j < nS; j += blockDim.x) {
+        for (int i = 0; i < j; ++i) Li[(long long)i * nS + j] = 0.0;
+        Li[(long long)j * nS + j] = 1.0 / G[(long long)j * nS + j];
+        for (int i = j + 1; i < nS; ++i) {
+            double acc = 0.0;
+            for (int c = j; c < i; ++c)
+                acc = __fma_rn(G[(long long)i * nS + c], Li[(long long)c * nS + j], acc);
+            Li[(long long)i * nS + j] = -acc / G[(long long)i * nS + i];
+        }
+    }
+    __syncthreads();
+    for (long long idx = threadIdx.x; idx < (long long)nS * nS; idx += blockDim.x) {
+        int i = (int)(idx / nS), j = (int)(idx % nS);
+        if (j > i) continue;
+        double acc = 0.0;
+        for (int c = i; c < nS; ++c)
+            acc = __fma_rn(Li[(long long)c * nS + i], Li[(long long)c * nS + j], acc);
+        // the factor's (i, j) is read by nobody after the Linv pass
+        G[(long long)i * nS + j] = acc;
+    }
+    __syncthreads();
+    for (long long idx = threadIdx.x; idx < (long long)nS * nS; idx += blockDim.x) {
+        int i = (int)(idx / nS), j = (int)(idx % nS);
+        if (j > i) G[(long long)i * nS + j] = G[(long long)j * nS + i];
+    }
+}
+
 // ------------------------------------------------------------ static ops
 // One block of threads per static block t.  Inputs: the block's coupled
 // flags and S offsets; outputs W on S (row-major |S|^2 at w_ss + w_ptr[t]),
@@ -301,12 +334,20 @@ __global__ void k_static_ops(const int *__restrict__ rowptr, const int *__restri
                              const int *__restrict__ s_ptr, const long long *__restrict__ w_ptr,
                              uint16_t *__restrict__ s_idx, int *__restrict__ s_pos,
                              double *__restrict__ w_ss, double *__restrict__ w_diag,
-                             double *__restrict__ linv, int *__restrict__ status) {
+                             double *__restrict__ linv, const long long *__restrict__ wood_ptr,
+                             int *__restrict__ status) {
     __shared__ int scan_scratch[33];
     __shared__ int bad;
     __shared__ double gdiag[kMaxBlockRows];
     const int t = blockIdx.x;
     const int r0 = off[t], s = off[t + 1] - r0;
+    if (wood_ptr && wood_ptr[t] >= 0) {          // the n x n form serves this block
+        for (int a = threadIdx.x; a < s; a += blockDim.x) {
+            s_pos[r0 + a] = -1;
+            w_diag[r0 + a] = 0.0;
+        }
+        return;
+    }
     const int sb = s_ptr[t], nS = s_ptr[t + 1] - sb;
     double *G = w_ss + w_ptr[t];
     double *Li = linv + w_ptr[t];
@@ -355,36 +396,67 @@ __global__ void k_static_ops(const int *__restrict__ rowptr, const int *__restri
         }
         __syncthreads();
         block_cholesky(G, nS, nS, &bad);
-        // Linv column by column: Linv_jj = 1/L_jj, Linv_ij = -(sum_{c=j}^{i-1}
-        // L_ic Linv_cj) / L_ii, c ascending.
-        for (int j = threadIdx.x; j < nS; j += blockDim.x) {
-            for (int i = 0; i < j; ++i) Li[(long long)i * nS + j] = 0.0;
-            Li[(long long)j * nS + j] = 1.0 / G[(long long)j * nS + j];
-            for (int i = j + 1; i < nS; ++i) {
-                double acc = 0.0;
-                for (int c = j; c < i; ++c)
-                    acc = __fma_rn(G[(long long)i * nS + c], Li[(long long)c * nS + j], acc);
-                Li[(long long)i * nS + j] = -acc / G[(long long)i * nS + i];
+        spd_inverse_from_factor(G, Li, nS);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && bad) set_status(status, kDevNotSpd);
+}
+
+// ------------------------------------------------- the s >= n operators
+// Lemma 1 and Section 3.1: a block with at least as many rows as A has columns
+// stores V_t = (A_t^T A_t + mu I)^{-1} (n x n row-major at wood + wood_ptr[t])
+// instead of W_t.  One block of threads per static block; blocks without the
+// form return.  G_cd is the sum over the block's rows, ascending, of
+// a_rc a_rd where both are stored: the merge of the two columns' segments of
+// the column-sorted copy (rows ascending in each), one fused chain from 0;
+// then mu on the diagonal, the Cholesky factor and the explicit inverse as for
+// W_t.  linv has the layout of wood.
+__global__ void k_wood_ops(const int *__restrict__ rowptr, const int *__restrict__ off, int n, double mu,
+                           const long long *__restrict__ wood_ptr, const int *__restrict__ bt_col,
+                           const uint16_t *__restrict__ bt_row, const double *__restrict__ bt_val,
+                           double *__restrict__ wood, double *__restrict__ linv, int *__restrict__ status) {
+    __shared__ int seg[kMaxBlockRows];         // n <= s <= kMaxBlockRows
+    __shared__ int bad;
+    const int t = blockIdx.x;
+    const long long wp = wood_ptr[t];
+    if (wp < 0) return;
+    const int r0 = off[t], s = off[t + 1] - r0;
+    const int p0 = rowptr[r0], pend = rowptr[r0 + s];
+    double *G = wood + wp, *Li = linv + wp;
+    if (threadIdx.x == 0) bad = 0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const int lo = lower_bound_col(bt_col, p0, pend, c);
+        seg[c] = (lo < pend && bt_col[lo] == c) ? lo : -1;
+    }
+    __syncthreads();
+    const long long pairs = (long long)n * (n + 1) / 2;
+    for (long long idx = threadIdx.x; idx < pairs; idx += blockDim.x) {
+        int i = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+        while ((long long)(i + 1) * (i + 2) / 2 <= idx) ++i;
+        while ((long long)i * (i + 1) / 2 > idx) --i;
+        const int j = (int)(idx - (long long)i * (i + 1) / 2);
+        double g = 0.0;
+        int p = seg[i], q = seg[j];
+        if (p >= 0 && q >= 0) {
+            while (p < pend && q < pend && bt_col[p] == i && bt_col[q] == j) {
+                const int ri = bt_row[p], rj = bt_row[q];
+                if (ri == rj) {
+                    g = __fma_rn(bt_val[p], bt_val[q], g);
+                    ++p;
+                    ++q;
+                } else if (ri < rj) {
+                    ++p;
+                } else {
+                    ++q;
+                }
             }
         }
-        __syncthreads();
-        // W_ij = sum_{c >= max(i,j)} Linv_ci Linv_cj (c ascending), written
-        // over the factor.
-        for (long long idx = threadIdx.x; idx < (long long)nS * nS; idx += blockDim.x) {
-            int i = (int)(idx / nS), j = (int)(idx % nS);
-            if (j > i) continue;
-            double acc = 0.0;
-            for (int c = i; c < nS; ++c)
-                acc = __fma_rn(Li[(long long)c * nS + i], Li[(long long)c * nS + j], acc);
-            // the factor's (i, j) is read by nobody after the Linv pass
-            G[(long long)i * nS + j] = acc;
-        }
-        __syncthreads();
-        for (long long idx = threadIdx.x; idx < (long long)nS * nS; idx += blockDim.x) {
-            int i = (int)(idx / nS), j = (int)(idx % nS);
-            if (j > i) G[(long long)i * nS + j] = G[(long long)j * nS + i];
-        }
+        if (i == j) g = __dadd_rn(g, mu);
+        G[(long long)i * n + j] = g;
     }
+    __syncthreads();
+    block_cholesky(G, n, n, &bad);
+    spd_inverse_from_factor(G, Li, n);
     __syncthreads();
     if (threadIdx.x == 0 && bad) set_status(status, kDevNotSpd);
 }
@@ -591,6 +663,23 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
                                                 cudaMemcpyDeviceToHost, s), "coupled counts")))
             return st;
         if ((st = cuda_check(h, cudaStreamSynchronize(s), "coupled counts"))) return st;
+        // blocks with at least n rows take the n x n form (Lemma 1, Section 3.1)
+        std::vector<long long> woodp(k, -1);
+        long long wtot = 0;
+        h->n_wood = 0;
+        for (int t = 0; t < k; ++t)
+            if (h->h_off[t + 1] - h->h_off[t] >= n) {
+                woodp[t] = wtot;
+                wtot += (long long)n * n;
+                hcnt[t] = 0;
+                ++h->n_wood;
+            }
+        if (h->n_wood) {
+            h->wood_ptr = (long long *)dev_alloc(h, (size_t)k * sizeof(long long));
+            h->wood_ss = (double *)dev_alloc(h, (size_t)wtot * sizeof(double));
+            if (!h->wood_ptr || !h->wood_ss) return fail(h, RORBK_ERR_OOM, "s >= n operators");
+            cudaMemcpyAsync(h->wood_ptr, woodp.data(), (size_t)k * sizeof(long long), cudaMemcpyHostToDevice, s);
+        }
         std::vector<int> sptr(k + 1, 0);
         std::vector<long long> wptr(k + 1, 0);
         for (int t = 0; t < k; ++t) {
@@ -616,11 +705,21 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
         cudaMemsetAsync(flags, 0, sizeof(int), s);
         k_static_ops<<<k, 256, 0, s>>>(h->rowptr, h->col, h->val, h->off, h->mu, coupled,
                                        h->ops.s_ptr, h->ops.w_ptr, h->ops.s_idx, h->ops.s_pos,
-                                       h->ops.w_ss, h->ops.w_diag, linv, flags);
+                                       h->ops.w_ss, h->ops.w_diag, linv, h->wood_ptr, flags);
+        double *linv2 = nullptr;
+        if (h->n_wood) {
+            if (cudaMalloc(&linv2, (size_t)wtot * sizeof(double)) != cudaSuccess) {
+                cudaFree(linv);
+                return fail(h, RORBK_ERR_OOM, "s >= n operator scratch");
+            }
+            k_wood_ops<<<k, 256, 0, s>>>(h->rowptr, h->off, (int)n, h->mu, h->wood_ptr, h->bt.col, h->bt.row,
+                                         h->bt.val, h->wood_ss, linv2, flags);
+        }
         int spd = 0;
         st = cuda_check(h, cudaMemcpyAsync(&spd, flags, sizeof(int), cudaMemcpyDeviceToHost, s), "static ops");
         if (!st) st = cuda_check(h, cudaStreamSynchronize(s), "static ops");
         cudaFree(linv);
+        if (linv2) cudaFree(linv2);
         if (st) return st;
         if (spd) return fail(h, RORBK_ERR_NOT_SPD, "a static block Gram is not positive definite (lambda = 0 with dependent rows?)");
         if (h->precision_built) {
@@ -632,6 +731,11 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
             k_narrow<<<gs, 256, 0, s>>>(h->ops.w_ss, h->ops.w_ss32, std::max(1LL, wptr[k]));
             k_narrow<<<gs, 256, 0, s>>>(h->ops.w_diag, h->ops.w_diag32, m);
             k_narrow<<<gs, 256, 0, s>>>(h->bt.val, h->bt.val32, nnz);
+            if (h->n_wood) {
+                h->wood_ss32 = (float *)dev_alloc(h, (size_t)wtot * sizeof(float));
+                if (!h->wood_ss32) return fail(h, RORBK_ERR_OOM, "fp32 s >= n operators");
+                k_narrow<<<gs, 256, 0, s>>>(h->wood_ss, h->wood_ss32, wtot);
+            }
         }
     }
     return cuda_check(h, cudaStreamSynchronize(s), "setup");

@@ -272,6 +272,10 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         cudaMemsetAsync(D.shared, 0, n * sizeof(unsigned), s);
         cudaMemsetAsync(D.epoch, 0, sizeof(unsigned), s);
     }
+    if (h->K >= n) {   // the dynamic block in the n x n form: its rows as a dense K x n array, A_I^T r_I
+        h->dynw = (double *)dev_alloc(h, ((size_t)h->K * n + n) * sizeof(double));
+        if (!h->dynw) return fail(h, RORBK_ERR_OOM, "n x n dynamic workspace");
+    }
     if (h->precision_built) {
         h->r32 = (float *)dev_alloc(h, m * sizeof(float));
         h->b32 = (float *)dev_alloc(h, m * sizeof(float));
@@ -512,11 +516,9 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
     if (inc && opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED)
         return fail(h, RORBK_ERR_UNSUPPORTED, "the incremental residual is not combined with residual-weighted draws");
     if (inc && opt.refresh < 0) return fail(h, RORBK_ERR_INVALID_ARG, "refresh >= 0");
-    if (mixed && h->smax > h->n)
+    if (inc && h->K >= h->n)
         return fail(h, RORBK_ERR_UNSUPPORTED,
-                    "mixed precision needs blocks of at most n rows: with s > n the stored "
-                    "inverse scales the null space of A_t A_t^T by 1/mu, which FP32 cannot "
-                    "carry (the s >= n form of Lemma 1 is not built)");
+                    "the incremental residual does not log the n x n form of the dynamic update (K >= n)");
     if (inc) {
         rorbk_status st = ensure_incremental(h);
         if (st) return st;
@@ -906,6 +908,14 @@ rorbk_status rorbk_get_static_operator(rorbk_handle h, int64_t t, double *W_host
     if (!h || !W_host || t < 0 || t >= h->k) return RORBK_ERR_INVALID_ARG;
     cudaSetDevice(h->device);
     const int r0 = (int)h->h_off[t], s = (int)(h->h_off[t + 1] - h->h_off[t]);
+    if (h->n_wood) {   // a block in the s >= n form stores V_t (n x n) instead
+        long long wpw = -1;
+        rorbk_status st0 = cuda_check(h, cudaMemcpy(&wpw, h->wood_ptr + t, sizeof(long long), cudaMemcpyDeviceToHost), "V");
+        if (st0) return st0;
+        if (wpw >= 0)
+            return cuda_check(h, cudaMemcpy(W_host, h->wood_ss + wpw, (size_t)h->n * h->n * sizeof(double),
+                                            cudaMemcpyDeviceToHost), "V");
+    }
     int sp[2];
     long long wp;
     rorbk_status st = cuda_check(h, cudaMemcpy(sp, h->ops.s_ptr + t, 2 * sizeof(int), cudaMemcpyDeviceToHost), "W");
