@@ -70,7 +70,11 @@ def test_dense_single_dynamic_update_equals_oracle(cuda_ok):
         I = np.sort(rng.choice(s.m, K, replace=False)).astype(np.int32)
         x = _dev(x0)
         h.dynamic_update(_dev(I), _dev(r), x)
-        xo = oracle.update_with_cholesky(s, I, s.lam, r[I], x0)
+        # K = n = 256 here: the n x n form of Lemma 1 applies (K >= n)
+        if K >= s.n:
+            xo = oracle.update_woodbury_cholesky(s, I, s.lam, r[I], x0)
+        else:
+            xo = oracle.update_with_cholesky(s, I, s.lam, r[I], x0)
     np.testing.assert_array_equal(x.cpu().numpy(), xo)
 
 
