@@ -310,6 +310,8 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         // takes the a-th longest row la of the block
         int q0 = 0, q1 = 0, pos = -1, la = 0;
         T bi = T(0), wd = T(0);
+        const int sb = A.s_ptr[tau], nS = A.s_ptr[tau + 1] - sb;   // W_tau on the coupled rows
+        const long long wb = A.w_ptr[tau];
         if (a < s) {
             la = A.bperm[r0 + a];
             q0 = A.rowptr[r0 + la];
@@ -362,9 +364,11 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
             if (pos < 0) {
                 y[la] = Ar<T>::fma(wd, rloc[la], T(0));
             } else {
-                const int sb = A.s_ptr[tau], nS = A.s_ptr[tau + 1] - sb;
-                const T *Wr = A.w_ss + A.w_ptr[tau] + (long long)pos * nS;
+                // the loads of W's row and of the row indices do not depend on
+                // the chain: unrolled, they are in flight ahead of it
+                const T *Wr = A.w_ss + wb + (long long)pos * nS;
                 T acc2 = T(0);
+#pragma unroll 8
                 for (int q = 0; q < nS; ++q) acc2 = Ar<T>::fma(Wr[q], rloc[A.s_idx[sb + q]], acc2);
                 y[la] = acc2;
             }
