@@ -271,18 +271,6 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// ------------------------------------------- programmatic dependent launch
-// A kernel launched with programmatic stream serialization may start while its
-// predecessor in the stream is finishing.  pdl_enter waits until the
-// predecessor grid has completed and its memory operations are visible
-// (griddepcontrol.wait), then lets this grid's own successor be scheduled
-// (griddepcontrol.launch_dependents).  Both are no-ops for a kernel launched
-// without the attribute.  Every kernel that takes part calls it first.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // ------------------------------------------- 5th-generation tensor cores
 // tcgen05 (sm_100 family): the accumulator lives in tensor memory (TMEM,
 // 512 columns x 128 lanes of 32 bits per SM), allocated by one warp; one

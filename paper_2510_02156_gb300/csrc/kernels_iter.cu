@@ -267,7 +267,6 @@ template <typename T, bool LOG = false, bool WOOD = false>
 __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__ b, T *x,
                                                  Ctl *ctl, int force_tau, int use_stages,
                                                  int l_begin) {
-    pdl_enter();
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ T rloc[kMaxBlockRows];
     __shared__ T y[kMaxBlockRows];
@@ -465,7 +464,6 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
                                                   const T *__restrict__ x, T *__restrict__ r,
                                                   double *partials, unsigned *hist1, Ctl *ctl,
                                                   int finalize) {
-    pdl_enter();
     __shared__ unsigned hist[kHistBins];
     __shared__ double red[32];
     __shared__ int is_last;
@@ -593,7 +591,6 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_inc_apply(const int *__restrict__ cptr,
                                                    const int *__restrict__ crow,
                                                    const T *__restrict__ cval, T *r, Ctl *ctl) {
-    pdl_enter();
     if (ctl->done || ctl->halt || ctl->inc_full) return;
     const int nlog = min(ctl->nlog, ctl->log_cap);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -613,7 +610,6 @@ __global__ void __launch_bounds__(256) k_inc_apply(const int *__restrict__ cptr,
 template <typename T>
 __global__ void __launch_bounds__(256) k_inc_finish(const T *__restrict__ r, int m, int K,
                                                     double *partials, unsigned *hist1, Ctl *ctl) {
-    pdl_enter();
     __shared__ unsigned hist[kHistBins];
     __shared__ double red[32];
     __shared__ int is_last, stop;
@@ -705,7 +701,6 @@ __global__ void __launch_bounds__(256) k_topk_hist1(const T *__restrict__ r, int
 template <typename T>
 __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int m, int K,
                                                     unsigned *hist2, Ctl *ctl, int check_done) {
-    pdl_enter();
     __shared__ unsigned hist[kHistBins];
     __shared__ int is_last;
     if (check_done && (ctl->done || ctl->halt)) return;
@@ -904,7 +899,6 @@ __global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, i
                                                       const int *rowptr, int *in_list,
                                                       int *eq_list, Dyn D, Ctl *ctl,
                                                       int check_done) {
-    pdl_enter();
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ int is_last;
     if (check_done && (ctl->done || ctl->halt)) return;
@@ -1380,7 +1374,6 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
 template <typename T>
 __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict__ r, Dyn D,
                                                   Ctl *ctl, int check_done) {
-    pdl_enter();
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ int is_last;
     if (check_done && (ctl->done || ctl->halt)) return;
@@ -1473,7 +1466,6 @@ template <typename T, bool LOG = false>
 __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ctl, int count_iter,
                                                      int use_cond,
                                                      cudaGraphConditionalHandle hcond) {
-    pdl_enter();
     __shared__ int is_last;
     if (ctl->done || ctl->status || ctl->halt) {
         if (count_iter && blockIdx.x == 0) end_iteration<T>(x, n, ctl, use_cond, hcond);
@@ -1522,7 +1514,6 @@ __global__ void __launch_bounds__(256) k_wweights(const double *__restrict__ r,
                                                   const int *__restrict__ off, int k,
                                                   const double *__restrict__ pbar,
                                                   double *__restrict__ w, Ctl *ctl) {
-    pdl_enter();
     if (ctl->done || ctl->halt) return;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -1535,7 +1526,6 @@ __global__ void __launch_bounds__(256) k_wweights(const double *__restrict__ r,
 __global__ void __launch_bounds__(1024) k_wcdf(const double *__restrict__ w, int k,
                                                double *__restrict__ wcdf,
                                                const double *__restrict__ cdf, Ctl *ctl) {
-    pdl_enter();
     __shared__ double tot[1024];
     if (ctl->done || ctl->halt) return;
     const int nc = (k + kWChunk - 1) / kWChunk;
@@ -2230,24 +2220,6 @@ __global__ void __launch_bounds__(256) k_outer_update(double *__restrict__ x, co
 }
 
 // ------------------------------------------------------------- launchers
-// Launch with programmatic stream serialization (see pdl_enter): the kernel
-// may be scheduled while its predecessor finishes; it waits for it first.
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                       Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
-
 static size_t collect_smem_bytes() { return (size_t)kEqCap * (8 + 4) + (size_t)kMaxDynRows * 4; }
 static size_t factor_smem_bytes() {
     return (size_t)(kShCap + kPairCap) * 8 + (size_t)kMaxDynRows * 8 + (size_t)kGPack * 8 +
@@ -2378,11 +2350,10 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
         return;
     }
     Mat<T> A = make_mat<T>(h);
-    launch_pdl(k_dyn_mark<T>, dim3(h->num_sms), dim3(512), factor_smem_bytes(), h->stream, A, r, dyn_bufs(h),
-               ctl, check_done);
-    launch_pdl(inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>, dim3(2 * h->num_sms), dim3(512), 0,
-               h->stream, x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond,
-               (cudaGraphConditionalHandle)hcond);
+    k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
+                                                                        check_done);
+    (inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>)<<<2 * h->num_sms, 512, 0, h->stream>>>(
+        x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond, (cudaGraphConditionalHandle)hcond);
 }
 
 template <typename T>
@@ -2418,38 +2389,33 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
              : (wd ? k_static<T, false, true> : k_static<T, false, false>))<<<1, 1024, static_smem_bytes<T>(),
                                                                                h->stream>>>(A, b, x, ctl, -1, 1, 0);
     }
-    // the kernels after the first of the iteration start while their
-    // predecessor finishes (programmatic dependent launch)
     if (inc) {   // r from the change log; the exact kernel below runs only when asked to
-        launch_pdl(k_inc_apply<T>, dim3(4 * h->num_sms), dim3(256), 0, h->stream, h->csc_ptr, h->csc_row,
-                   csc_values<T>(h), r, ctl);
-        launch_pdl(k_inc_finish<T>, dim3(grid_stream(h, (int)h->m)), dim3(256), 0, h->stream, r, (int)h->m, h->K,
-                   h->partials, h->hist1, ctl);
+        k_inc_apply<T><<<4 * h->num_sms, 256, 0, h->stream>>>(h->csc_ptr, h->csc_row, csc_values<T>(h),
+                                                              r, ctl);
+        k_inc_finish<T><<<grid_stream(h, (int)h->m), 256, 0, h->stream>>>(r, (int)h->m, h->K, h->partials,
+                                                                         h->hist1, ctl);
     }
     if constexpr (sizeof(T) == sizeof(float)) {
-        launch_pdl(k_residual<T, float>, dim3(h->grid_res), dim3(256), 0, h->stream, A, b, x, r, h->partials,
-                   h->hist1, ctl, 1);
+        k_residual<T, float><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
     } else {
         if (h->vdtype == RORBK_F32)
-            launch_pdl(k_residual<T, float>, dim3(h->grid_res), dim3(256), 0, h->stream, A, b, x, r, h->partials,
-                       h->hist1, ctl, 1);
+            k_residual<T, float><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
         else
-            launch_pdl(k_residual<T, double>, dim3(h->grid_res), dim3(256), 0, h->stream, A, b, x, r, h->partials,
-                       h->hist1, ctl, 1);
+            k_residual<T, double><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
     }
     if constexpr (sizeof(T) == sizeof(double))
         if (weighted) launch_weights(h, r);      // the draws of the next iteration
     const int g = grid_stream(h, (int)h->m);
-    launch_pdl(k_topk_hist2<T>, dim3(g), dim3(256), 0, h->stream, r, (int)h->m, h->K, h->hist2, ctl, 1);
-    launch_pdl(k_topk_collect<T>, dim3(std::max(1, g / 2)), dim3(512), collect_smem_bytes(), h->stream, r,
-               (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1);
+    k_topk_hist2<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1);
+    k_topk_collect<T><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
+        r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1);
     launch_dynamic_tail<T>(h, r, x, ctl, 1, 1, use_cond, hcond, inc);
 }
 
 void launch_weights(rorbk_ctx *h, const double *r) {
-    launch_pdl(k_wweights, dim3(std::max(1, std::min(4 * h->num_sms, (h->k + 255) / 256))), dim3(256), 0,
-               h->stream, r, h->off, h->k, h->pbar, h->wgt, h->ctl);
-    launch_pdl(k_wcdf, dim3(1), dim3(1024), 0, h->stream, h->wgt, h->k, h->wcdf, h->cdf, h->ctl);
+    k_wweights<<<std::max(1, std::min(4 * h->num_sms, (h->k + 255) / 256)), 256, 0, h->stream>>>(
+        r, h->off, h->k, h->pbar, h->wgt, h->ctl);
+    k_wcdf<<<1, 1024, 0, h->stream>>>(h->wgt, h->k, h->wcdf, h->cdf, h->ctl);
 }
 
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
