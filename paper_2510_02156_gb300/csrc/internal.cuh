@@ -73,13 +73,6 @@ struct Ctl {
     int *log_col;          // [log_cap] changed columns
     double *log_val;       // [log_cap] their increments
     const double *scdf;    // the running sum the static draws use (P's, or the weighted one)
-    // top-K candidates: the residual pass keeps the rows whose |r| key is at
-    // least kguess (from the previous iteration's K-th key divided by
-    // 2^kshift); with K <= ncand <= kEqCap the exact top-K is among them
-    unsigned long long kguess;
-    unsigned long long *cand_key;
-    int *cand_row;
-    int ncand, kshift;
     int pad2_;
 };
 
@@ -186,8 +179,6 @@ struct rorbk_ctx {
     // mixed-precision dense dynamic Gram on the tensor cores: FP32 partial
     // tiles [gram_tiles][gram_splits][128][128]
     float *gram_part = nullptr;
-    unsigned long long *cand_key = nullptr;   // [kEqCap] top-K candidates of an iteration
-    int *cand_row = nullptr;
     int gram_tiles = 0, gram_splits = 0;
     int *csc_ptr = nullptr, *csc_row = nullptr;
     double *csc_val = nullptr;

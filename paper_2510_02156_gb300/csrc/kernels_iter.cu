@@ -130,27 +130,6 @@ __device__ __forceinline__ void inc_log(Ctl *ctl, int c, double v) {
     }
 }
 
-// Appends a top-K candidate (|r| key, row); entries past kEqCap only count.
-__device__ __forceinline__ void cand_push(Ctl *ctl, unsigned long long key, int row) {
-    const unsigned mask = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&ctl->ncand, __popc(mask));
-    base = __shfl_sync(mask, base, leader);
-    const int idx = base + __popc(mask & ((1u << lane) - 1u));
-    if (idx < kEqCap) {
-        ctl->cand_key[idx] = key;
-        ctl->cand_row[idx] = row;
-    }
-}
-
-// The guess for the next iteration: key divided by 2^shift (shift binades).
-__device__ __forceinline__ unsigned long long lower_key(unsigned long long key, int shift) {
-    const unsigned long long d = (unsigned long long)shift << 52;
-    return key > d ? key - d : 0ull;
-}
-
 // ------------------------------------------------------------------ begin
 // ||b||, x = x0 or 0, loop state.  One block; sets the WHILE condition.
 __global__ void k_begin(const double *__restrict__ b, int m, const double *__restrict__ x0,
@@ -181,9 +160,6 @@ __global__ void k_begin(const double *__restrict__ b, int m, const double *__res
         ctl->inc_count = 0;
         ctl->nlog = 0;
         ctl->log_full = 0;
-        ctl->kguess = ~0ull;       // no top-K candidates until a K-th key is known
-        ctl->kshift = 1;
-        ctl->ncand = 0;
         if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
     }
 }
@@ -496,7 +472,6 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
     const V *__restrict__ val = sell_values<V, T>(A);
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
-    const unsigned long long kg = finalize == 1 ? ctl->kguess : ~0ull;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     double rr = 0.0;
     __syncthreads();
@@ -550,9 +525,7 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
             const T ri = Ar<T>::sub(b[row], acc);
             r[row] = ri;
             rr = __fma_rn((double)ri, (double)ri, rr);
-            const unsigned long long key = abs_key(ri);
-            bin = (unsigned)(key >> 52);
-            if (key >= kg) cand_push(ctl, key, row);
+            bin = (unsigned)(abs_key(ri) >> 52);
         }
         if (finalize == 1) hist_add(hist, bin, act);
     }
@@ -731,7 +704,6 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
     __shared__ unsigned hist[kHistBins];
     __shared__ int is_last;
     if (check_done && (ctl->done || ctl->halt)) return;
-    if (check_done && ctl->ncand >= K && ctl->ncand <= kEqCap) return;   // k_topk_collect selects among them
     const unsigned sel1 = (unsigned)ctl->sel1;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
@@ -930,44 +902,6 @@ __global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, i
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ int is_last;
     if (check_done && (ctl->done || ctl->halt)) return;
-    const int nc = check_done ? ctl->ncand : 0;
-    if (nc >= K && nc <= kEqCap) {
-        // Every row whose key reaches the guess is a candidate and there are at
-        // least K of them, so the K-th largest key reaches the guess too: the
-        // top-K (|r| descending, ties to the lower row) is the first K of the
-        // candidates in that order.  One block selects and publishes it.
-        if (blockIdx.x != 0) return;
-        unsigned long long *skey = dsm_u64;
-        int *sidx = (int *)(skey + kEqCap);
-        int *sI = sidx + kEqCap;
-        const int np = next_pow2(nc);
-        for (int e = threadIdx.x; e < np; e += blockDim.x) {
-            if (e < nc) { skey[e] = ctl->cand_key[e]; sidx[e] = ctl->cand_row[e]; }
-            else { skey[e] = 0ull; sidx[e] = 0x7fffffff; }
-        }
-        __syncthreads();
-        block_bitonic_sort_desc(skey, sidx, np);
-        const unsigned long long kth = skey[K - 1];
-        for (int a = threadIdx.x; a < K; a += blockDim.x) sI[a] = sidx[a];
-        __syncthreads();
-        const int np2 = next_pow2(K);                 // I ascending
-        for (int a = threadIdx.x; a < np2; a += blockDim.x)
-            skey[a] = a < K ? (unsigned long long)(unsigned)sI[a] : ~0ull;
-        __syncthreads();
-        block_bitonic_sort(skey, np2);
-        for (int a = threadIdx.x; a < K; a += blockDim.x) sI[a] = (int)skey[a];
-        __syncthreads();
-        publish_rows(rowptr, sI, K, D, ctl, 1);
-        if (threadIdx.x == 0) {
-            int sh = ctl->kshift;                     // keep the count well inside [K, kEqCap]
-            if (nc > kEqCap / 2 && sh > 0) --sh;
-            else if (nc < 2 * K && sh < 8) ++sh;
-            ctl->kshift = sh;
-            ctl->kguess = lower_key(kth, sh);
-            ctl->ncand = 0;
-        }
-        return;
-    }
     const unsigned long long P = (unsigned long long)(unsigned)ctl->prefix;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         unsigned long long pre = abs_key(r[i]) >> 41;
@@ -989,17 +923,7 @@ __global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, i
     int *sI = sidx + kEqCap;
     finalize_topk<T>(r, m, K, in_list, eq_list, ctl, sI, skey, sidx);
     publish_rows(rowptr, sI, K, D, ctl, 1);
-    if (threadIdx.x == 0) {
-        ctl->ticket = 0;
-        if (check_done) {                             // the next iteration's guess
-            int sh = ctl->kshift;
-            if (nc < K && sh < 8) ++sh;
-            else if (nc > kEqCap && sh > 0) --sh;
-            ctl->kshift = sh;
-            ctl->kguess = lower_key(P << 41, sh);
-            ctl->ncand = 0;
-        }
-    }
+    if (threadIdx.x == 0) ctl->ticket = 0;
 }
 
 // Single-step API: a given ascending I.
@@ -2267,11 +2191,6 @@ __global__ void __launch_bounds__(256) k_inner_prep(const double *__restrict__ r
         in->log_cap = out->log_cap;
         in->log_col = out->log_col;
         in->log_val = out->log_val;
-        in->kguess = ~0ull;
-        in->kshift = 1;
-        in->ncand = 0;
-        in->cand_key = out->cand_key;
-        in->cand_row = out->cand_row;
         if (use_cond) cudaGraphSetConditional(hcond, in->halt ? 0u : 1u);
     }
 }

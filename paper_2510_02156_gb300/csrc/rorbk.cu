@@ -240,8 +240,6 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
     h->hist1 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
     h->hist2 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
     h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
-    h->cand_key = (unsigned long long *)dev_alloc(h, kEqCap * sizeof(unsigned long long));
-    h->cand_row = (int *)dev_alloc(h, kEqCap * sizeof(int));
     h->eq_list = (int *)dev_alloc(h, kEqCap * sizeof(int));
     h->ctl = (Ctl *)dev_alloc(h, sizeof(Ctl));
     h->ctl_in = (Ctl *)dev_alloc(h, sizeof(Ctl));
@@ -295,7 +293,6 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         }
     }
     if (!h->r || !h->xb || !h->bb || !h->partials || !h->sd_scratch || !h->wgt || !h->wcdf ||
-        !h->cand_key || !h->cand_row ||
         !h->hist1 || !h->hist2 || !h->in_list ||
         !h->eq_list || !h->ctl || !h->ctl_in)
         return fail(h, RORBK_ERR_OOM, "workspace");
@@ -547,8 +544,6 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
     c.log_cap = inc ? h->ilog_cap : 0;
     c.log_col = inc ? h->ilog_col : nullptr;
     c.log_val = inc ? h->ilog_val : nullptr;
-    c.cand_key = h->cand_key;
-    c.cand_row = h->cand_row;
     if (opt.trace && !mixed) {
         c.trace_cap = opt.trace->capacity;
         c.tr_tau = (long long *)opt.trace->tau;
