@@ -1371,65 +1371,16 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
 
 // Gathers the nonzeros of A_I (row order), marks each column's lowest entry
 // and entry count, forms ||A_i||^2 + mu; the last block factors.
-// End of an iteration: trace x, advance, loop condition (one block).
-template <typename T>
-__device__ void end_iteration(const T *x, int n, Ctl *ctl, int use_cond,
-                              cudaGraphConditionalHandle hcond) {
-    if (ctl->tr_x && ctl->iter < ctl->trace_cap && sizeof(T) == sizeof(double))
-        for (int c = threadIdx.x; c < n; c += blockDim.x)
-            ctl->tr_x[ctl->iter * (long long)n + c] = (double)x[c];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (!ctl->halt) {
-            const long long it = ctl->iter + 1;
-            ctl->iter = it;
-            if (ctl->done || ctl->status != 0 || it >= ctl->maxit) ctl->halt = 1;
-        }
-        if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
-    }
-}
-
-// x += A_I^T y over the gathered entries with the threads of one block (the
-// arithmetic of k_dyn_scatter): a column used by one row of I takes its single
-// product; a shared column is summed over its rows in ascending order by the
-// entry that owns it.
-template <typename T>
-__device__ void dyn_scatter_block(T *x, Dyn D, Ctl *ctl) {
-    const int E = ctl->dynE, nsh = ctl->dyn_nsh;
-    const unsigned ep = *D.epoch;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const int c = D.ecol[e];
-        if (D.shared[c] != ep) {
-            x[c] = Ar<T>::add(x[c], Ar<T>::fma(as<T>(D.eval[e]), as<T>(D.y[D.erow[e]]), T(0)));
-        } else if ((unsigned)D.skeys[D.segpos[c]] == (unsigned)e) {
-            T acc = T(0);
-            for (int u = D.segpos[c]; u < nsh && (int)(D.skeys[u] >> 32) == c; ++u) {
-                const unsigned e2 = (unsigned)D.skeys[u];
-                acc = Ar<T>::fma(as<T>(D.eval[e2]), as<T>(D.y[D.erow[e2]]), acc);
-            }
-            x[c] = Ar<T>::add(x[c], acc);
-        }
-    }
-    __syncthreads();
-}
-
 template <typename T>
 __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict__ r, Dyn D,
-                                                  Ctl *ctl, int check_done, T *x, int fuse,
-                                                  int use_cond, cudaGraphConditionalHandle hcond) {
+                                                  Ctl *ctl, int check_done) {
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ int is_last;
-    // fuse: the last block also applies x += A_I^T y and ends the iteration
-    // (k_dyn_scatter's work; one launch fewer per iteration)
-    if (check_done && (ctl->done || ctl->halt)) {
-        if (fuse && blockIdx.x == 0) end_iteration<T>(x, A.n, ctl, use_cond, hcond);
-        return;
-    }
+    if (check_done && (ctl->done || ctl->halt)) return;
     const int K = A.K;
     const int E = ctl->dynE;
     if (E > D.ecap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&ctl->status, kDevBounds);
-        if (fuse && blockIdx.x == 0) end_iteration<T>(x, A.n, ctl, use_cond, hcond);
         return;
     }
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
@@ -1488,10 +1439,23 @@ __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict_
     __threadfence();
     dyn_factor<T>(r, K, D, ctl, dsm_u64);
     if (threadIdx.x == 0) ctl->ticket = 0;
-    if (fuse) {
-        __syncthreads();
-        if (!ctl->status) dyn_scatter_block<T>(x, D, ctl);
-        end_iteration<T>(x, A.n, ctl, use_cond, hcond);
+}
+
+// End of an iteration: trace x, advance, loop condition (one block).
+template <typename T>
+__device__ void end_iteration(const T *x, int n, Ctl *ctl, int use_cond,
+                              cudaGraphConditionalHandle hcond) {
+    if (ctl->tr_x && ctl->iter < ctl->trace_cap && sizeof(T) == sizeof(double))
+        for (int c = threadIdx.x; c < n; c += blockDim.x)
+            ctl->tr_x[ctl->iter * (long long)n + c] = (double)x[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!ctl->halt) {
+            const long long it = ctl->iter + 1;
+            ctl->iter = it;
+            if (ctl->done || ctl->status != 0 || it >= ctl->maxit) ctl->halt = 1;
+        }
+        if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
     }
 }
 
@@ -2386,13 +2350,10 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
         return;
     }
     Mat<T> A = make_mat<T>(h);
-    const int fuse = count_iter && !inc;
-    k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl, check_done, x,
-                                                                        fuse, use_cond,
-                                                                        (cudaGraphConditionalHandle)hcond);
-    if (!fuse)
-        (inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>)<<<2 * h->num_sms, 512, 0, h->stream>>>(
-            x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond, (cudaGraphConditionalHandle)hcond);
+    k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
+                                                                        check_done);
+    (inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>)<<<2 * h->num_sms, 512, 0, h->stream>>>(
+        x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond, (cudaGraphConditionalHandle)hcond);
 }
 
 template <typename T>
