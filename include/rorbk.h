@@ -12,12 +12,22 @@
  *       C(i,j) = |<Abar_i,Abar_j>| / (|Abar_i| |Abar_j|);
  *     - Pbar_t = exp(-2 sum_j C(t,j) / n),  P = Pbar / sum(Pbar);
  *     - for each block, W_t = (A_t A_t^T + mu I)^{-1}, formed once and stored
- *       (Section 3.1), here through a Cholesky factor L_t: W_t = L_t^-T L_t^-1.
+ *       (Section 3.1), here through a Cholesky factor L_t: W_t = L_t^-T L_t^-1;
+ *       a block with at least n rows stores V_t = (A_t^T A_t + mu I)^{-1}
+ *       instead (Lemma 1, Section 3.1).
  *   iteration j (Algorithm 1, the loop body)
- *     - 3 times: draw tau ~ P; x += A_tau^T W_tau (b_tau - A_tau x);
+ *     - 3 times: draw tau ~ P; x += A_tau^T W_tau (b_tau - A_tau x)
+ *       (or x += V_tau A_tau^T (b_tau - A_tau x));
  *     - r = b - A x; stop if ||r|| / ||b|| <= tol;
  *     - I = the floor(m/k) rows with the largest r_i^2;
- *       x += A_I^T (A_I A_I^T + mu I)^{-1} r_I   (Gram + Cholesky per call).
+ *       x += A_I^T (A_I A_I^T + mu I)^{-1} r_I   (Gram + Cholesky per call;
+ *       the n x n form when K >= n).
+ *
+ * Beside the method: a mixed-precision form (FP64 refinement around FP32
+ * ROR-BK), an incremental residual, residual-weighted draws, Algorithm 2's
+ * initial solution, Algorithm 3 (FAB-GMRES with ROR-BK inner solves), batched
+ * solves, the adjoint solve of a differentiable solve, single steps for
+ * testing, and a residual entry point that allocates no memory.
  *
  * All arithmetic runs in CUDA kernels compiled for sm_103a; nothing falls back
  * to the CPU.  Every call returns an rorbk_status; on failure
