@@ -1,0 +1,36 @@
+"""bench.py's roofline helpers (no GPU): the algorithmic bytes of one
+residual, and the DRAM traffic record, which is reported only for the
+captured workload and only while the kernel sources match the capture."""
+import os
+import shutil
+import types
+
+import bench
+
+
+def test_spmv_bytes_counts_values_indices_and_vectors_once():
+    s = types.SimpleNamespace(nnz=10, n=7, m=5)
+    # 10 entries x (4 B value + 4 B index) + x (7 x 4 B) + b and r (2 x 5 x 4 B)
+    assert bench.spmv_bytes(s, 4, 4) == 10 * 8 + 7 * 4 + 2 * 5 * 4
+    assert bench.spmv_bytes(s, 8, 8) == 10 * 12 + 7 * 8 + 2 * 5 * 8
+
+
+def test_traffic_record_matches_the_committed_kernels():
+    s = types.SimpleNamespace(m=1 << 20, n=1 << 20, nnz=9692830)
+    t32 = bench.profiled_traffic("k_residual<float,float>", s)
+    t64 = bench.profiled_traffic("k_residual<double,float>", s)
+    assert t32 is not None and t64 is not None
+    # within 10% of the algorithmic bytes: no re-reads
+    assert 1.0 <= t32 / bench.spmv_bytes(s, 4, 4) <= 1.1
+    assert 1.0 <= t64 / bench.spmv_bytes(s, 4, 8) <= 1.1
+
+
+def test_traffic_record_is_dropped_for_other_workloads_or_changed_sources(tmp_path, monkeypatch):
+    s = types.SimpleNamespace(m=1 << 20, nnz=9692830)
+    assert bench.profiled_traffic("k_residual<float,float>", types.SimpleNamespace(m=1 << 18, nnz=5)) is None
+    changed = tmp_path / "kernels_iter.cu"
+    shutil.copy(os.path.join(bench.ROOT, bench.KERNEL_SOURCES[0]), changed)
+    with open(changed, "a") as fh:
+        fh.write("\n// changed\n")
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(changed), bench.KERNEL_SOURCES[1]))
+    assert bench.profiled_traffic("k_residual<float,float>", s) is None
