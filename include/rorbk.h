@@ -59,7 +59,7 @@ typedef enum {
     RORBK_ERR_NOT_SPD = -4,       /* a block Gram lost positive definiteness (only reachable with lambda = 0) */
     RORBK_ERR_NUMERIC = -5,       /* NaN/Inf in A, b or the residual          */
     RORBK_ERR_BOUNDS = -6,        /* an index escaped its range on the device */
-    RORBK_ERR_UNSUPPORTED = -7,   /* a mode this build does not provide       */
+    RORBK_ERR_UNSUPPORTED = -7,   /* a mode the library does not provide      */
     RORBK_ERR_DEVICE_TIMEOUT = -8 /* a bounded device-side wait gave up; the
                                      kernel returned instead of hanging      */
 } rorbk_status;

@@ -6,7 +6,7 @@ one static update, the residual, the top-K set, one dynamic update, and the
 whole iteration (x after each of the first 100 iterations, the tau and I
 sequences, the final relative residual).  The FP64 path evaluates every
 quantity in the oracle's order without contraction, so the expected
-difference is zero; the tests assert the benchmark spec's bound (relative 1e-9 per
+difference is zero; the tests assert the parity bound (relative 1e-9 per
 iterate) and report the observed maximum.
 """
 import numpy as np
@@ -148,8 +148,8 @@ def _gpu_trace(h, s, iters, seed=0, x0=None, tol=0.0):
 
 
 def test_first_100_iterations_match_oracle(case):
-    """North star: iterates within relative 1e-9 over the first 100
-    iterations under the same Philox block sequence."""
+    """The iterates stay within relative 1e-9 of the oracle's over the first
+    100 iterations under the same Philox block sequence."""
     name, s, h = case
     iters = 100
     res, x, tau, rrn, I, X = _gpu_trace(h, s, iters, seed=7)
