@@ -604,3 +604,56 @@ def test_tall_consistent_system_solved_by_one_full_rank_block():
     sp = _tall_sparse()
     r2 = oracle.solve(sp, maxit=3000, tol=1e-12, seed=2)
     assert r2.status == 0 and r2.rrn <= 1e-12
+
+
+def test_woodbury_at_the_boundary_s_equals_n():
+    """s = n takes the n x n form (the rule is s >= n); the step is still the
+    ridge closed form."""
+    s = W.gaussian_dense(400, 80, seed=13, num_blocks=5, lam=1e-4)    # blocks of exactly 80 rows
+    off = oracle.partition(s.m, 5)
+    assert off[1] - off[0] == s.n
+    rng = np.random.default_rng(14)
+    x = rng.standard_normal(s.n)
+    b = s.b + 0.05 * rng.standard_normal(s.m)
+    V = oracle.column_operator(s, 5, 0, 1e-4)
+    rows = np.arange(off[0], off[1])
+    x_w = oracle.update_woodbury(s, rows, V, b, x)
+    assert np.linalg.norm(x_w - _ridge(s.dense[rows], b[rows], x, 1e-4)) <= 1e-9 * np.linalg.norm(x_w)
+
+
+def test_woodbury_sparse_and_dense_storage_give_the_same_bits():
+    """Unstored entries count as zero in the column sums: the same tall block
+    held as CSR and as a dense array gives the same V and the same update,
+    bit for bit, and the same solve."""
+    sp_sys = _tall_sparse()
+    A = sp_sys.to_dense()
+    de_sys = W.System("tall_dense", sp_sys.m, sp_sys.n, dense=A, b=sp_sys.b, x_true=sp_sys.x_true,
+                      num_blocks=sp_sys.num_blocks, lam=sp_sys.lam, tol=sp_sys.tol)
+    k = sp_sys.num_blocks
+    off = oracle.partition(sp_sys.m, k)
+    rows = np.arange(off[2], off[3])
+    Vs = oracle.column_operator(sp_sys, k, 2, sp_sys.lam)
+    Vd = oracle.column_operator(de_sys, k, 2, sp_sys.lam)
+    np.testing.assert_array_equal(Vs, Vd)
+    x0 = np.random.default_rng(15).standard_normal(sp_sys.n)
+    np.testing.assert_array_equal(oracle.update_woodbury(sp_sys, rows, Vs, sp_sys.b, x0),
+                                  oracle.update_woodbury(de_sys, rows, Vd, sp_sys.b, x0))
+    r1 = oracle.solve(sp_sys, maxit=30, tol=0.0, seed=4)
+    r2 = oracle.solve(de_sys, maxit=30, tol=0.0, seed=4)
+    np.testing.assert_array_equal(r1.x, r2.x)
+
+
+def test_woodbury_with_mu_zero_is_the_block_least_squares_solution():
+    """mu = 0 and a full-column-rank tall block: x + (A_B^T A_B)^{-1} A_B^T
+    (b_B - A_B x) is the block's least-squares solution, whatever x was."""
+    s = W.gaussian_dense(600, 50, seed=16, num_blocks=4, lam=0.0)
+    off = oracle.partition(s.m, 4)
+    rows = np.arange(off[1], off[2])
+    rng = np.random.default_rng(17)
+    b = s.b + 0.1 * rng.standard_normal(s.m)
+    V = oracle.column_operator(s, 4, 1, 0.0)
+    x_ls = np.linalg.lstsq(s.dense[rows], b[rows], rcond=None)[0]
+    for _ in range(2):
+        x = rng.standard_normal(s.n)
+        x_w = oracle.update_woodbury(s, rows, V, b, x)
+        assert np.linalg.norm(x_w - x_ls) <= 1e-10 * np.linalg.norm(x_ls)
