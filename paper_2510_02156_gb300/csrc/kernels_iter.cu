@@ -458,8 +458,9 @@ __device__ __forceinline__ void hist_add(unsigned *hist, unsigned bin, bool acti
 // column order.  Longest slices come first.  V is the stored value type (an
 // FP32-stored system is read as FP32 and widened exactly).
 // finalize: 1 = convergence test + first radix level (iteration), 2 = ||r||^2
-// only (single-step API).
-template <typename T, typename V>
+// only (single-step API).  DN: A is dense, so entry j of a row is in column j
+// and the column indices are not read (x_j is the same for the warp's lanes).
+template <typename T, typename V, bool DN = false>
 __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restrict__ b,
                                                   const T *__restrict__ x, T *__restrict__ r,
                                                   double *partials, unsigned *hist1, Ctl *ctl,
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
         for (int u = 0; u < 8; ++u) {
             const bool in = u < len;
             const long long d = base + 32LL * u;
-            cn[u] = in ? A.scol[d] : 0;
+            cn[u] = in ? (DN ? u : A.scol[d]) : 0;
             vn[u] = in ? val[d] : V(0);
         }
         for (int c0 = 0; c0 < L; c0 += 8) {
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
                 const int j = c0 + 8 + u;
                 const bool in = j < len;
                 const long long d = base + 32LL * j;
-                cn[u] = in ? A.scol[d] : 0;
+                cn[u] = in ? (DN ? j : A.scol[d]) : 0;
                 vn[u] = in ? val[d] : V(0);
             }
 #pragma unroll
@@ -2363,6 +2364,19 @@ const double *csc_values<double>(const rorbk_ctx *h) { return h->csc_val; }
 template <>
 const float *csc_values<float>(const rorbk_ctx *h) { return h->csc_val32; }
 
+// The residual kernel for this handle's format (the dense instance reads no
+// column indices).
+template <typename T, typename V>
+static void residual_launch(rorbk_ctx *h, const Mat<T> &A, const T *b, const T *x, T *r, Ctl *ctl,
+                            int finalize) {
+    if (h->format == RORBK_FORMAT_DENSE)
+        k_residual<T, V, true><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl,
+                                                                   finalize);
+    else
+        k_residual<T, V, false><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl,
+                                                                    finalize);
+}
+
 template <typename T>
 void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_cond,
                         unsigned long long hcond, int weighted = 0, int inc = 0) {
@@ -2396,12 +2410,12 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
                                                                          h->hist1, ctl);
     }
     if constexpr (sizeof(T) == sizeof(float)) {
-        k_residual<T, float><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
+        residual_launch<T, float>(h, A, b, x, r, ctl, 1);
     } else {
         if (h->vdtype == RORBK_F32)
-            k_residual<T, float><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
+            residual_launch<T, float>(h, A, b, x, r, ctl, 1);
         else
-            k_residual<T, double><<<h->grid_res, 256, 0, h->stream>>>(A, b, x, r, h->partials, h->hist1, ctl, 1);
+            residual_launch<T, double>(h, A, b, x, r, ctl, 1);
     }
     if constexpr (sizeof(T) == sizeof(double))
         if (weighted) launch_weights(h, r);      // the draws of the next iteration
@@ -2426,11 +2440,9 @@ void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int u
 void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner) {
     Mat<double> A = make_mat<double>(h);
     if (h->vdtype == RORBK_F32)
-        k_residual<double, float><<<h->grid_res, 256, 0, h->stream>>>(A, h->bb, h->xb, h->r, h->partials,
-                                                                      h->hist1, h->ctl, 3);
+        residual_launch<double, float>(h, A, h->bb, h->xb, h->r, h->ctl, 3);
     else
-        k_residual<double, double><<<h->grid_res, 256, 0, h->stream>>>(A, h->bb, h->xb, h->r, h->partials,
-                                                                       h->hist1, h->ctl, 3);
+        residual_launch<double, double>(h, A, h->bb, h->xb, h->r, h->ctl, 3);
     const int g = grid_stream(h, (int)std::max(h->m, h->n));
     k_inner_prep<<<g, 256, 0, h->stream>>>(h->r, (int)h->m, h->b32, h->d32, (int)h->n, h->partials,
                                            h->ctl, h->ctl_in, use_cond,
@@ -2455,16 +2467,13 @@ void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x) {
 
 void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r) {
     if (h->vdtype == RORBK_F32)
-        k_residual<double, float><<<h->grid_res, 256, 0, h->stream>>>(make_mat<double>(h), b, x, r,
-                                                                      h->partials, h->hist1, h->ctl, 2);
+        residual_launch<double, float>(h, make_mat<double>(h), b, x, r, h->ctl, 2);
     else
-        k_residual<double, double><<<h->grid_res, 256, 0, h->stream>>>(make_mat<double>(h), b, x, r,
-                                                                       h->partials, h->hist1, h->ctl, 2);
+        residual_launch<double, double>(h, make_mat<double>(h), b, x, r, h->ctl, 2);
 }
 
 void launch_residual32_only(rorbk_ctx *h, const float *b, const float *x, float *r) {
-    k_residual<float, float><<<h->grid_res, 256, 0, h->stream>>>(make_mat<float>(h), b, x, r, h->partials,
-                                                                 h->hist1, h->ctl, 2);
+    residual_launch<float, float>(h, make_mat<float>(h), b, x, r, h->ctl, 2);
 }
 
 void launch_topk_only(rorbk_ctx *h, const double *r, int *I) {
