@@ -79,6 +79,11 @@ def parse():
     p.add_argument("--profile", type=int, default=0,
                    help="profiling run: N iterations of each form, the loop driven from the "
                         "host (so that a profiler sees every kernel); prints no JSON")
+    p.add_argument("--profile-dense", choices=("fp64", "mixed"), default=None,
+                   help="profiling run of the dense path: two host-driven iterations on a "
+                        "25,600 x 2,048 Gaussian system with 100 blocks of 256 rows (the K, s "
+                        "and n of the 200,000 x 2,048 workload) in the given precision; "
+                        "prints no JSON")
     p.add_argument("--cache", default=os.path.join(ROOT, ".cache"))
     return p.parse_args()
 
@@ -191,26 +196,42 @@ def spmv_bytes(s, vbytes, xbytes):
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic_k_residual_powerlaw_n1048576.txt")
 KERNEL_SOURCES = ("paper_2510_02156_gb300/csrc/kernels_iter.cu", "paper_2510_02156_gb300/csrc/common.cuh")
+# the residual kernel's part of the first source: from its section marker to
+# the next kernel's comment (the kernel and the helpers it calls)
+RESIDUAL_REGION = ("// ---------------------------------------------------------------- residual",
+                   "// Incremental residual, first kernel")
+
+
+def residual_sources_sha256():
+    """sha256 of the residual kernel's source region of kernels_iter.cu and
+    of common.cuh: the code the traffic record was captured from."""
+    import hashlib
+    h = hashlib.sha256()
+    for i, f in enumerate(KERNEL_SOURCES):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            data = fh.read()
+        if i == 0:
+            a = data.find(RESIDUAL_REGION[0].encode())
+            z = data.find(RESIDUAL_REGION[1].encode())
+            data = data[a:z] if 0 <= a < z else data
+        h.update(data)
+    return h.hexdigest()
 
 
 def profiled_traffic(kernel, s):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or
-    None when the workload differs from the captured one or the kernel sources
-    changed since the capture."""
-    import hashlib
+    None when the workload differs from the captured one or the kernel's
+    source changed since the capture."""
     if (s.m, s.nnz) != (1 << 20, 9692830) or not os.path.exists(TRAFFIC_FILE):
         return None
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    digest = residual_sources_sha256()
     rec = {}
     with open(TRAFFIC_FILE) as fh:
         for ln in fh:
             if ln.strip() and not ln.startswith("#"):
                 k, v = ln.split()
                 rec[k] = v
-    if rec.get("sources_sha256") != h.hexdigest() or kernel not in rec:
+    if rec.get("sources_sha256") != digest or kernel not in rec:
         return None
     return int(rec[kernel])
 
@@ -718,11 +739,28 @@ def run_profile(args):
     h.close()
 
 
+def run_profile_dense(args):
+    import torch
+    from paper_2510_02156_gb300 import binding as B
+    from paper_2510_02156_gb300 import workloads as W
+    prec = B.PREC_MIXED if args.profile_dense == "mixed" else B.PREC_FP64
+    s = W.gaussian_dense(25_600, 2048, seed=8, num_blocks=100, lam=2.56e-4)
+    with B.Handle.from_system(s, precision=prec) as h:
+        b = torch.as_tensor(s.b, device="cuda")
+        x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        res = h.solve(b, x, tol=0.0, maxit=2, seed=1, precision=prec, host_loop=1)
+        torch.cuda.synchronize()
+    print(f"dense profile run ({args.profile_dense}): {res.iters} iterations, rrn {res.rrn:.4e}")
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.profile:
         run_profile(args)
+        return
+    if args.profile_dense:
+        run_profile_dense(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world, local)

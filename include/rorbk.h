@@ -164,8 +164,21 @@ typedef struct {
     int32_t residual_mode;  /* RORBK_RESIDUAL_*: how r = b - A x is formed   (EXACT) */
     int32_t refresh;        /* INCREMENTAL: an exact residual every `refresh`
                                iterations (0: 50)                          (0)    */
-    int32_t reserved_;
+    int32_t fault_inject;   /* RORBK_FAULT_*: host-chosen failure injection for
+                               tests of the failure paths              (NONE) */
 } rorbk_options;
+
+/* Failure injection (rorbk_options.fault_inject); nothing faults, traps or
+ * hangs the GPU.
+ *   NONE       : normal operation.
+ *   WAIT_LIMIT : the first bounded wait of each sampled update whose block was
+ *                staged by asynchronous copies waits, with a limit of one
+ *                poll, on a barrier that nothing completes, so the wait gives
+ *                up the way a copy that never lands would make it: the kernel
+ *                records RORBK_ERR_DEVICE_TIMEOUT, waits (bounded) for the
+ *                copies it did issue, and returns; the solve ends with that
+ *                status and the handle stays usable. */
+enum { RORBK_FAULT_NONE = 0, RORBK_FAULT_WAIT_LIMIT = 1 };
 
 /* How the full residual of each iteration is formed (rorbk_options.residual_mode).
  *   EXACT       : r = b - A x over all of A (Algorithm 1).
@@ -312,9 +325,21 @@ rorbk_status rorbk_topk(rorbk_handle h, const double *r, int32_t *I);
 
 /* Dynamic update for the ascending row set I[K] (device) with the residual r
  * (device, m doubles, read at I): x += A_I^T (A_I A_I^T + mu I)^{-1} r_I, or,
- * when K >= n, x += (A_I^T A_I + mu I)^{-1} A_I^T r_I (Lemma 1). */
+ * when K >= n, x += (A_I^T A_I + mu I)^{-1} A_I^T r_I (Lemma 1).  The kernel
+ * checks I before any row is read: an entry outside [0, m) or a set that is
+ * not strictly ascending leaves x unchanged and returns RORBK_ERR_BOUNDS. */
 rorbk_status rorbk_dynamic_update(rorbk_handle h, const int32_t *I,
                                   const double *r, double *x);
+
+/* The residual-weighted running sum (RORBK_DIST_RESIDUAL_WEIGHTED) that the
+ * draws after the residual r (device, m doubles) use: w_t = Pbar_t * rho_t,
+ * rho_t = sum of r_i^2 over block t's rows (one fused chain, rows ascending),
+ * and its running sum formed as the solve forms it (chunks of 64 blocks, each
+ * from zero, then the chunk totals in order); cdf_host receives k doubles.
+ * The result differs from the sequential running sum by rounding only (at
+ * most a few units in the last place of cdf[k-1] per 64 blocks).  Not in the
+ * paper, whose proposal is static. */
+rorbk_status rorbk_weighted_cdf(rorbk_handle h, const double *r, double *cdf_host);
 
 /* The dynamic block's Gram G = A_I A_I^T + mu I for the ascending row set I[K]
  * (device int32) of a DENSE handle, written packed lower (row-major: entry
@@ -451,11 +476,14 @@ rorbk_status rorbk_value_grad(rorbk_handle h, const double *g, const double *x, 
  * (the arithmetic of rorbk_residual), the sum of squares a fixed tree.
  * The scratch (about 512 KiB) is held by every GPU that loads the library
  * until the process exits.  All calls on a device share it and it keeps the
- * last call's contents: the kernel resets the counter it consumes, so calls
- * ordered on one stream are independent, but calls that overlap on the GPU
- * race and give wrong results.  The first call on a device looks up the
- * scratch's device address (once per device, with that device current);
- * make that first call before any stream capture begins.
+ * last call's contents: each call clears the completion counter on its stream
+ * before its kernel starts (a 4-byte cudaMemsetAsync, not an allocation), so
+ * calls ordered on one stream are independent, even after a call whose kernel
+ * never finished; calls that overlap on the GPU race and give wrong results.
+ * The first call on a device looks up the scratch's device address (once per
+ * device, with that device current) and keeps it for the process: make that
+ * first call before any stream capture begins, and do not use the entry point
+ * after cudaDeviceReset (the kept address belongs to the reset context).
  * Errors: RORBK_ERR_INVALID_ARG (message in rorbk_last_error(NULL)),
  * RORBK_ERR_CUDA. */
 rorbk_status rorbk_csr_residual_noalloc(int64_t m, int64_t n, int64_t nnz,

@@ -13,5 +13,5 @@ from .oracle import (  # noqa: F401
     proposal, sample, residual, topk, block_gram, cholesky, chol_solve,
     spd_inverse, static_operator, update_with_inverse, update_with_cholesky,
     solve, SolveResult, initial_solution, fabgmres, block_norms, weighted_cdf, PAPER, RESIDUAL_WEIGHTED,
-    column_gram, column_operator, update_woodbury, update_woodbury_cholesky,
+    column_gram, column_operator, update_woodbury, update_woodbury_cholesky, thread_count,
 )

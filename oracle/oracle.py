@@ -24,11 +24,11 @@ ORC_OK, ORC_NOT_CONVERGED = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, -O2, no fast-math)."""
+    """Compile the oracle with gcc (plain C11 with POSIX threads, -O2, no fast-math)."""
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         os.makedirs(os.path.dirname(_OUT), exist_ok=True)
         tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
                                "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
@@ -67,8 +67,9 @@ def lib():
                 "orc_update_with_inverse": (None, [_P, _P, _I64, _P, _P, _P, _P, _P]),
                 "orc_update_with_cholesky": (C.c_int, [_P, _P, _I64, _D, _P, _P, _P]),
                 "orc_solve": (C.c_int, [_P, _I64, _D, _P, _P, _P, _D, _I64,
-                                        C.c_uint64, C.c_uint64, _I64, _I64, C.c_int,
+                                        C.c_uint64, C.c_uint64, _I64, _I64, C.c_int, _P,
                                         _P, _P, _P, _P, _P, _P]),
+                "orc_thread_count": (C.c_int, [_I64]),
                 "orc_block_norms": (None, [_P, _P, _I64, _P]),
                 "orc_initial_solution": (C.c_int, [_P, _I64, _I64, _P, _P]),
                 "orc_fabgmres": (C.c_int, [_P, _I64, _D, _P, _P, _P, _D, _I64, _D, _I64,
@@ -310,11 +311,12 @@ PAPER, RESIDUAL_WEIGHTED = 0, 1
 
 def solve(system, b=None, x0=None, *, k=None, mu=None, tol=None, maxit=100,
           seed=0, sysid=0, n_static=3, start_iter=0, trace_tau=False,
-          trace_rrn=False, trace_I=False, trace_x=False, dist_mode=PAPER):
+          trace_rrn=False, trace_I=False, trace_x=False, dist_mode=PAPER, force_tau=None):
     """Algorithm 1 on one right-hand side.  ``system`` is a workloads.System
     (or its prepared matrix); b defaults to system.b.  dist_mode=RESIDUAL_WEIGHTED
     draws the static blocks with weights Pbar_t * ||r_{B_t}||^2 from the
-    previous iteration's residual (not in the paper)."""
+    previous iteration's residual (not in the paper).  force_tau (iterations x
+    n_static, -1 = draw) replays given blocks in place of the draws."""
     M = _mat(system)
     k = system.num_blocks if k is None else k
     mu = system.lam if mu is None else mu
@@ -327,12 +329,17 @@ def solve(system, b=None, x0=None, *, k=None, mu=None, tol=None, maxit=100,
     tr_rrn = np.full(maxit, np.nan) if trace_rrn else None
     tr_I = np.full(maxit * K, -1, dtype=np.int64) if trace_I else None
     tr_x = np.zeros(maxit * M.n) if trace_x else None
+    ft = None
+    if force_tau is not None:
+        ft = np.full(maxit * n_static, -1, dtype=np.int64)
+        given = np.ascontiguousarray(force_tau, dtype=np.int64).ravel()[: ft.size]
+        ft[: given.size] = given
     iters = C.c_int64(0)
     rrn = C.c_double(0.0)
     st = lib().orc_solve(M.ref, k, mu, _ptr(b), _ptr(x0), _ptr(x), tol, maxit,
                          C.c_uint64(seed), C.c_uint64(sysid), n_static, start_iter,
-                         int(dist_mode), C.byref(iters), C.byref(rrn), _ptr(tr_tau), _ptr(tr_rrn),
-                         _ptr(tr_I), _ptr(tr_x))
+                         int(dist_mode), _ptr(ft), C.byref(iters), C.byref(rrn), _ptr(tr_tau),
+                         _ptr(tr_rrn), _ptr(tr_I), _ptr(tr_x))
     if st < 0:
         raise RuntimeError(f"oracle solve failed with status {st}")
     it = iters.value
@@ -386,12 +393,17 @@ def block_norms(r, off):
 
 
 def weighted_cdf(Pbar, rho):
-    """Running sum of Pbar_t * rho_t in 64-block chunks; returns the cdf."""
+    """Running sum cdf_t = sum_{i <= t} Pbar_i * rho_i in block order."""
     Pbar = np.ascontiguousarray(Pbar, dtype=np.float64)
     rho = np.ascontiguousarray(rho, dtype=np.float64)
     cdf = np.zeros(Pbar.size)
     lib().orc_weighted_cdf(_ptr(Pbar), _ptr(rho), Pbar.size, _ptr(cdf))
     return cdf
+
+
+def thread_count(rows):
+    """Host threads the oracle's residual and top-K use for ``rows`` rows."""
+    return int(lib().orc_thread_count(int(rows)))
 
 
 def prepare(system):

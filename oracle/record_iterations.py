@@ -1,12 +1,15 @@
 """Record how many iterations the FP64 oracle needs to reach the tolerance on
 the benchmark workload (the 2^20-row power-law system, 4096 blocks,
-lambda = 1e-8, tol = 1e-8, x0 = 0, seed 1).  Calls only the oracle; the
-result is written to iterations_to_tol.json beside this file and is used by
-the benchmark's reference arm to scale its bounded per-iteration sample.
+lambda = 1e-8, tol = 1e-8, x0 = 0, seed 1), and the solution it reaches.
+Calls only the oracle; the count is written to iterations_to_tol.json beside
+this file (the benchmark's reference arm scales its bounded per-iteration
+sample by it) and the solution to x_<key>.npy (the benchmark states the
+mixed-precision result's distance to it).
 
     python oracle/record_iterations.py [--n 1048576] [--blocks 4096]
 """
 import argparse
+import hashlib
 import json
 import os
 import sys
@@ -14,6 +17,8 @@ import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(HERE))
+
+import numpy as np  # noqa: E402
 
 import oracle  # noqa: E402
 from paper_2510_02156_gb300 import workloads as W  # noqa: E402
@@ -36,8 +41,11 @@ def main():
     path = os.path.join(HERE, "iterations_to_tol.json")
     d = json.load(open(path)) if os.path.exists(path) else {}
     d[key] = res.iters
+    xfile = f"x_{key}.npy"
+    np.save(os.path.join(HERE, xfile), res.x)
     d[key + "_meta"] = {"converged": bool(res.converged), "rrn": res.rrn,
-                        "oracle_seconds": dt, "cores": 1}
+                        "oracle_seconds": dt, "threads": oracle.thread_count(s.m),
+                        "x_file": xfile, "x_sha256": hashlib.sha256(res.x.tobytes()).hexdigest()}
     json.dump(d, open(path, "w"), indent=1, sort_keys=True)
     print(key, res.iters, res.converged, res.rrn, f"{dt:.0f}s")
 

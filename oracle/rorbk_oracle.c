@@ -52,10 +52,13 @@
  *   - y = W r sums over ascending columns of W;
  *   - norms are sequential sums of squares.
  */
+#define _GNU_SOURCE
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 /* ------------------------------------------------------------------------ */
 /* Matrix view: CSR (int64 row pointers, int32 columns, FP64 values) or dense
@@ -291,61 +294,152 @@ int64_t orc_sample(const double *cdf, int64_t k, uint64_t seed, uint64_t sysid,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Host threads.  The residual's rows and the top-K scan are split into
+ * contiguous row ranges over the host cores; each row's arithmetic and every
+ * result are the same as with one thread (rows are independent, the sum of
+ * squares stays one sequential chain, and the top-K set is unique).
+ * ORC_THREADS overrides the count; inputs under 65536 rows use one thread. */
+int orc_thread_count(int64_t rows)
+{
+    if (rows < 65536) return 1;
+    const char *e = getenv("ORC_THREADS");
+    long t = e ? atol(e) : sysconf(_SC_NPROCESSORS_ONLN);
+    if (t < 1) t = 1;
+    if (t > 256) t = 256;
+    return (int)t;
+}
+
+typedef struct {
+    const orc_matrix *A;
+    const double *b, *x;
+    double *r;
+    int64_t i0, i1;
+} residual_job;
+
+static void *residual_rows(void *arg)
+{
+    residual_job *j = (residual_job *)arg;
+    for (int64_t i = j->i0; i < j->i1; ++i) j->r[i] = j->b[i] - row_dot(j->A, i, j->x);
+    return NULL;
+}
+
 /* Algorithm 1: r = b - A x and ||r||^2 (sequential sum). */
 double orc_residual(const orc_matrix *A, const double *b, const double *x, double *r)
 {
-    double rr = 0.0;
-    for (int64_t i = 0; i < A->m; ++i) {
-        r[i] = b[i] - row_dot(A, i, x);
-        rr = fma(r[i], r[i], rr);
+    const int T = orc_thread_count(A->m);
+    residual_job jobs[256];
+    pthread_t th[256];
+    int started[256];
+    for (int t = 0; t < T; ++t) {
+        jobs[t].A = A; jobs[t].b = b; jobs[t].x = x; jobs[t].r = r;
+        jobs[t].i0 = A->m * t / T;
+        jobs[t].i1 = A->m * (t + 1) / T;
+        started[t] = t > 0 && pthread_create(&th[t], NULL, residual_rows, &jobs[t]) == 0;
     }
+    for (int t = 0; t < T; ++t)
+        if (!started[t]) residual_rows(&jobs[t]);
+    for (int t = 1; t < T; ++t)
+        if (started[t]) pthread_join(th[t], NULL);
+    double rr = 0.0;
+    for (int64_t i = 0; i < A->m; ++i) rr = fma(r[i], r[i], rr);
     return rr;
 }
 
 /* Algorithm 1 (residual-based dynamic aggregation): indices of the K largest
  * |r_i| (ties to the lower index), written in ascending order.  A bounded
- * min-heap keyed on (|r|, -index) keeps the current best K. */
+ * min-heap keyed on (|r|, -index) keeps the current best K.  With several
+ * threads each keeps the best K of its row range and the ranges' survivors
+ * are offered to one heap: the K best under this strict order are unique, so
+ * the set is the one-thread set. */
 static int heap_less(double ka, int64_t ia, double kb, int64_t ib)
 {   /* "a ranks below b": smaller key, or equal key and larger index */
     return ka < kb || (ka == kb && ia > ib);
 }
+
+typedef struct {
+    double *hk;
+    int64_t *hi;
+    int64_t size, K;
+} topk_heap;
+
+static void heap_offer(topk_heap *h, double key, int64_t i)
+{
+    double *hk = h->hk;
+    int64_t *hi = h->hi;
+    const int64_t K = h->K;
+    if (h->size < K) {
+        int64_t c = h->size++;
+        hk[c] = key; hi[c] = i;
+        while (c > 0) {
+            int64_t p = (c - 1) / 2;
+            if (heap_less(hk[c], hi[c], hk[p], hi[p])) {
+                double tk = hk[c]; hk[c] = hk[p]; hk[p] = tk;
+                int64_t ti = hi[c]; hi[c] = hi[p]; hi[p] = ti;
+                c = p;
+            } else break;
+        }
+    } else if (heap_less(hk[0], hi[0], key, i)) {
+        hk[0] = key; hi[0] = i;
+        int64_t c = 0;
+        for (;;) {
+            int64_t a = 2 * c + 1, b2 = a + 1, s = c;
+            if (a < K && heap_less(hk[a], hi[a], hk[s], hi[s])) s = a;
+            if (b2 < K && heap_less(hk[b2], hi[b2], hk[s], hi[s])) s = b2;
+            if (s == c) break;
+            double tk = hk[c]; hk[c] = hk[s]; hk[s] = tk;
+            int64_t ti = hi[c]; hi[c] = hi[s]; hi[s] = ti;
+            c = s;
+        }
+    }
+}
+
+typedef struct {
+    const double *r;
+    int64_t i0, i1;
+    topk_heap h;
+} topk_job;
+
+static void *topk_rows(void *arg)
+{
+    topk_job *j = (topk_job *)arg;
+    for (int64_t i = j->i0; i < j->i1; ++i) heap_offer(&j->h, fabs(j->r[i]), i);
+    return NULL;
+}
+
 int orc_topk(const double *r, int64_t m, int64_t K, int64_t *I)
 {
     if (K < 0 || K > m) return ORC_ERR_ARG;
     if (K == 0) return ORC_OK;
-    double *hk = (double *)malloc((size_t)K * sizeof(double));
-    int64_t *hi = (int64_t *)malloc((size_t)K * sizeof(int64_t));
+    const int T = orc_thread_count(m);
+    double *hk = (double *)malloc((size_t)(T + 1) * K * sizeof(double));
+    int64_t *hi = (int64_t *)malloc((size_t)(T + 1) * K * sizeof(int64_t));
     if (!hk || !hi) { free(hk); free(hi); return ORC_ERR_OOM; }
-    int64_t size = 0;
-    for (int64_t i = 0; i < m; ++i) {
-        double key = fabs(r[i]);
-        if (size < K) {
-            int64_t c = size++;
-            hk[c] = key; hi[c] = i;
-            while (c > 0) {
-                int64_t p = (c - 1) / 2;
-                if (heap_less(hk[c], hi[c], hk[p], hi[p])) {
-                    double tk = hk[c]; hk[c] = hk[p]; hk[p] = tk;
-                    int64_t ti = hi[c]; hi[c] = hi[p]; hi[p] = ti;
-                    c = p;
-                } else break;
-            }
-        } else if (heap_less(hk[0], hi[0], key, i)) {
-            hk[0] = key; hi[0] = i;
-            int64_t c = 0;
-            for (;;) {
-                int64_t a = 2 * c + 1, b2 = a + 1, s = c;
-                if (a < K && heap_less(hk[a], hi[a], hk[s], hi[s])) s = a;
-                if (b2 < K && heap_less(hk[b2], hi[b2], hk[s], hi[s])) s = b2;
-                if (s == c) break;
-                double tk = hk[c]; hk[c] = hk[s]; hk[s] = tk;
-                int64_t ti = hi[c]; hi[c] = hi[s]; hi[s] = ti;
-                c = s;
-            }
-        }
+    topk_job jobs[256];
+    pthread_t th[256];
+    int started[256];
+    for (int t = 0; t < T; ++t) {
+        jobs[t].r = r;
+        jobs[t].i0 = m * t / T;
+        jobs[t].i1 = m * (t + 1) / T;
+        jobs[t].h.hk = hk + (int64_t)(t + 1) * K;
+        jobs[t].h.hi = hi + (int64_t)(t + 1) * K;
+        jobs[t].h.size = 0;
+        jobs[t].h.K = K;
+        started[t] = T > 1 && t > 0 && pthread_create(&th[t], NULL, topk_rows, &jobs[t]) == 0;
+    }
+    for (int t = 0; t < T; ++t)
+        if (!started[t]) topk_rows(&jobs[t]);
+    for (int t = 1; t < T; ++t)
+        if (started[t]) pthread_join(th[t], NULL);
+    topk_heap best = {hk, hi, 0, K};
+    if (T == 1) {
+        best = jobs[0].h;
+    } else {
+        for (int t = 0; t < T; ++t)
+            for (int64_t a = 0; a < jobs[t].h.size; ++a) heap_offer(&best, jobs[t].h.hk[a], jobs[t].h.hi[a]);
     }
     /* ascending row order (insertion sort of K indices) */
-    for (int64_t a = 0; a < K; ++a) I[a] = hi[a];
+    for (int64_t a = 0; a < K; ++a) I[a] = best.hi[a];
     for (int64_t a = 1; a < K; ++a) {
         int64_t v = I[a], b2 = a - 1;
         while (b2 >= 0 && I[b2] > v) { I[b2 + 1] = I[b2]; --b2; }
@@ -703,12 +797,8 @@ int orc_initial_solution(const orc_matrix *A, int64_t first, int64_t count,
 /* The residual-weighted proposal (not in the paper: its P is static, Algorithm
  * 1's proposal).  Block t is drawn with weight w_t = Pbar_t * rho_t, where rho_t is
  * the squared norm of the residual on block t's rows: one fused chain over the
- * rows in ascending order.  The running sum of the weights is formed in chunks
- * of ORC_WCHUNK blocks: each chunk's running sum from zero, then the chunks'
- * totals summed in chunk order, and each entry offset by the total of the
- * chunks before it. */
-#define ORC_WCHUNK 64
-
+ * rows in ascending order.  The draws use the running sum of the weights,
+ * cdf_t = w_0 + ... + w_t, summed in block order as P's running sum is. */
 void orc_block_norms(const double *r, const int64_t *off, int64_t k, double *rho)
 {
     for (int64_t t = 0; t < k; ++t) {
@@ -721,17 +811,11 @@ void orc_block_norms(const double *r, const int64_t *off, int64_t k, double *rho
 /* Returns the total weight (cdf[k-1]). */
 double orc_weighted_cdf(const double *Pbar, const double *rho, int64_t k, double *cdf)
 {
-    int64_t nc = (k + ORC_WCHUNK - 1) / ORC_WCHUNK;
-    double off = 0.0;
-    for (int64_t c = 0; c < nc; ++c) {
-        int64_t t0 = c * ORC_WCHUNK, t1 = t0 + ORC_WCHUNK < k ? t0 + ORC_WCHUNK : k;
-        double s = 0.0;
-        for (int64_t t = t0; t < t1; ++t) {
-            s = s + Pbar[t] * rho[t];
-            cdf[t] = s;
-        }
-        for (int64_t t = t0; t < t1; ++t) cdf[t] = off + cdf[t];
-        off = off + s;
+    double s = 0.0;
+    for (int64_t t = 0; t < k; ++t) {
+        const double w = Pbar[t] * rho[t];
+        s = s + w;
+        cdf[t] = s;
     }
     return cdf[k - 1];
 }
@@ -739,7 +823,7 @@ double orc_weighted_cdf(const double *Pbar, const double *rho, int64_t k, double
 int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
               const double *x0, double *x, double tol, int64_t maxit,
               uint64_t seed, uint64_t sysid, int64_t n_static, int64_t start_iter,
-              int dist_mode,
+              int dist_mode, const int64_t *force_tau,
               int64_t *iters, double *rrn_out,
               int64_t *tr_tau, double *tr_rrn, int64_t *tr_I, double *tr_x)
 {
@@ -791,7 +875,10 @@ int orc_solve(const orc_matrix *A, int64_t k, double mu, const double *b,
     }
     for (int64_t j = 0; j < maxit; ++j) {
         for (int64_t l = 0; l < n_static; ++l) {
-            int64_t tau = orc_sample(dcdf, k, seed, sysid, start_iter + j, l);
+            int64_t tau = force_tau && force_tau[j * n_static + l] >= 0
+                              ? force_tau[j * n_static + l]
+                              : orc_sample(dcdf, k, seed, sysid, start_iter + j, l);
+            if (tau < 0 || tau >= k) { st = ORC_ERR_ARG; goto done; }
             if (tr_tau) tr_tau[j * n_static + l] = tau;
             int64_t s = off[tau + 1] - off[tau];
             const int wood = s >= n;        /* the n x n form (Lemma 1, Section 3.1) */
@@ -891,7 +978,7 @@ int orc_fabgmres(const orc_matrix *A, int64_t k, double mu, const double *b,
         double *vj = V + j * m, *zj = Z + j * n;
         int64_t it = 0;
         double rr = 0.0;
-        int e = orc_solve(A, k, mu, vj, NULL, zj, eta, lmax, seed, sysid, n_static, inner, 0,
+        int e = orc_solve(A, k, mu, vj, NULL, zj, eta, lmax, seed, sysid, n_static, inner, 0, NULL,
                           &it, &rr, NULL, NULL, NULL, NULL);
         if (e < 0) { st = e; goto done; }
         inner += it;

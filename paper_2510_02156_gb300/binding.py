@@ -25,6 +25,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 OK, NOT_CONVERGED = 0, 1
 DIST_PAPER, DIST_RESIDUAL_WEIGHTED = 0, 1
 RESIDUAL_EXACT, RESIDUAL_INCREMENTAL = 0, 1
+FAULT_NONE, FAULT_WAIT_LIMIT = 0, 1
 
 
 class RorbkError(RuntimeError):
@@ -54,7 +55,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("start_iter", C.c_int64), ("inner_tol", C.c_double),
                 ("inner_maxit", C.c_int64), ("host_loop", C.c_int32), ("poll", C.c_int32),
                 ("trace", C.c_void_p), ("stream", C.c_void_p), ("dist_mode", C.c_int32),
-                ("residual_mode", C.c_int32), ("refresh", C.c_int32), ("reserved_", C.c_int32)]
+                ("residual_mode", C.c_int32), ("refresh", C.c_int32), ("fault_inject", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -88,6 +89,7 @@ SIGNATURES = {
     "rorbk_topk": (C.c_int, [_P, _P, _P]),
     "rorbk_dynamic_update": (C.c_int, [_P, _P, _P, _P]),
     "rorbk_dense_gram": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "rorbk_weighted_cdf": (C.c_int, [_P, _P, _P]),
     "rorbk_initial_solution": (C.c_int, [_P, _I64, _P, _P]),
     "rorbk_fabgmres": (C.c_int, [_P, _P, _P, _P, _D, _I64, _D, _I64, _P, _P]),
     "rorbk_clone": (C.c_int, [_P, _P]),
@@ -282,14 +284,14 @@ class Handle:
     def solve(self, b, x, x0=None, tol=1e-8, maxit=1000, seed=0, system_id=0, n_static=3,
               start_iter=0, precision=PREC_FP64, trace=None, stream=None, inner_tol=1e-4,
               inner_maxit=2000000, host_loop=0, poll=64, dist_mode=DIST_PAPER,
-              residual_mode=RESIDUAL_EXACT, refresh=0):
+              residual_mode=RESIDUAL_EXACT, refresh=0, fault_inject=FAULT_NONE):
         """rorbk_solve on device tensors b (m), x (n), x0 (n or None)."""
         opt = default_options(seed=seed, system_id=system_id, n_static=n_static,
                               start_iter=start_iter, precision=precision,
                               stream=_stream_ptr(stream), inner_tol=inner_tol,
                               inner_maxit=inner_maxit, host_loop=host_loop, poll=poll,
                               dist_mode=dist_mode, residual_mode=residual_mode,
-                              refresh=refresh)
+                              refresh=refresh, fault_inject=fault_inject)
         if trace is not None:
             opt.trace = C.cast(C.pointer(trace), C.c_void_p)
         res = Result()
@@ -353,6 +355,13 @@ class Handle:
 
     def dynamic_update(self, I, r, x):
         _check(lib().rorbk_dynamic_update(self.h, _ptr(I), _ptr(r), _ptr(x)), self.h)
+
+    def weighted_cdf(self, r):
+        """rorbk_weighted_cdf: the residual-weighted running sum after the
+        device residual r (numpy array of k doubles)."""
+        cdf = np.zeros(self.info.num_blocks)
+        _check(lib().rorbk_weighted_cdf(self.h, _ptr(r), _ptr(cdf)), self.h)
+        return cdf
 
     def dense_gram(self, I, G, precision=PREC_FP64):
         """rorbk_dense_gram: packed lower A_I A_I^T + mu I into the device tensor G."""

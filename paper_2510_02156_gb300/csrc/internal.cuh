@@ -73,7 +73,7 @@ struct Ctl {
     int *log_col;          // [log_cap] changed columns
     double *log_val;       // [log_cap] their increments
     const double *scdf;    // the running sum the static draws use (P's, or the weighted one)
-    int pad2_;
+    int fault;             // RORBK_FAULT_* injected by the host (tests of the failure paths)
 };
 
 // Sparse operator of one static block t (Section 3.1's stored inverse
@@ -203,7 +203,7 @@ struct rorbk_ctx {
         unsigned *shared = nullptr, *epoch = nullptr;
         int *segpos = nullptr;
         unsigned long long *raw = nullptr, *skeys = nullptr, *pkeys = nullptr;
-        long long pcap = 0;
+        long long pcap = 0, skcap = 0;
         double *g = nullptr;
     } dyn;
     rorbk::Ctl *ctl = nullptr;

@@ -110,6 +110,43 @@ Mat<float> make_mat<float>(rorbk_ctx *h) {
                       h->sell.val32, h->wood_ptr, h->wood_ss32};
 }
 
+// -------------------------------------------------------- several columns
+// The kernels of the iteration also run one solve per right-hand side of a
+// block of nr columns (rorbk_multi_create): grid dimension y is the column,
+// each column has its own loop state (ctl + column) and dynamic-block
+// workspace (dyn_col), x and b are row-major n x nr and m x nr (entry c of
+// column j at c * ld + j), and the residual columns are stored one after the
+// other in the SELL copy's row order (position p holds row perm[p], -1 for a
+// padding lane).  One column (ld = 1, perm = nullptr) is the plain solve.
+struct Cols {
+    int ld;               // distance between consecutive entries of x and of b
+    long long rs;         // distance between the residual columns
+    int mpos;             // residual positions per column (m, or the SELL length)
+    const int *perm;      // SELL position -> row (nullptr: positions are rows)
+    const int *iperm;     // row -> SELL position
+    unsigned *grp;        // [0] column ticket of the group, [1] 1 while any column runs
+};
+static inline Cols one_col(int m) { return Cols{1, 0, m, nullptr, nullptr, nullptr}; }
+// MC (several columns) is a template flag of every kernel that takes Cols, so
+// the one-column instances compile without the column arithmetic.
+template <bool MC>
+__device__ __forceinline__ int rpos(const Cols &cl, int i) { return MC && cl.iperm ? cl.iperm[i] : i; }
+
+// Called once per column and launch by one thread, after that column's loop
+// state is final: the last column to arrive sets the WHILE condition to
+// "some column has not halted" and records it for a host-driven loop.
+__device__ void group_condition(const Ctl *ctl0, int nr, unsigned *grp, int use_cond,
+                                cudaGraphConditionalHandle hcond) {
+    __threadfence();
+    if (atomicAdd(&grp[0], 1u) != (unsigned)nr - 1u) return;
+    __threadfence();
+    int any = 0;
+    for (int j = 0; j < nr; ++j) any |= !((volatile const Ctl *)ctl0)[j].halt;
+    grp[1] = (unsigned)any;
+    grp[0] = 0u;
+    if (use_cond) cudaGraphSetConditional(hcond, any ? 1u : 0u);
+}
+
 // ---------------------------------------------------- incremental residual
 // Appends (c, v) for an update x_c += v to the iteration's change log.  The
 // calling lanes of a warp take consecutive slots from one atomic; entries past
@@ -145,13 +182,14 @@ __global__ void k_begin(const double *__restrict__ b, int m, const double *__res
     for (int c = threadIdx.x; c < n; c += blockDim.x)
         x[c] = (bn == 0.0 || x0 == nullptr || !ctl->has_x0) ? 0.0 : x0[c];
     if (threadIdx.x == 0) {
+        const bool finite = isfinite(bn);
         ctl->bnorm = bn;
         ctl->iter = 0;
         ctl->rr = 0.0;
         ctl->rrn = bn == 0.0 ? 0.0 : 1.0;
         ctl->done = bn == 0.0;
-        ctl->halt = !(bn > 0.0 && ctl->maxit > 0);
-        ctl->status = 0;
+        ctl->halt = !(finite && bn > 0.0 && ctl->maxit > 0);
+        ctl->status = finite ? 0 : kDevNumeric;      // NaN or Inf in b
         ctl->ticket = 0;
         ctl->n_in = 0;
         ctl->n_eq = 0;
@@ -238,7 +276,7 @@ template <typename T>
 __device__ __forceinline__ void static_update_wood(int n, int ns, const int *bt_seg, const int *bt_col,
                                                 const uint16_t *bt_row, const T *bt_val, const T *V,
                                                 int p0, int pend, const T *rloc, T *y, T *x, Ctl *ctl,
-                                                bool lg) {
+                                                bool lg, int ld) {
     const int a = threadIdx.x;
     for (int c = a; c < n; c += blockDim.x) y[c] = T(0);
     __syncthreads();
@@ -254,7 +292,7 @@ __device__ __forceinline__ void static_update_wood(int n, int ns, const int *bt_
         const T *Vr = V + (long long)c * n;
         T acc4 = T(0);
         for (int d = 0; d < n; ++d) acc4 = Ar<T>::fma(Vr[d], y[d], acc4);
-        x[c] = Ar<T>::add(x[c], acc4);
+        x[(long long)c * ld] = Ar<T>::add(x[(long long)c * ld], acc4);
         if (lg) inc_log(ctl, c, (double)acc4);
     }
     __syncthreads();
@@ -263,16 +301,22 @@ __device__ __forceinline__ void static_update_wood(int n, int ns, const int *bt_
 // LOG: the incremental residual's variant, which logs every change of x.
 // WOOD: the variant for handles with blocks in the s >= n form (the other
 // instances compile without that branch).
-template <typename T, bool LOG = false, bool WOOD = false>
+template <typename T, bool LOG = false, bool WOOD = false, bool MC = false>
 __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__ b, T *x,
                                                  Ctl *ctl, int force_tau, int use_stages,
-                                                 int l_begin) {
+                                                 int l_begin, int ld_) {
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ T rloc[kMaxBlockRows];
     __shared__ T y[kMaxBlockRows];
     __shared__ int taus[64];
     __shared__ int s_a0[2];
     __shared__ int s_fail;
+    if constexpr (MC) {                               // column blockIdx.y of a block of columns
+        ctl += blockIdx.y;
+        x += blockIdx.y;
+        b += blockIdx.y;
+    }
+    const int ld = MC ? ld_ : 1;
     if (force_tau < 0 && (ctl->done || ctl->halt)) return;
     const bool lg = LOG && force_tau < 0;            // log x's changes
     const int nst = force_tau >= 0 ? 1 : ctl->n_static;
@@ -290,10 +334,12 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         if (force_tau < 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
             ctl->tr_tau[ctl->iter * nst + a] = tau;
     }
+    const bool inject = ctl->fault == RORBK_FAULT_WAIT_LIMIT && force_tau < 0;
     if (a == 0) {
         s_fail = 0;
         s_a0[0] = s_a0[1] = -1;
         if (use_stages) { mbar_init(&bar[0], 1); mbar_init(&bar[1], 1); }
+        if (inject) mbar_init(&bar[2], 1);           // a barrier that nothing completes
     }
     __syncthreads();
     if (use_stages && a == 0) {
@@ -316,7 +362,7 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
             la = A.bperm[r0 + a];
             q0 = A.rowptr[r0 + la];
             q1 = A.rowptr[r0 + la + 1];
-            bi = b[r0 + la];
+            bi = b[(long long)(r0 + la) * ld];
             pos = A.s_pos[r0 + la];
             wd = A.w_diag[r0 + la];
         }
@@ -324,7 +370,10 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         const int a0 = use_stages ? s_a0[sidx] : -1;
         const bool staged = a0 >= 0;
         if (staged) {
-            if (!mbar_wait_bounded(&bar[sidx], phase[sidx], kWaitTries)) atomicOr(&s_fail, 1);
+            // fault injection: the wait gives up as if the copies never landed
+            const bool ok = inject ? mbar_wait_bounded(&bar[2], 0u, 1)
+                                   : mbar_wait_bounded(&bar[sidx], phase[sidx], kWaitTries);
+            if (!ok) atomicOr(&s_fail, 1);
             phase[sidx] ^= 1u;
         }
         __syncthreads();
@@ -341,7 +390,7 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         T acc = T(0);
         if (staged) {
             const Stage<T> st = stg[sidx];
-            for (int p = p0 + a; p < pend; p += blockDim.x) sx[p - p0] = x[st.col[p - a0]];
+            for (int p = p0 + a; p < pend; p += blockDim.x) sx[p - p0] = x[(long long)st.col[p - a0] * ld];
             __syncthreads();
             for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(st.val[p - a0], sx[p - p0], acc);
         } else {
@@ -349,14 +398,14 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
             // straight from global memory (loads unrolled ahead of the chain),
             // so the rows proceed side by side however long they are
 #pragma unroll 8
-            for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(A.val[p], x[A.col[p]], acc);
+            for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(A.val[p], x[(long long)A.col[p] * ld], acc);
         }
         if (a < s) rloc[la] = Ar<T>::sub(bi, acc);
         __syncthreads();
         const long long wp = WOOD ? A.wood_ptr[tau] : -1;
         if (WOOD && wp >= 0) {
             static_update_wood<T>(A.n, A.nseg[tau], A.bt_seg, A.bt_col, A.bt_row, A.bt_val, A.wood + wp, p0,
-                                  pend, rloc, y, x, ctl, lg);
+                                  pend, rloc, y, x, ctl, lg, ld);
             if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stg[sidx], &bar[sidx]) : -1;
             continue;
         }
@@ -382,7 +431,7 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
                 T acc3 = T(0);
                 for (int u = q; u < pend && st.btcol[u - a0] == c; ++u)
                     acc3 = Ar<T>::fma(st.btval[u - a0], y[st.btrow[u - a0]], acc3);
-                x[c] = Ar<T>::add(x[c], acc3);
+                x[(long long)c * ld] = Ar<T>::add(x[(long long)c * ld], acc3);
                 if (lg) inc_log(ctl, c, (double)acc3);
             }
         } else {
@@ -393,7 +442,7 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
                 T acc3 = T(0);
                 for (; q < pend && A.bt_col[q] == c; ++q)
                     acc3 = Ar<T>::fma(A.bt_val[q], y[A.bt_row[q]], acc3);
-                x[c] = Ar<T>::add(x[c], acc3);
+                x[(long long)c * ld] = Ar<T>::add(x[(long long)c * ld], acc3);
                 if (lg) inc_log(ctl, c, (double)acc3);
             }
         }
@@ -669,16 +718,25 @@ __global__ void __launch_bounds__(256) k_inc_finish(const T *__restrict__ r, int
     }
 }
 
-// First radix level over a given r (single-step top-K).
-template <typename T>
+// First radix level over a given r (single-step top-K, and the iteration of
+// a block of columns, whose residual pass leaves it out: check_done).
+template <typename T, bool MC = false>
 __global__ void __launch_bounds__(256) k_topk_hist1(const T *__restrict__ r, int m, int K,
-                                                    unsigned *hist1, Ctl *ctl) {
+                                                    unsigned *hist1, Ctl *ctl, Cols cl,
+                                                    int check_done) {
     __shared__ unsigned hist[kHistBins];
     __shared__ int is_last;
+    if constexpr (MC) {
+        ctl += blockIdx.y;
+        r += blockIdx.y * cl.rs;
+        hist1 += blockIdx.y * kHistBins;
+    }
+    if (check_done && (ctl->done || ctl->halt)) return;
+    const int mp = MC ? cl.mpos : m;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-        atomicAdd(&hist[(unsigned)(abs_key(r[i]) >> 52)], 1u);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += gridDim.x * blockDim.x)
+        if (!MC || !cl.perm || cl.perm[i] >= 0) atomicAdd(&hist[(unsigned)(abs_key(r[i]) >> 52)], 1u);
     __syncthreads();
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
         if (hist[i]) atomicAdd(&hist1[i], hist[i]);
@@ -699,16 +757,24 @@ __global__ void __launch_bounds__(256) k_topk_hist1(const T *__restrict__ r, int
     }
 }
 
-template <typename T>
+template <typename T, bool MC = false>
 __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int m, int K,
-                                                    unsigned *hist2, Ctl *ctl, int check_done) {
+                                                    unsigned *hist2, Ctl *ctl, int check_done,
+                                                    Cols cl) {
     __shared__ unsigned hist[kHistBins];
     __shared__ int is_last;
+    if constexpr (MC) {
+        ctl += blockIdx.y;
+        r += blockIdx.y * cl.rs;
+        hist2 += blockIdx.y * kHistBins;
+    }
     if (check_done && (ctl->done || ctl->halt)) return;
     const unsigned sel1 = (unsigned)ctl->sel1;
+    const int mp = MC ? cl.mpos : m;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += gridDim.x * blockDim.x) {
+        if (MC && cl.perm && cl.perm[i] < 0) continue;
         unsigned long long key = abs_key(r[i]);
         if ((unsigned)(key >> 52) == sel1) atomicAdd(&hist[(unsigned)(key >> 41) & 2047u], 1u);
     }
@@ -737,10 +803,11 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
 // threshold prefix, the block resolves the remaining 41 key bits itself by
 // scanning r.  Writes I ascending to sI.  Shared scratch: keys and idx
 // arrays of kEqCap entries.
-template <typename T>
+// The lists hold rows; r is read at rpos(cl, row).
+template <typename T, bool MC>
 __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *in_list,
                               const int *eq_list, Ctl *ctl, int *sI,
-                              unsigned long long *skey, int *sidx) {
+                              unsigned long long *skey, int *sidx, const Cols &cl) {
     __shared__ int sc[33];
     __shared__ int s_need, s_nin, s_neq, s_fill;
     __shared__ unsigned long long s_pref;
@@ -757,7 +824,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
     if (need > 0 && neq <= kEqCap) {
         const int np = next_pow2(neq);
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
-            if (e < neq) { int i = eq_list[e]; skey[e] = abs_key(r[i]); sidx[e] = i; }
+            if (e < neq) { int i = eq_list[e]; skey[e] = abs_key(r[rpos<MC>(cl, i)]); sidx[e] = i; }
             else { skey[e] = 0ull; sidx[e] = 0x7fffffff; }
         }
         __syncthreads();
@@ -782,7 +849,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
             const unsigned long long pref = s_pref;
             const int sh = s_shift;
             for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                unsigned long long key = abs_key(r[i]);
+                unsigned long long key = abs_key(r[rpos<MC>(cl, i)]);
                 if ((key >> sh) == pref)
                     atomicAdd(&shist[(unsigned)((key >> nshift) & ((1ull << digit_bits) - 1))], 1u);
             }
@@ -802,7 +869,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
             // rows strictly above the chosen digit are in
             const int dig = s_dig;
             for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                unsigned long long key = abs_key(r[i]);
+                unsigned long long key = abs_key(r[rpos<MC>(cl, i)]);
                 if ((key >> sh) == pref &&
                     (int)((key >> nshift) & ((1ull << digit_bits) - 1)) > dig)
                     sI[atomicAdd(&s_fill, 1)] = i;
@@ -820,7 +887,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
         int taken = 0;
         for (int base = 0; base < m && taken < want; base += blockDim.x) {
             int i = base + threadIdx.x;
-            int f = (i < m && abs_key(r[i]) == T0) ? 1 : 0;
+            int f = (i < m && abs_key(r[rpos<MC>(cl, i)]) == T0) ? 1 : 0;
             int total;
             int pre = block_exclusive_scan(f, sc, &total);
             if (f && taken + pre < want) sI[s_fill + taken + pre] = i;
@@ -861,7 +928,31 @@ struct Dyn {
     unsigned long long *pkeys;  // [pcap] Gram contributions (fallback)
     long long pcap;
     double *g;                  // [K(K+1)/2] packed Gram fallback
+    int K, n;                   // sizes of one column's buffers (a block of columns
+    long long skcap;            // keeps its columns' buffers one after the other)
 };
+
+// The buffers of column jc of a block of columns.
+__device__ __forceinline__ Dyn dyn_col(Dyn D, int jc) {
+    if (jc == 0) return D;
+    const long long K = D.K, n = D.n;
+    D.I += jc * K;
+    D.estart += jc * (K + 1);
+    D.gdiag += jc * K;
+    D.y += jc * K;
+    D.ecol += jc * D.ecap;
+    D.eval += jc * D.ecap;
+    D.erow += jc * D.ecap;
+    D.owner += jc * n;
+    D.shared += jc * n;
+    D.segpos += jc * n;
+    D.epoch += jc;
+    D.raw += jc * 2 * D.ecap;
+    D.skeys += jc * D.skcap;
+    D.pkeys += jc * D.pcap;
+    D.g += jc * (K * (K + 1) / 2);
+    return D;
+}
 
 __device__ __forceinline__ long long pidx(int i, int j) {     // packed lower, row-major
     return (long long)i * (i + 1) / 2 + j;
@@ -895,17 +986,27 @@ __device__ void publish_rows(const int *rowptr, const int *sI, int K, Dyn D, Ctl
 
 // Rows above the 22-bit threshold and the candidates on it; the last block
 // completes the exact top-K set and publishes it.
-template <typename T>
+template <typename T, bool MC = false>
 __global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, int m, int K,
                                                       const int *rowptr, int *in_list,
                                                       int *eq_list, Dyn D, Ctl *ctl,
-                                                      int check_done) {
+                                                      int check_done, Cols cl) {
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ int is_last;
+    if constexpr (MC) {
+        ctl += blockIdx.y;
+        r += blockIdx.y * cl.rs;
+        in_list += (long long)blockIdx.y * K;
+        eq_list += (long long)blockIdx.y * kEqCap;
+        D = dyn_col(D, blockIdx.y);
+    }
     if (check_done && (ctl->done || ctl->halt)) return;
     const unsigned long long P = (unsigned long long)(unsigned)ctl->prefix;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        unsigned long long pre = abs_key(r[i]) >> 41;
+    const int mp = MC ? cl.mpos : m;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mp; p += gridDim.x * blockDim.x) {
+        const int i = MC && cl.perm ? cl.perm[p] : p;      // the row at this position
+        if (i < 0) continue;
+        unsigned long long pre = abs_key(r[p]) >> 41;
         if (pre > P) {
             in_list[atomicAdd(&ctl->n_in, 1)] = i;
         } else if (pre == P) {
@@ -922,17 +1023,30 @@ __global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, i
     unsigned long long *skey = dsm_u64;
     int *sidx = (int *)(skey + kEqCap);
     int *sI = sidx + kEqCap;
-    finalize_topk<T>(r, m, K, in_list, eq_list, ctl, sI, skey, sidx);
+    finalize_topk<T, MC>(r, m, K, in_list, eq_list, ctl, sI, skey, sidx, cl);
     publish_rows(rowptr, sI, K, D, ctl, 1);
     if (threadIdx.x == 0) ctl->ticket = 0;
 }
 
-// Single-step API: a given ascending I.
-__global__ void __launch_bounds__(512) k_dyn_set_rows(const int *rowptr, const int *I, int K,
+// Single-step API: a given ascending I, checked before any row is read (an
+// entry outside [0, m) or a set that is not strictly ascending records
+// kDevBounds, and the kernels after this one do nothing).
+__global__ void __launch_bounds__(512) k_dyn_set_rows(const int *rowptr, const int *I, int K, int m,
                                                       Dyn D, Ctl *ctl) {
     __shared__ int sI[kMaxDynRows];
-    for (int a = threadIdx.x; a < K; a += blockDim.x) sI[a] = I[a];
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
     __syncthreads();
+    for (int a = threadIdx.x; a < K; a += blockDim.x) {
+        const int i = I[a];
+        sI[a] = i;
+        if (i < 0 || i >= m || (a > 0 && I[a - 1] >= i)) bad = 1;
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) { set_status(&ctl->status, kDevBounds); ctl->done = 1; }
+        return;
+    }
     publish_rows(rowptr, sI, K, D, ctl, 0);
 }
 
@@ -1220,9 +1334,9 @@ __device__ void column_solve(const double *G, int nS, double *z, unsigned char *
 // from the shared columns only (each entry summed over ascending columns), its
 // Cholesky, and y = (A_I A_I^T + mu I)^{-1} r_I by two triangular solves
 // (y_a = (r_a / L_aa) / L_aa outside S).
-template <typename T>
+template <typename T, bool MC>
 __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
-                           unsigned long long *dsm) {
+                           unsigned long long *dsm, const Cols &cl) {
     __shared__ int s_nsh, s_npk, s_nS, s_bad, s_fill, s_fill2, s_nlev, s_uselev;
     __shared__ int sc[33];
     unsigned long long *sk = dsm;                                   // kShCap
@@ -1341,7 +1455,7 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
         G[pidx(spos[a_hi], spos[a_lo])] = acc;
     }
     __syncthreads();
-    for (int q = tid; q < nS; q += blockDim.x) z[q] = (double)r[D.I[sidx[q]]];
+    for (int q = tid; q < nS; q += blockDim.x) z[q] = (double)r[rpos<MC>(cl, D.I[sidx[q]])];
     __syncthreads();
     if (nS > 0) {
         if (nS <= kSymMax) symbolic(G, nS, S, &s_nlev, &s_uselev);
@@ -1372,12 +1486,17 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
 
 // Gathers the nonzeros of A_I (row order), marks each column's lowest entry
 // and entry count, forms ||A_i||^2 + mu; the last block factors.
-template <typename T>
+template <typename T, bool MC = false>
 __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict__ r, Dyn D,
-                                                  Ctl *ctl, int check_done) {
+                                                  Ctl *ctl, int check_done, Cols cl) {
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ int is_last;
-    if (check_done && (ctl->done || ctl->halt)) return;
+    if constexpr (MC) {
+        ctl += blockIdx.y;
+        r += blockIdx.y * cl.rs;
+        D = dyn_col(D, blockIdx.y);
+    }
+    if ((check_done && (ctl->done || ctl->halt)) || ctl->status) return;
     const int K = A.K;
     const int E = ctl->dynE;
     if (E > D.ecap) {
@@ -1400,7 +1519,7 @@ __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict_
         D.gdiag[a] = g;
         if (!(g > 0.0)) { set_status(&ctl->status, kDevNotSpd); g = 1.0; }
         const double l = sqrt(g);
-        D.y[a] = ((double)r[i] / l) / l;
+        D.y[a] = ((double)r[rpos<MC>(cl, i)] / l) / l;
     }
     for (int e = gt; e < E; e += gs) {
         int lo = 0, hi = K;                          // last a with estart[a] <= e
@@ -1438,17 +1557,19 @@ __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict_
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    dyn_factor<T>(r, K, D, ctl, dsm_u64);
+    dyn_factor<T, MC>(r, K, D, ctl, dsm_u64, cl);
     if (threadIdx.x == 0) ctl->ticket = 0;
 }
 
 // End of an iteration: trace x, advance, loop condition (one block).
+// A block of columns (grp != nullptr) sets the condition from all columns.
 template <typename T>
 __device__ void end_iteration(const T *x, int n, Ctl *ctl, int use_cond,
-                              cudaGraphConditionalHandle hcond) {
+                              cudaGraphConditionalHandle hcond, int ld = 1,
+                              unsigned *grp = nullptr) {
     if (ctl->tr_x && ctl->iter < ctl->trace_cap && sizeof(T) == sizeof(double))
         for (int c = threadIdx.x; c < n; c += blockDim.x)
-            ctl->tr_x[ctl->iter * (long long)n + c] = (double)x[c];
+            ctl->tr_x[ctl->iter * (long long)n + c] = (double)x[(long long)c * ld];
     __syncthreads();
     if (threadIdx.x == 0) {
         if (!ctl->halt) {
@@ -1456,20 +1577,28 @@ __device__ void end_iteration(const T *x, int n, Ctl *ctl, int use_cond,
             ctl->iter = it;
             if (ctl->done || ctl->status != 0 || it >= ctl->maxit) ctl->halt = 1;
         }
-        if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
+        if (grp) group_condition(ctl - blockIdx.y, gridDim.y, grp, use_cond, hcond);
+        else if (use_cond) cudaGraphSetConditional(hcond, ctl->halt ? 0u : 1u);
     }
 }
 
 // x += A_I^T y: a column used by one row of I takes its single product; a
 // shared column is summed over its rows in ascending order by the entry that
 // owns it.  The last block clears the column marks and ends the iteration.
-template <typename T, bool LOG = false>
+template <typename T, bool LOG = false, bool MC = false>
 __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ctl, int count_iter,
                                                      int use_cond,
-                                                     cudaGraphConditionalHandle hcond) {
+                                                     cudaGraphConditionalHandle hcond, Cols cl) {
     __shared__ int is_last;
+    if constexpr (MC) {
+        ctl += blockIdx.y;
+        x += blockIdx.y;
+        D = dyn_col(D, blockIdx.y);
+    }
+    const int ld = MC ? cl.ld : 1;
+    unsigned *grp = MC ? cl.grp : nullptr;
     if (ctl->done || ctl->status || ctl->halt) {
-        if (count_iter && blockIdx.x == 0) end_iteration<T>(x, n, ctl, use_cond, hcond);
+        if (count_iter && blockIdx.x == 0) end_iteration<T>(x, n, ctl, use_cond, hcond, ld, grp);
         return;
     }
     const int E = ctl->dynE, nsh = ctl->dyn_nsh;
@@ -1480,7 +1609,7 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
         const int c = D.ecol[e];
         if (D.shared[c] != ep) {
             const T d = Ar<T>::fma(as<T>(D.eval[e]), as<T>(D.y[D.erow[e]]), T(0));
-            x[c] = Ar<T>::add(x[c], d);
+            x[(long long)c * ld] = Ar<T>::add(x[(long long)c * ld], d);
             if (lg) inc_log(ctl, c, (double)d);
         } else if ((unsigned)D.skeys[D.segpos[c]] == (unsigned)e) {
             T acc = T(0);
@@ -1488,7 +1617,7 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
                 const unsigned e2 = (unsigned)D.skeys[u];
                 acc = Ar<T>::fma(as<T>(D.eval[e2]), as<T>(D.y[D.erow[e2]]), acc);
             }
-            x[c] = Ar<T>::add(x[c], acc);
+            x[(long long)c * ld] = Ar<T>::add(x[(long long)c * ld], acc);
             if (lg) inc_log(ctl, c, (double)acc);
         }
     }
@@ -1500,7 +1629,7 @@ __global__ void __launch_bounds__(512) k_dyn_scatter(T *x, int n, Dyn D, Ctl *ct
     __threadfence();
     if (threadIdx.x == 0) ctl->ticket = 0;
     __syncthreads();
-    if (count_iter) end_iteration<T>(x, n, ctl, use_cond, hcond);
+    if (count_iter) end_iteration<T>(x, n, ctl, use_cond, hcond, ld, grp);
 }
 
 // ---- residual-weighted draws (not in the paper) -----------------------------
@@ -2192,6 +2321,7 @@ __global__ void __launch_bounds__(256) k_inner_prep(const double *__restrict__ r
         in->log_cap = out->log_cap;
         in->log_col = out->log_col;
         in->log_val = out->log_val;
+        in->fault = out->fault;
         if (use_cond) cudaGraphSetConditional(hcond, in->halt ? 0u : 1u);
     }
 }
@@ -2231,7 +2361,8 @@ static size_t factor_smem_bytes() {
 static Dyn dyn_bufs(rorbk_ctx *h) {
     return Dyn{h->dyn.I, h->dyn.estart, h->dyn.gdiag, h->dyn.y, h->dyn.ecol, h->dyn.eval,
                h->dyn.erow, h->dyn.ecap, h->dyn.owner, h->dyn.shared, h->dyn.segpos,
-               h->dyn.epoch, h->dyn.raw, h->dyn.skeys, h->dyn.pkeys, h->dyn.pcap, h->dyn.g};
+               h->dyn.epoch, h->dyn.raw, h->dyn.skeys, h->dyn.pkeys, h->dyn.pcap, h->dyn.g,
+               h->K, (int)h->n, h->dyn.skcap};
 }
 
 static int grid_stream(rorbk_ctx *h, int m) {
@@ -2352,9 +2483,10 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
     }
     Mat<T> A = make_mat<T>(h);
     k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
-                                                                        check_done);
+                                                                        check_done, one_col((int)h->m));
     (inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>)<<<2 * h->num_sms, 512, 0, h->stream>>>(
-        x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond, (cudaGraphConditionalHandle)hcond);
+        x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond, (cudaGraphConditionalHandle)hcond,
+        one_col((int)h->m));
 }
 
 template <typename T>
@@ -2396,12 +2528,12 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
         // updates beyond kDenseStatic (n_static > 3), if any
         (h->n_wood ? k_static<T, false, true> : k_static<T, false, false>)<<<1, 1024, static_smem_bytes<T>(),
                                                                               h->stream>>>(A, b, x, ctl, -1, 0,
-                                                                                           kDenseStatic);
+                                                                                           kDenseStatic, 1);
     } else {
         const bool wd = h->n_wood > 0;
         (inc ? (wd ? k_static<T, true, true> : k_static<T, true, false>)
              : (wd ? k_static<T, false, true> : k_static<T, false, false>))<<<1, 1024, static_smem_bytes<T>(),
-                                                                               h->stream>>>(A, b, x, ctl, -1, 1, 0);
+                                                                               h->stream>>>(A, b, x, ctl, -1, 1, 0, 1);
     }
     if (inc) {   // r from the change log; the exact kernel below runs only when asked to
         k_inc_apply<T><<<4 * h->num_sms, 256, 0, h->stream>>>(h->csc_ptr, h->csc_row, csc_values<T>(h),
@@ -2420,9 +2552,9 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
     if constexpr (sizeof(T) == sizeof(double))
         if (weighted) launch_weights(h, r);      // the draws of the next iteration
     const int g = grid_stream(h, (int)h->m);
-    k_topk_hist2<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1);
+    k_topk_hist2<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1, one_col((int)h->m));
     k_topk_collect<T><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
-        r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1);
+        r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1, one_col((int)h->m));
     launch_dynamic_tail<T>(h, r, x, ctl, 1, 1, use_cond, hcond, inc);
 }
 
@@ -2462,7 +2594,7 @@ void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_ou
 void launch_static_forced(rorbk_ctx *h, int tau, const double *b, double *x) {
     (h->n_wood ? k_static<double, false, true> : k_static<double, false, false>)<<<
         1, 1024, static_smem_bytes<double>(), h->stream>>>(make_mat<double>(h), b, x,
-                                                                          h->ctl, tau, 0, 0);
+                                                                          h->ctl, tau, 0, 0, 1);
 }
 
 void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r) {
@@ -2478,15 +2610,16 @@ void launch_residual32_only(rorbk_ctx *h, const float *b, const float *x, float 
 
 void launch_topk_only(rorbk_ctx *h, const double *r, int *I) {
     const int g = grid_stream(h, (int)h->m);
-    k_topk_hist1<double><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist1, h->ctl);
-    k_topk_hist2<double><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, h->ctl, 0);
+    const Cols one = one_col((int)h->m);
+    k_topk_hist1<double><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist1, h->ctl, one, 0);
+    k_topk_hist2<double><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, h->ctl, 0, one);
     k_topk_collect<double><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
-        r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), h->ctl, 0);
+        r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), h->ctl, 0, one);
     cudaMemcpyAsync(I, h->dyn.I, h->K * sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
 }
 
 void launch_dynamic_given(rorbk_ctx *h, const int *I, const double *r, double *x) {
-    k_dyn_set_rows<<<1, 512, 0, h->stream>>>(h->rowptr, I, h->K, dyn_bufs(h), h->ctl);
+    k_dyn_set_rows<<<1, 512, 0, h->stream>>>(h->rowptr, I, h->K, (int)h->m, dyn_bufs(h), h->ctl);
     launch_dynamic_tail<double>(h, r, x, h->ctl, 0, 0, 0, 0);
 }
 

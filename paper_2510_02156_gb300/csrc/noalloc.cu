@@ -13,13 +13,16 @@
 //   - every GPU that loads the library holds kScratchBlocks doubles plus a
 //     counter until the process exits (about 512 KiB);
 //   - all calls on one device share it and it keeps the last call's contents;
-//     the completion counter is reset by the kernel that consumes it, so calls
-//     issued in stream order are independent, but calls that overlap on the
-//     GPU (different streams, no ordering) race on the scratch and give wrong
-//     results;
+//     every call clears the completion counter on its stream before its
+//     kernel (a 4-byte cudaMemsetAsync, which allocates nothing), so calls
+//     issued in stream order are independent even after a launch that never
+//     finished; calls that overlap on the GPU (different streams, no
+//     ordering) race on the scratch and give wrong results;
 //   - the first call on each device looks up the scratch's device address
-//     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture begins.
+//     (cudaGetSymbolAddress) with that device current and keeps it for the
+//     process; make that first call before any stream capture begins, and do
+//     not call the entry point after cudaDeviceReset, which ends the context
+//     the kept address belongs to.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -124,6 +127,11 @@ extern "C" rorbk_status rorbk_csr_residual_noalloc(int64_t m, int64_t n, int64_t
                     "rorbk_csr_residual_noalloc: the scratch's device address could not be found");
     const unsigned grid = (unsigned)((m + kRowsPerBlock - 1) / kRowsPerBlock);
     cudaStream_t s = (cudaStream_t)stream;
+    // a launch that stopped part-way (an earlier error on the stream) may have
+    // left the counter raised: clear it in stream order before this kernel
+    rorbk_status st = cuda_check(nullptr, cudaMemsetAsync(&scratch->ticket, 0, sizeof(unsigned), s),
+                                 "rorbk_csr_residual_noalloc");
+    if (st) return st;
     if (dtype == RORBK_F64)
         k_csr_residual_noalloc<double><<<grid, kRowsPerBlock, 0, s>>>(
             (int)m, row_ptr, col_idx, (const double *)values, b, x, r, rr_out, scratch);

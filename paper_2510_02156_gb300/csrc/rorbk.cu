@@ -262,6 +262,7 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         D.epoch = (unsigned *)dev_alloc(h, sizeof(unsigned));
         D.segpos = (int *)dev_alloc(h, n * sizeof(int));
         D.raw = (unsigned long long *)dev_alloc(h, 2 * D.ecap * sizeof(unsigned long long));
+        D.skcap = np2;
         D.skeys = (unsigned long long *)dev_alloc(h, np2 * sizeof(unsigned long long));
         D.pkeys = (unsigned long long *)dev_alloc(h, D.pcap * sizeof(unsigned long long));
         D.g = (double *)dev_alloc(h, ((size_t)h->K * (h->K + 1) / 2) * sizeof(double));
@@ -516,6 +517,8 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
     if (inc && opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED)
         return fail(h, RORBK_ERR_UNSUPPORTED, "the incremental residual is not combined with residual-weighted draws");
     if (inc && opt.refresh < 0) return fail(h, RORBK_ERR_INVALID_ARG, "refresh >= 0");
+    if (opt.fault_inject != RORBK_FAULT_NONE && opt.fault_inject != RORBK_FAULT_WAIT_LIMIT)
+        return fail(h, RORBK_ERR_INVALID_ARG, "unknown fault_inject");
     if (inc && h->K >= h->n)
         return fail(h, RORBK_ERR_UNSUPPORTED,
                     "the incremental residual does not log the n x n form of the dynamic update (K >= n)");
@@ -544,6 +547,7 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
     c.log_cap = inc ? h->ilog_cap : 0;
     c.log_col = inc ? h->ilog_col : nullptr;
     c.log_val = inc ? h->ilog_val : nullptr;
+    c.fault = opt.fault_inject;
     if (opt.trace && !mixed) {
         c.trace_cap = opt.trace->capacity;
         c.tr_tau = (long long *)opt.trace->tau;
@@ -720,6 +724,25 @@ rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
     *out = c;
     cudaSetDevice(cur);
     return RORBK_OK;
+}
+
+rorbk_status rorbk_weighted_cdf(rorbk_handle h, const double *r, double *cdf_host) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!r || !cdf_host) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_weighted_cdf: NULL r or cdf_host");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    cudaMemsetAsync(&h->ctl->done, 0, sizeof(int), s);
+    cudaMemsetAsync(&h->ctl->halt, 0, sizeof(int), s);
+    launch_weights(h, r);
+    rorbk_status st = cuda_check(h, cudaGetLastError(), "rorbk_weighted_cdf");
+    if (!st)
+        st = cuda_check(h, cudaMemcpyAsync(cdf_host, h->wcdf, (size_t)h->k * sizeof(double),
+                                           cudaMemcpyDeviceToHost, s), "rorbk_weighted_cdf");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(s), "rorbk_weighted_cdf");
+    cudaSetDevice(cur);
+    return st;
 }
 
 rorbk_status rorbk_dense_gram(rorbk_handle h, const int32_t *I, double *G, int32_t precision) {

@@ -2,7 +2,6 @@
 residual, and the DRAM traffic record, which is reported only for the
 captured workload and only while the kernel sources match the capture."""
 import os
-import shutil
 import types
 
 import bench
@@ -28,9 +27,15 @@ def test_traffic_record_matches_the_committed_kernels():
 def test_traffic_record_is_dropped_for_other_workloads_or_changed_sources(tmp_path, monkeypatch):
     s = types.SimpleNamespace(m=1 << 20, nnz=9692830)
     assert bench.profiled_traffic("k_residual<float,float>", types.SimpleNamespace(m=1 << 18, nnz=5)) is None
-    changed = tmp_path / "kernels_iter.cu"
-    shutil.copy(os.path.join(bench.ROOT, bench.KERNEL_SOURCES[0]), changed)
-    with open(changed, "a") as fh:
-        fh.write("\n// changed\n")
-    monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(changed), bench.KERNEL_SOURCES[1]))
+    src = open(os.path.join(bench.ROOT, bench.KERNEL_SOURCES[0])).read()
+    marker = bench.RESIDUAL_REGION[0]
+    # a change outside the residual kernel's region keeps the record ...
+    outside = tmp_path / "outside.cu"
+    outside.write_text(src + "\n// changed elsewhere\n")
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(outside), bench.KERNEL_SOURCES[1]))
+    assert bench.profiled_traffic("k_residual<float,float>", s) is not None
+    # ... a change inside it drops the record
+    inside = tmp_path / "inside.cu"
+    inside.write_text(src.replace(marker, marker + "\n// changed"))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(inside), bench.KERNEL_SOURCES[1]))
     assert bench.profiled_traffic("k_residual<float,float>", s) is None

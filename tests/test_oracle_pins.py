@@ -395,16 +395,43 @@ def test_solve_not_spd_with_zero_mu_and_dependent_rows():
 # (not in the paper, whose P is static: the weighted variant draws block t with
 # weight Pbar_t * ||r_{B_t}||^2 from the previous iteration's residual.)
 def test_weighted_cdf_is_a_running_sum_of_the_weights():
-    """The chunked running sum equals the running sum numpy forms (to
-    rounding), for sizes that end inside and on a chunk boundary."""
+    """cdf_t = sum_{i <= t} Pbar_i rho_i in block order: numpy's sequential
+    accumulate of the rounded products gives the same numbers bit for bit, and
+    the total agrees with an exactly rounded sum (math.fsum) within the
+    sequential sum's error bound."""
+    import math
     rng = np.random.default_rng(51)
     for k in (1, 63, 64, 65, 300, 4096):
         Pbar = rng.uniform(0.9, 1.0, k)
         rho = rng.uniform(0.0, 5.0, k) ** 3
         cdf = oracle.weighted_cdf(Pbar, rho)
-        ref = np.cumsum(Pbar * rho)
-        np.testing.assert_allclose(cdf, ref, rtol=1e-13, atol=0)
+        w = Pbar * rho
+        np.testing.assert_array_equal(cdf, np.add.accumulate(w))
+        exact = math.fsum(w.tolist())
+        assert abs(cdf[-1] - exact) <= k * 2.0 ** -53 * exact
         assert np.all(np.diff(cdf) >= 0)
+
+
+def test_threaded_residual_and_topk_equal_one_thread(monkeypatch):
+    """The residual rows and the top-K scan run on several host threads above
+    65536 rows; every number and the top-K set equal the one-thread run (and
+    the top-K set equals a brute-force sort with planted ties)."""
+    s = W.powerlaw(n=1 << 17, num_blocks=512, seed=5, lam=1e-8)
+    rng = np.random.default_rng(53)
+    x = rng.standard_normal(s.n)
+    out = {}
+    for t in ("1", "5"):
+        monkeypatch.setenv("ORC_THREADS", t)
+        assert oracle.thread_count(s.m) == int(t)
+        r, rr = oracle.residual(s, s.b, x)
+        r[[7, 70000, 130000]] = np.max(np.abs(r)) * 2.0     # a tie across thread ranges
+        out[t] = (r, rr, oracle.topk(r, 256))
+    np.testing.assert_array_equal(out["1"][0], out["5"][0])
+    assert out["1"][1] == out["5"][1]
+    np.testing.assert_array_equal(out["1"][2], out["5"][2])
+    r = out["1"][0]
+    order = np.lexsort((np.arange(r.size), -np.abs(r)))
+    np.testing.assert_array_equal(out["5"][2], np.sort(order[:256]))
 
 
 def test_block_norms_are_squared_block_residuals():
