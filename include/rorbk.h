@@ -397,7 +397,8 @@ rorbk_status rorbk_fabgmres(rorbk_handle h, const double *b, const double *x0, d
  *   src and its clones is freed (rorbk_free), in any order.  Errors:
  *   RORBK_ERR_INVALID_ARG (NULL), RORBK_ERR_OOM, RORBK_ERR_CUDA.
  * rorbk_batch_create: captures the whole solve loop of each of count
- *   distinct handles (systems of any sizes, clones, or both; one device) as
+ *   distinct handles (systems of any sizes, clones, blocks of right-hand
+ *   sides from rorbk_multi_create, or a mix; one device) as
  *   independent components of one CUDA graph, for precision FP64 or MIXED
  *   (MIXED needs handles set up for it).  The handles must outlive the batch
  *   and must not be solved on their own while a batch solve runs.  Errors:
@@ -406,7 +407,8 @@ rorbk_status rorbk_fabgmres(rorbk_handle h, const double *b, const double *x0, d
  * rorbk_batch_solve: one graph launch that runs every handle's solve to its
  *   own stop (tolerance, maxit or error): solve i takes device vectors b[i]
  *   (its m), x0[i] (its n; x0 == NULL or x0[i] == NULL: zero) and writes
- *   x[i] (its n).  opt is shared (precision must be the batch's; host_loop and
+ *   x[i] (its n); for a block of nr right-hand sides these are its m x nr and
+ *   n x nr row-major arrays.  opt is shared (precision must be the batch's; host_loop and
  *   trace are not available); system_ids[i] (NULL: all opt->system_id) is
  *   solve i's Philox key word 1, so clones given the same id share the
  *   sampled block stream.  res[count] (may be NULL) receives each solve's
@@ -423,6 +425,56 @@ rorbk_status rorbk_batch_solve(rorbk_batch batch, const double *const *b, const 
                                const rorbk_options *opt, const uint64_t *system_ids,
                                rorbk_result *res);
 void rorbk_batch_free(rorbk_batch batch);
+
+/* ---- a block of right-hand sides ----------------------------------------
+ * (Beside the paper, which solves one right-hand side.)  A x_j = b_j for
+ * j = 0 .. nr-1, each column solved exactly as rorbk_solve would solve it
+ * alone: its own Philox stream (key (seed, system_id), counter start_iter + j'
+ * for its iteration j'), its own top-K sets, dynamic updates and stopping test
+ * (a column that reaches the tolerance stops while the others continue), so
+ * its iterates are those of the one-column solve.  What the block shares is
+ * the data movement: the residual R = B - A X of all columns is one pass over
+ * A, each gather of x bringing one contiguous row of X; the sampled updates of
+ * all columns run side by side (one block of threads per column) and the
+ * top-K and dynamic-update kernels run with one grid row per column.
+ *
+ * rorbk_multi_create: a handle *out for nr = 2, 4, 8, 16 or 32 right-hand sides
+ *   of src's system.  It shares src's set-up (as rorbk_clone does) and owns
+ *   nr per-column workspaces.  Sparse (CSR) systems whose static blocks and
+ *   dynamic block have fewer rows than A has columns (else
+ *   RORBK_ERR_UNSUPPORTED); src must be a one-column handle.  Free with
+ *   rorbk_free; rorbk_solve on it is RORBK_ERR_INVALID_ARG.
+ * rorbk_solve_multi: B (device, m x nr row-major: B[i * nr + j] = b_j[i]),
+ *   X0 (n x nr row-major or NULL for 0) and X (n x nr row-major, may alias
+ *   X0) as rorbk_solve's b, x0 and x for every column; tol, maxit and opt as
+ *   rorbk_solve (FP64 or MIXED precision, the paper's draws, the exact
+ *   residual; host_loop allowed; opt->trace, if not NULL, points to an array
+ *   of nr records, one per column, FP64 only).  res (may be NULL) receives
+ *   nr results, column j's in res[j].  Returns the first error of any column,
+ *   else RORBK_NOT_CONVERGED if some column stopped at maxit, else RORBK_OK.
+ * rorbk_solve_multi_host: the same with host buffers (copies inside the call).
+ * rorbk_multi_results: the nr per-column results of the handle's last solve
+ *   (also after rorbk_batch_solve, whose res entry for such a handle holds
+ *   the largest iteration count and RRN and converged = all columns). */
+rorbk_status rorbk_multi_create(rorbk_handle src, int32_t nr, rorbk_handle *out);
+rorbk_status rorbk_solve_multi(rorbk_handle h, const double *B, const double *X0, double *X,
+                               double tol, int64_t maxit, const rorbk_options *opt,
+                               rorbk_result *res);
+rorbk_status rorbk_solve_multi_host(rorbk_handle h, const double *B_host, const double *X0_host,
+                                    double *X_host, double tol, int64_t maxit,
+                                    const rorbk_options *opt, rorbk_result *res);
+rorbk_status rorbk_multi_results(rorbk_handle h, rorbk_result *res);
+
+/* The block's residual as a single step: R = B - A X for all nr columns in one
+ * pass over A.  precision = RORBK_PREC_FP64: B (m x nr), X (n x nr), R (m x nr)
+ * are FP64, each entry one fused chain over the row's stored entries in order
+ * (as rorbk_residual); RORBK_PREC_MIXED: FP32 arrays and FP32 chains (as
+ * rorbk_residual32; the handle must be set up for mixed precision).  All
+ * row-major, device memory.  R == NULL keeps the residual in the handle only
+ * (for timing).  rr_host (nr doubles) receives ||r_j||^2; with rr_host == NULL
+ * the call only enqueues on the handle's stream. */
+rorbk_status rorbk_residual_multi(rorbk_handle h, int32_t precision, const void *B, const void *X,
+                                  void *R, double *rr_host);
 
 /* ---- the differentiable solve ------------------------------------------
  * (No counterpart in the paper, which never differentiates its solution.)

@@ -96,6 +96,11 @@ SIGNATURES = {
     "rorbk_batch_create": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "rorbk_batch_solve": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P, _P]),
     "rorbk_batch_free": (None, [_P]),
+    "rorbk_multi_create": (C.c_int, [_P, C.c_int32, _P]),
+    "rorbk_solve_multi": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P]),
+    "rorbk_solve_multi_host": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P]),
+    "rorbk_multi_results": (C.c_int, [_P, _P]),
+    "rorbk_residual_multi": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "rorbk_setup_adjoint": (C.c_int, [_P, _P, _D, _P, _P]),
     "rorbk_adjoint_solve": (C.c_int, [_P, _P, _P, _D, _I64, _P, _P]),
     "rorbk_value_grad": (C.c_int, [_P, _P, _P, _P]),
@@ -195,6 +200,8 @@ class Handle:
         self.info = Info()
         _check(lib().rorbk_get_info(self.h, C.byref(self.info)), self.h)
 
+    nr = 0
+
     @classmethod
     def _adopt(cls, raw):
         """Wrap an rorbk_handle made by the library (rorbk_setup_adjoint)."""
@@ -226,6 +233,59 @@ class Handle:
         raw = C.c_void_p()
         _check(lib().rorbk_clone(self.h, C.byref(raw)), self.h)
         return Handle._adopt(raw)
+
+    def multi(self, nr):
+        """rorbk_multi_create: a Handle for a block of nr right-hand sides of
+        this system (nr = 2, 4, 8, 16 or 32)."""
+        raw = C.c_void_p()
+        _check(lib().rorbk_multi_create(self.h, nr, C.byref(raw)), self.h)
+        h = Handle._adopt(raw)
+        h.nr = nr
+        return h
+
+    def solve_multi(self, B, X, X0=None, tol=1e-8, maxit=1000, seed=0, system_id=0, n_static=3,
+                    start_iter=0, precision=PREC_FP64, traces=None, stream=None, inner_tol=1e-4,
+                    inner_maxit=2000000, host_loop=0, poll=64, fault_inject=FAULT_NONE):
+        """rorbk_solve_multi on device tensors B (m x nr), X (n x nr), X0 (or
+        None), row-major; returns the list of per-column Results."""
+        opt = default_options(seed=seed, system_id=system_id, n_static=n_static,
+                              start_iter=start_iter, precision=precision,
+                              stream=_stream_ptr(stream), inner_tol=inner_tol,
+                              inner_maxit=inner_maxit, host_loop=host_loop, poll=poll,
+                              fault_inject=fault_inject)
+        if traces is not None:
+            arr = (Trace * len(traces))(*traces)
+            self._keep.append(arr)
+            opt.trace = C.cast(arr, C.c_void_p)
+        res = (Result * self.nr)()
+        st = lib().rorbk_solve_multi(self.h, _ptr(B), _ptr(X0), _ptr(X), tol, maxit, C.byref(opt), res)
+        _check(st, self.h)
+        return list(res)
+
+    def solve_multi_host(self, B, X, X0=None, tol=1e-8, maxit=1000, seed=0, precision=PREC_FP64,
+                         inner_tol=1e-4, stream=None):
+        """rorbk_solve_multi_host on numpy arrays (m x nr, n x nr row-major)."""
+        opt = default_options(seed=seed, precision=precision, stream=_stream_ptr(stream),
+                              inner_tol=inner_tol)
+        res = (Result * self.nr)()
+        st = lib().rorbk_solve_multi_host(self.h, _ptr(B), _ptr(X0), _ptr(X), tol, maxit,
+                                          C.byref(opt), res)
+        _check(st, self.h)
+        return list(res)
+
+    def residual_multi(self, B, X, R=None, precision=PREC_FP64, wait=True):
+        """rorbk_residual_multi on row-major device tensors; returns the nr
+        values ||r_j||^2 (or None with wait=False: enqueue only)."""
+        rr = np.zeros(self.nr)
+        _check(lib().rorbk_residual_multi(self.h, precision, _ptr(B), _ptr(X), _ptr(R),
+                                          _ptr(rr) if wait else None), self.h)
+        return rr if wait else None
+
+    def multi_results(self):
+        """rorbk_multi_results: the per-column results of the last solve."""
+        res = (Result * self.nr)()
+        _check(lib().rorbk_multi_results(self.h, res), self.h)
+        return list(res)
 
     def setup_adjoint(self, num_blocks, lam, precision=PREC_FP64, offsets=None, stream=None):
         """rorbk_setup_adjoint: a Handle for A^T built from this handle's A."""

@@ -206,6 +206,18 @@ struct rorbk_ctx {
         long long pcap = 0, skcap = 0;
         double *g = nullptr;
     } dyn;
+    // a block of nr right-hand sides (rorbk_multi_create; 0: one right-hand
+    // side): x, b are row-major n x nr and m x nr, r and r32 hold nr columns in
+    // the SELL copy's row order, the loop state and the dynamic-block buffers
+    // are nr one-column sets side by side
+    int nr = 0;
+    struct {
+        int *iperm = nullptr;       // [m] SELL position of each row
+        unsigned *grp = nullptr;    // [8] loop tickets and "some column runs" flags, residual ticket
+        long long mpos = 0;         // SELL positions (32 per slice)
+        int grid = 0;               // blocks of the column-block residual
+        std::vector<rorbk_result> last;   // per-column results of the last solve
+    } mr;
     rorbk::Ctl *ctl = nullptr;
     rorbk::Ctl *ctl_in = nullptr;       // inner (FP32) loop state of the mixed form
     // graphs
@@ -235,6 +247,7 @@ void fill_dense_columns(rorbk_ctx *h);        // column indices of a dense A hel
 // iteration launches (kernels_iter.cu); all enqueue on h->stream
 void configure_kernels();
 int residual_grid(rorbk_ctx *h);   // one resident wave of the residual kernel
+int mres_grid(rorbk_ctx *h, int nr);   // one resident wave of the column-block residual
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
                   unsigned long long hcond);
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
@@ -247,6 +260,9 @@ void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_ou
 void launch_residual_only(rorbk_ctx *h, const double *b, const double *x, double *r);
 void launch_topk_only(rorbk_ctx *h, const double *r, int *I);
 void launch_residual32_only(rorbk_ctx *h, const float *b, const float *x, float *r);
+// a block of right-hand sides: R = B - A X for all columns (FP32 or FP64), into
+// the handle's residual buffer, and to R (m x nr row-major) if R != nullptr
+void launch_residual_multi(rorbk_ctx *h, int fp32, const void *B, const void *X, void *R);
 void launch_dynamic_given(rorbk_ctx *h, const int *I, const double *r, double *x);
 void launch_dense_gram(rorbk_ctx *h, Ctl *ctl, int tensor_cores);   // dense A: G of the rows dyn.I into dyn.g
 void launch_sample_probe(rorbk_ctx *h, uint64_t seed, uint64_t sysid, int64_t it, int64_t l,

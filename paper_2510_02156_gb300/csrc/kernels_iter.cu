@@ -2350,6 +2350,311 @@ __global__ void __launch_bounds__(256) k_outer_update(double *__restrict__ x, co
     if (use_cond) cudaGraphSetConditional(hcond, out->halt ? 0u : 1u);
 }
 
+// ------------------------------------------------- a block of right-hand sides
+// rorbk_multi_create: nr right-hand sides of one system, each solved exactly
+// as rorbk_solve would solve it alone (its own draws, top-K set, dynamic
+// update and stopping test), with X (n x nr) and B (m x nr) row-major.  The
+// residual R = B - A X is one pass over A for all columns (k_mres): each
+// gather of x brings a whole row of X (nr contiguous values) instead of one
+// value per 32-byte sector, so A is read once for nr columns.  Its columns are
+// written in the SELL copy's row order (position p = 32 s + l holds row
+// sell.row[p]), coalesced through a per-warp staging tile.  The other steps run
+// the one-column kernels with one grid row (blockIdx.y) per column.
+
+// k_begin for a block of columns: ||b_j||, x_j = x0_j or 0, loop state; the
+// last column sets the WHILE condition.  Grid (1, nr).
+__global__ void k_mr_begin(const double *__restrict__ b, int m, const double *__restrict__ x0,
+                           double *__restrict__ x, int n, Ctl *ctl0, int nr, unsigned *grp,
+                           int use_cond, cudaGraphConditionalHandle hcond) {
+    __shared__ double red[32];
+    __shared__ double bn;
+    const int jc = blockIdx.y;
+    Ctl *ctl = ctl0 + jc;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double v = b[(long long)i * nr + jc];
+        s = __fma_rn(v, v, s);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) bn = sqrt(s);
+    __syncthreads();
+    const bool zero = bn == 0.0 || x0 == nullptr || !ctl->has_x0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        x[(long long)c * nr + jc] = zero ? 0.0 : x0[(long long)c * nr + jc];
+    if (threadIdx.x == 0) {
+        const bool finite = isfinite(bn);
+        ctl->bnorm = bn;
+        ctl->iter = 0;
+        ctl->rr = 0.0;
+        ctl->rrn = bn == 0.0 ? 0.0 : 1.0;
+        ctl->done = bn == 0.0;
+        ctl->halt = !(finite && bn > 0.0 && ctl->maxit > 0);
+        ctl->status = finite ? 0 : kDevNumeric;
+        ctl->ticket = 0;
+        ctl->n_in = 0;
+        ctl->n_eq = 0;
+        ctl->outer = 0;
+        group_condition(ctl0, nr, grp, use_cond, hcond);
+    }
+}
+
+// R = B - A X for NR columns over the SELL-32 copy of A.  A warp takes a
+// slice of 32 rows; lane l works on column l % NR of rows g * (32 / NR) + l / NR
+// (g = 0 .. NR-1), so the NR lanes of one row read one contiguous row of X.
+// Each (row, column) is one chain over the row's entries in stored order:
+// the arithmetic of k_residual, column by column.  Entry j of the slice's
+// rows is present for the first cnt_j rows (lengths fall within a slice).
+// The sums of squares per column are formed per lane (FP32 inner residual:
+// per slice in FP32, then in FP64), per block in warp order and over the
+// blocks in block order by the last block, which runs the stopping test of
+// every column still running (finalize 1: the iteration's, 3: the outer
+// residual of the mixed form's refinement).
+template <typename T>
+struct SqAcc;
+template <>
+struct SqAcc<double> {
+    using type = double;
+    static __device__ __forceinline__ double add(double s, double r) { return __fma_rn(r, r, s); }
+};
+template <>
+struct SqAcc<float> {
+    using type = float;
+    static __device__ __forceinline__ float add(float s, float r) { return __fmaf_rn(r, r, s); }
+};
+
+constexpr int kMrWarps = 8;
+
+template <typename T, int NR>
+__host__ __device__ constexpr size_t mres_smem_bytes() {
+    return (size_t)kMrWarps * 32 * (NR + 1) * sizeof(T);
+}
+
+template <typename T, typename V, int NR>
+__global__ void __launch_bounds__(kMrWarps * 32, 2)
+    k_mres(Mat<T> A, const T *__restrict__ B, const T *__restrict__ X, T *__restrict__ R,
+           long long rs, double *partials, unsigned *tick, Ctl *ctl0, int finalize) {
+    constexpr int RPS = 32 / NR;            // rows per step
+    constexpr int GC = NR < 8 ? NR : 8;     // steps whose loads are issued together
+    extern __shared__ unsigned long long dsm_u64[];
+    __shared__ double red[kMrWarps][NR];
+    __shared__ int is_last;
+    T *stage = (T *)dsm_u64 + (threadIdx.x >> 5) * 32 * (NR + 1);
+    const V *__restrict__ val = sell_values<V, T>(A);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int jc = lane % NR, rsub = lane / NR;
+    const int W = gridDim.x * kMrWarps;
+    const int gw = wid * gridDim.x + blockIdx.x;
+    double rr = 0.0;
+    for (int rnd = 0;; ++rnd) {
+        const int sl = rnd * W + ((rnd & 1) ? W - 1 - gw : gw);
+        if (sl >= A.nslices) break;
+        const long long base = A.sptr[sl];
+        const int L = A.slen[sl];
+        const int mylen = A.srlen[sl * 32 + lane];      // lane l holds row l's length
+        T acc[NR];
+#pragma unroll
+        for (int g = 0; g < NR; ++g) acc[g] = T(0);
+        for (int j = 0; j < L; ++j) {
+            const int cnt = __popc(__ballot_sync(0xffffffffu, j < mylen));
+            const long long d0 = base + 32LL * j + rsub;
+#pragma unroll
+            for (int g0 = 0; g0 < NR; g0 += GC) {
+                int c[GC];
+                V a[GC];
+                T xv[GC];
+#pragma unroll
+                for (int u = 0; u < GC; ++u) {
+                    const bool in = (g0 + u) * RPS + rsub < cnt;
+                    c[u] = in ? A.scol[d0 + (g0 + u) * RPS] : 0;
+                    a[u] = in ? val[d0 + (g0 + u) * RPS] : V(0);
+                }
+#pragma unroll
+                for (int u = 0; u < GC; ++u)
+                    xv[u] = (g0 + u) * RPS + rsub < cnt ? X[(long long)c[u] * NR + jc] : T(0);
+#pragma unroll
+                for (int u = 0; u < GC; ++u)
+                    if ((g0 + u) * RPS + rsub < cnt) acc[g0 + u] = Ar<T>::fma(wide<T>(a[u]), xv[u], acc[g0 + u]);
+            }
+        }
+        typename SqAcc<T>::type sq = 0;
+#pragma unroll
+        for (int g = 0; g < NR; ++g) {
+            const int q = g * RPS + rsub;
+            const int row = A.srow[sl * 32 + q];
+            T ri = T(0);
+            if (row >= 0) {
+                ri = Ar<T>::sub(B[(long long)row * NR + jc], acc[g]);
+                sq = SqAcc<T>::add(sq, ri);
+            }
+            stage[q * (NR + 1) + jc] = ri;
+        }
+        rr += (double)sq;
+        __syncwarp();
+#pragma unroll 4
+        for (int c2 = 0; c2 < NR; ++c2) R[c2 * rs + (long long)sl * 32 + lane] = stage[lane * (NR + 1) + c2];
+        __syncwarp();
+    }
+    // sums of squares: lanes of one column, then warps, then blocks
+#pragma unroll
+    for (int o = NR; o < 32; o <<= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    if (lane < NR) red[wid][lane] = rr;
+    __syncthreads();
+    if (threadIdx.x < NR) {
+        double t = 0.0;
+        for (int w = 0; w < kMrWarps; ++w) t += red[w][threadIdx.x];
+        partials[(long long)blockIdx.x * NR + threadIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(tick, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x < NR) {
+        double tot = 0.0;
+        for (int b2 = 0; b2 < (int)gridDim.x; ++b2) tot += partials[(long long)b2 * NR + threadIdx.x];
+        Ctl *ctl = ctl0 + threadIdx.x;
+        if (finalize == 2) {                     // single-step: ||r_j||^2 only
+            ctl->rr = tot;
+        } else if (!(ctl->done || ctl->halt)) {
+            ctl->rr = tot;
+            const double rrn = sqrt(tot) / ctl->bnorm;
+            ctl->rrn = rrn;
+            if (finalize == 1 && ctl->tr_rrn && ctl->iter < ctl->trace_cap) ctl->tr_rrn[ctl->iter] = rrn;
+            if (!isfinite(rrn)) { set_status(&ctl->status, kDevNumeric); ctl->done = 1; }
+            else if (rrn <= ctl->tol) ctl->done = 1;
+            ctl->n_in = 0;
+            ctl->n_eq = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *tick = 0u;
+}
+
+// Residual columns from the SELL order to the caller's m x nr row-major layout.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mr_unpermute(const T *__restrict__ Rs, long long mpos,
+                                                      const int *__restrict__ perm, int nr,
+                                                      T *__restrict__ Rout) {
+    const long long tot = mpos * nr;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long p = e / nr;
+        const int j = (int)(e - p * nr);
+        const int i = perm[p];
+        if (i >= 0) Rout[(long long)i * nr + j] = Rs[j * mpos + p];
+    }
+}
+
+// The mixed form's refinement set-up for a block of columns: column j's
+// b32 = fl32(r) (r read in SELL order, written to its row), d = 0, and its
+// inner loop state; a column whose outer loop has stopped runs no inner
+// iteration.  Grid (g, nr); the last block of each column finishes it and the
+// last column sets the inner WHILE condition.
+__global__ void __launch_bounds__(256) k_mr_inner_prep(const double *__restrict__ r64, long long rs,
+                                                       const int *__restrict__ perm, int mpos,
+                                                       float *__restrict__ b32, float *__restrict__ d32,
+                                                       int n, int nr, double *partials, Ctl *out0,
+                                                       Ctl *in0, unsigned *grp, int use_cond,
+                                                       cudaGraphConditionalHandle hcond) {
+    __shared__ double red[32];
+    __shared__ int is_last;
+    const int jc = blockIdx.y;
+    Ctl *out = out0 + jc, *in = in0 + jc;
+    const bool active = !(out->done || out->status || out->halt);
+    double acc = 0.0;
+    if (active) {
+        const double *r = r64 + jc * rs;
+        for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mpos; p += gridDim.x * blockDim.x) {
+            const int i = perm[p];
+            if (i < 0) continue;
+            const float v = (float)r[p];
+            b32[(long long)i * nr + jc] = v;
+            acc = __fma_rn((double)v, (double)v, acc);
+        }
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+            d32[(long long)c * nr + jc] = 0.f;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        partials[(long long)jc * gridDim.x + blockIdx.x] = acc;
+        __threadfence();
+        is_last = atomicAdd(&out->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double tot = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += partials[(long long)jc * gridDim.x + i];
+    tot = block_sum(tot, red);
+    if (threadIdx.x == 0) {
+        out->ticket = 0;
+        if (active) {
+            const double bn = sqrt(tot);
+            const long long left = out->maxit - out->iter;
+            in->bnorm = bn;
+            in->iter = 0;
+            in->maxit = left < out->inner_maxit ? left : out->inner_maxit;
+            in->iter_base = out->iter_base + out->iter;
+            in->seed = out->seed;
+            in->sysid = out->sysid;
+            in->n_static = out->n_static;
+            in->tol = out->inner_tol;
+            in->rr = 0.0;
+            in->rrn = 1.0;
+            in->done = bn == 0.0;
+            in->halt = !(bn > 0.0 && in->maxit > 0);
+            in->status = 0;
+        } else {
+            in->done = 1;
+            in->halt = 1;
+        }
+        in->ticket = 0;
+        in->n_in = 0;
+        in->n_eq = 0;
+        in->trace_cap = 0;
+        in->tr_tau = nullptr;
+        in->tr_rrn = nullptr;
+        in->tr_I = nullptr;
+        in->tr_x = nullptr;
+        in->tr_dyn = nullptr;
+        in->inc = 0;
+        in->fault = out->fault;
+        group_condition(in0, nr, grp + 2, use_cond, hcond);
+    }
+}
+
+// x_j += d_j in FP64 for every column whose outer loop runs, then each
+// column's refinement bookkeeping (as k_outer_update); the last column sets
+// the outer WHILE condition.  Grid (g, nr).
+__global__ void __launch_bounds__(256) k_mr_outer_update(double *__restrict__ x, const float *__restrict__ d32,
+                                                         int n, int nr, Ctl *out0, Ctl *in0, unsigned *grp,
+                                                         int use_cond, cudaGraphConditionalHandle hcond) {
+    __shared__ int is_last;
+    const int jc = blockIdx.y;
+    Ctl *out = out0 + jc, *in = in0 + jc;
+    const bool active = !(out->done || out->status || out->halt);
+    if (active)
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+            const long long q = (long long)c * nr + jc;
+            x[q] = __dadd_rn(x[q], (double)d32[q]);
+        }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&out->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last || threadIdx.x != 0) return;
+    out->ticket = 0;
+    if (active) {
+        out->iter += in->iter;
+        out->outer += 1;
+        if (in->status) set_status(&out->status, in->status);
+        if (in->iter == 0 || out->iter >= out->maxit) out->halt = 1;
+    }
+    if (out->done || out->status) out->halt = 1;
+    group_condition(out0, nr, grp, use_cond, hcond);
+}
+
 // ------------------------------------------------------------- launchers
 static size_t collect_smem_bytes() { return (size_t)kEqCap * (8 + 4) + (size_t)kMaxDynRows * 4; }
 static size_t factor_smem_bytes() {
@@ -2377,6 +2682,41 @@ int residual_grid(rorbk_ctx *h) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, double>, 256, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_residual<float, float>, 256, 0);
     return std::max(1, std::min(per_sm, per_sm32 > 0 ? per_sm32 : per_sm)) * h->num_sms;
+}
+
+template <int NR>
+static void configure_mres() {
+    cudaFuncSetAttribute(k_mres<double, double, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)mres_smem_bytes<double, NR>());
+    cudaFuncSetAttribute(k_mres<double, float, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)mres_smem_bytes<double, NR>());
+    cudaFuncSetAttribute(k_mres<float, float, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)mres_smem_bytes<float, NR>());
+}
+
+template <int NR>
+static int mres_blocks_per_sm() {
+    int a = 0, b = 0, c = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mres<double, double, NR>, kMrWarps * 32,
+                                                  mres_smem_bytes<double, NR>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mres<double, float, NR>, kMrWarps * 32,
+                                                  mres_smem_bytes<double, NR>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_mres<float, float, NR>, kMrWarps * 32,
+                                                  mres_smem_bytes<float, NR>());
+    return std::max(1, std::min(a, std::min(b, c)));
+}
+
+// One resident wave of the column-block residual for nr columns.
+int mres_grid(rorbk_ctx *h, int nr) {
+    int per_sm = 1;
+    switch (nr) {
+        case 2: per_sm = mres_blocks_per_sm<2>(); break;
+        case 4: per_sm = mres_blocks_per_sm<4>(); break;
+        case 8: per_sm = mres_blocks_per_sm<8>(); break;
+        case 16: per_sm = mres_blocks_per_sm<16>(); break;
+        default: per_sm = mres_blocks_per_sm<32>(); break;
+    }
+    return per_sm * h->num_sms;
 }
 
 void configure_kernels() {
@@ -2409,10 +2749,33 @@ void configure_kernels() {
                          (int)sd_rows_smem<double>());
     cudaFuncSetAttribute(k_sd_rows_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sd_rows_smem<float>());
+    // the column-block instances
+    cudaFuncSetAttribute(k_static<double, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<double>());
+    cudaFuncSetAttribute(k_static<float, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)static_smem_bytes<float>());
+    cudaFuncSetAttribute(k_topk_collect<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)collect_smem_bytes());
+    cudaFuncSetAttribute(k_topk_collect<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)collect_smem_bytes());
+    cudaFuncSetAttribute(k_dyn_mark<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)factor_smem_bytes());
+    cudaFuncSetAttribute(k_dyn_mark<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)factor_smem_bytes());
+    configure_mres<2>();
+    configure_mres<4>();
+    configure_mres<8>();
+    configure_mres<16>();
+    configure_mres<32>();
 }
 
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
                   unsigned long long hcond) {
+    if (h->nr) {
+        k_mr_begin<<<dim3(1, h->nr), 1024, 0, h->stream>>>(b, (int)h->m, x0, x, (int)h->n, h->ctl, h->nr,
+                                                           h->mr.grp, use_cond, (cudaGraphConditionalHandle)hcond);
+        return;
+    }
     k_begin<<<1, 1024, 0, h->stream>>>(b, (int)h->m, x0, x, (int)h->n, h->ctl, use_cond,
                                        (cudaGraphConditionalHandle)hcond);
 }
@@ -2558,6 +2921,64 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
     launch_dynamic_tail<T>(h, r, x, ctl, 1, 1, use_cond, hcond, inc);
 }
 
+// R = B - A X for the handle's nr columns (finalize as k_residual's).
+template <typename T, typename V>
+static void mres_launch(rorbk_ctx *h, const Mat<T> &A, const T *B, const T *X, T *R, Ctl *ctl, int finalize) {
+    const dim3 grid(h->mr.grid), block(kMrWarps * 32);
+    const long long rs = h->mr.mpos;
+    unsigned *tick = h->mr.grp + 4;
+    switch (h->nr) {
+        case 2: k_mres<T, V, 2><<<grid, block, mres_smem_bytes<T, 2>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
+        case 4: k_mres<T, V, 4><<<grid, block, mres_smem_bytes<T, 4>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
+        case 8: k_mres<T, V, 8><<<grid, block, mres_smem_bytes<T, 8>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
+        case 16: k_mres<T, V, 16><<<grid, block, mres_smem_bytes<T, 16>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
+        default: k_mres<T, V, 32><<<grid, block, mres_smem_bytes<T, 32>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
+    }
+}
+
+// One iteration for every column of a column-block handle: the sampled
+// updates (one block of threads per column), the residual of all columns in
+// one pass over A, the three top-K levels and the dynamic update (one grid
+// row per column).  grp: the ticket/flag pair of the loop being run.
+template <typename T>
+static void launch_mr_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_cond,
+                                  unsigned long long hcond, unsigned *grp) {
+    Mat<T> A = make_mat<T>(h);
+    const int nr = h->nr, m = (int)h->m, K = h->K;
+    const Cols cl{nr, h->mr.mpos, (int)h->mr.mpos, h->sell.row, h->mr.iperm, grp};
+    cudaStream_t st = h->stream;
+    k_static<T, false, false, true><<<dim3(1, nr), 1024, static_smem_bytes<T>(), st>>>(A, b, x, ctl, -1, 1, 0, nr);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        mres_launch<T, float>(h, A, b, x, r, ctl, 1);
+    } else {
+        if (h->vdtype == RORBK_F32) mres_launch<T, float>(h, A, b, x, r, ctl, 1);
+        else mres_launch<T, double>(h, A, b, x, r, ctl, 1);
+    }
+    const int g = std::max(1, std::min(4 * h->num_sms / nr, (int)((h->mr.mpos + 255) / 256)));
+    k_topk_hist1<T, true><<<dim3(g, nr), 256, 0, st>>>(r, m, K, h->hist1, ctl, cl, 1);
+    k_topk_hist2<T, true><<<dim3(g, nr), 256, 0, st>>>(r, m, K, h->hist2, ctl, 1, cl);
+    k_topk_collect<T, true><<<dim3(std::max(1, g / 2), nr), 512, collect_smem_bytes(), st>>>(
+        r, m, K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1, cl);
+    k_dyn_mark<T, true><<<dim3(std::max(1, h->num_sms / nr), nr), 512, factor_smem_bytes(), st>>>(
+        A, r, dyn_bufs(h), ctl, 1, cl);
+    k_dyn_scatter<T, false, true><<<dim3(std::max(1, 2 * h->num_sms / nr), nr), 512, 0, st>>>(
+        x, (int)h->n, dyn_bufs(h), ctl, 1, use_cond, (cudaGraphConditionalHandle)hcond, cl);
+}
+
+void launch_residual_multi(rorbk_ctx *h, int fp32, const void *B, const void *X, void *R) {
+    const int g = std::max(1, std::min(8 * h->num_sms, (int)((h->mr.mpos * h->nr + 255) / 256)));
+    if (fp32) {
+        mres_launch<float, float>(h, make_mat<float>(h), (const float *)B, (const float *)X, h->r32, h->ctl, 2);
+        if (R) k_mr_unpermute<float><<<g, 256, 0, h->stream>>>(h->r32, h->mr.mpos, h->sell.row, h->nr, (float *)R);
+    } else {
+        if (h->vdtype == RORBK_F32)
+            mres_launch<double, float>(h, make_mat<double>(h), (const double *)B, (const double *)X, h->r, h->ctl, 2);
+        else
+            mres_launch<double, double>(h, make_mat<double>(h), (const double *)B, (const double *)X, h->r, h->ctl, 2);
+        if (R) k_mr_unpermute<double><<<g, 256, 0, h->stream>>>(h->r, h->mr.mpos, h->sell.row, h->nr, (double *)R);
+    }
+}
+
 void launch_weights(rorbk_ctx *h, const double *r) {
     k_wweights<<<std::max(1, std::min(4 * h->num_sms, (h->k + 255) / 256)), 256, 0, h->stream>>>(
         r, h->off, h->k, h->pbar, h->wgt, h->ctl);
@@ -2566,11 +2987,21 @@ void launch_weights(rorbk_ctx *h, const double *r) {
 
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,
                       unsigned long long hcond, int weighted, int inc) {
-    launch_iteration_t<double>(h, b, x, r, h->ctl, use_cond, hcond, weighted, inc);
+    if (h->nr) launch_mr_iteration_t<double>(h, b, x, r, h->ctl, use_cond, hcond, h->mr.grp);
+    else launch_iteration_t<double>(h, b, x, r, h->ctl, use_cond, hcond, weighted, inc);
 }
 
 void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner) {
     Mat<double> A = make_mat<double>(h);
+    if (h->nr) {
+        if (h->vdtype == RORBK_F32) mres_launch<double, float>(h, A, h->bb, h->xb, h->r, h->ctl, 3);
+        else mres_launch<double, double>(h, A, h->bb, h->xb, h->r, h->ctl, 3);
+        const int g = std::max(1, std::min(4 * h->num_sms / h->nr, (int)((std::max<long long>(h->mr.mpos, h->n) + 255) / 256)));
+        k_mr_inner_prep<<<dim3(g, h->nr), 256, 0, h->stream>>>(
+            h->r, h->mr.mpos, h->sell.row, (int)h->mr.mpos, h->b32, h->d32, (int)h->n, h->nr, h->partials,
+            h->ctl, h->ctl_in, h->mr.grp, use_cond, (cudaGraphConditionalHandle)hcond_inner);
+        return;
+    }
     if (h->vdtype == RORBK_F32)
         residual_launch<double, float>(h, A, h->bb, h->xb, h->r, h->ctl, 3);
     else
@@ -2582,10 +3013,17 @@ void launch_mixed_outer(rorbk_ctx *h, int use_cond, unsigned long long hcond_inn
 }
 
 void launch_mixed_inner(rorbk_ctx *h, int use_cond, unsigned long long hcond_inner, int inc) {
-    launch_iteration_t<float>(h, h->b32, h->d32, h->r32, h->ctl_in, use_cond, hcond_inner, 0, inc);
+    if (h->nr) launch_mr_iteration_t<float>(h, h->b32, h->d32, h->r32, h->ctl_in, use_cond, hcond_inner, h->mr.grp + 2);
+    else launch_iteration_t<float>(h, h->b32, h->d32, h->r32, h->ctl_in, use_cond, hcond_inner, 0, inc);
 }
 
 void launch_mixed_update(rorbk_ctx *h, int use_cond, unsigned long long hcond_outer) {
+    if (h->nr) {
+        const int g = std::max(1, std::min(4 * h->num_sms / h->nr, (int)((h->n + 255) / 256)));
+        k_mr_outer_update<<<dim3(g, h->nr), 256, 0, h->stream>>>(h->xb, h->d32, (int)h->n, h->nr, h->ctl, h->ctl_in,
+                                                                h->mr.grp, use_cond, (cudaGraphConditionalHandle)hcond_outer);
+        return;
+    }
     const int g = grid_stream(h, (int)h->n);
     k_outer_update<<<g, 256, 0, h->stream>>>(h->xb, h->d32, (int)h->n, h->ctl, h->ctl_in, use_cond,
                                              (cudaGraphConditionalHandle)hcond_outer);

@@ -229,20 +229,24 @@ static rorbk_status build_graph_mixed(rorbk_ctx *h, cudaGraph_t parent = nullptr
 // of it, so clones share that and own only this.
 static rorbk_status alloc_workspace(rorbk_ctx *h) {
     const int64_t m = h->m, n = h->n;
+    // a column-block handle keeps nr of every per-solve buffer, side by side;
+    // its residual columns span the SELL copy's positions
+    const int64_t nr = std::max(1, h->nr), mr = h->nr ? h->mr.mpos : m;
     cudaStream_t s = h->stream;
-    h->r = (double *)dev_alloc(h, m * sizeof(double));
-    h->xb = (double *)dev_alloc(h, n * sizeof(double));
-    h->bb = (double *)dev_alloc(h, m * sizeof(double));
-    h->partials = (double *)dev_alloc(h, std::max(h->grid_res, 4 * h->num_sms) * sizeof(double) + 64);
+    h->r = (double *)dev_alloc(h, nr * mr * sizeof(double));
+    h->xb = (double *)dev_alloc(h, nr * n * sizeof(double));
+    h->bb = (double *)dev_alloc(h, nr * m * sizeof(double));
+    h->partials = (double *)dev_alloc(h, nr * std::max(std::max(h->grid_res, h->mr.grid), 4 * h->num_sms) *
+                                             sizeof(double) + 64);
     h->sd_scratch = (double *)dev_alloc(h, 2 * kMaxBlockRows * sizeof(double));
     h->wgt = (double *)dev_alloc(h, h->k * sizeof(double));
     h->wcdf = (double *)dev_alloc(h, h->k * sizeof(double));
-    h->hist1 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
-    h->hist2 = (unsigned *)dev_alloc(h, kHistBins * sizeof(unsigned));
-    h->in_list = (int *)dev_alloc(h, std::max(1, h->K) * sizeof(int));
-    h->eq_list = (int *)dev_alloc(h, kEqCap * sizeof(int));
-    h->ctl = (Ctl *)dev_alloc(h, sizeof(Ctl));
-    h->ctl_in = (Ctl *)dev_alloc(h, sizeof(Ctl));
+    h->hist1 = (unsigned *)dev_alloc(h, nr * kHistBins * sizeof(unsigned));
+    h->hist2 = (unsigned *)dev_alloc(h, nr * kHistBins * sizeof(unsigned));
+    h->in_list = (int *)dev_alloc(h, nr * std::max(1, h->K) * sizeof(int));
+    h->eq_list = (int *)dev_alloc(h, nr * kEqCap * sizeof(int));
+    h->ctl = (Ctl *)dev_alloc(h, nr * sizeof(Ctl));
+    h->ctl_in = (Ctl *)dev_alloc(h, nr * sizeof(Ctl));
     {
         auto &D = h->dyn;
         D.ecap = std::max<int64_t>(1, (int64_t)h->K * h->maxrow);
@@ -250,37 +254,37 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         while (np2 < 2 * D.ecap) np2 <<= 1;
         D.pcap = 1;
         while (D.pcap < std::max<int64_t>(16 * D.ecap, 1 << 16)) D.pcap <<= 1;
-        D.I = (int *)dev_alloc(h, h->K * sizeof(int));
-        D.estart = (int *)dev_alloc(h, (h->K + 1) * sizeof(int));
-        D.gdiag = (double *)dev_alloc(h, h->K * sizeof(double));
-        D.y = (double *)dev_alloc(h, h->K * sizeof(double));
-        D.ecol = (int *)dev_alloc(h, D.ecap * sizeof(int));
-        D.eval = (double *)dev_alloc(h, D.ecap * sizeof(double));
-        D.erow = (uint16_t *)dev_alloc(h, D.ecap * sizeof(uint16_t));
-        D.owner = (unsigned long long *)dev_alloc(h, n * sizeof(unsigned long long));
-        D.shared = (unsigned *)dev_alloc(h, n * sizeof(unsigned));
-        D.epoch = (unsigned *)dev_alloc(h, sizeof(unsigned));
-        D.segpos = (int *)dev_alloc(h, n * sizeof(int));
-        D.raw = (unsigned long long *)dev_alloc(h, 2 * D.ecap * sizeof(unsigned long long));
+        D.I = (int *)dev_alloc(h, nr * h->K * sizeof(int));
+        D.estart = (int *)dev_alloc(h, nr * (h->K + 1) * sizeof(int));
+        D.gdiag = (double *)dev_alloc(h, nr * h->K * sizeof(double));
+        D.y = (double *)dev_alloc(h, nr * h->K * sizeof(double));
+        D.ecol = (int *)dev_alloc(h, nr * D.ecap * sizeof(int));
+        D.eval = (double *)dev_alloc(h, nr * D.ecap * sizeof(double));
+        D.erow = (uint16_t *)dev_alloc(h, nr * D.ecap * sizeof(uint16_t));
+        D.owner = (unsigned long long *)dev_alloc(h, nr * n * sizeof(unsigned long long));
+        D.shared = (unsigned *)dev_alloc(h, nr * n * sizeof(unsigned));
+        D.epoch = (unsigned *)dev_alloc(h, nr * sizeof(unsigned));
+        D.segpos = (int *)dev_alloc(h, nr * n * sizeof(int));
+        D.raw = (unsigned long long *)dev_alloc(h, nr * 2 * D.ecap * sizeof(unsigned long long));
         D.skcap = np2;
-        D.skeys = (unsigned long long *)dev_alloc(h, np2 * sizeof(unsigned long long));
-        D.pkeys = (unsigned long long *)dev_alloc(h, D.pcap * sizeof(unsigned long long));
-        D.g = (double *)dev_alloc(h, ((size_t)h->K * (h->K + 1) / 2) * sizeof(double));
+        D.skeys = (unsigned long long *)dev_alloc(h, nr * np2 * sizeof(unsigned long long));
+        D.pkeys = (unsigned long long *)dev_alloc(h, nr * D.pcap * sizeof(unsigned long long));
+        D.g = (double *)dev_alloc(h, nr * ((size_t)h->K * (h->K + 1) / 2) * sizeof(double));
         if (!D.I || !D.estart || !D.gdiag || !D.y || !D.ecol || !D.eval || !D.erow || !D.owner ||
             !D.shared || !D.epoch || !D.segpos || !D.raw || !D.skeys || !D.pkeys || !D.g)
             return fail(h, RORBK_ERR_OOM, "dynamic-block workspace");
-        cudaMemsetAsync(D.owner, 0, n * sizeof(unsigned long long), s);   // epoch 0: never
-        cudaMemsetAsync(D.shared, 0, n * sizeof(unsigned), s);
-        cudaMemsetAsync(D.epoch, 0, sizeof(unsigned), s);
+        cudaMemsetAsync(D.owner, 0, nr * n * sizeof(unsigned long long), s);   // epoch 0: never
+        cudaMemsetAsync(D.shared, 0, nr * n * sizeof(unsigned), s);
+        cudaMemsetAsync(D.epoch, 0, nr * sizeof(unsigned), s);
     }
     if (h->K >= n) {   // the dynamic block in the n x n form: its rows as a dense K x n array, A_I^T r_I
         h->dynw = (double *)dev_alloc(h, ((size_t)h->K * n + n) * sizeof(double));
         if (!h->dynw) return fail(h, RORBK_ERR_OOM, "n x n dynamic workspace");
     }
     if (h->precision_built) {
-        h->r32 = (float *)dev_alloc(h, m * sizeof(float));
-        h->b32 = (float *)dev_alloc(h, m * sizeof(float));
-        h->d32 = (float *)dev_alloc(h, n * sizeof(float));
+        h->r32 = (float *)dev_alloc(h, nr * mr * sizeof(float));
+        h->b32 = (float *)dev_alloc(h, nr * m * sizeof(float));
+        h->d32 = (float *)dev_alloc(h, nr * n * sizeof(float));
         if (!h->r32 || !h->b32 || !h->d32) return fail(h, RORBK_ERR_OOM, "mixed workspace");
         if (h->format == RORBK_FORMAT_DENSE) {
             // tensor-core dynamic Gram: 128 x 128 lower tiles, the column chunks
@@ -297,10 +301,10 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
         !h->hist1 || !h->hist2 || !h->in_list ||
         !h->eq_list || !h->ctl || !h->ctl_in)
         return fail(h, RORBK_ERR_OOM, "workspace");
-    cudaMemsetAsync(h->hist1, 0, kHistBins * sizeof(unsigned), s);
-    cudaMemsetAsync(h->hist2, 0, kHistBins * sizeof(unsigned), s);
-    cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s);
-    cudaMemsetAsync(h->ctl_in, 0, sizeof(Ctl), s);
+    cudaMemsetAsync(h->hist1, 0, nr * kHistBins * sizeof(unsigned), s);
+    cudaMemsetAsync(h->hist2, 0, nr * kHistBins * sizeof(unsigned), s);
+    cudaMemsetAsync(h->ctl, 0, nr * sizeof(Ctl), s);
+    cudaMemsetAsync(h->ctl_in, 0, nr * sizeof(Ctl), s);
     return cuda_check(h, cudaGetLastError(), "workspace");
 }
 
@@ -522,13 +526,16 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
     if (inc && h->K >= h->n)
         return fail(h, RORBK_ERR_UNSUPPORTED,
                     "the incremental residual does not log the n x n form of the dynamic update (K >= n)");
+    if (h->nr && (inc || opt.dist_mode != RORBK_DIST_PAPER))
+        return fail(h, RORBK_ERR_UNSUPPORTED,
+                    "a block of right-hand sides is solved with the paper's draws and the exact residual");
     if (inc) {
         rorbk_status st = ensure_incremental(h);
         if (st) return st;
     }
-    const int64_t m = h->m, n = h->n;
-    cudaMemcpyAsync(h->bb, b, m * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
-    if (x0) cudaMemcpyAsync(h->xb, x0, n * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    const int64_t m = h->m, n = h->n, nr = std::max(1, h->nr);
+    cudaMemcpyAsync(h->bb, b, nr * m * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    if (x0) cudaMemcpyAsync(h->xb, x0, nr * n * sizeof(double), b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
     Ctl c;
     memset(&c, 0, sizeof(c));
     c.maxit = maxit;
@@ -548,24 +555,32 @@ static rorbk_status solve_prepare(rorbk_handle h, const double *b, const double 
     c.log_col = inc ? h->ilog_col : nullptr;
     c.log_val = inc ? h->ilog_val : nullptr;
     c.fault = opt.fault_inject;
-    if (opt.trace && !mixed) {
-        c.trace_cap = opt.trace->capacity;
-        c.tr_tau = (long long *)opt.trace->tau;
-        c.tr_rrn = opt.trace->rrn;
-        c.tr_I = opt.trace->I;
-        c.tr_x = opt.trace->x;
-        c.tr_dyn = opt.trace->dyn;
-    }
+    // one loop state per column; a block of columns reads opt->trace as an
+    // array of nr records, one per column
+    std::vector<Ctl> cs(nr, c);
+    if (opt.trace && !mixed)
+        for (int64_t j = 0; j < nr; ++j) {
+            const rorbk_trace &t = opt.trace[j];
+            cs[j].trace_cap = t.capacity;
+            cs[j].tr_tau = (long long *)t.tau;
+            cs[j].tr_rrn = t.rrn;
+            cs[j].tr_I = t.I;
+            cs[j].tr_x = t.x;
+            cs[j].tr_dyn = t.dyn;
+        }
     // the pageable source is copied before cudaMemcpyAsync returns
-    return cuda_check(h, cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s), "solve prologue");
+    return cuda_check(h, cudaMemcpyAsync(h->ctl, cs.data(), nr * sizeof(Ctl), cudaMemcpyHostToDevice, s),
+                      "solve prologue");
 }
 
 // Enqueues on s the copy of the solution out of the workspace and of the
 // final loop state into *c.
+// (*c holds one loop state per column: nr of them for a block of columns.)
 static cudaError_t solve_collect(rorbk_handle h, double *x, bool x_host, cudaStream_t s, Ctl *c) {
-    cudaError_t e = cudaMemcpyAsync(x, h->xb, h->n * sizeof(double),
+    const int64_t nr = std::max(1, h->nr);
+    cudaError_t e = cudaMemcpyAsync(x, h->xb, nr * h->n * sizeof(double),
                                     x_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c, h->ctl, nr * sizeof(Ctl), cudaMemcpyDeviceToHost, s);
     return e;
 }
 
@@ -584,6 +599,47 @@ static rorbk_status solve_result(rorbk_handle h, const Ctl &c, bool mixed, float
     return st;
 }
 
+// A block of columns: every column's result kept in h->mr.last (and written
+// to res[0 .. nr-1] when res_cols is set); the status is the first error of
+// any column, else NOT_CONVERGED if one stopped at maxit, else OK.  *agg gets
+// the block's summary: the largest iteration count and RRN, converged if all
+// columns converged.
+static rorbk_status solve_results_cols(rorbk_handle h, const Ctl *cs, bool mixed, float ms,
+                                       rorbk_result *res_cols, rorbk_result *agg) {
+    const int nr = h->nr;
+    h->mr.last.assign(nr, rorbk_result{});
+    rorbk_status worst = RORBK_OK;
+    rorbk_result a{};
+    a.converged = 1;
+    for (int j = 0; j < nr; ++j) {
+        const rorbk_status sj = solve_result(h, cs[j], mixed, ms, &h->mr.last[j]);
+        if (sj < 0 && worst >= 0) worst = sj;
+        else if (sj == RORBK_NOT_CONVERGED && worst == RORBK_OK) worst = sj;
+        a.iters = std::max<int64_t>(a.iters, h->mr.last[j].iters);
+        a.rrn = std::max(a.rrn, h->mr.last[j].rrn);
+        a.converged &= h->mr.last[j].converged;
+        a.refinements = std::max<int64_t>(a.refinements, h->mr.last[j].refinements);
+    }
+    a.status = worst;
+    a.time_ms = ms;
+    if (res_cols) std::copy(h->mr.last.begin(), h->mr.last.end(), res_cols);
+    if (agg) *agg = a;
+    return worst;
+}
+
+// The loop flag the host polls: the handle's own stop flag, or for a block of
+// columns the group's "some column runs" flag (inverted on read).
+static const int *halt_flag(rorbk_handle h, bool inner) {
+    if (h->nr) return (const int *)(h->mr.grp + (inner ? 3 : 1));
+    return inner ? &h->ctl_in->halt : &h->ctl->halt;
+}
+static cudaError_t read_halt(rorbk_handle h, bool inner, int *halt, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(halt, halt_flag(h, inner), sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && h->nr) *halt = !*halt;
+    return e;
+}
+
 static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0, bool b_host,
                                double *x, bool x_host, double tol, int64_t maxit,
                                const rorbk_options *opt_in, rorbk_result *res) {
@@ -595,7 +651,8 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
     rorbk_status st;
     if ((st = solve_prepare(h, b, x0, b_host, tol, maxit, opt, s))) return st;
     const bool mixed = opt.precision == RORBK_PREC_MIXED;
-    Ctl c;
+    std::vector<Ctl> cs(std::max(1, h->nr));
+    Ctl &c = cs[0];
     const int weighted = opt.dist_mode == RORBK_DIST_RESIDUAL_WEIGHTED;
     const int inc = opt.residual_mode == RORBK_RESIDUAL_INCREMENTAL;
     cudaGraphExec_t *exec = mixed ? (inc ? &h->exec_mixed_inc : &h->exec_mixed)
@@ -625,63 +682,109 @@ static rorbk_status solve_impl(rorbk_handle h, const double *b, const double *x0
                 launch_weights(h, h->r);
             }
             int64_t launched = 0;
+            if (h->nr) e = read_halt(h, false, &halt, s);
             while (e == cudaSuccess && !halt && launched < maxit) {
                 for (int q = 0; q < poll && launched < maxit; ++q, ++launched)
                     launch_iteration(h, h->bb, h->xb, h->r, 0, 0, weighted, inc);
                 e = cudaGetLastError();
-                if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e == cudaSuccess) e = read_halt(h, false, &halt, s);
             }
         } else {
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) e = read_halt(h, false, &halt, s);
             while (e == cudaSuccess && !halt) {
                 launch_mixed_outer(h, 0, 0);
                 int ihalt = 0;
                 e = cudaGetLastError();
-                if (e == cudaSuccess) e = cudaMemcpyAsync(&ihalt, &h->ctl_in->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e == cudaSuccess) e = read_halt(h, true, &ihalt, s);
                 int odone = 0;
-                if (e == cudaSuccess) e = cudaMemcpy(&odone, &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess && !h->nr) e = cudaMemcpy(&odone, &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost);
                 while (e == cudaSuccess && !ihalt && !odone) {
                     for (int q = 0; q < poll; ++q) launch_mixed_inner(h, 0, 0, inc);
                     e = cudaGetLastError();
-                    if (e == cudaSuccess) e = cudaMemcpyAsync(&ihalt, &h->ctl_in->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
-                    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                    if (e == cudaSuccess) e = read_halt(h, true, &ihalt, s);
                 }
                 if (e == cudaSuccess) launch_mixed_update(h, 0, 0);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(&halt, &h->ctl->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e == cudaSuccess) e = read_halt(h, false, &halt, s);
             }
         }
         h->stream = saved;
     }
     cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = solve_collect(h, x, x_host, s, &c);
+    if (e == cudaSuccess) e = solve_collect(h, x, x_host, s, cs.data());
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     float ms = 0.f;
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if ((st = cuda_check(h, e, "solve"))) return st;
+    if (h->nr) return solve_results_cols(h, cs.data(), mixed, ms, res, nullptr);
     return solve_result(h, c, mixed, ms, res);
 }
 
 rorbk_status rorbk_solve(rorbk_handle h, const double *b, const double *x0, double *x, double tol,
                          int64_t maxit, const rorbk_options *opt, rorbk_result *res) {
+    if (h && h->nr) return fail(h, RORBK_ERR_INVALID_ARG, "a block of right-hand sides: use rorbk_solve_multi");
     return solve_impl(h, b, x0, false, x, false, tol, maxit, opt, res);
 }
 
 rorbk_status rorbk_solve_host(rorbk_handle h, const double *b_host, const double *x0_host,
                               double *x_host, double tol, int64_t maxit, const rorbk_options *opt,
                               rorbk_result *res) {
+    if (h && h->nr) return fail(h, RORBK_ERR_INVALID_ARG, "a block of right-hand sides: use rorbk_solve_multi");
     return solve_impl(h, b_host, x0_host, true, x_host, true, tol, maxit, opt, res);
 }
 
-rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
-    if (!out) return RORBK_ERR_INVALID_ARG;
-    *out = nullptr;
-    if (!src) return RORBK_ERR_INVALID_ARG;
+rorbk_status rorbk_solve_multi(rorbk_handle h, const double *B, const double *X0, double *X, double tol,
+                               int64_t maxit, const rorbk_options *opt, rorbk_result *res) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!h->nr) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_solve_multi: the handle is not a block of right-hand sides");
+    return solve_impl(h, B, X0, false, X, false, tol, maxit, opt, res);
+}
+
+rorbk_status rorbk_solve_multi_host(rorbk_handle h, const double *B_host, const double *X0_host,
+                                    double *X_host, double tol, int64_t maxit, const rorbk_options *opt,
+                                    rorbk_result *res) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!h->nr) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_solve_multi_host: the handle is not a block of right-hand sides");
+    return solve_impl(h, B_host, X0_host, true, X_host, true, tol, maxit, opt, res);
+}
+
+rorbk_status rorbk_residual_multi(rorbk_handle h, int32_t precision, const void *B, const void *X,
+                                  void *R, double *rr_host) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!h->nr) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_residual_multi: not a block of right-hand sides");
+    if (!B || !X) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_residual_multi: NULL B or X");
+    if (precision != RORBK_PREC_FP64 && precision != RORBK_PREC_MIXED)
+        return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_residual_multi: unknown precision");
+    const bool fp32 = precision == RORBK_PREC_MIXED;
+    if (fp32 && !h->precision_built)
+        return fail(h, RORBK_ERR_UNSUPPORTED, "rorbk_residual_multi: the FP32 residual needs a mixed-precision handle");
+    cudaSetDevice(h->device);
+    launch_residual_multi(h, fp32, B, X, R);
+    rorbk_status st = cuda_check(h, cudaGetLastError(), "rorbk_residual_multi");
+    if (st || !rr_host) return st;
+    std::vector<Ctl> cs(h->nr);
+    st = cuda_check(h, cudaMemcpyAsync(cs.data(), h->ctl, h->nr * sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream),
+                    "rorbk_residual_multi");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(h->stream), "rorbk_residual_multi");
+    if (!st)
+        for (int j = 0; j < h->nr; ++j) rr_host[j] = cs[j].rr;
+    return st;
+}
+
+rorbk_status rorbk_multi_results(rorbk_handle h, rorbk_result *res) {
+    if (!h || !res) return RORBK_ERR_INVALID_ARG;
+    if (!h->nr) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_multi_results: not a block of right-hand sides");
+    if ((int)h->mr.last.size() != h->nr) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_multi_results: no solve yet");
+    std::copy(h->mr.last.begin(), h->mr.last.end(), res);
+    return RORBK_OK;
+}
+
+}  // extern "C"
+
+// A handle sharing src's set-up with its own per-solve workspace: one
+// right-hand side (nr = 0, rorbk_clone) or a block of nr (rorbk_multi_create).
+static rorbk_status clone_impl(rorbk_handle src, int nr, rorbk_handle *out) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(src->device);
@@ -697,6 +800,8 @@ rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
     c->allocs.clear();
     c->tmp.clear();
     c->bytes = 0;
+    c->nr = 0;                  // one right-hand side (rorbk_multi_create makes blocks)
+    c->mr = decltype(c->mr)();
     c->exec_fp64 = c->exec_mixed = c->exec_fp64_w = c->exec_fp64_inc = c->exec_mixed_inc = nullptr;
     // the incremental residual's CSC copy and log belong to the handle that
     // built them: a clone builds its own at its first incremental solve
@@ -713,6 +818,25 @@ rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
         cudaSetDevice(cur);
         return e;
     };
+    if (nr) {
+        // the residual columns live in the SELL copy's row order: the
+        // position of every row, the group tickets, one resident wave
+        c->nr = nr;
+        c->mr.mpos = (long long)src->sell.nslices * 32;
+        c->mr.grid = mres_grid(c, nr);
+        std::vector<int> row((size_t)c->mr.mpos), ipos((size_t)c->m, -1);
+        if ((st = cuda_check(c, cudaMemcpy(row.data(), src->sell.row, row.size() * sizeof(int),
+                                           cudaMemcpyDeviceToHost), "rorbk_multi_create")))
+            return bail(st);
+        for (long long p = 0; p < c->mr.mpos; ++p)
+            if (row[p] >= 0) ipos[row[p]] = (int)p;
+        c->mr.iperm = (int *)dev_alloc(c, ipos.size() * sizeof(int));
+        c->mr.grp = (unsigned *)dev_alloc(c, 8 * sizeof(unsigned));
+        if (!c->mr.iperm || !c->mr.grp) return bail(fail(c, RORBK_ERR_OOM, "rorbk_multi_create"));
+        cudaMemcpy(c->mr.iperm, ipos.data(), ipos.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if ((st = cuda_check(c, cudaMemset(c->mr.grp, 0, 8 * sizeof(unsigned)), "rorbk_multi_create")))
+            return bail(st);
+    }
     if ((st = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream")))
         return bail(st);
     if ((st = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking), "stream")))
@@ -724,6 +848,29 @@ rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
     *out = c;
     cudaSetDevice(cur);
     return RORBK_OK;
+}
+
+extern "C" {
+
+rorbk_status rorbk_clone(rorbk_handle src, rorbk_handle *out) {
+    if (!out) return RORBK_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!src) return RORBK_ERR_INVALID_ARG;
+    return clone_impl(src, 0, out);
+}
+
+rorbk_status rorbk_multi_create(rorbk_handle src, int32_t nr, rorbk_handle *out) {
+    if (!out) return RORBK_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!src) return RORBK_ERR_INVALID_ARG;
+    if (nr != 2 && nr != 4 && nr != 8 && nr != 16 && nr != 32)
+        return fail(src, RORBK_ERR_INVALID_ARG, "rorbk_multi_create: nr must be 2, 4, 8, 16 or 32");
+    if (src->nr) return fail(src, RORBK_ERR_INVALID_ARG, "rorbk_multi_create: the source is already a block");
+    if (src->format != RORBK_FORMAT_CSR || src->n_wood || src->K >= src->n || !src->sell.nslices)
+        return fail(src, RORBK_ERR_UNSUPPORTED,
+                    "rorbk_multi_create: sparse (CSR) systems whose blocks and dynamic block have "
+                    "fewer rows than A has columns");
+    return clone_impl(src, nr, out);
 }
 
 rorbk_status rorbk_weighted_cdf(rorbk_handle h, const double *r, double *cdf_host) {
@@ -870,14 +1017,15 @@ rorbk_status rorbk_batch_solve(rorbk_batch bt, const double *const *b, const dou
         if (st) record_setup_error(bt->hs[i]->err);
     }
     if (st) { cudaSetDevice(cur); return st; }
-    std::vector<Ctl> cs(count);
+    std::vector<std::vector<Ctl>> cs(count);
+    for (int i = 0; i < count; ++i) cs[i].resize(std::max(1, bt->hs[i]->nr));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     cudaError_t e = cudaGraphLaunch(bt->exec, s);
     cudaEventRecord(e1, s);
-    for (int i = 0; i < count && e == cudaSuccess; ++i) e = solve_collect(bt->hs[i], x[i], false, s, &cs[i]);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) e = solve_collect(bt->hs[i], x[i], false, s, cs[i].data());
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     float ms = 0.f;
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
@@ -892,7 +1040,9 @@ rorbk_status rorbk_batch_solve(rorbk_batch bt, const double *const *b, const dou
     const bool mixed = opt.precision == RORBK_PREC_MIXED;
     rorbk_status worst = RORBK_OK;
     for (int i = 0; i < count; ++i) {
-        const rorbk_status si = solve_result(bt->hs[i], cs[i], mixed, ms, res ? res + i : nullptr);
+        const rorbk_status si = bt->hs[i]->nr
+                                    ? solve_results_cols(bt->hs[i], cs[i].data(), mixed, ms, nullptr, res ? res + i : nullptr)
+                                    : solve_result(bt->hs[i], cs[i][0], mixed, ms, res ? res + i : nullptr);
         if (si < 0 && worst >= 0) worst = si;
         else if (si == RORBK_NOT_CONVERGED && worst == RORBK_OK) worst = si;
     }

@@ -87,7 +87,8 @@ def _csr_matvec(row_ptr, col_idx, values, x):
     if x.ndim == 1:
         return np.bincount(rows, weights=prod, minlength=len(row_ptr) - 1)
     out = np.zeros((len(row_ptr) - 1, x.shape[1]))
-    np.add.at(out, rows, prod)
+    for j in range(x.shape[1]):
+        out[:, j] = np.bincount(rows, weights=prod[:, j], minlength=len(row_ptr) - 1)
     return out
 
 
@@ -186,6 +187,32 @@ def powerlaw(n: int = 1 << 20, seed: int = 1, num_blocks: int = 4096,
                  col_idx=col_idx, values=values, x_true=x_true, b=b)
     return System(key, n, n, row_ptr=row_ptr, col_idx=col_idx, values=values,
                   x_true=x_true, b=b, num_blocks=num_blocks, lam=lam, tol=tol)
+
+
+def batched_sizes(count: int = 256, nmin: int = 5000, nmax: int = 200000,
+                  seed: int = 42) -> np.ndarray:
+    """Row counts of the batched workload: n ~ U[nmin, nmax] (integers,
+    inclusive), one per system, from ``numpy.random.default_rng(seed)``."""
+    return np.random.default_rng(seed).integers(nmin, nmax + 1, count)
+
+
+def batched_system(i: int, n: int, lam: float = 1e-8, tol: float = 1e-8,
+                   cache: Optional[str] = None) -> System:
+    """System i of the batched workload: the power-law recipe with at most 50
+    off-diagonals per row, generator seed 100 + i, blocks of 256 rows."""
+    return powerlaw(n=int(n), num_blocks=max(1, int(n) // 256), seed=100 + i, dmax=50,
+                    lam=lam, tol=tol, cache=cache)
+
+
+def rhs_block(system: System, nrhs: int, seed: int) -> np.ndarray:
+    """B = A X_true (m x nrhs, row-major, FP64 products of the stored values)
+    for X_true ~ N(0,1) (n x nrhs) from ``numpy.random.default_rng(seed)``;
+    column 0 is the system's own b."""
+    rng = np.random.default_rng(seed)
+    Xt = rng.standard_normal((system.n, nrhs))
+    Bm = _csr_matvec(system.row_ptr, system.col_idx, system.values, Xt)
+    Bm[:, 0] = system.b
+    return np.ascontiguousarray(Bm)
 
 
 def dense_usv(m: int, n: int, seed: int = 2, smin: float = 1e-8,
