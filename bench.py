@@ -73,6 +73,15 @@ def parse():
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched measurement (16 right-hand sides of a 65,536-row "
                         "system, and 16 systems of 5,000-200,000 rows, each in one launch)")
+    p.add_argument("--no-multi-rhs", action="store_true",
+                   help="skip the block of 16 right-hand sides of the main workload (one residual "
+                        "pass over A for all columns), mixed and FP64 to the tolerance")
+    p.add_argument("--no-batched-scale", action="store_true",
+                   help="skip the batched configuration at its stated size (256 power-law "
+                        "systems of 5,000-200,000 rows with 16 right-hand sides each, plus a dense "
+                        "2,048 x 100,000 minimum-norm system, in one graph launch)")
+    p.add_argument("--batch-systems", type=int, default=256)
+    p.add_argument("--dense-wide-lam", type=float, default=1e-10)
     p.add_argument("--no-autograd", action="store_true",
                    help="skip the differentiable-solve measurement (forward + adjoint backward "
                         "on the 262,144-unknown power-law system)")
@@ -482,6 +491,173 @@ def batched_measurement(args):
     for h in hs:
         h.close()
     out["multi_system"] = ms
+    return out
+
+
+def mres_bytes(s, nr, vbytes, xbytes):
+    """Algorithmic bytes of one block residual R = B - A X for nr columns: A's
+    values and column indices once, X read once, B read and R written."""
+    return s.nnz * (vbytes + 4) + nr * xbytes * (s.n + 2 * s.m)
+
+
+def multi_rhs_measurement(args, s, flush, t_single_mixed, t_single_fp64):
+    """16 right-hand sides of the main workload as one block (B = A X_true,
+    column 0 = b, X_true ~ N(0,1) seed 77): every column solved to the
+    tolerance in one graph launch, mixed precision and FP64; each column's
+    FP64 RRN re-checked on the host; the block residual k_mres timed alone
+    (cold L2) against the HBM roofline.  The one-column solve times of the
+    headline give the 16 solves one after another."""
+    import torch
+    import scipy.sparse as sp
+    from paper_2510_02156_gb300 import binding as B
+    from paper_2510_02156_gb300 import workloads as W
+    nr = 16
+    Bm = W.rhs_block(s, nr, seed=77)
+    A = sp.csr_matrix((s.values.astype(np.float64), s.col_idx, s.row_ptr), shape=(s.m, s.n))
+    h0 = B.Handle.from_system(s, precision=B.PREC_MIXED)
+    h = h0.multi(nr)
+    Bd = torch.as_tensor(Bm, device="cuda")
+    out = {"workload": (f"{nr} right-hand sides of the power-law system n={s.n} (B = A X_true, "
+                        f"X_true ~ N(0,1), column 0 = b), one block (rorbk_multi_create), tol={s.tol:g}")}
+    single = {"mixed": t_single_mixed, "fp64": t_single_fp64}
+    for name, prec in (("mixed", B.PREC_MIXED), ("fp64", B.PREC_FP64)):
+        X = torch.zeros((s.n, nr), dtype=torch.float64, device="cuda")
+        h.solve_multi(Bd, X, tol=s.tol, maxit=3, seed=1, precision=prec, inner_tol=args.inner_tol)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = h.solve_multi(Bd, X, tol=s.tol, maxit=args.maxit, seed=1, precision=prec,
+                            inner_tol=args.inner_tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        Xh = X.cpu().numpy()
+        rrn_host = [float(np.linalg.norm(Bm[:, j] - A @ Xh[:, j]) / np.linalg.norm(Bm[:, j]))
+                    for j in range(nr)]
+        its = [int(r.iters) for r in res]
+        out[name] = {"time_s": dt, "device_ms": float(res[0].time_ms), "iters_max": max(its),
+                     "iters_min": min(its), "all_converged": bool(all(r.converged for r in res)),
+                     "rrn_host_max": max(rrn_host),
+                     "sequential_s": nr * single[name] if single[name] else None,
+                     "speedup_vs_sequential": nr * single[name] / dt if single[name] else None,
+                     "sequential_note": f"{nr} x the one-column solve time of this run"}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+    Xm = torch.as_tensor(np.random.default_rng(3).standard_normal((s.n, nr)) * 0.5, device="cuda")
+    B32, X32 = Bd.float(), Xm.float()
+    c32, w32 = time_kernel(lambda: h.residual_multi(B32, X32, None, precision=B.PREC_MIXED, wait=False),
+                           flush, torch)
+    c64, w64 = time_kernel(lambda: h.residual_multi(Bd, Xm, None, wait=False), flush, torch)
+    h.close()
+    h0.close()
+    peak, kind = measured_hbm_peak()
+    by32, by64 = mres_bytes(s, nr, 4, 4), mres_bytes(s, nr, 4, 8)
+    out["roofline_fp32"] = {"bound": "hbm", "kernel": f"k_mres<float,float,{nr}>",
+                            "achieved": by32 / (c32 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": by32 / (c32 * 1e-3) / 1e9 / peak, "bytes_per_launch": by32,
+                            "launch_ms_cold_l2": c32, "launch_ms_warm_l2": w32,
+                            "traffic": profiled_traffic(f"k_mres<float,float,{nr}>", s),
+                            "peak_source": f"{kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
+    out["roofline_fp64"] = {"bound": "hbm", "kernel": f"k_mres<double,float,{nr}>",
+                            "achieved": by64 / (c64 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": by64 / (c64 * 1e-3) / 1e9 / peak, "bytes_per_launch": by64,
+                            "launch_ms_cold_l2": c64, "launch_ms_warm_l2": w64,
+                            "traffic": profiled_traffic(f"k_mres<double,float,{nr}>", s)}
+    return out
+
+
+def _batched_system(a):
+    i, n, lam, tol, cache = a
+    from paper_2510_02156_gb300 import workloads as W
+    return W.batched_system(i, n, lam=lam, tol=tol, cache=cache)
+
+
+def batched_scale_measurement(args, flush):
+    """The batched configuration at its stated size, in one graph launch:
+    256 power-law systems (n ~ U[5000, 200000], 3-50 off-diagonals per row,
+    blocks of 256 rows), each a block of 16 right-hand sides (B = A X_true,
+    X_true ~ N(0,1), column 0 = b), plus a dense wide system m = 2,048,
+    n = 100,000 (A = U diag(s) V^T, s geometric from 1 to 0.1, 8 blocks of 256
+    rows) whose limit from x0 = 0 is the minimum-norm solution (Lemma 2).
+    Every column and the dense system solved to the tolerance, mixed precision;
+    the dense system's distance to A+ b and to range(A^T) is reported."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import torch
+    from paper_2510_02156_gb300 import binding as B
+    from paper_2510_02156_gb300 import workloads as W
+    nr = 16
+    sizes = W.batched_sizes(args.batch_systems)
+    t0 = time.time()
+    with cf.ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)),
+                                mp_context=mp.get_context("spawn")) as ex:
+        systems = list(ex.map(_batched_system, [(i, int(n), args.lam, args.tol, args.cache)
+                                                 for i, n in enumerate(sizes)]))
+    gen_s = time.time() - t0
+    t0 = time.time()
+    handles, blocks, Bs, Xs = [], [], [], []
+    for i, q in enumerate(systems):
+        h = B.Handle.from_system(q, precision=B.PREC_MIXED)
+        blocks.append(h.multi(nr))
+        handles.append(h)
+        # B = A X_true formed on the device (input construction only)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1000 + i)
+        Xt = torch.randn((q.n, nr), generator=g, device="cuda", dtype=torch.float64)
+        At = torch.sparse_csr_tensor(torch.as_tensor(q.row_ptr, device="cuda"),
+                                     torch.as_tensor(q.col_idx.astype(np.int64), device="cuda"),
+                                     torch.as_tensor(q.values.astype(np.float64), device="cuda"),
+                                     size=(q.m, q.n))
+        Bq = (At @ Xt).contiguous()
+        Bq[:, 0] = torch.as_tensor(q.b, device="cuda")
+        Bs.append(Bq)
+        Xs.append(torch.zeros((q.n, nr), dtype=torch.float64, device="cuda"))
+        del At, Xt
+    rows, nnz = int(sum(q.m for q in systems)), int(sum(q.nnz for q in systems))
+    del systems
+    d = W.dense_usv_cuda(2048, 100_000, seed=4, smin=0.1, block_rows=256, lam=args.dense_wide_lam,
+                         tol=args.tol)
+    hd = B.Handle.from_system(d, precision=B.PREC_MIXED)
+    bd = torch.as_tensor(d.b, device="cuda")
+    xd = torch.zeros(d.n, dtype=torch.float64, device="cuda")
+    setup_s = time.time() - t0
+    members = blocks + [hd]
+    bs, xs = Bs + [bd], Xs + [xd]
+    out = {"workload": (f"{len(blocks)} power-law CSR systems, n in [5000, 200000] ({rows} rows, {nnz} nnz "
+                        f"in total), 3-50 off-diagonals per row, blocks of 256 rows, lambda={args.lam:g}, "
+                        f"{nr} right-hand sides each; plus dense A = U diag(s) V^T, 2048 x 100000, s "
+                        f"geometric 1..0.1, 8 blocks of 256 rows, lambda={args.dense_wide_lam:g}; "
+                        f"tol={args.tol:g}; one graph launch"),
+           "generation_s": gen_s, "setup_s": setup_s,
+           "right_hand_sides": len(blocks) * nr + 1}
+    with B.Batch(members, precision=B.PREC_MIXED) as bt:
+        bt.solve(bs, xs, tol=args.tol, maxit=3, seed=1, inner_tol=args.inner_tol)     # warm-up
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st, res = bt.solve(bs, xs, tol=args.tol, maxit=args.maxit, seed=1, inner_tol=args.inner_tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+    cols = [r for m in blocks for r in m.multi_results()]
+    out["mixed"] = {"time_s": dt, "status": int(st),
+                    "all_converged": bool(all(r.converged for r in cols) and res[-1].converged),
+                    "iters_max": int(max(r.iters for r in cols)),
+                    "iters_sum": int(sum(r.iters for r in cols)),
+                    "rhs_solved_per_s": (len(cols) + 1) / dt,
+                    "dense_member": {"iters": int(res[-1].iters), "rrn": float(res[-1].rrn),
+                                     "refinements": int(res[-1].refinements)}}
+    # Lemma 2: from x0 = 0 the iterates stay in range(A^T), so the limit is
+    # the minimum-norm solution A+ b; both checked in FP64 on the device
+    Ad = torch.as_tensor(d.dense, device="cuda")
+    Q, Rf = torch.linalg.qr(Ad.T)               # A^T = Q R: Q spans range(A^T)
+    # A x = R^T Q^T x = b with x = Q y: the minimum-norm solution
+    xmn = (Q @ torch.linalg.solve_triangular(Rf.T, bd.unsqueeze(1), upper=False)).squeeze(1)
+    out["mixed"]["dense_member"]["rel_err_vs_min_norm"] = float(torch.linalg.norm(xd - xmn) / torch.linalg.norm(xmn))
+    out["mixed"]["dense_member"]["off_range_rel"] = float(torch.linalg.norm(xd - Q @ (Q.T @ xd)) / torch.linalg.norm(xd))
+    del Ad, Q, Rf, xmn
+    for m in blocks:
+        m.close()
+    for h in handles:
+        h.close()
+    hd.close()
     return out
 
 

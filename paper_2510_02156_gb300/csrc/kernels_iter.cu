@@ -735,8 +735,12 @@ __global__ void __launch_bounds__(256) k_topk_hist1(const T *__restrict__ r, int
     const int mp = MC ? cl.mpos : m;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += gridDim.x * blockDim.x)
-        if (!MC || !cl.perm || cl.perm[i] >= 0) atomicAdd(&hist[(unsigned)(abs_key(r[i]) >> 52)], 1u);
+    // warp-aggregated: the keys of a residual crowd into few exponent bins
+    for (int i0 = blockIdx.x * blockDim.x; i0 < mp; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool act = i < mp && (!MC || !cl.perm || cl.perm[i] >= 0);
+        hist_add(hist, act ? (unsigned)(abs_key(r[i]) >> 52) : 0u, act);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
         if (hist[i]) atomicAdd(&hist1[i], hist[i]);
@@ -1051,22 +1055,33 @@ __global__ void __launch_bounds__(512) k_dyn_set_rows(const int *rowptr, const i
 }
 
 // ---- factorisation of the coupled rows --------------------------------
+// RC (the mixed form's inner solve, which applies the factor in FP32 and needs
+// no bit-exact factor): the diagonal holds 1 / L_jj, from CUDA's rsqrt, and
+// every division by L_jj becomes a multiplication, so the serial chain of a
+// column takes one rsqrt instead of a square root and a division per entry.
+// The FP64 form (RC = false) keeps L_jj and IEEE square roots and divisions.
+template <bool RC>
+__device__ __forceinline__ double chol_diag(double d) { return RC ? rsqrt(d) : sqrt(d); }
+template <bool RC>
+__device__ __forceinline__ double chol_div(double v, double dg) { return RC ? v * dg : v / dg; }
+
 // Right-looking packed Cholesky (zero multipliers skipped: the same numbers
 // as the dense algorithm).  One block of threads.
+template <bool RC>
 __device__ void packed_cholesky(double *G, int nS, int *bad) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < nS; ++j) {
         if (threadIdx.x == 0) {
             double d = G[pidx(j, j)];
             if (!(d > 0.0)) { *bad = 1; d = 1.0; }
-            G[pidx(j, j)] = sqrt(d);
+            G[pidx(j, j)] = chol_diag<RC>(d);
         }
         __syncthreads();
         const double l = G[pidx(j, j)];
         int any = 0;
         for (int i = j + 1 + threadIdx.x; i < nS; i += blockDim.x) {
             const double v = G[pidx(i, j)];
-            if (v != 0.0) { G[pidx(i, j)] = v / l; any = 1; }
+            if (v != 0.0) { G[pidx(i, j)] = chol_div<RC>(v, l); any = 1; }
         }
         if (!__syncthreads_or(any)) continue;
         for (int a = j + 1 + wid; a < nS; a += nw) {
@@ -1220,6 +1235,7 @@ __device__ __forceinline__ int kth_bit(const unsigned *w, int k) {
     return -1;
 }
 
+template <bool RC>
 __device__ void level_cholesky(double *G, int nS, Sym S, int nlev, int *bad) {
     for (int L = 0; L < nlev; ++L) {
         const int q0 = S.lvl_off[L], q1 = S.lvl_off[L + 1];
@@ -1234,7 +1250,7 @@ __device__ void level_cholesky(double *G, int nS, Sym S, int nlev, int *bad) {
                     v = __fma_rn(-lbj, lbj, v);
                 }
             if (!(v > 0.0)) { *bad = 1; v = 1.0; }
-            G[pidx(b, b)] = sqrt(v);
+            G[pidx(b, b)] = chol_diag<RC>(v);
         }
         __syncthreads();
         const int e0 = S.eoff[q0], e1 = S.eoff[q1];
@@ -1253,7 +1269,7 @@ __device__ void level_cholesky(double *G, int nS, Sym S, int nlev, int *bad) {
                     const int j = wd * 32 + __ffs(w) - 1;
                     v = __fma_rn(-G[pidx(a, j)], G[pidx(b, j)], v);
                 }
-            G[pidx(a, b)] = v / G[pidx(b, b)];
+            G[pidx(a, b)] = chol_div<RC>(v, G[pidx(b, b)]);
         }
         __syncthreads();
     }
@@ -1262,6 +1278,7 @@ __device__ void level_cholesky(double *G, int nS, Sym S, int nlev, int *bad) {
 // z <- L^{-T} L^{-1} z on the coupled rows, by tree levels (forward:
 // ascending levels, row sums over ascending columns; backward: descending
 // levels, sums over descending rows), one thread per row.
+template <bool RC>
 __device__ void level_solve(const double *G, int nS, Sym S, int nlev, double *z) {
     for (int L = 0; L < nlev; ++L) {
         for (int q = S.lvl_off[L] + threadIdx.x; q < S.lvl_off[L + 1]; q += blockDim.x) {
@@ -1273,7 +1290,7 @@ __device__ void level_solve(const double *G, int nS, Sym S, int nlev, double *z)
                     const int j = wd * 32 + __ffs(w) - 1;
                     v = __fma_rn(-G[pidx(b, j)], z[j], v);
                 }
-            z[b] = v / G[pidx(b, b)];
+            z[b] = chol_div<RC>(v, G[pidx(b, b)]);
         }
         __syncthreads();
     }
@@ -1289,13 +1306,14 @@ __device__ void level_solve(const double *G, int nS, Sym S, int nlev, double *z)
                     const int c = wd * 32 + hb;
                     v = __fma_rn(-G[pidx(c, b)], z[c], v);
                 }
-            z[b] = v / G[pidx(b, b)];
+            z[b] = chol_div<RC>(v, G[pidx(b, b)]);
         }
         __syncthreads();
     }
 }
 
 // Column-by-column solves (right-looking order) with zero columns skipped.
+template <bool RC>
 __device__ void column_solve(const double *G, int nS, double *z, unsigned char *cz,
                              unsigned char *rz) {
     const int tid = threadIdx.x;
@@ -1304,7 +1322,7 @@ __device__ void column_solve(const double *G, int nS, double *z, unsigned char *
             if (G[pidx(i, j)] != 0.0) { cz[j] = 1; rz[i] = 1; }
     __syncthreads();
     for (int j = 0; j < nS; ++j) {                       // forward
-        if (tid == 0) z[j] = z[j] / G[pidx(j, j)];
+        if (tid == 0) z[j] = chol_div<RC>(z[j], G[pidx(j, j)]);
         if (!cz[j]) continue;
         __syncthreads();
         const double zj = z[j];
@@ -1316,7 +1334,7 @@ __device__ void column_solve(const double *G, int nS, double *z, unsigned char *
     }
     __syncthreads();
     for (int j = nS - 1; j >= 0; --j) {                  // backward
-        if (tid == 0) z[j] = z[j] / G[pidx(j, j)];
+        if (tid == 0) z[j] = chol_div<RC>(z[j], G[pidx(j, j)]);
         if (!rz[j]) continue;
         __syncthreads();
         const double zj = z[j];
@@ -1337,6 +1355,7 @@ __device__ void column_solve(const double *G, int nS, double *z, unsigned char *
 template <typename T, bool MC>
 __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
                            unsigned long long *dsm, const Cols &cl) {
+    constexpr bool RC = sizeof(T) == sizeof(float);   // the mixed form's inner solve
     __shared__ int s_nsh, s_npk, s_nS, s_bad, s_fill, s_fill2, s_nlev, s_uselev;
     __shared__ int sc[33];
     unsigned long long *sk = dsm;                                   // kShCap
@@ -1462,11 +1481,11 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
         else if (tid == 0) s_uselev = 0;
         __syncthreads();
         if (s_uselev) {
-            level_cholesky(G, nS, S, s_nlev, &s_bad);
-            level_solve(G, nS, S, s_nlev, z);
+            level_cholesky<RC>(G, nS, S, s_nlev, &s_bad);
+            level_solve<RC>(G, nS, S, s_nlev, z);
         } else {
-            packed_cholesky(G, nS, &s_bad);
-            column_solve(G, nS, z, cz, rz);
+            packed_cholesky<RC>(G, nS, &s_bad);
+            column_solve<RC>(G, nS, z, cz, rz);
         }
     }
     for (int q = tid; q < nS; q += blockDim.x) D.y[sidx[q]] = z[q];
@@ -1518,8 +1537,13 @@ __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict_
         g = __dadd_rn(g, A.mu);
         D.gdiag[a] = g;
         if (!(g > 0.0)) { set_status(&ctl->status, kDevNotSpd); g = 1.0; }
-        const double l = sqrt(g);
-        D.y[a] = ((double)r[rpos<MC>(cl, i)] / l) / l;
+        if constexpr (sizeof(T) == sizeof(float)) {    // mixed form: rsqrt, products
+            const double il = rsqrt(g);
+            D.y[a] = ((double)r[rpos<MC>(cl, i)] * il) * il;
+        } else {
+            const double l = sqrt(g);
+            D.y[a] = ((double)r[rpos<MC>(cl, i)] / l) / l;
+        }
     }
     for (int e = gt; e < E; e += gs) {
         int lo = 0, hi = K;                          // last a with estart[a] <= e
@@ -2399,16 +2423,21 @@ __global__ void k_mr_begin(const double *__restrict__ b, int m, const double *__
 }
 
 // R = B - A X for NR columns over the SELL-32 copy of A.  A warp takes a
-// slice of 32 rows; lane l works on column l % NR of rows g * (32 / NR) + l / NR
-// (g = 0 .. NR-1), so the NR lanes of one row read one contiguous row of X.
-// Each (row, column) is one chain over the row's entries in stored order:
-// the arithmetic of k_residual, column by column.  Entry j of the slice's
-// rows is present for the first cnt_j rows (lengths fall within a slice).
-// The sums of squares per column are formed per lane (FP32 inner residual:
-// per slice in FP32, then in FP64), per block in warp order and over the
-// blocks in block order by the last block, which runs the stopping test of
+// slice of 32 rows.  Its lanes load the slice's column indices and values
+// coalesced (lane l for row l, the next entries in flight during the current
+// ones).  For entry j, lane l then works on VEC consecutive columns
+// (l % LPR) * VEC .. + VEC-1 of rows g * RPS + l / LPR (g = 0 .. LPR-1),
+// taking each row's index and value by a warp shuffle, so one 16-byte load
+// brings a lane's VEC values of a row of X and the LPR lanes of a row read the
+// whole row (NR contiguous values) -- a handful of load instructions per
+// entry of the slice for all NR columns.  Each (row, column) is one chain over
+// the row's entries in stored order: the arithmetic of k_residual, column by
+// column.  Entry j is present for the first cnt_j rows (lengths fall within a
+// slice).  The sums of squares per column are formed per lane (FP32 inner
+// residual: per slice in FP32, then in FP64), per block in warp order and over
+// the blocks in block order by the last block, which runs the stopping test of
 // every column still running (finalize 1: the iteration's, 3: the outer
-// residual of the mixed form's refinement).
+// residual of the mixed form's refinement, 2: ||r_j||^2 only).
 template <typename T>
 struct SqAcc;
 template <>
@@ -2422,6 +2451,26 @@ struct SqAcc<float> {
     static __device__ __forceinline__ float add(float s, float r) { return __fmaf_rn(r, r, s); }
 };
 
+// VEC values of T in one aligned load (16 bytes at most).
+template <typename T, int VEC>
+struct VecT {
+    T v[VEC];
+};
+template <typename T, int VEC>
+__device__ __forceinline__ VecT<T, VEC> vload(const T *p) {
+    VecT<T, VEC> r;
+    if constexpr (sizeof(T) * VEC == 16) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        memcpy(&r, &q, 16);
+    } else if constexpr (sizeof(T) * VEC == 8) {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        memcpy(&r, &q, 8);
+    } else {
+        r.v[0] = __ldg(p);
+    }
+    return r;
+}
+
 constexpr int kMrWarps = 8;
 
 template <typename T, int NR>
@@ -2433,71 +2482,118 @@ template <typename T, typename V, int NR>
 __global__ void __launch_bounds__(kMrWarps * 32, 2)
     k_mres(Mat<T> A, const T *__restrict__ B, const T *__restrict__ X, T *__restrict__ R,
            long long rs, double *partials, unsigned *tick, Ctl *ctl0, int finalize) {
-    constexpr int RPS = 32 / NR;            // rows per step
-    constexpr int GC = NR < 8 ? NR : 8;     // steps whose loads are issued together
+    constexpr int VEC = (int)(16 / sizeof(T)) < NR ? (int)(16 / sizeof(T)) : NR;   // columns per lane
+    constexpr int LPR = NR / VEC;           // lanes per row
+    constexpr int RPS = 32 / LPR;           // rows per step; LPR steps cover the slice
+    // entries whose gathers are issued together (two where the registers allow)
+    constexpr int JS = NR * sizeof(T) <= 64 ? 2 : 1;
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ double red[kMrWarps][NR];
     __shared__ int is_last;
     T *stage = (T *)dsm_u64 + (threadIdx.x >> 5) * 32 * (NR + 1);
     const V *__restrict__ val = sell_values<V, T>(A);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int jc = lane % NR, rsub = lane / NR;
+    const int lc = lane % LPR, rsub = lane / LPR;
+    const int c0 = lc * VEC;                // this lane's first column
     const int W = gridDim.x * kMrWarps;
     const int gw = wid * gridDim.x + blockIdx.x;
-    double rr = 0.0;
+    double rr[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) rr[v] = 0.0;
     for (int rnd = 0;; ++rnd) {
         const int sl = rnd * W + ((rnd & 1) ? W - 1 - gw : gw);
         if (sl >= A.nslices) break;
-        const long long base = A.sptr[sl];
+        const long long base = A.sptr[sl] + lane;
         const int L = A.slen[sl];
         const int mylen = A.srlen[sl * 32 + lane];      // lane l holds row l's length
-        T acc[NR];
+        T acc[LPR][VEC];
 #pragma unroll
-        for (int g = 0; g < NR; ++g) acc[g] = T(0);
-        for (int j = 0; j < L; ++j) {
-            const int cnt = __popc(__ballot_sync(0xffffffffu, j < mylen));
-            const long long d0 = base + 32LL * j + rsub;
+        for (int g = 0; g < LPR; ++g)
 #pragma unroll
-            for (int g0 = 0; g0 < NR; g0 += GC) {
-                int c[GC];
-                V a[GC];
-                T xv[GC];
+            for (int v = 0; v < VEC; ++v) acc[g][v] = T(0);
+        // JS entries of the lane's row in registers, the next JS in flight
+        int cc[JS];
+        V ac[JS];
 #pragma unroll
-                for (int u = 0; u < GC; ++u) {
-                    const bool in = (g0 + u) * RPS + rsub < cnt;
-                    c[u] = in ? A.scol[d0 + (g0 + u) * RPS] : 0;
-                    a[u] = in ? val[d0 + (g0 + u) * RPS] : V(0);
+        for (int u = 0; u < JS; ++u) {
+            cc[u] = u < L ? A.scol[base + 32LL * u] : 0;
+            ac[u] = u < L ? val[base + 32LL * u] : V(0);
+        }
+        for (int j0 = 0; j0 < L; j0 += JS) {
+            int cn[JS];
+            V an[JS];
+            int cnt[JS];
+#pragma unroll
+            for (int u = 0; u < JS; ++u) {
+                const int j = j0 + JS + u;
+                cn[u] = j < L ? A.scol[base + 32LL * j] : 0;
+                an[u] = j < L ? val[base + 32LL * j] : V(0);
+                cnt[u] = __popc(__ballot_sync(0xffffffffu, j0 + u < mylen));
+            }
+            VecT<T, VEC> xg[JS][LPR];
+            V ag[JS][LPR];
+#pragma unroll
+            for (int u = 0; u < JS; ++u)
+#pragma unroll
+                for (int g = 0; g < LPR; ++g) {
+                    const int q = g * RPS + rsub;
+                    const int c = __shfl_sync(0xffffffffu, cc[u], q);
+                    ag[u][g] = __shfl_sync(0xffffffffu, ac[u], q);
+                    if (q < cnt[u]) xg[u][g] = vload<T, VEC>(X + (long long)c * NR + c0);
                 }
 #pragma unroll
-                for (int u = 0; u < GC; ++u)
-                    xv[u] = (g0 + u) * RPS + rsub < cnt ? X[(long long)c[u] * NR + jc] : T(0);
+            for (int u = 0; u < JS; ++u)
 #pragma unroll
-                for (int u = 0; u < GC; ++u)
-                    if ((g0 + u) * RPS + rsub < cnt) acc[g0 + u] = Ar<T>::fma(wide<T>(a[u]), xv[u], acc[g0 + u]);
+                for (int g = 0; g < LPR; ++g) {
+                    if (g * RPS + rsub < cnt[u]) {
+                        const T w = wide<T>(ag[u][g]);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[g][v] = Ar<T>::fma(w, xg[u][g].v[v], acc[g][v]);
+                    }
+                }
+#pragma unroll
+            for (int u = 0; u < JS; ++u) {
+                cc[u] = cn[u];
+                ac[u] = an[u];
             }
         }
-        typename SqAcc<T>::type sq = 0;
+        typename SqAcc<T>::type sq[VEC];
 #pragma unroll
-        for (int g = 0; g < NR; ++g) {
+        for (int v = 0; v < VEC; ++v) sq[v] = 0;
+#pragma unroll
+        for (int g = 0; g < LPR; ++g) {
             const int q = g * RPS + rsub;
             const int row = A.srow[sl * 32 + q];
-            T ri = T(0);
-            if (row >= 0) {
-                ri = Ar<T>::sub(B[(long long)row * NR + jc], acc[g]);
-                sq = SqAcc<T>::add(sq, ri);
+            VecT<T, VEC> bv;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) bv.v[v] = T(0);
+            if (row >= 0) bv = vload<T, VEC>(B + (long long)row * NR + c0);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                T ri = T(0);
+                if (row >= 0) {
+                    ri = Ar<T>::sub(bv.v[v], acc[g][v]);
+                    sq[v] = SqAcc<T>::add(sq[v], ri);
+                }
+                stage[q * (NR + 1) + c0 + v] = ri;
             }
-            stage[q * (NR + 1) + jc] = ri;
         }
-        rr += (double)sq;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) rr[v] += (double)sq[v];
         __syncwarp();
 #pragma unroll 4
         for (int c2 = 0; c2 < NR; ++c2) R[c2 * rs + (long long)sl * 32 + lane] = stage[lane * (NR + 1) + c2];
         __syncwarp();
     }
-    // sums of squares: lanes of one column, then warps, then blocks
+    // sums of squares: lanes of one column group, then warps, then blocks
 #pragma unroll
-    for (int o = NR; o < 32; o <<= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
-    if (lane < NR) red[wid][lane] = rr;
+    for (int v = 0; v < VEC; ++v) {
+#pragma unroll
+        for (int o = LPR; o < 32; o <<= 1) rr[v] += __shfl_xor_sync(0xffffffffu, rr[v], o);
+    }
+    if (lane < LPR)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) red[wid][c0 + v] = rr[v];
     __syncthreads();
     if (threadIdx.x < NR) {
         double t = 0.0;

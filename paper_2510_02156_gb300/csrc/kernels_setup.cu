@@ -133,6 +133,77 @@ __global__ void k_block_transpose(const int *__restrict__ rowptr, const int *__r
     }
 }
 
+// A dense A (every entry stored, rows of n entries): block t's column-sorted
+// copy is its transpose -- segment c holds rows 0 .. s-1 of column c in order --
+// and every row of a block with two or more rows shares a column with another
+// (all are coupled).  The same arrays as k_block_transpose, formed by a
+// grid-wide transpose instead of one block of threads ranking every entry
+// (which costs s binary searches per entry: minutes for 256 x 100,000 blocks).
+__global__ void k_block_transpose_dense(const double *__restrict__ val, const int *__restrict__ off,
+                                        int n, int *__restrict__ bt_col, uint16_t *__restrict__ bt_row,
+                                        double *__restrict__ bt_val, int *__restrict__ bt_seg,
+                                        int *__restrict__ nseg_out, unsigned char *__restrict__ coupled,
+                                        int *__restrict__ ncoupled_out) {
+    const int t = blockIdx.y;
+    const int r0 = off[t], s = off[t + 1] - r0;
+    const long long p0 = (long long)r0 * n, E = (long long)s * n;
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long d = gt; d < E; d += gs) {
+        const long long c = d / s;
+        const int a = (int)(d - c * s);
+        bt_col[p0 + d] = (int)c;
+        bt_row[p0 + d] = (uint16_t)a;
+        bt_val[p0 + d] = val[p0 + (long long)a * n + c];
+    }
+    for (long long c = gt; c < n; c += gs) bt_seg[p0 + c] = (int)(p0 + c * s);
+    for (long long a = gt; a < s; a += gs) coupled[r0 + a] = s > 1 ? 1 : 0;
+    if (gt == 0) {
+        nseg_out[t] = n;
+        ncoupled_out[t] = s > 1 ? s : 0;
+    }
+}
+
+// The Gram of every static block of a dense A on its coupled rows (all of
+// them): G_ij = sum over ascending columns of a_ic a_jc, one fused chain from
+// 0 (k_static_ops' merge of two dense rows visits the same columns in the same
+// order), mu added to the diagonal.  Grid (tiles of kSgT x kSgT entries of
+// the lower triangle, blocks); the rows' next kSgC columns are staged in
+// shared memory.  k_static_ops then factors the block without forming G.
+constexpr int kSgT = 16, kSgC = 64;
+__global__ void __launch_bounds__(kSgT * kSgT) k_dense_static_gram(const double *__restrict__ val,
+                                                                   const int *__restrict__ off, int n,
+                                                                   double mu,
+                                                                   const long long *__restrict__ w_ptr,
+                                                                   double *__restrict__ w_ss) {
+    __shared__ double sa[kSgT][kSgC + 1], sb[kSgT][kSgC + 1];
+    const int t = blockIdx.y;
+    const int r0 = off[t], s = off[t + 1] - r0;
+    if (s < 2) return;                          // no coupled rows: W_t is diagonal
+    const int nt = (s + kSgT - 1) / kSgT;
+    int q = blockIdx.x, ti = 0;                 // tile (ti, tj), tj <= ti
+    if (q >= nt * (nt + 1) / 2) return;
+    while (q > ti) { q -= ti + 1; ++ti; }
+    const int tj = q, tid = threadIdx.x;
+    const int ta = tid / kSgT, tb = tid % kSgT;
+    const int a = ti * kSgT + ta, b = tj * kSgT + tb;
+    double acc = 0.0;
+    for (int c0 = 0; c0 < n; c0 += kSgC) {
+        const int w = min(kSgC, n - c0);
+        for (int e = tid; e < kSgT * kSgC; e += blockDim.x) {
+            const int rr = e / kSgC, cc = e % kSgC;
+            const int ra = ti * kSgT + rr, rb = tj * kSgT + rr;
+            sa[rr][cc] = (ra < s && cc < w) ? val[(long long)(r0 + ra) * n + c0 + cc] : 0.0;
+            sb[rr][cc] = (rb < s && cc < w) ? val[(long long)(r0 + rb) * n + c0 + cc] : 0.0;
+        }
+        __syncthreads();
+        if (a < s && b <= a)
+            for (int cc = 0; cc < w; ++cc) acc = __fma_rn(sa[ta][cc], sb[tb][cc], acc);
+        __syncthreads();
+    }
+    if (a < s && b <= a) w_ss[w_ptr[t] + (long long)a * s + b] = a == b ? __dadd_rn(acc, mu) : acc;
+}
+
 // ------------------------------------------------------------ device scans
 // Exclusive scan of n ints in place (n < 2^31), three launches.
 __global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out,
@@ -335,7 +406,7 @@ __global__ void k_static_ops(const int *__restrict__ rowptr, const int *__restri
                              uint16_t *__restrict__ s_idx, int *__restrict__ s_pos,
                              double *__restrict__ w_ss, double *__restrict__ w_diag,
                              double *__restrict__ linv, const long long *__restrict__ wood_ptr,
-                             int *__restrict__ status) {
+                             int *__restrict__ status, int gram_ready) {
     __shared__ int scan_scratch[33];
     __shared__ int bad;
     __shared__ double gdiag[kMaxBlockRows];
@@ -380,8 +451,9 @@ __global__ void k_static_ops(const int *__restrict__ rowptr, const int *__restri
     }
     __syncthreads();
     if (nS > 0) {
-        // G on S: merges of the coupled rows (lower triangle + diagonal)
-        long long pairs = (long long)nS * (nS + 1) / 2;
+        // G on S: merges of the coupled rows (lower triangle + diagonal),
+        // unless k_dense_static_gram formed it already (gram_ready)
+        long long pairs = gram_ready ? 0 : (long long)nS * (nS + 1) / 2;
         for (long long idx = threadIdx.x; idx < pairs; idx += blockDim.x) {
             int i = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
             while ((long long)(i + 1) * (i + 2) / 2 <= idx) ++i;
@@ -625,8 +697,14 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
     if (!h->bt.col || !h->bt.row || !h->bt.val || !h->bt.seg || !h->bt.seg_ptr || !coupled ||
         !ncoupled)
         return fail(h, RORBK_ERR_OOM, "block transpose");
-    k_block_transpose<<<k, 256, 0, s>>>(h->rowptr, h->col, h->val, h->off, h->bt.col, h->bt.row,
-                                        h->bt.val, h->bt.seg, h->bt.seg_ptr, coupled, ncoupled);
+    if (h->format == RORBK_FORMAT_DENSE) {
+        const int gx = std::max(1, std::min(4 * h->num_sms, (int)((h->nnz / k + 255) / 256)));
+        k_block_transpose_dense<<<dim3(gx, k), 256, 0, s>>>(h->val, h->off, n, h->bt.col, h->bt.row, h->bt.val,
+                                                            h->bt.seg, h->bt.seg_ptr, coupled, ncoupled);
+    } else {
+        k_block_transpose<<<k, 256, 0, s>>>(h->rowptr, h->col, h->val, h->off, h->bt.col, h->bt.row,
+                                            h->bt.val, h->bt.seg, h->bt.seg_ptr, coupled, ncoupled);
+    }
     if ((st = cuda_check(h, cudaGetLastError(), "block transpose"))) return st;
 
     // centroids, C row sums, proposal
@@ -703,9 +781,17 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
         cudaMemcpyAsync(h->ops.s_ptr, sptr.data(), (k + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(h->ops.w_ptr, wptr.data(), (k + 1) * sizeof(long long), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(flags, 0, sizeof(int), s);
+        // a dense A: every block's Gram by the grid (the blocks' rows are long)
+        const bool dense_gram = h->format == RORBK_FORMAT_DENSE && !h->n_wood;
+        if (dense_gram) {
+            const int nt = (h->smax + kSgT - 1) / kSgT;
+            k_dense_static_gram<<<dim3(nt * (nt + 1) / 2, k), kSgT * kSgT, 0, s>>>(h->val, h->off, n, h->mu,
+                                                                                 h->ops.w_ptr, h->ops.w_ss);
+        }
         k_static_ops<<<k, 256, 0, s>>>(h->rowptr, h->col, h->val, h->off, h->mu, coupled,
                                        h->ops.s_ptr, h->ops.w_ptr, h->ops.s_idx, h->ops.s_pos,
-                                       h->ops.w_ss, h->ops.w_diag, linv, h->wood_ptr, flags);
+                                       h->ops.w_ss, h->ops.w_diag, linv, h->wood_ptr, flags,
+                                       dense_gram ? 1 : 0);
         double *linv2 = nullptr;
         if (h->n_wood) {
             if (cudaMalloc(&linv2, (size_t)wtot * sizeof(double)) != cudaSuccess) {
