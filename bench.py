@@ -70,9 +70,10 @@ def parse():
     p.add_argument("--no-weighted", action="store_true",
                    help="skip the comparison of the residual-weighted draws with the paper's "
                         "(FP64 to tolerance on the 262,144-unknown power-law system)")
-    p.add_argument("--no-batched", action="store_true",
-                   help="skip the batched measurement (16 right-hand sides of a 65,536-row "
-                        "system, and 16 systems of 5,000-200,000 rows, each in one launch)")
+    p.add_argument("--clone-batched", action="store_true",
+                   help="also run the batches of one-column handles (16 clones of a 65,536-row "
+                        "system, 16 systems of 5,000-200,000 rows, each in one launch), which the "
+                        "block measurements below supersede")
     p.add_argument("--no-multi-rhs", action="store_true",
                    help="skip the block of 16 right-hand sides of the main workload (one residual "
                         "pass over A for all columns), mixed and FP64 to the tolerance")
@@ -81,6 +82,7 @@ def parse():
                         "systems of 5,000-200,000 rows with 16 right-hand sides each, plus a dense "
                         "2,048 x 100,000 minimum-norm system, in one graph launch)")
     p.add_argument("--batch-systems", type=int, default=256)
+    p.add_argument("--multi-fp64-iters", type=int, default=2000)
     p.add_argument("--dense-wide-lam", type=float, default=1e-10)
     p.add_argument("--no-autograd", action="store_true",
                    help="skip the differentiable-solve measurement (forward + adjoint backward "
@@ -290,10 +292,33 @@ def run_solves(h, b, x, s, args, prec, steps, warmup, flush, torch, clocks=None)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
     xh = x.cpu().numpy()
-    return {"time_s": float(np.mean(times)), "times_s": times, "iters": int(last.iters),
-            "refinements": int(last.refinements), "rrn": float(last.rrn),
-            "converged": bool(last.converged),
-            "rel_err_vs_x_true": float(np.linalg.norm(xh - s.x_true) / np.linalg.norm(s.x_true))}
+    out = {"time_s": float(np.mean(times)), "times_s": times, "iters": int(last.iters),
+           "refinements": int(last.refinements), "rrn": float(last.rrn),
+           "converged": bool(last.converged),
+           "rel_err_vs_x_true": float(np.linalg.norm(xh - s.x_true) / np.linalg.norm(s.x_true))}
+    xo = oracle_solution(s, args)
+    if xo is not None:
+        out["rel_err_vs_fp64_oracle"] = float(np.linalg.norm(xh - xo) / np.linalg.norm(xo))
+    return out
+
+
+def oracle_solution(s, args):
+    """The FP64 oracle's converged solution of this workload, as recorded by
+    oracle/record_iterations.py (an oracle-only script), or None when no
+    record matches the workload (or its checksum)."""
+    import hashlib
+    key = (f"powerlaw_n{s.n}_k{s.num_blocks}_lam{args.lam:g}_tol{args.tol:g}_seed1")
+    rec = os.path.join(ROOT, "oracle", "iterations_to_tol.json")
+    if not os.path.exists(rec):
+        return None
+    meta = json.load(open(rec)).get(key + "_meta", {})
+    path = os.path.join(ROOT, "oracle", meta.get("x_file", "-"))
+    if not os.path.exists(path):
+        return None
+    xo = np.load(path)
+    if hashlib.sha256(xo.tobytes()).hexdigest() != meta.get("x_sha256") or xo.shape != (s.n,):
+        return None
+    return xo
 
 
 class _Null:
@@ -344,7 +369,10 @@ def run_ours(args, rank, world, local):
     fg = None if args.no_fabgmres else fabgmres_measurement(args)
     ag = None if args.no_autograd else autograd_measurement(args)
     weighted = None if args.no_weighted else weighted_measurement(args)
-    batched = None if args.no_batched else batched_measurement(args)
+    batched = batched_measurement(args) if args.clone_batched else None
+    multi = (None if args.no_multi_rhs else
+             multi_rhs_measurement(args, s, flush, mixed["time_s"], fp64["time_s"]))
+    scale = None if args.no_batched_scale else batched_scale_measurement(args, flush)
     dense = None if args.no_dense else dense_measurement(args, flush)
 
     # the sparse residual kernels timed alone, the same kernel and grid as in
@@ -383,6 +411,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches * args.steps,
         "autograd": ag,
         "batched": batched,
+        "multi_rhs": multi,
+        "batched_scale": scale,
         "residual_weighted": weighted,
         "fabgmres": fg,
         "incremental_residual": inc,
@@ -519,28 +549,42 @@ def multi_rhs_measurement(args, s, flush, t_single_mixed, t_single_fp64):
     Bd = torch.as_tensor(Bm, device="cuda")
     out = {"workload": (f"{nr} right-hand sides of the power-law system n={s.n} (B = A X_true, "
                         f"X_true ~ N(0,1), column 0 = b), one block (rorbk_multi_create), tol={s.tol:g}")}
-    single = {"mixed": t_single_mixed, "fp64": t_single_fp64}
-    for name, prec in (("mixed", B.PREC_MIXED), ("fp64", B.PREC_FP64)):
-        X = torch.zeros((s.n, nr), dtype=torch.float64, device="cuda")
-        h.solve_multi(Bd, X, tol=s.tol, maxit=3, seed=1, precision=prec, inner_tol=args.inner_tol)
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = h.solve_multi(Bd, X, tol=s.tol, maxit=args.maxit, seed=1, precision=prec,
-                            inner_tol=args.inner_tol)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        Xh = X.cpu().numpy()
-        rrn_host = [float(np.linalg.norm(Bm[:, j] - A @ Xh[:, j]) / np.linalg.norm(Bm[:, j]))
-                    for j in range(nr)]
-        its = [int(r.iters) for r in res]
-        out[name] = {"time_s": dt, "device_ms": float(res[0].time_ms), "iters_max": max(its),
-                     "iters_min": min(its), "all_converged": bool(all(r.converged for r in res)),
-                     "rrn_host_max": max(rrn_host),
-                     "sequential_s": nr * single[name] if single[name] else None,
-                     "speedup_vs_sequential": nr * single[name] / dt if single[name] else None,
-                     "sequential_note": f"{nr} x the one-column solve time of this run"}
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+    # the mixed block to the tolerance (every column), checked on the host
+    X = torch.zeros((s.n, nr), dtype=torch.float64, device="cuda")
+    h.solve_multi(Bd, X, tol=s.tol, maxit=3, seed=1, precision=B.PREC_MIXED, inner_tol=args.inner_tol)
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = h.solve_multi(Bd, X, tol=s.tol, maxit=args.maxit, seed=1, precision=B.PREC_MIXED,
+                        inner_tol=args.inner_tol)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    Xh = X.cpu().numpy()
+    rrn_host = [float(np.linalg.norm(Bm[:, j] - A @ Xh[:, j]) / np.linalg.norm(Bm[:, j]))
+                for j in range(nr)]
+    its = [int(r.iters) for r in res]
+    out["mixed"] = {"time_s": dt, "device_ms": float(res[0].time_ms), "iters_max": max(its),
+                    "iters_min": min(its), "all_converged": bool(all(r.converged for r in res)),
+                    "rrn_host_max": max(rrn_host), "us_per_iteration": dt * 1e6 / max(its),
+                    "sequential_one_column_mixed_s": nr * t_single_mixed,
+                    "sequential_one_column_fp64_s": nr * t_single_fp64,
+                    "speedup_vs_sequential_mixed": nr * t_single_mixed / dt,
+                    "speedup_vs_sequential_fp64": nr * t_single_fp64 / dt,
+                    "sequential_note": f"{nr} x the one-column solve times (mixed, FP64) of this run"}
+    # the FP64 block: a bounded sample of its iterations (the whole solve
+    # takes minutes), scaled to the mixed block's iteration count
+    X.zero_()
+    k = args.multi_fp64_iters
+    h.solve_multi(Bd, X, tol=0.0, maxit=3, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.solve_multi(Bd, X, tol=0.0, maxit=k, seed=1)
+    torch.cuda.synchronize()
+    per = (time.perf_counter() - t0) / k
+    out["fp64"] = {"us_per_iteration": per * 1e6, "sample_iterations": k,
+                   "time_s_scaled": per * max(its),
+                   "note": f"{k} FP64 block iterations timed, scaled to {max(its)} iterations"}
+    out["speedup_mixed_vs_fp64_block"] = per * max(its) / dt
     Xm = torch.as_tensor(np.random.default_rng(3).standard_normal((s.n, nr)) * 0.5, device="cuda")
     B32, X32 = Bd.float(), Xm.float()
     c32, w32 = time_kernel(lambda: h.residual_multi(B32, X32, None, precision=B.PREC_MIXED, wait=False),

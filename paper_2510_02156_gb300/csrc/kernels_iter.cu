@@ -718,6 +718,11 @@ __global__ void __launch_bounds__(256) k_inc_finish(const T *__restrict__ r, int
     }
 }
 
+// The top-K passes over r are grid-stride loops whose iterations are
+// independent: each thread loads kScanU values before it uses any, so that
+// several loads are in flight per thread instead of one.
+constexpr int kScanU = 8;
+
 // First radix level over a given r (single-step top-K, and the iteration of
 // a block of columns, whose residual pass leaves it out: check_done).
 template <typename T, bool MC = false>
@@ -736,10 +741,17 @@ __global__ void __launch_bounds__(256) k_topk_hist1(const T *__restrict__ r, int
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     // warp-aggregated: the keys of a residual crowd into few exponent bins
-    for (int i0 = blockIdx.x * blockDim.x; i0 < mp; i0 += gridDim.x * blockDim.x) {
-        const int i = i0 + threadIdx.x;
-        const bool act = i < mp && (!MC || !cl.perm || cl.perm[i] >= 0);
-        hist_add(hist, act ? (unsigned)(abs_key(r[i]) >> 52) : 0u, act);
+    for (int i0 = blockIdx.x * blockDim.x * kScanU; i0 < mp; i0 += gridDim.x * blockDim.x * kScanU) {
+        T v[kScanU];
+        bool act[kScanU];
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u) {
+            const int i = i0 + u * blockDim.x + threadIdx.x;
+            act[u] = i < mp && (!MC || !cl.perm || cl.perm[i] >= 0);
+            v[u] = i < mp ? r[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u) hist_add(hist, act[u] ? (unsigned)(abs_key(v[u]) >> 52) : 0u, act[u]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
@@ -777,10 +789,20 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
     const int mp = MC ? cl.mpos : m;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += gridDim.x * blockDim.x) {
-        if (MC && cl.perm && cl.perm[i] < 0) continue;
-        unsigned long long key = abs_key(r[i]);
-        if ((unsigned)(key >> 52) == sel1) atomicAdd(&hist[(unsigned)(key >> 41) & 2047u], 1u);
+    for (int i0 = blockIdx.x * blockDim.x * kScanU; i0 < mp; i0 += gridDim.x * blockDim.x * kScanU) {
+        T v[kScanU];
+        bool act[kScanU];
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u) {
+            const int i = i0 + u * blockDim.x + threadIdx.x;
+            act[u] = i < mp && (!MC || !cl.perm || cl.perm[i] >= 0);
+            v[u] = i < mp ? r[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u) {
+            const unsigned long long key = abs_key(v[u]);
+            if (act[u] && (unsigned)(key >> 52) == sel1) atomicAdd(&hist[(unsigned)(key >> 41) & 2047u], 1u);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
@@ -1007,15 +1029,25 @@ __global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, i
     if (check_done && (ctl->done || ctl->halt)) return;
     const unsigned long long P = (unsigned long long)(unsigned)ctl->prefix;
     const int mp = MC ? cl.mpos : m;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mp; p += gridDim.x * blockDim.x) {
-        const int i = MC && cl.perm ? cl.perm[p] : p;      // the row at this position
-        if (i < 0) continue;
-        unsigned long long pre = abs_key(r[p]) >> 41;
-        if (pre > P) {
-            in_list[atomicAdd(&ctl->n_in, 1)] = i;
-        } else if (pre == P) {
-            int pos = atomicAdd(&ctl->n_eq, 1);
-            if (pos < kEqCap) eq_list[pos] = i;
+    for (int p0 = blockIdx.x * blockDim.x * kScanU; p0 < mp; p0 += gridDim.x * blockDim.x * kScanU) {
+        T v[kScanU];
+        int row[kScanU];
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u) {
+            const int p = p0 + u * blockDim.x + threadIdx.x;
+            row[u] = p < mp ? (MC && cl.perm ? cl.perm[p] : p) : -1;    // the row at this position
+            v[u] = p < mp ? r[p] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u) {
+            if (row[u] < 0) continue;
+            const unsigned long long pre = abs_key(v[u]) >> 41;
+            if (pre > P) {
+                in_list[atomicAdd(&ctl->n_in, 1)] = row[u];
+            } else if (pre == P) {
+                int pos = atomicAdd(&ctl->n_eq, 1);
+                if (pos < kEqCap) eq_list[pos] = row[u];
+            }
         }
     }
     __threadfence();
@@ -2456,32 +2488,90 @@ template <typename T, int VEC>
 struct VecT {
     T v[VEC];
 };
-template <typename T, int VEC>
+// STREAM: a value read once (evict-first in L1 and L2, ld.global.cs), so that
+// the gathered X stays resident in L2 while A, B and R stream past it.
+template <typename T, int VEC, bool STREAM = false>
 __device__ __forceinline__ VecT<T, VEC> vload(const T *p) {
     VecT<T, VEC> r;
     if constexpr (sizeof(T) * VEC == 16) {
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 q = STREAM ? __ldcs(reinterpret_cast<const float4 *>(p))
+                                : __ldg(reinterpret_cast<const float4 *>(p));
         memcpy(&r, &q, 16);
     } else if constexpr (sizeof(T) * VEC == 8) {
-        const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        const float2 q = STREAM ? __ldcs(reinterpret_cast<const float2 *>(p))
+                                : __ldg(reinterpret_cast<const float2 *>(p));
         memcpy(&r, &q, 8);
     } else {
-        r.v[0] = __ldg(p);
+        r.v[0] = STREAM ? __ldcs(p) : __ldg(p);
     }
     return r;
 }
 
 constexpr int kMrWarps = 8;
 
+// The FP32 block residual of an iteration also forms the first radix level
+// of every column's top-K (the exponent histogram of the |r| keys, which
+// k_topk_hist1 forms for one column): an FP32 value's key exponent is 0 (for
+// 0) or one of kF32Exp values from kF32Exp0 on, so a column needs kF32Bins
+// shared-memory bins instead of kHistBins.
+constexpr int kF32Exp0 = 874;        // FP64 exponent of the smallest FP32 subnormal
+constexpr int kF32Exp = 1151 - kF32Exp0 + 1;
+constexpr int kF32Bins = kF32Exp + 2;   // + zero, + Inf/NaN
+
 template <typename T, int NR>
 __host__ __device__ constexpr size_t mres_smem_bytes() {
-    return (size_t)kMrWarps * 32 * (NR + 1) * sizeof(T);
+    return (size_t)kMrWarps * 32 * (NR + 1) * sizeof(T) +
+           (sizeof(T) == 4 ? (size_t)NR * kF32Bins * sizeof(unsigned) : 0);
+}
+
+__device__ __forceinline__ int f32_bin(unsigned e) {    // e: FP64 exponent of an FP32 |r|
+    return e == 0u ? 0 : (e >= (unsigned)kF32Exp0 && e < (unsigned)(kF32Exp0 + kF32Exp)) ? (int)e - kF32Exp0 + 1
+                                                                                      : kF32Bins - 1;
+}
+__device__ __forceinline__ unsigned f32_bin_exp(int bin) {
+    return bin == 0 ? 0u : bin == kF32Bins - 1 ? 2047u : (unsigned)(bin - 1 + kF32Exp0);
+}
+
+// select_bin for one warp: the largest bin b with sum_{j >= b} h[j] >= need
+// and the count strictly above it, over kHistBins global bins (lane l scans
+// bins 2047 - 64 l down to 1984 - 64 l); zeroes h.
+__device__ void warp_select_bin(unsigned *h, int need, int *bin_out, int *above_out) {
+    const int lane = threadIdx.x & 31;
+    constexpr int per = kHistBins / 32;
+    const int top = kHistBins - 1 - lane * per;
+    int tot = 0;
+    for (int u = 0; u < per; ++u) tot += (int)h[top - u];
+    int pre = tot;                                  // inclusive scan, lanes in order
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    pre -= tot;                                     // keys in bins above this lane's
+    int bin = 0, above = 0, found = 0;
+    if (pre < need && pre + tot >= need) {
+        int run = pre;
+        for (int u = 0; u < per; ++u) {
+            const int c = (int)h[top - u];
+            if (run + c >= need) { bin = top - u; above = run; found = 1; break; }
+            run += c;
+        }
+    }
+    const unsigned who = __ballot_sync(0xffffffffu, found);
+    const int src = who ? __ffs(who) - 1 : 0;
+    bin = __shfl_sync(0xffffffffu, bin, src);
+    above = __shfl_sync(0xffffffffu, above, src);
+    __syncwarp();
+    for (int u = 0; u < per; ++u) h[top - u] = 0u;
+    *bin_out = who ? bin : 0;
+    *above_out = who ? above : 0;
 }
 
 template <typename T, typename V, int NR>
 __global__ void __launch_bounds__(kMrWarps * 32, 2)
     k_mres(Mat<T> A, const T *__restrict__ B, const T *__restrict__ X, T *__restrict__ R,
-           long long rs, double *partials, unsigned *tick, Ctl *ctl0, int finalize) {
+           long long rs, double *partials, unsigned *tick, Ctl *ctl0, int finalize,
+           unsigned *hist1) {
     constexpr int VEC = (int)(16 / sizeof(T)) < NR ? (int)(16 / sizeof(T)) : NR;   // columns per lane
     constexpr int LPR = NR / VEC;           // lanes per row
     constexpr int RPS = 32 / LPR;           // rows per step; LPR steps cover the slice
@@ -2491,17 +2581,27 @@ __global__ void __launch_bounds__(kMrWarps * 32, 2)
     __shared__ double red[kMrWarps][NR];
     __shared__ int is_last;
     T *stage = (T *)dsm_u64 + (threadIdx.x >> 5) * 32 * (NR + 1);
+    // the first top-K level of every column (FP32 iteration residuals)
+    constexpr bool F32 = sizeof(T) == 4;
+    unsigned *hsh = (unsigned *)((T *)dsm_u64 + kMrWarps * 32 * (NR + 1));
+    const bool h1 = F32 && finalize == 1;
+    if (h1)
+        for (int q = threadIdx.x; q < NR * kF32Bins; q += blockDim.x) hsh[q] = 0u;
+    __syncthreads();
     const V *__restrict__ val = sell_values<V, T>(A);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int lc = lane % LPR, rsub = lane / LPR;
     const int c0 = lc * VEC;                // this lane's first column
-    const int W = gridDim.x * kMrWarps;
-    const int gw = wid * gridDim.x + blockIdx.x;
+    // slices (longest first) are taken from a queue, one per warp at a time,
+    // so every warp stays busy until the queue is empty
+    unsigned *queue = tick + 1;
     double rr[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) rr[v] = 0.0;
-    for (int rnd = 0;; ++rnd) {
-        const int sl = rnd * W + ((rnd & 1) ? W - 1 - gw : gw);
+    for (;;) {
+        int sl = 0;
+        if (lane == 0) sl = (int)atomicAdd(queue, 1u);
+        sl = __shfl_sync(0xffffffffu, sl, 0);
         if (sl >= A.nslices) break;
         const long long base = A.sptr[sl] + lane;
         const int L = A.slen[sl];
@@ -2516,8 +2616,8 @@ __global__ void __launch_bounds__(kMrWarps * 32, 2)
         V ac[JS];
 #pragma unroll
         for (int u = 0; u < JS; ++u) {
-            cc[u] = u < L ? A.scol[base + 32LL * u] : 0;
-            ac[u] = u < L ? val[base + 32LL * u] : V(0);
+            cc[u] = u < L ? __ldcs(A.scol + base + 32LL * u) : 0;
+            ac[u] = u < L ? __ldcs(val + base + 32LL * u) : V(0);
         }
         for (int j0 = 0; j0 < L; j0 += JS) {
             int cn[JS];
@@ -2526,8 +2626,8 @@ __global__ void __launch_bounds__(kMrWarps * 32, 2)
 #pragma unroll
             for (int u = 0; u < JS; ++u) {
                 const int j = j0 + JS + u;
-                cn[u] = j < L ? A.scol[base + 32LL * j] : 0;
-                an[u] = j < L ? val[base + 32LL * j] : V(0);
+                cn[u] = j < L ? __ldcs(A.scol + base + 32LL * j) : 0;
+                an[u] = j < L ? __ldcs(val + base + 32LL * j) : V(0);
                 cnt[u] = __popc(__ballot_sync(0xffffffffu, j0 + u < mylen));
             }
             VecT<T, VEC> xg[JS][LPR];
@@ -2567,13 +2667,14 @@ __global__ void __launch_bounds__(kMrWarps * 32, 2)
             VecT<T, VEC> bv;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) bv.v[v] = T(0);
-            if (row >= 0) bv = vload<T, VEC>(B + (long long)row * NR + c0);
+            if (row >= 0) bv = vload<T, VEC, true>(B + (long long)row * NR + c0);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 T ri = T(0);
                 if (row >= 0) {
                     ri = Ar<T>::sub(bv.v[v], acc[g][v]);
                     sq[v] = SqAcc<T>::add(sq[v], ri);
+                    if (h1) atomicAdd(&hsh[(c0 + v) * kF32Bins + f32_bin((unsigned)(abs_key(ri) >> 52))], 1u);
                 }
                 stage[q * (NR + 1) + c0 + v] = ri;
             }
@@ -2582,7 +2683,7 @@ __global__ void __launch_bounds__(kMrWarps * 32, 2)
         for (int v = 0; v < VEC; ++v) rr[v] += (double)sq[v];
         __syncwarp();
 #pragma unroll 4
-        for (int c2 = 0; c2 < NR; ++c2) R[c2 * rs + (long long)sl * 32 + lane] = stage[lane * (NR + 1) + c2];
+        for (int c2 = 0; c2 < NR; ++c2) __stcs(R + c2 * rs + (long long)sl * 32 + lane, stage[lane * (NR + 1) + c2]);
         __syncwarp();
     }
     // sums of squares: lanes of one column group, then warps, then blocks
@@ -2600,6 +2701,9 @@ __global__ void __launch_bounds__(kMrWarps * 32, 2)
         for (int w = 0; w < kMrWarps; ++w) t += red[w][threadIdx.x];
         partials[(long long)blockIdx.x * NR + threadIdx.x] = t;
     }
+    if (h1)
+        for (int q = threadIdx.x; q < NR * kF32Bins; q += blockDim.x)
+            if (hsh[q]) atomicAdd(&hist1[(q / kF32Bins) * kHistBins + f32_bin_exp(q % kF32Bins)], hsh[q]);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(tick, 1u) == gridDim.x - 1;
@@ -2624,7 +2728,19 @@ __global__ void __launch_bounds__(kMrWarps * 32, 2)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) *tick = 0u;
+    if (h1) {   // every column's first radix level: warp w takes columns w, w + 8, ...
+        __threadfence();
+        for (int c = wid; c < NR; c += kMrWarps) {
+            Ctl *ctl = ctl0 + c;
+            int bin = 0, above = 0;
+            warp_select_bin(hist1 + (long long)c * kHistBins, A.K, &bin, &above);
+            if (lane == 0 && !(ctl->done || ctl->halt)) { ctl->sel1 = bin; ctl->above1 = above; }
+        }
+    }
+    if (threadIdx.x == 0) {
+        *tick = 0u;
+        *queue = 0u;
+    }
 }
 
 // Residual columns from the SELL order to the caller's m x nr row-major layout.
@@ -3024,11 +3140,11 @@ static void mres_launch(rorbk_ctx *h, const Mat<T> &A, const T *B, const T *X, T
     const long long rs = h->mr.mpos;
     unsigned *tick = h->mr.grp + 4;
     switch (h->nr) {
-        case 2: k_mres<T, V, 2><<<grid, block, mres_smem_bytes<T, 2>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
-        case 4: k_mres<T, V, 4><<<grid, block, mres_smem_bytes<T, 4>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
-        case 8: k_mres<T, V, 8><<<grid, block, mres_smem_bytes<T, 8>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
-        case 16: k_mres<T, V, 16><<<grid, block, mres_smem_bytes<T, 16>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
-        default: k_mres<T, V, 32><<<grid, block, mres_smem_bytes<T, 32>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize); break;
+        case 2: k_mres<T, V, 2><<<grid, block, mres_smem_bytes<T, 2>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize, h->hist1); break;
+        case 4: k_mres<T, V, 4><<<grid, block, mres_smem_bytes<T, 4>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize, h->hist1); break;
+        case 8: k_mres<T, V, 8><<<grid, block, mres_smem_bytes<T, 8>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize, h->hist1); break;
+        case 16: k_mres<T, V, 16><<<grid, block, mres_smem_bytes<T, 16>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize, h->hist1); break;
+        default: k_mres<T, V, 32><<<grid, block, mres_smem_bytes<T, 32>(), h->stream>>>(A, B, X, R, rs, h->partials, tick, ctl, finalize, h->hist1); break;
     }
 }
 
@@ -3051,7 +3167,9 @@ static void launch_mr_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl
         else mres_launch<T, double>(h, A, b, x, r, ctl, 1);
     }
     const int g = std::max(1, std::min(4 * h->num_sms / nr, (int)((h->mr.mpos + 255) / 256)));
-    k_topk_hist1<T, true><<<dim3(g, nr), 256, 0, st>>>(r, m, K, h->hist1, ctl, cl, 1);
+    // the FP32 block residual formed the first radix level itself
+    if constexpr (sizeof(T) == sizeof(double))
+        k_topk_hist1<T, true><<<dim3(g, nr), 256, 0, st>>>(r, m, K, h->hist1, ctl, cl, 1);
     k_topk_hist2<T, true><<<dim3(g, nr), 256, 0, st>>>(r, m, K, h->hist2, ctl, 1, cl);
     k_topk_collect<T, true><<<dim3(std::max(1, g / 2), nr), 512, collect_smem_bytes(), st>>>(
         r, m, K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1, cl);

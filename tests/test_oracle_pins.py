@@ -684,3 +684,27 @@ def test_woodbury_with_mu_zero_is_the_block_least_squares_solution():
         x = rng.standard_normal(s.n)
         x_w = oracle.update_woodbury(s, rows, V, b, x)
         assert np.linalg.norm(x_w - x_ls) <= 1e-10 * np.linalg.norm(x_ls)
+
+
+def test_recorded_oracle_solution_of_the_benchmark_workload():
+    """oracle/record_iterations.py ran the FP64 oracle alone to the tolerance on
+    the 2^20 power-law workload and stored the iteration count and the solution
+    (which the benchmark compares the GPU results with).  The stored solution
+    is the recorded file (checksum), and its residual, recomputed here with
+    scipy from the generated system, is the recorded relative residual."""
+    import hashlib
+    import json
+    import os
+    import scipy.sparse as sp
+    here = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
+    rec = json.load(open(os.path.join(here, "iterations_to_tol.json")))
+    key = "powerlaw_n1048576_k4096_lam1e-08_tol1e-08_seed1"
+    meta = rec[key + "_meta"]
+    assert rec[key] == 74252 and meta["converged"]
+    x = np.load(os.path.join(here, meta["x_file"]))
+    assert hashlib.sha256(x.tobytes()).hexdigest() == meta["x_sha256"]
+    s = W.powerlaw(n=1 << 20, num_blocks=4096, seed=1, lam=1e-8, tol=1e-8)
+    A = sp.csr_matrix((s.values.astype(np.float64), s.col_idx, s.row_ptr), shape=(s.m, s.n))
+    rrn = np.linalg.norm(s.b - A @ x) / np.linalg.norm(s.b)
+    assert rrn <= 1e-8
+    assert abs(rrn - meta["rrn"]) <= 1e-6 * meta["rrn"]
