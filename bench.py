@@ -83,6 +83,8 @@ def parse():
                         "2,048 x 100,000 minimum-norm system, in one graph launch)")
     p.add_argument("--batch-systems", type=int, default=256)
     p.add_argument("--multi-fp64-iters", type=int, default=2000)
+    p.add_argument("--tune-iters", type=int, default=100,
+                   help="iterations per candidate of rorbk_autotune before the timed solves")
     p.add_argument("--dense-wide-lam", type=float, default=1e-10)
     p.add_argument("--no-autograd", action="store_true",
                    help="skip the differentiable-solve measurement (forward + adjoint backward "
@@ -95,6 +97,10 @@ def parse():
                         "25,600 x 2,048 Gaussian system with 100 blocks of 256 rows (the K, s "
                         "and n of the 200,000 x 2,048 workload) in the given precision; "
                         "prints no JSON")
+    p.add_argument("--profile-multi", type=int, default=0,
+                   help="profiling run of a block of 16 right-hand sides of the main workload: "
+                        "three block residuals alone (FP32), then N host-driven iterations of the "
+                        "mixed form's inner solve; prints no JSON")
     p.add_argument("--cache", default=os.path.join(ROOT, ".cache"))
     return p.parse_args()
 
@@ -346,6 +352,10 @@ def run_ours(args, rank, world, local):
     b = torch.as_tensor(s.b, device="cuda")
     x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # launch shapes chosen by measurement for the mixed form's inner iteration
+    # (rorbk_autotune; grids that leave every result unchanged)
+    tune = h.autotune(b, precision=B.PREC_MIXED, iters=args.tune_iters)
+    tuning = tuning_dict(tune)
     if dist:
         dist.barrier()
     clk = ClockSampler(local)
@@ -404,7 +414,7 @@ def run_ours(args, rank, world, local):
         "config": config(args, s, {"precision": "mixed (headline) and fp64",
                                    "inner_tol": args.inner_tol,
                                    "solves_per_s_all_ranks": world / t_step}),
-        "mixed": mixed, "fp64": fp64,
+        "mixed": mixed, "fp64": fp64, "autotune": tuning,
         "speedup_mixed_vs_fp64": fp64["time_s"] / mixed["time_s"],
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * s.m,
                 "d2h_bytes_per_step": 8 * s.n},
@@ -524,6 +534,14 @@ def batched_measurement(args):
     return out
 
 
+def tuning_dict(t):
+    """The launch shapes rorbk_autotune chose, and its per-iteration times."""
+    return {"topk_blocks": t.topk_blocks, "collect_blocks": t.collect_blocks,
+            "dyn_mark_blocks": t.dyn_mark_blocks, "dyn_scatter_blocks": t.dyn_scatter_blocks,
+            "residual_blocks": t.residual_blocks, "us_per_iteration_default": t.us_default,
+            "us_per_iteration_tuned": t.us_tuned}
+
+
 def mres_bytes(s, nr, vbytes, xbytes):
     """Algorithmic bytes of one block residual R = B - A X for nr columns: A's
     values and column indices once, X read once, B read and R written."""
@@ -549,6 +567,7 @@ def multi_rhs_measurement(args, s, flush, t_single_mixed, t_single_fp64):
     Bd = torch.as_tensor(Bm, device="cuda")
     out = {"workload": (f"{nr} right-hand sides of the power-law system n={s.n} (B = A X_true, "
                         f"X_true ~ N(0,1), column 0 = b), one block (rorbk_multi_create), tol={s.tol:g}")}
+    out["autotune"] = tuning_dict(h.autotune(Bd, precision=B.PREC_MIXED, iters=args.tune_iters))
     # the mixed block to the tolerance (every column), checked on the host
     X = torch.zeros((s.n, nr), dtype=torch.float64, device="cuda")
     h.solve_multi(Bd, X, tol=s.tol, maxit=3, seed=1, precision=B.PREC_MIXED, inner_tol=args.inner_tol)
@@ -882,10 +901,24 @@ def autograd_measurement(args):
             "converged": bool(f.converged and a.converged)}
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), or the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def oracle_per_iteration(s, iters):
-    """Seconds per iteration of the FP64 oracle on this solve (1 host core),
-    from a bounded run of `iters` iterations; the oracle's set-up
-    (orthogonality) is timed separately and removed."""
+    """Seconds per iteration of the FP64 oracle on this solve (its residual and
+    top-K on all host cores, the block solves on one), from a bounded run of
+    `iters` iterations; the oracle's set-up (orthogonality) is timed
+    separately and removed."""
     import oracle
     t0 = time.perf_counter()
     res = oracle.solve(s, maxit=iters, tol=0.0, seed=1)
@@ -897,10 +930,14 @@ def oracle_per_iteration(s, iters):
 
 
 def cpu_baseline(s, args, iters_to_tol):
+    import oracle
     per_it, done = oracle_per_iteration(s, args.oracle_iters)
-    return {"value": per_it * iters_to_tol, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"{done} FP64 oracle iterations of this solve on 1 host core "
-                       f"({per_it * 1e3:.1f} ms/iteration, set-up excluded), scaled to the "
+    cores = oracle.thread_count(s.m)
+    return {"value": per_it * iters_to_tol, "unit": "s", "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": (f"{done} FP64 oracle iterations of this solve from x0 = 0 (residual and "
+                       f"top-K on {cores} host threads, block solves on one; "
+                       f"{per_it * 1e3:.1f} ms/iteration, set-up excluded), scaled to the "
                        f"{iters_to_tol} iterations the solve takes")}
 
 
@@ -921,23 +958,35 @@ def run_reference(args, rank, world, local):
         return
     s = workload(args, 0)
     iters, src = reference_iterations(args)
-    per = []
+    import oracle
+    per, walls = [], []
     for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         per_it, done = oracle_per_iteration(s, args.oracle_iters)
+        walls.append(time.perf_counter() - t0)
         per.append(per_it)
     per_it = float(np.mean(per[args.warmup:]))
+    step_s = float(np.mean(walls[args.warmup:]))
+    cores = oracle.thread_count(s.m)
     if iters is None:
         print(json.dumps({"impl": "reference",
                           "unavailable": "the oracle's iteration count on this workload is not "
                                          "recorded (run oracle/record_iterations.py)"}))
         return
     val = per_it * iters
+    # a step is the bounded sample (its wall time is ms_per_step); value is the
+    # time to tolerance it implies: the sample's seconds per iteration times
+    # the oracle's own recorded iteration count
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "value_note": (f"{per_it * 1e3:.1f} ms per oracle iteration (each step a sample of "
+                           f"{args.oracle_iters} iterations) x {iters} iterations to tolerance"),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args, s),
-            "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": (f"{args.oracle_iters} oracle iterations per step, "
+            "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle",
+                             "cpu": cpu_model(),
+                             "sample": (f"{args.oracle_iters} oracle iterations per step (residual "
+                                        f"and top-K on {cores} host threads), "
                                         f"{per_it * 1e3:.1f} ms/iteration (set-up excluded), "
                                         f"scaled to {iters} iterations to tolerance ({src})")},
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -973,11 +1022,36 @@ def run_profile_dense(args):
     print(f"dense profile run ({args.profile_dense}): {res.iters} iterations, rrn {res.rrn:.4e}")
 
 
+def run_profile_multi(args):
+    import torch
+    from paper_2510_02156_gb300 import binding as B
+    from paper_2510_02156_gb300 import workloads as W
+    s = workload(args, 0)
+    nr = 16
+    h0 = B.Handle.from_system(s, precision=B.PREC_MIXED)
+    h = h0.multi(nr)
+    Bd = torch.as_tensor(W.rhs_block(s, nr, seed=77), device="cuda")
+    Xm = torch.as_tensor(np.random.default_rng(3).standard_normal((s.n, nr)) * 0.5, device="cuda")
+    for _ in range(3):
+        h.residual_multi(Bd.float(), Xm.float(), None, precision=B.PREC_MIXED, wait=False)
+    X = torch.zeros((s.n, nr), dtype=torch.float64, device="cuda")
+    res = h.solve_multi(Bd, X, tol=s.tol, maxit=args.profile_multi, seed=1, precision=B.PREC_MIXED,
+                        inner_tol=args.inner_tol, host_loop=1, poll=args.profile_multi)
+    torch.cuda.synchronize()
+    print(f"profile run: {nr} columns, {res[0].iters} iterations, "
+          f"{res[0].time_ms / max(1, res[0].iters) * 1e3:.1f} us/iteration (host-driven loop)")
+    h.close()
+    h0.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.profile:
         run_profile(args)
+        return
+    if args.profile_multi:
+        run_profile_multi(args)
         return
     if args.profile_dense:
         run_profile_dense(args)

@@ -476,6 +476,43 @@ rorbk_status rorbk_multi_results(rorbk_handle h, rorbk_result *res);
 rorbk_status rorbk_residual_multi(rorbk_handle h, int32_t precision, const void *B, const void *X,
                                   void *R, double *rr_host);
 
+/* ---- launch shapes ------------------------------------------------------
+ * (Beside the paper.)  Grids that leave every result unchanged: the top-K
+ * passes (their counts are exact whatever the grid), the dynamic update's
+ * gather and scatter (each entry's arithmetic is fixed), and, for a block of
+ * right-hand sides, the block residual (whose grid changes only the order in
+ * which per-block sums of squares are added, so a stopping test can move
+ * only when the relative residual lies within rounding of the tolerance).
+ * All counts are per column of a block; 0 selects the library's default.
+ *   us_default, us_tuned: microseconds per iteration measured by
+ *   rorbk_autotune with the defaults and with the chosen shapes. */
+typedef struct {
+    int32_t topk_blocks;         /* first/second top-K pass             */
+    int32_t collect_blocks;      /* top-K candidates pass               */
+    int32_t dyn_mark_blocks;     /* dynamic update: gather and marks    */
+    int32_t dyn_scatter_blocks;  /* dynamic update: x += A_I^T y        */
+    int32_t residual_blocks;     /* block residual (blocks of columns)  */
+    int32_t reserved_;
+    double us_default, us_tuned;
+} rorbk_tuning;
+
+/* rorbk_autotune: chooses the shapes above for this handle by timing iters
+ * host-driven iterations per candidate (coordinate descent over each shape in
+ * turn, candidates 1/4 .. 4 x the default), every candidate from the same
+ * state: the iterate after iters iterations from x0 = 0 on the right-hand
+ * side b (device; m doubles, or m x nr row-major for a block), with the same
+ * draws.  precision: the iteration to tune (RORBK_PREC_FP64, or
+ * RORBK_PREC_MIXED for the FP32 inner iterations).  cache_file (may be NULL):
+ * a text file of earlier choices, one line per (m, nnz, k, nr, precision,
+ * SMs); a matching line is applied without timing, a new choice is appended.
+ * The shapes are applied to h (and kept by later clones); *out (may be NULL)
+ * receives them.  Allocates a scratch copy of x for the call.  Errors: as
+ * rorbk_solve; RORBK_ERR_INVALID_ARG for b == NULL or iters < 1.
+ * rorbk_set_tuning: applies given shapes (NULL: the defaults). */
+rorbk_status rorbk_autotune(rorbk_handle h, const double *b, int32_t precision, int64_t iters,
+                            const char *cache_file, rorbk_tuning *out);
+rorbk_status rorbk_set_tuning(rorbk_handle h, const rorbk_tuning *t);
+
 /* ---- the differentiable solve ------------------------------------------
  * (No counterpart in the paper, which never differentiates its solution.)
  * For square non-singular A and a loss L(x) with x = A^{-1} b:

@@ -70,6 +70,13 @@ class Info(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("topk_blocks", C.c_int32), ("collect_blocks", C.c_int32),
+                ("dyn_mark_blocks", C.c_int32), ("dyn_scatter_blocks", C.c_int32),
+                ("residual_blocks", C.c_int32), ("reserved_", C.c_int32),
+                ("us_default", C.c_double), ("us_tuned", C.c_double)]
+
+
 # the entry points declared in include/rorbk.h, with their ctypes signatures
 _P, _I64, _U64, _D = C.c_void_p, C.c_int64, C.c_uint64, C.c_double
 SIGNATURES = {
@@ -101,6 +108,8 @@ SIGNATURES = {
     "rorbk_solve_multi_host": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P]),
     "rorbk_multi_results": (C.c_int, [_P, _P]),
     "rorbk_residual_multi": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "rorbk_autotune": (C.c_int, [_P, _P, C.c_int32, _I64, C.c_char_p, _P]),
+    "rorbk_set_tuning": (C.c_int, [_P, _P]),
     "rorbk_setup_adjoint": (C.c_int, [_P, _P, _D, _P, _P]),
     "rorbk_adjoint_solve": (C.c_int, [_P, _P, _P, _D, _I64, _P, _P]),
     "rorbk_value_grad": (C.c_int, [_P, _P, _P, _P]),
@@ -280,6 +289,18 @@ class Handle:
         _check(lib().rorbk_residual_multi(self.h, precision, _ptr(B), _ptr(X), _ptr(R),
                                           _ptr(rr) if wait else None), self.h)
         return rr if wait else None
+
+    def autotune(self, b, precision=PREC_FP64, iters=50, cache_file=None):
+        """rorbk_autotune: choose the launch shapes for this handle (b: device
+        right-hand side(s)); returns the Tuning applied."""
+        t = Tuning()
+        path = None if cache_file is None else str(cache_file).encode()
+        _check(lib().rorbk_autotune(self.h, _ptr(b), precision, iters, path, C.byref(t)), self.h)
+        return t
+
+    def set_tuning(self, t=None):
+        """rorbk_set_tuning: apply given shapes (None: the defaults)."""
+        _check(lib().rorbk_set_tuning(self.h, None if t is None else C.byref(t)), self.h)
 
     def multi_results(self):
         """rorbk_multi_results: the per-column results of the last solve."""

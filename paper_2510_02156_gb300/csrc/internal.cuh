@@ -144,6 +144,7 @@ struct rorbk_ctx {
     // proposal
     double *cdf = nullptr, *crowsum = nullptr;
     double *pbar = nullptr;             // [k] Pbar_t (the weights before the running sum)
+    double *rn = nullptr, *rn32 = nullptr;   // [m] ||A_i||^2 from the FP64 values / the FP32 copy
     rorbk::StaticOps ops;
     rorbk::BlockT bt;
     // residual tiles (single-step residual on CSR) and the SELL-32 copy of A
@@ -215,9 +216,13 @@ struct rorbk_ctx {
         int *iperm = nullptr;       // [m] SELL position of each row
         unsigned *grp = nullptr;    // [8] loop tickets and "some column runs" flags, residual ticket
         long long mpos = 0;         // SELL positions (32 per slice)
-        int grid = 0;               // blocks of the column-block residual
+        int grid = 0, grid32 = 0;   // blocks of the column-block residual (FP64, FP32)
         std::vector<rorbk_result> last;   // per-column results of the last solve
     } mr;
+    // launch shapes that do not change results (rorbk_autotune; 0: default)
+    struct Tune {
+        int topk = 0, collect = 0, mark = 0, scatter = 0, residual = 0;
+    } tune;
     rorbk::Ctl *ctl = nullptr;
     rorbk::Ctl *ctl_in = nullptr;       // inner (FP32) loop state of the mixed form
     // graphs
@@ -247,7 +252,12 @@ void fill_dense_columns(rorbk_ctx *h);        // column indices of a dense A hel
 // iteration launches (kernels_iter.cu); all enqueue on h->stream
 void configure_kernels();
 int residual_grid(rorbk_ctx *h);   // one resident wave of the residual kernel
-int mres_grid(rorbk_ctx *h, int nr);   // one resident wave of the column-block residual
+int mres_grid(rorbk_ctx *h, int nr, int fp32);   // one resident wave of the column-block residual
+// the tunable grids (per column), defaults where h->tune holds 0
+int grid_topk(rorbk_ctx *h);
+int grid_collect(rorbk_ctx *h);
+int grid_mark(rorbk_ctx *h);
+int grid_scatter(rorbk_ctx *h);
 void launch_begin(rorbk_ctx *h, const double *b, const double *x0, double *x, int use_cond,
                   unsigned long long hcond);
 void launch_iteration(rorbk_ctx *h, const double *b, double *x, double *r, int use_cond,

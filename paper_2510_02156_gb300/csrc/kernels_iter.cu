@@ -52,6 +52,32 @@ template <> __device__ __forceinline__ double wide<double>(float v) { return wid
 template <> __device__ __forceinline__ float wide<float>(float v) { return v; }
 template <typename T> __device__ __forceinline__ T wide(double v) { return (T)v; }
 
+// VEC values of T in one aligned load (16 bytes at most).
+template <typename T, int VEC>
+struct VecT {
+    T v[VEC];
+};
+// STREAM: a value read once (evict-first in L1 and L2, ld.global.cs), so that
+// the gathered X stays resident in L2 while A, B and R stream past it.
+template <typename T, int VEC, bool STREAM = false>
+__device__ __forceinline__ VecT<T, VEC> vload(const T *p) {
+    VecT<T, VEC> r;
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        const float4 q = STREAM ? __ldcs(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
+        r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        const float2 q = STREAM ? __ldcs(reinterpret_cast<const float2 *>(p)) : __ldg(reinterpret_cast<const float2 *>(p));
+        r.v[0] = q.x; r.v[1] = q.y;
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        const double2 q = STREAM ? __ldcs(reinterpret_cast<const double2 *>(p)) : __ldg(reinterpret_cast<const double2 *>(p));
+        r.v[0] = q.x; r.v[1] = q.y;
+    } else {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) r.v[u] = STREAM ? __ldcs(p + u) : __ldg(p + u);
+    }
+    return r;
+}
+
 // Matrix and operator pointers for one compute type.
 template <typename T>
 struct Mat {
@@ -87,6 +113,7 @@ struct Mat {
     // (n x n row-major) when wood_ptr != nullptr and wood_ptr[t] >= 0
     const long long *wood_ptr;
     const T *wood;
+    const double *rn;           // ||A_i||^2 of the values this instance reads
 };
 
 template <typename T>
@@ -98,7 +125,7 @@ Mat<double> make_mat<double>(rorbk_ctx *h) {
                        h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val, h->bt.seg, h->bt.seg_ptr,
                        h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                        h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
-                       h->sell.val32, h->wood_ptr, h->wood_ss};
+                       h->sell.val32, h->wood_ptr, h->wood_ss, h->rn};
 }
 template <>
 Mat<float> make_mat<float>(rorbk_ctx *h) {
@@ -107,7 +134,7 @@ Mat<float> make_mat<float>(rorbk_ctx *h) {
                       h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val32, h->bt.seg, h->bt.seg_ptr,
                       h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                       h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
-                      h->sell.val32, h->wood_ptr, h->wood_ss32};
+                      h->sell.val32, h->wood_ptr, h->wood_ss32, h->rn32};
 }
 
 // -------------------------------------------------------- several columns
@@ -509,6 +536,8 @@ __device__ __forceinline__ void hist_add(unsigned *hist, unsigned bin, bool acti
 // finalize: 1 = convergence test + first radix level (iteration), 2 = ||r||^2
 // only (single-step API).  DN: A is dense, so entry j of a row is in column j
 // and the column indices are not read (x_j is the same for the warp's lanes).
+constexpr int kDnAhead = 4;      // dense residual: 16-byte loads per lane in flight
+
 template <typename T, typename V, bool DN = false>
 __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restrict__ b,
                                                   const T *__restrict__ x, T *__restrict__ r,
@@ -537,16 +566,44 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
         const int L = A.slen[sl];
         const int slot = sl * 32 + lane;
         const int row = A.srow[slot], len = A.srlen[slot];
+        T acc = T(0);
+        if constexpr (DN) {
+            // a dense A: entry j of lane l is at 32 VW (j / VW) + VW l + j % VW
+            // of the slice, so each load brings VW consecutive entries of the
+            // lane's own row (16 bytes); kDnAhead such loads are in flight while
+            // the chain runs over the previous ones, columns ascending as ever
+            constexpr int VW = 16 / sizeof(V);
+            const V *vb = val + A.sptr[sl] + VW * lane;
+            VecT<V, VW> vq[kDnAhead];
+#pragma unroll
+            for (int q = 0; q < kDnAhead; ++q)
+                if (q * VW < len) vq[q] = vload<V, VW, true>(vb + 32LL * VW * q);
+            for (int q0 = 0; q0 * VW < L; q0 += kDnAhead) {
+                VecT<V, VW> vc[kDnAhead];
+#pragma unroll
+                for (int q = 0; q < kDnAhead; ++q) vc[q] = vq[q];
+#pragma unroll
+                for (int q = 0; q < kDnAhead; ++q)
+                    if ((q0 + kDnAhead + q) * VW < len)
+                        vq[q] = vload<V, VW, true>(vb + 32LL * VW * (q0 + kDnAhead + q));
+#pragma unroll
+                for (int q = 0; q < kDnAhead; ++q)
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) {
+                        const int j = (q0 + q) * VW + u;
+                        if (j < len) acc = Ar<T>::fma(wide<T>(vc[q].v[u]), x[j], acc);
+                    }
+            }
+        } else {
         // software pipeline, 8 deep: the x gathers of chunk k and the index /
         // value loads of chunk k+1 are in flight while chunk k's chain runs
-        T acc = T(0);
         int cn[8];
         V vn[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const bool in = u < len;
             const long long d = base + 32LL * u;
-            cn[u] = in ? (DN ? u : A.scol[d]) : 0;
+            cn[u] = in ? A.scol[d] : 0;
             vn[u] = in ? val[d] : V(0);
         }
         for (int c0 = 0; c0 < L; c0 += 8) {
@@ -562,12 +619,13 @@ __global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restri
                 const int j = c0 + 8 + u;
                 const bool in = j < len;
                 const long long d = base + 32LL * j;
-                cn[u] = in ? (DN ? j : A.scol[d]) : 0;
+                cn[u] = in ? A.scol[d] : 0;
                 vn[u] = in ? val[d] : V(0);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u)
                 if (c0 + u < len) acc = Ar<T>::fma(wide<T>(vc[u]), xv[u], acc);
+        }
         }
         const bool act = row >= 0;
         unsigned bin = 0;
@@ -794,8 +852,10 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
         bool act[kScanU];
 #pragma unroll
         for (int u = 0; u < kScanU; ++u) {
+            // padding positions of a column block hold exact zeros; their
+            // count is taken off the zero bin below instead of reading perm
             const int i = i0 + u * blockDim.x + threadIdx.x;
-            act[u] = i < mp && (!MC || !cl.perm || cl.perm[i] >= 0);
+            act[u] = i < mp;
             v[u] = i < mp ? r[i] : T(0);
         }
 #pragma unroll
@@ -814,6 +874,8 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
     if (!is_last) return;
     __threadfence();
     int bin, above;
+    if (MC && cl.perm && sel1 == 0u && threadIdx.x == 0) hist2[0] -= (unsigned)(mp - m);   // padding zeros
+    __syncthreads();
     select_bin(hist2, K - ctl->above1, &bin, &above);
     if (threadIdx.x == 0) {
         ctl->prefix = (int)((sel1 << 11) | (unsigned)bin);
@@ -1035,18 +1097,21 @@ __global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, i
 #pragma unroll
         for (int u = 0; u < kScanU; ++u) {
             const int p = p0 + u * blockDim.x + threadIdx.x;
-            row[u] = p < mp ? (MC && cl.perm ? cl.perm[p] : p) : -1;    // the row at this position
+            row[u] = p < mp ? p : -1;
             v[u] = p < mp ? r[p] : T(0);
         }
 #pragma unroll
         for (int u = 0; u < kScanU; ++u) {
             if (row[u] < 0) continue;
             const unsigned long long pre = abs_key(v[u]) >> 41;
+            if (pre < P) continue;
+            const int i = MC && cl.perm ? cl.perm[row[u]] : row[u];   // the row at this position
+            if (i < 0) continue;
             if (pre > P) {
-                in_list[atomicAdd(&ctl->n_in, 1)] = row[u];
-            } else if (pre == P) {
+                in_list[atomicAdd(&ctl->n_in, 1)] = i;
+            } else {
                 int pos = atomicAdd(&ctl->n_eq, 1);
-                if (pos < kEqCap) eq_list[pos] = row[u];
+                if (pos < kEqCap) eq_list[pos] = i;
             }
         }
     }
@@ -1561,11 +1626,7 @@ __global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict_
     // Rows go to different blocks so that their chains run on different SMs.
     for (int a = blockIdx.x + gridDim.x * threadIdx.x; a < K; a += gs) {
         const int i = D.I[a];
-        double g = 0.0;
-        for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p) {
-            const double v = (double)A.val[p];
-            g = __fma_rn(v, v, g);
-        }
+        double g = A.rn[i];                          // the row's fused chain, formed at set-up
         g = __dadd_rn(g, A.mu);
         D.gdiag[a] = g;
         if (!(g > 0.0)) { set_status(&ctl->status, kDevNotSpd); g = 1.0; }
@@ -2483,30 +2544,6 @@ struct SqAcc<float> {
     static __device__ __forceinline__ float add(float s, float r) { return __fmaf_rn(r, r, s); }
 };
 
-// VEC values of T in one aligned load (16 bytes at most).
-template <typename T, int VEC>
-struct VecT {
-    T v[VEC];
-};
-// STREAM: a value read once (evict-first in L1 and L2, ld.global.cs), so that
-// the gathered X stays resident in L2 while A, B and R stream past it.
-template <typename T, int VEC, bool STREAM = false>
-__device__ __forceinline__ VecT<T, VEC> vload(const T *p) {
-    VecT<T, VEC> r;
-    if constexpr (sizeof(T) * VEC == 16) {
-        const float4 q = STREAM ? __ldcs(reinterpret_cast<const float4 *>(p))
-                                : __ldg(reinterpret_cast<const float4 *>(p));
-        memcpy(&r, &q, 16);
-    } else if constexpr (sizeof(T) * VEC == 8) {
-        const float2 q = STREAM ? __ldcs(reinterpret_cast<const float2 *>(p))
-                                : __ldg(reinterpret_cast<const float2 *>(p));
-        memcpy(&r, &q, 8);
-    } else {
-        r.v[0] = STREAM ? __ldcs(p) : __ldg(p);
-    }
-    return r;
-}
-
 constexpr int kMrWarps = 8;
 
 // The FP32 block residual of an iteration also forms the first radix level
@@ -2532,15 +2569,22 @@ __device__ __forceinline__ unsigned f32_bin_exp(int bin) {
     return bin == 0 ? 0u : bin == kF32Bins - 1 ? 2047u : (unsigned)(bin - 1 + kF32Exp0);
 }
 
-// select_bin for one warp: the largest bin b with sum_{j >= b} h[j] >= need
-// and the count strictly above it, over kHistBins global bins (lane l scans
-// bins 2047 - 64 l down to 1984 - 64 l); zeroes h.
-__device__ void warp_select_bin(unsigned *h, int need, int *bin_out, int *above_out) {
+// select_bin for one warp over the histogram of an FP32 residual's keys,
+// whose nonzero bins are among the kF32Bins FP32 exponents: the largest bin b
+// with sum_{j >= b} h[j] >= need and the count strictly above it.  Lane l
+// holds compressed bins kF32Bins - 1 - kSelPer l - u (u < kSelPer, descending
+// keys) in registers; zeroes them in h.
+constexpr int kSelPer = (kF32Bins + 31) / 32;
+__device__ void warp_select_bin_f32(unsigned *h, int need, int *bin_out, int *above_out) {
     const int lane = threadIdx.x & 31;
-    constexpr int per = kHistBins / 32;
-    const int top = kHistBins - 1 - lane * per;
+    int c[kSelPer];
     int tot = 0;
-    for (int u = 0; u < per; ++u) tot += (int)h[top - u];
+#pragma unroll
+    for (int u = 0; u < kSelPer; ++u) {
+        const int q = kF32Bins - 1 - kSelPer * lane - u;
+        c[u] = q >= 0 ? (int)h[f32_bin_exp(q)] : 0;
+        tot += c[u];
+    }
     int pre = tot;                                  // inclusive scan, lanes in order
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -2548,27 +2592,38 @@ __device__ void warp_select_bin(unsigned *h, int need, int *bin_out, int *above_
         if (lane >= o) pre += v;
     }
     pre -= tot;                                     // keys in bins above this lane's
-    int bin = 0, above = 0, found = 0;
-    if (pre < need && pre + tot >= need) {
-        int run = pre;
-        for (int u = 0; u < per; ++u) {
-            const int c = (int)h[top - u];
-            if (run + c >= need) { bin = top - u; above = run; found = 1; break; }
-            run += c;
+    int bin = 0, above = 0, found = 0, run = pre;
+#pragma unroll
+    for (int u = 0; u < kSelPer; ++u) {
+        if (!found && run < need && run + c[u] >= need) {
+            bin = (int)f32_bin_exp(kF32Bins - 1 - kSelPer * lane - u);
+            above = run;
+            found = 1;
         }
+        run += c[u];
     }
     const unsigned who = __ballot_sync(0xffffffffu, found);
     const int src = who ? __ffs(who) - 1 : 0;
     bin = __shfl_sync(0xffffffffu, bin, src);
     above = __shfl_sync(0xffffffffu, above, src);
-    __syncwarp();
-    for (int u = 0; u < per; ++u) h[top - u] = 0u;
+#pragma unroll
+    for (int u = 0; u < kSelPer; ++u) {
+        const int q = kF32Bins - 1 - kSelPer * lane - u;
+        if (q >= 0) h[f32_bin_exp(q)] = 0u;
+    }
     *bin_out = who ? bin : 0;
     *above_out = who ? above : 0;
 }
 
+// Resident blocks per SM the register budget is set for.  Two (128
+// registers): a budget of 80 for three blocks fits the FP32 16-column chains
+// without spilling but keeps fewer loads in flight per thread, and measured
+// slower on GB300 (0.27 against 0.17 ms at 2^20 rows).
 template <typename T, typename V, int NR>
-__global__ void __launch_bounds__(kMrWarps * 32, 2)
+constexpr int mres_min_blocks() { return 2; }
+
+template <typename T, typename V, int NR>
+__global__ void __launch_bounds__(kMrWarps * 32, (mres_min_blocks<T, V, NR>()))
     k_mres(Mat<T> A, const T *__restrict__ B, const T *__restrict__ X, T *__restrict__ R,
            long long rs, double *partials, unsigned *tick, Ctl *ctl0, int finalize,
            unsigned *hist1) {
@@ -2733,7 +2788,7 @@ __global__ void __launch_bounds__(kMrWarps * 32, 2)
         for (int c = wid; c < NR; c += kMrWarps) {
             Ctl *ctl = ctl0 + c;
             int bin = 0, above = 0;
-            warp_select_bin(hist1 + (long long)c * kHistBins, A.K, &bin, &above);
+            warp_select_bin_f32(hist1 + (long long)c * kHistBins, A.K, &bin, &above);
             if (lane == 0 && !(ctl->done || ctl->halt)) { ctl->sel1 = bin; ctl->above1 = above; }
         }
     }
@@ -2886,6 +2941,21 @@ static int grid_stream(rorbk_ctx *h, int m) {
     return std::max(1, std::min(4 * h->num_sms, (m + 255) / 256));
 }
 
+// Launch shapes that leave every result unchanged, per column of a block
+// (rorbk_autotune / rorbk_set_tuning; 0: the defaults below).  The top-K
+// counts, the dynamic update's arithmetic and the scatters do not depend on
+// the grid; the block residual's grid changes only the order in which its
+// per-block sums of squares are added.
+static int tuned(int v, int def) { return v > 0 ? v : std::max(1, def); }
+int grid_topk(rorbk_ctx *h) {
+    const int nr = std::max(1, h->nr);
+    const long long mp = h->nr ? h->mr.mpos : h->m;
+    return tuned(h->tune.topk, std::min<long long>(4 * h->num_sms / nr, (mp + 255) / 256));
+}
+int grid_collect(rorbk_ctx *h) { return tuned(h->tune.collect, grid_topk(h) / 2); }
+int grid_mark(rorbk_ctx *h) { return tuned(h->tune.mark, h->num_sms / std::max(1, h->nr)); }
+int grid_scatter(rorbk_ctx *h) { return tuned(h->tune.scatter, 2 * h->num_sms / std::max(1, h->nr)); }
+
 int residual_grid(rorbk_ctx *h) {
     int per_sm = 0, per_sm32 = 0;
     if (h->vdtype == RORBK_F32)
@@ -2906,27 +2976,32 @@ static void configure_mres() {
                          (int)mres_smem_bytes<float, NR>());
 }
 
+// Resident blocks per SM of the FP32 (fp32 != 0) or the FP64 instances.
 template <int NR>
-static int mres_blocks_per_sm() {
+static int mres_blocks_per_sm(int fp32) {
     int a = 0, b = 0, c = 0;
+    if (fp32) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_mres<float, float, NR>, kMrWarps * 32,
+                                                      mres_smem_bytes<float, NR>());
+        return std::max(1, c);
+    }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mres<double, double, NR>, kMrWarps * 32,
                                                   mres_smem_bytes<double, NR>());
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mres<double, float, NR>, kMrWarps * 32,
                                                   mres_smem_bytes<double, NR>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_mres<float, float, NR>, kMrWarps * 32,
-                                                  mres_smem_bytes<float, NR>());
-    return std::max(1, std::min(a, std::min(b, c)));
+    return std::max(1, std::min(a, b));
 }
 
-// One resident wave of the column-block residual for nr columns.
-int mres_grid(rorbk_ctx *h, int nr) {
+// One resident wave of the column-block residual for nr columns (slices are
+// handed out by a queue, so every resident warp takes part).
+int mres_grid(rorbk_ctx *h, int nr, int fp32) {
     int per_sm = 1;
     switch (nr) {
-        case 2: per_sm = mres_blocks_per_sm<2>(); break;
-        case 4: per_sm = mres_blocks_per_sm<4>(); break;
-        case 8: per_sm = mres_blocks_per_sm<8>(); break;
-        case 16: per_sm = mres_blocks_per_sm<16>(); break;
-        default: per_sm = mres_blocks_per_sm<32>(); break;
+        case 2: per_sm = mres_blocks_per_sm<2>(fp32); break;
+        case 4: per_sm = mres_blocks_per_sm<4>(fp32); break;
+        case 8: per_sm = mres_blocks_per_sm<8>(fp32); break;
+        case 16: per_sm = mres_blocks_per_sm<16>(fp32); break;
+        default: per_sm = mres_blocks_per_sm<32>(fp32); break;
     }
     return per_sm * h->num_sms;
 }
@@ -3057,9 +3132,9 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
         return;
     }
     Mat<T> A = make_mat<T>(h);
-    k_dyn_mark<T><<<h->num_sms, 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
+    k_dyn_mark<T><<<grid_mark(h), 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
                                                                         check_done, one_col((int)h->m));
-    (inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>)<<<2 * h->num_sms, 512, 0, h->stream>>>(
+    (inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>)<<<grid_scatter(h), 512, 0, h->stream>>>(
         x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond, (cudaGraphConditionalHandle)hcond,
         one_col((int)h->m));
 }
@@ -3126,9 +3201,8 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
     }
     if constexpr (sizeof(T) == sizeof(double))
         if (weighted) launch_weights(h, r);      // the draws of the next iteration
-    const int g = grid_stream(h, (int)h->m);
-    k_topk_hist2<T><<<g, 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1, one_col((int)h->m));
-    k_topk_collect<T><<<std::max(1, g / 2), 512, collect_smem_bytes(), h->stream>>>(
+    k_topk_hist2<T><<<grid_topk(h), 256, 0, h->stream>>>(r, (int)h->m, h->K, h->hist2, ctl, 1, one_col((int)h->m));
+    k_topk_collect<T><<<grid_collect(h), 512, collect_smem_bytes(), h->stream>>>(
         r, (int)h->m, h->K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1, one_col((int)h->m));
     launch_dynamic_tail<T>(h, r, x, ctl, 1, 1, use_cond, hcond, inc);
 }
@@ -3136,7 +3210,8 @@ void launch_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl, int use_
 // R = B - A X for the handle's nr columns (finalize as k_residual's).
 template <typename T, typename V>
 static void mres_launch(rorbk_ctx *h, const Mat<T> &A, const T *B, const T *X, T *R, Ctl *ctl, int finalize) {
-    const dim3 grid(h->mr.grid), block(kMrWarps * 32);
+    const int wave = sizeof(T) == 4 ? h->mr.grid32 : h->mr.grid;
+    const dim3 grid(h->tune.residual > 0 ? std::min(h->tune.residual, wave) : wave), block(kMrWarps * 32);
     const long long rs = h->mr.mpos;
     unsigned *tick = h->mr.grp + 4;
     switch (h->nr) {
@@ -3166,16 +3241,16 @@ static void launch_mr_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl
         if (h->vdtype == RORBK_F32) mres_launch<T, float>(h, A, b, x, r, ctl, 1);
         else mres_launch<T, double>(h, A, b, x, r, ctl, 1);
     }
-    const int g = std::max(1, std::min(4 * h->num_sms / nr, (int)((h->mr.mpos + 255) / 256)));
+    const int g = grid_topk(h);
     // the FP32 block residual formed the first radix level itself
     if constexpr (sizeof(T) == sizeof(double))
         k_topk_hist1<T, true><<<dim3(g, nr), 256, 0, st>>>(r, m, K, h->hist1, ctl, cl, 1);
     k_topk_hist2<T, true><<<dim3(g, nr), 256, 0, st>>>(r, m, K, h->hist2, ctl, 1, cl);
-    k_topk_collect<T, true><<<dim3(std::max(1, g / 2), nr), 512, collect_smem_bytes(), st>>>(
+    k_topk_collect<T, true><<<dim3(grid_collect(h), nr), 512, collect_smem_bytes(), st>>>(
         r, m, K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1, cl);
-    k_dyn_mark<T, true><<<dim3(std::max(1, h->num_sms / nr), nr), 512, factor_smem_bytes(), st>>>(
+    k_dyn_mark<T, true><<<dim3(grid_mark(h), nr), 512, factor_smem_bytes(), st>>>(
         A, r, dyn_bufs(h), ctl, 1, cl);
-    k_dyn_scatter<T, false, true><<<dim3(std::max(1, 2 * h->num_sms / nr), nr), 512, 0, st>>>(
+    k_dyn_scatter<T, false, true><<<dim3(grid_scatter(h), nr), 512, 0, st>>>(
         x, (int)h->n, dyn_bufs(h), ctl, 1, use_cond, (cudaGraphConditionalHandle)hcond, cl);
 }
 

@@ -204,6 +204,23 @@ __global__ void __launch_bounds__(kSgT * kSgT) k_dense_static_gram(const double 
     if (a < s && b <= a) w_ss[w_ptr[t] + (long long)a * s + b] = a == b ? __dadd_rn(acc, mu) : acc;
 }
 
+// ||A_i||^2 of every row, one fused chain over the row's stored entries in
+// order from 0: the dynamic update's Gram diagonal (before mu), formed once
+// here instead of in every dynamic update (the same operations in the same
+// order, so the same numbers).  V: the stored values the iteration reads.
+template <typename V>
+__global__ void k_row_norms(const int *__restrict__ rowptr, const V *__restrict__ val, int m,
+                            double *__restrict__ rn) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        double g = 0.0;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            const double v = (double)val[p];
+            g = __fma_rn(v, v, g);
+        }
+        rn[i] = g;
+    }
+}
+
 // ------------------------------------------------------------ device scans
 // Exclusive scan of n ints in place (n < 2^31), three launches.
 __global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out,
@@ -543,13 +560,14 @@ void widen_values(rorbk_ctx *h, int dtype) {
 }
 
 // SELL-32 copy of A: lane l of slice s holds row sell_row[32 s + l]; entry j
-// of that lane sits at ptr[s] + 32 j + l.
+// of that lane sits at ptr[s] + 32 j + l (the values of a dense A: grouped
+// VW consecutive entries per lane, see below).
 __global__ void k_sell_fill(const int *__restrict__ rowptr, const int *__restrict__ col,
                             const double *__restrict__ val, const float *__restrict__ val32,
                             int nslices, const long long *__restrict__ ptr,
                             const int *__restrict__ srow, const int *__restrict__ srlen,
                             int *__restrict__ scol, double *__restrict__ sval,
-                            float *__restrict__ sval32) {
+                            float *__restrict__ sval32, int dense) {
     const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (slot >= (long long)nslices * 32) return;
     const int s = (int)(slot >> 5), lane = (int)(slot & 31);
@@ -560,8 +578,12 @@ __global__ void k_sell_fill(const int *__restrict__ rowptr, const int *__restric
         const long long d = base + 32LL * j;
         const bool in = j < len;
         scol[d] = in ? col[p0 + j] : 0;
-        if (sval) sval[d] = in ? val[p0 + j] : 0.0;
-        if (sval32) sval32[d] = in ? val32[p0 + j] : 0.0f;
+        // a dense A's values: entry j of lane l at 32 VW (j / VW) + VW l + j % VW,
+        // VW = 16 bytes / value size, so a lane reads VW entries per load
+        const long long d64 = dense ? ptr[s] + 64LL * (j >> 1) + 2 * lane + (j & 1) : d;
+        const long long d32 = dense ? ptr[s] + 128LL * (j >> 2) + 4 * lane + (j & 3) : d;
+        if (sval) sval[d64] = in ? val[p0 + j] : 0.0;
+        if (sval32) sval32[d32] = in ? val32[p0 + j] : 0.0f;
     }
 }
 
@@ -618,7 +640,10 @@ static rorbk_status build_sell(rorbk_ctx *h, const std::vector<int> &hrp) {
             }
         }
         len[sl] = L;
-        ptr[sl + 1] = ptr[sl] + 32LL * L;
+        // a dense A's slices span a multiple of 4 entries per lane (its values
+        // are grouped 4 (FP32) or 2 (FP64) entries per lane)
+        const int Lp = h->format == RORBK_FORMAT_DENSE ? (L + 3) & ~3 : L;
+        ptr[sl + 1] = ptr[sl] + 32LL * Lp;
     }
     auto &S = h->sell;
     S.nslices = ns;
@@ -639,7 +664,8 @@ static rorbk_status build_sell(rorbk_ctx *h, const std::vector<int> &hrp) {
     cudaMemcpyAsync(S.row, row.data(), (size_t)ns * 32 * sizeof(int), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(S.rlen, rlen.data(), (size_t)ns * 32 * sizeof(int), cudaMemcpyHostToDevice, st);
     k_sell_fill<<<(unsigned)((ns * 32LL + 255) / 256), 256, 0, st>>>(
-        h->rowptr, h->col, h->val, h->val32, ns, S.ptr, S.row, S.rlen, S.col, S.val, S.val32);
+        h->rowptr, h->col, h->val, h->val32, ns, S.ptr, S.row, S.rlen, S.col, S.val, S.val32,
+        h->format == RORBK_FORMAT_DENSE ? 1 : 0);
     return cuda_check(h, cudaStreamSynchronize(st), "SELL copy of A");
 }
 
@@ -684,6 +710,17 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
     if (hf[0] & 2) return fail(h, RORBK_ERR_NUMERIC, "A holds NaN or Inf");
     if ((st = build_sell(h, hrp))) return st;
     if ((st = build_block_order(h, hrp))) return st;
+    // row norms for the dynamic update: from the FP64 values, and from the
+    // FP32 copy that the mixed form's inner solve reads when it differs
+    h->rn = (double *)dev_alloc(h, (size_t)m * sizeof(double));
+    if (!h->rn) return fail(h, RORBK_ERR_OOM, "row norms");
+    k_row_norms<double><<<gs, 256, 0, s>>>(h->rowptr, h->val, m, h->rn);
+    h->rn32 = h->rn;
+    if (h->val32 && h->vdtype == RORBK_F64) {
+        h->rn32 = (double *)dev_alloc(h, (size_t)m * sizeof(double));
+        if (!h->rn32) return fail(h, RORBK_ERR_OOM, "row norms");
+        k_row_norms<float><<<gs, 256, 0, s>>>(h->rowptr, h->val32, m, h->rn32);
+    }
 
     // block transpose, coupled rows
     const long long nnz = h->nnz;

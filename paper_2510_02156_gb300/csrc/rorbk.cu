@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -236,8 +237,8 @@ static rorbk_status alloc_workspace(rorbk_ctx *h) {
     h->r = (double *)dev_alloc(h, nr * mr * sizeof(double));
     h->xb = (double *)dev_alloc(h, nr * n * sizeof(double));
     h->bb = (double *)dev_alloc(h, nr * m * sizeof(double));
-    h->partials = (double *)dev_alloc(h, nr * std::max(std::max(h->grid_res, h->mr.grid), 4 * h->num_sms) *
-                                             sizeof(double) + 64);
+    h->partials = (double *)dev_alloc(h, nr * std::max(std::max(h->grid_res, std::max(h->mr.grid, h->mr.grid32)),
+                                                       4 * h->num_sms) * sizeof(double) + 64);
     h->sd_scratch = (double *)dev_alloc(h, 2 * kMaxBlockRows * sizeof(double));
     h->wgt = (double *)dev_alloc(h, h->k * sizeof(double));
     h->wcdf = (double *)dev_alloc(h, h->k * sizeof(double));
@@ -772,6 +773,137 @@ rorbk_status rorbk_residual_multi(rorbk_handle h, int32_t precision, const void 
     return st;
 }
 
+}  // extern "C"
+
+static void tuning_out(const rorbk_ctx *h, double us0, double us1, rorbk_tuning *t) {
+    t->topk_blocks = grid_topk((rorbk_ctx *)h);
+    t->collect_blocks = grid_collect((rorbk_ctx *)h);
+    t->dyn_mark_blocks = grid_mark((rorbk_ctx *)h);
+    t->dyn_scatter_blocks = grid_scatter((rorbk_ctx *)h);
+    t->residual_blocks = h->tune.residual;
+    t->reserved_ = 0;
+    t->us_default = us0;
+    t->us_tuned = us1;
+}
+
+extern "C" {
+
+rorbk_status rorbk_set_tuning(rorbk_handle h, const rorbk_tuning *t) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!t) { h->tune = rorbk_ctx::Tune(); return RORBK_OK; }
+    if (t->topk_blocks < 0 || t->collect_blocks < 0 || t->dyn_mark_blocks < 0 || t->dyn_scatter_blocks < 0 ||
+        t->residual_blocks < 0)
+        return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_set_tuning: negative block count");
+    h->tune.topk = t->topk_blocks;
+    h->tune.collect = t->collect_blocks;
+    h->tune.mark = t->dyn_mark_blocks;
+    h->tune.scatter = t->dyn_scatter_blocks;
+    h->tune.residual = t->residual_blocks;
+    return RORBK_OK;
+}
+
+rorbk_status rorbk_autotune(rorbk_handle h, const double *b, int32_t precision, int64_t iters,
+                            const char *cache_file, rorbk_tuning *out) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!b || iters < 1) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_autotune: b and iters >= 1");
+    if (precision != RORBK_PREC_FP64 && precision != RORBK_PREC_MIXED)
+        return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_autotune: unknown precision");
+    const int nr = std::max(1, h->nr);
+    char key[256];
+    snprintf(key, sizeof(key), "m=%lld nnz=%lld k=%d nr=%d prec=%d sms=%d", (long long)h->m, (long long)h->nnz,
+             h->k, nr, precision, h->num_sms);
+    if (cache_file) {   // an earlier choice for this shape of problem
+        FILE *f = fopen(cache_file, "r");
+        if (f) {
+            char line[512];
+            while (fgets(line, sizeof(line), f)) {
+                if (strncmp(line, key, strlen(key)) != 0 || line[strlen(key)] != ' ') continue;
+                int v[5];
+                double us0 = 0, us1 = 0;
+                if (sscanf(line + strlen(key), " topk=%d collect=%d mark=%d scatter=%d residual=%d us=%lf,%lf",
+                           &v[0], &v[1], &v[2], &v[3], &v[4], &us0, &us1) == 7) {
+                    fclose(f);
+                    h->tune.topk = v[0];
+                    h->tune.collect = v[1];
+                    h->tune.mark = v[2];
+                    h->tune.scatter = v[3];
+                    h->tune.residual = v[4];
+                    if (out) tuning_out(h, us0, us1, out);
+                    return RORBK_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    cudaSetDevice(h->device);
+    const size_t xbytes = (size_t)nr * h->n * sizeof(double);
+    double *x0 = nullptr, *x = nullptr;
+    if (cudaMalloc(&x0, xbytes) != cudaSuccess || cudaMalloc(&x, xbytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (x0) cudaFree(x0);
+        return fail(h, RORBK_ERR_OOM, "rorbk_autotune: scratch x");
+    }
+    rorbk_options o;
+    rorbk_default_options(&o);
+    o.precision = precision;
+    o.inner_tol = 1e-30;                      // the mixed form: inner iterations only
+    o.stream = h->stream;
+    std::vector<rorbk_result> res(nr);
+    // the starting state: iters iterations from 0
+    rorbk_status st = solve_impl(h, b, nullptr, false, x0, false, 0.0, iters, &o, res.data());
+    if (st < 0) { cudaFree(x0); cudaFree(x); return st; }
+    o.start_iter = iters;
+    o.host_loop = 1;
+    o.poll = (int32_t)std::min<int64_t>(iters, 1 << 20);
+    auto time_it = [&](double *us) -> rorbk_status {
+        double best = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            rorbk_status s2 = solve_impl(h, b, x0, false, x, false, 0.0, iters, &o, res.data());
+            if (s2 < 0) return s2;
+            best = std::min(best, res[0].time_ms * 1e3 / (double)iters);
+        }
+        *us = best;
+        return RORBK_OK;
+    };
+    const auto saved = h->tune;
+    h->tune = rorbk_ctx::Tune();
+    double us0 = 0, cur = 0;
+    st = time_it(&us0);
+    cur = us0;
+    // coordinate descent: each shape over 1/4 .. 4 x its default
+    int *fields[5] = {&h->tune.topk, &h->tune.collect, &h->tune.mark, &h->tune.scatter, &h->tune.residual};
+    const int defs[5] = {grid_topk(h), grid_collect(h), grid_mark(h), grid_scatter(h),
+                         h->nr ? (precision == RORBK_PREC_MIXED ? h->mr.grid32 : h->mr.grid) : 0};
+    static const double mult[4] = {0.25, 0.5, 2.0, 4.0};
+    for (int f = 0; f < 5 && st == RORBK_OK; ++f) {
+        if (defs[f] <= 0) continue;
+        int best_v = *fields[f];
+        for (double mlt : mult) {
+            int v = std::max(1, (int)(defs[f] * mlt));
+            if (f == 4) v = std::min(v, defs[f]);   // the residual: at most one resident wave
+            if (v == defs[f]) continue;
+            *fields[f] = v;
+            double us = 0;
+            if ((st = time_it(&us))) break;
+            if (us < 0.98 * cur) { cur = us; best_v = v; }
+        }
+        *fields[f] = best_v;
+    }
+    cudaFree(x0);
+    cudaFree(x);
+    if (st) { h->tune = saved; return st; }
+    if (cache_file) {
+        FILE *f = fopen(cache_file, "a");
+        if (f) {
+            fprintf(f, "%s topk=%d collect=%d mark=%d scatter=%d residual=%d us=%.3f,%.3f\n", key,
+                    h->tune.topk, h->tune.collect, h->tune.mark, h->tune.scatter, h->tune.residual, us0, cur);
+            fclose(f);
+        }
+    }
+    if (out) tuning_out(h, us0, cur, out);
+    return RORBK_OK;
+}
+
 rorbk_status rorbk_multi_results(rorbk_handle h, rorbk_result *res) {
     if (!h || !res) return RORBK_ERR_INVALID_ARG;
     if (!h->nr) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_multi_results: not a block of right-hand sides");
@@ -823,7 +955,8 @@ static rorbk_status clone_impl(rorbk_handle src, int nr, rorbk_handle *out) {
         // position of every row, the group tickets, one resident wave
         c->nr = nr;
         c->mr.mpos = (long long)src->sell.nslices * 32;
-        c->mr.grid = mres_grid(c, nr);
+        c->mr.grid = mres_grid(c, nr, 0);
+        c->mr.grid32 = mres_grid(c, nr, 1);
         std::vector<int> row((size_t)c->mr.mpos), ipos((size_t)c->m, -1);
         if ((st = cuda_check(c, cudaMemcpy(row.data(), src->sell.row, row.size() * sizeof(int),
                                            cudaMemcpyDeviceToHost), "rorbk_multi_create")))

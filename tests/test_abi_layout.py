@@ -19,6 +19,7 @@ STRUCTS = {
     "rorbk_options": B.Options,
     "rorbk_result": B.Result,
     "rorbk_info": B.Info,
+    "rorbk_tuning": B.Tuning,
 }
 # ctypes names that differ from the C member (a Python keyword)
 RENAMED = {"lambda_": "lambda"}
