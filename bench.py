@@ -99,8 +99,8 @@ def parse():
                         "prints no JSON")
     p.add_argument("--profile-multi", type=int, default=0,
                    help="profiling run of a block of 16 right-hand sides of the main workload: "
-                        "three block residuals alone (FP32), then N host-driven iterations of the "
-                        "mixed form's inner solve; prints no JSON")
+                        "three block residuals alone in FP32 and three in FP64, then N host-driven "
+                        "iterations of the mixed form; prints no JSON")
     p.add_argument("--cache", default=os.path.join(ROOT, ".cache"))
     return p.parse_args()
 
@@ -212,38 +212,55 @@ def spmv_bytes(s, vbytes, xbytes):
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic_k_residual_powerlaw_n1048576.txt")
+MRES_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic_k_mres_powerlaw_n1048576_nr16.txt")
 KERNEL_SOURCES = ("paper_2510_02156_gb300/csrc/kernels_iter.cu", "paper_2510_02156_gb300/csrc/common.cuh")
 # the residual kernel's part of the first source: from its section marker to
 # the next kernel's comment (the kernel and the helpers it calls)
 RESIDUAL_REGION = ("// ---------------------------------------------------------------- residual",
                    "// Incremental residual, first kernel")
+# the block residual's part: the section of a block of right-hand sides up to
+# the kernel that unpermutes its columns
+MRES_REGION = ("// ------------------------------------------------- a block of right-hand sides",
+               "// Residual columns from the SELL order")
 
 
-def residual_sources_sha256():
-    """sha256 of the residual kernel's source region of kernels_iter.cu and
-    of common.cuh: the code the traffic record was captured from."""
+def region_sha256(region):
+    """sha256 of one kernel's source region of kernels_iter.cu and of
+    common.cuh: the code a traffic record was captured from."""
     import hashlib
     h = hashlib.sha256()
     for i, f in enumerate(KERNEL_SOURCES):
         with open(os.path.join(ROOT, f), "rb") as fh:
             data = fh.read()
         if i == 0:
-            a = data.find(RESIDUAL_REGION[0].encode())
-            z = data.find(RESIDUAL_REGION[1].encode())
+            a = data.find(region[0].encode())
+            z = data.find(region[1].encode())
             data = data[a:z] if 0 <= a < z else data
         h.update(data)
     return h.hexdigest()
+
+
+def residual_sources_sha256():
+    return region_sha256(RESIDUAL_REGION)
+
+
+def mres_sources_sha256():
+    return region_sha256(MRES_REGION)
 
 
 def profiled_traffic(kernel, s):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or
     None when the workload differs from the captured one or the kernel's
     source changed since the capture."""
-    if (s.m, s.nnz) != (1 << 20, 9692830) or not os.path.exists(TRAFFIC_FILE):
+    if kernel.startswith("k_mres<"):
+        path, region = MRES_TRAFFIC_FILE, MRES_REGION
+    else:
+        path, region = TRAFFIC_FILE, RESIDUAL_REGION
+    if (s.m, s.nnz) != (1 << 20, 9692830) or not os.path.exists(path):
         return None
-    digest = residual_sources_sha256()
+    digest = region_sha256(region)
     rec = {}
-    with open(TRAFFIC_FILE) as fh:
+    with open(path) as fh:
         for ln in fh:
             if ln.strip() and not ln.startswith("#"):
                 k, v = ln.split()
@@ -538,7 +555,8 @@ def tuning_dict(t):
     """The launch shapes rorbk_autotune chose, and its per-iteration times."""
     return {"topk_blocks": t.topk_blocks, "collect_blocks": t.collect_blocks,
             "dyn_mark_blocks": t.dyn_mark_blocks, "dyn_scatter_blocks": t.dyn_scatter_blocks,
-            "residual_blocks": t.residual_blocks, "us_per_iteration_default": t.us_default,
+            "residual_blocks": t.residual_blocks, "graph_unroll": t.graph_unroll,
+            "us_per_iteration_default": t.us_default,
             "us_per_iteration_tuned": t.us_tuned}
 
 
@@ -1032,8 +1050,12 @@ def run_profile_multi(args):
     h = h0.multi(nr)
     Bd = torch.as_tensor(W.rhs_block(s, nr, seed=77), device="cuda")
     Xm = torch.as_tensor(np.random.default_rng(3).standard_normal((s.n, nr)) * 0.5, device="cuda")
+    # three FP32 block residuals, then three FP64 ones (the launches a
+    # traffic capture of k_mres takes), then the iterations
     for _ in range(3):
         h.residual_multi(Bd.float(), Xm.float(), None, precision=B.PREC_MIXED, wait=False)
+    for _ in range(3):
+        h.residual_multi(Bd, Xm, None, wait=False)
     X = torch.zeros((s.n, nr), dtype=torch.float64, device="cuda")
     res = h.solve_multi(Bd, X, tol=s.tol, maxit=args.profile_multi, seed=1, precision=B.PREC_MIXED,
                         inner_tol=args.inner_tol, host_loop=1, poll=args.profile_multi)

@@ -492,14 +492,18 @@ typedef struct {
     int32_t dyn_mark_blocks;     /* dynamic update: gather and marks    */
     int32_t dyn_scatter_blocks;  /* dynamic update: x += A_I^T y        */
     int32_t residual_blocks;     /* block residual (blocks of columns)  */
-    int32_t reserved_;
+    int32_t graph_unroll;        /* iterations per execution of the graph
+                                    loop's body (1..16): the body holds that
+                                    many iterations, and those after the
+                                    loop's end return at once             */
     double us_default, us_tuned;
 } rorbk_tuning;
 
 /* rorbk_autotune: chooses the shapes above for this handle by timing iters
  * host-driven iterations per candidate (coordinate descent over each shape in
- * turn, candidates 1/4 .. 4 x the default), every candidate from the same
- * state: the iterate after iters iterations from x0 = 0 on the right-hand
+ * turn, candidates 1/4 .. 4 x the default), then the graph's unroll (1, 2, 4
+ * or 8; iters graph-launched iterations per candidate), every candidate from
+ * the same state: the iterate after iters iterations from x0 = 0 on the right-hand
  * side b (device; m doubles, or m x nr row-major for a block), with the same
  * draws.  precision: the iteration to tune (RORBK_PREC_FP64, or
  * RORBK_PREC_MIXED for the FP32 inner iterations).  cache_file (may be NULL):
@@ -512,6 +516,9 @@ typedef struct {
 rorbk_status rorbk_autotune(rorbk_handle h, const double *b, int32_t precision, int64_t iters,
                             const char *cache_file, rorbk_tuning *out);
 rorbk_status rorbk_set_tuning(rorbk_handle h, const rorbk_tuning *t);
+/* A change of shapes drops the handle's instantiated graphs (the next solve
+ * captures them again); a batch built earlier keeps the shapes it was built
+ * with. */
 
 /* ---- the differentiable solve ------------------------------------------
  * (No counterpart in the paper, which never differentiates its solution.)

@@ -73,7 +73,7 @@ class Info(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("topk_blocks", C.c_int32), ("collect_blocks", C.c_int32),
                 ("dyn_mark_blocks", C.c_int32), ("dyn_scatter_blocks", C.c_int32),
-                ("residual_blocks", C.c_int32), ("reserved_", C.c_int32),
+                ("residual_blocks", C.c_int32), ("graph_unroll", C.c_int32),
                 ("us_default", C.c_double), ("us_tuned", C.c_double)]
 
 

@@ -15,6 +15,8 @@ namespace rorbk {
 
 // ---------------------------------------------------------------- limits
 constexpr int kMaxBlockRows = 1024;     // static block rows (one thread per row)
+constexpr int kGraphUnroll = 4;         // default iterations per graph WHILE-body execution
+constexpr int kMaxGraphUnroll = 16;
 constexpr int kMaxDynRows = 1024;       // K = floor(m/k)
 constexpr int kTileRows = 256;          // residual tile: rows ...
 constexpr int kTileNnz = 2048;          // ... and nonzeros per tile
@@ -222,6 +224,7 @@ struct rorbk_ctx {
     // launch shapes that do not change results (rorbk_autotune; 0: default)
     struct Tune {
         int topk = 0, collect = 0, mark = 0, scatter = 0, residual = 0;
+        int unroll = 0;   // iterations per WHILE-body execution of the graphs
     } tune;
     rorbk::Ctl *ctl = nullptr;
     rorbk::Ctl *ctl_in = nullptr;       // inner (FP32) loop state of the mixed form

@@ -1684,7 +1684,7 @@ template <typename T>
 __device__ void end_iteration(const T *x, int n, Ctl *ctl, int use_cond,
                               cudaGraphConditionalHandle hcond, int ld = 1,
                               unsigned *grp = nullptr) {
-    if (ctl->tr_x && ctl->iter < ctl->trace_cap && sizeof(T) == sizeof(double))
+    if (ctl->tr_x && !ctl->halt && ctl->iter < ctl->trace_cap && sizeof(T) == sizeof(double))
         for (int c = threadIdx.x; c < n; c += blockDim.x)
             ctl->tr_x[ctl->iter * (long long)n + c] = (double)x[(long long)c * ld];
     __syncthreads();
@@ -2478,6 +2478,34 @@ __global__ void __launch_bounds__(256) k_outer_update(double *__restrict__ x, co
 // sell.row[p]), coalesced through a per-warp staging tile.  The other steps run
 // the one-column kernels with one grid row (blockIdx.y) per column.
 
+// Loads that keep their line in L2 ahead of streamed data: an L2 eviction
+// policy made with createpolicy (evict_last for the whole access) passed as
+// a cache hint on the load.  The block residual gathers rows of X this way, so
+// X stays resident in L2 while A, B and R stream past it (evict-first).
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+template <typename T, int VEC>
+__device__ __forceinline__ VecT<T, VEC> vload_keep(const T *p, unsigned long long pol) {
+    VecT<T, VEC> r;
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3])
+                     : "l"(p), "l"(pol));
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;"
+                     : "=f"(r.v[0]), "=f"(r.v[1]) : "l"(p), "l"(pol));
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+                     : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(p), "l"(pol));
+    } else {
+        r = vload<T, VEC>(p);
+    }
+    return r;
+}
+
 // k_begin for a block of columns: ||b_j||, x_j = x0_j or 0, loop state; the
 // last column sets the WHILE condition.  Grid (1, nr).
 __global__ void k_mr_begin(const double *__restrict__ b, int m, const double *__restrict__ x0,
@@ -2647,6 +2675,7 @@ __global__ void __launch_bounds__(kMrWarps * 32, (mres_min_blocks<T, V, NR>()))
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int lc = lane % LPR, rsub = lane / LPR;
     const int c0 = lc * VEC;                // this lane's first column
+    const unsigned long long keep = l2_keep_policy();
     // slices (longest first) are taken from a queue, one per warp at a time,
     // so every warp stays busy until the queue is empty
     unsigned *queue = tick + 1;
@@ -2694,7 +2723,7 @@ __global__ void __launch_bounds__(kMrWarps * 32, (mres_min_blocks<T, V, NR>()))
                     const int q = g * RPS + rsub;
                     const int c = __shfl_sync(0xffffffffu, cc[u], q);
                     ag[u][g] = __shfl_sync(0xffffffffu, ac[u], q);
-                    if (q < cnt[u]) xg[u][g] = vload<T, VEC>(X + (long long)c * NR + c0);
+                    if (q < cnt[u]) xg[u][g] = vload_keep<T, VEC>(X + (long long)c * NR + c0, keep);
                 }
 #pragma unroll
             for (int u = 0; u < JS; ++u)

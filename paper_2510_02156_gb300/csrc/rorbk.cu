@@ -83,8 +83,29 @@ static cudaError_t begin_capture(cudaStream_t cs, cudaGraph_t parent) {
     return cudaStreamBeginCaptureToGraph(cs, parent, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
 }
 
-// Capture: k_begin, then WHILE(cond) { one iteration }.  With parent == NULL
-// the graph is instantiated into h->exec_fp64, else it is appended to parent.
+// Iterations per execution of a WHILE body.  Every iteration kernel returns at
+// once when its loop has halted, and the last one sets the condition from the
+// loop state, so a body of u iterations runs the same iterations as u
+// executions of a body of one; it saves the conditional node's turnaround on
+// u - 1 of every u iterations.
+static int graph_unroll(const rorbk_ctx *h) { return h->tune.unroll > 0 ? h->tune.unroll : kGraphUnroll; }
+
+// Destroys the handle's instantiated graphs; the next solve captures them again
+// (after a change of launch shapes).
+static void drop_graphs(rorbk_ctx *h) {
+    cudaGraphExec_t *g[5] = {&h->exec_fp64, &h->exec_mixed, &h->exec_fp64_w, &h->exec_fp64_inc,
+                             &h->exec_mixed_inc};
+    bool any = false;
+    for (auto *e : g) any = any || *e;
+    if (!any) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto *e : g)
+        if (*e) { cudaGraphExecDestroy(*e); *e = nullptr; }
+}
+
+// Capture: k_begin, then WHILE(cond) { graph_unroll(h) iterations }.  With
+// parent == NULL the graph is instantiated into h->exec_fp64, else it is
+// appended to parent.
 static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr, int weighted = 0,
                                      int inc = 0) {
     rorbk_status st;
@@ -124,7 +145,8 @@ static rorbk_status build_graph_fp64(rorbk_ctx *h, cudaGraph_t parent = nullptr,
         e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             h->stream = cs2;
-            launch_iteration(h, h->bb, h->xb, h->r, 1, (unsigned long long)hcond, weighted, inc);
+            for (int u = graph_unroll(h); u > 0; --u)
+                launch_iteration(h, h->bb, h->xb, h->r, 1, (unsigned long long)hcond, weighted, inc);
             cudaError_t e2 = cudaGetLastError();
             cudaGraph_t body_out = nullptr;
             e = cudaStreamEndCapture(cs2, &body_out);
@@ -173,7 +195,7 @@ static cudaError_t new_handle(cudaStream_t cs, cudaGraphConditionalHandle *hc) {
 }
 
 // Capture: k_begin, then WHILE(outer) { FP64 residual + inner set-up,
-// WHILE(inner) { one FP32 iteration }, x += d }.
+// WHILE(inner) { graph_unroll(h) FP32 iterations }, x += d }.
 static rorbk_status build_graph_mixed(rorbk_ctx *h, cudaGraph_t parent = nullptr, int inc = 0) {
     cudaStream_t saved = h->stream;
     cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2, cs3 = h->cap_stream3;
@@ -200,7 +222,8 @@ static rorbk_status build_graph_mixed(rorbk_ctx *h, cudaGraph_t parent = nullptr
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs3, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             h->stream = cs3;
-            launch_mixed_inner(h, 1, (unsigned long long)hin, inc);
+            for (int u = graph_unroll(h); u > 0; --u)
+                launch_mixed_inner(h, 1, (unsigned long long)hin, inc);
             cudaError_t e2 = cudaGetLastError();
             e = cudaStreamEndCapture(cs3, &tmp);
             if (e == cudaSuccess) e = e2;
@@ -781,7 +804,7 @@ static void tuning_out(const rorbk_ctx *h, double us0, double us1, rorbk_tuning 
     t->dyn_mark_blocks = grid_mark((rorbk_ctx *)h);
     t->dyn_scatter_blocks = grid_scatter((rorbk_ctx *)h);
     t->residual_blocks = h->tune.residual;
-    t->reserved_ = 0;
+    t->graph_unroll = graph_unroll(h);
     t->us_default = us0;
     t->us_tuned = us1;
 }
@@ -790,15 +813,20 @@ extern "C" {
 
 rorbk_status rorbk_set_tuning(rorbk_handle h, const rorbk_tuning *t) {
     if (!h) return RORBK_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    drop_graphs(h);
     if (!t) { h->tune = rorbk_ctx::Tune(); return RORBK_OK; }
     if (t->topk_blocks < 0 || t->collect_blocks < 0 || t->dyn_mark_blocks < 0 || t->dyn_scatter_blocks < 0 ||
         t->residual_blocks < 0)
         return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_set_tuning: negative block count");
+    if (t->graph_unroll < 0 || t->graph_unroll > kMaxGraphUnroll)
+        return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_set_tuning: graph_unroll outside 0..16");
     h->tune.topk = t->topk_blocks;
     h->tune.collect = t->collect_blocks;
     h->tune.mark = t->dyn_mark_blocks;
     h->tune.scatter = t->dyn_scatter_blocks;
     h->tune.residual = t->residual_blocks;
+    h->tune.unroll = t->graph_unroll;
     return RORBK_OK;
 }
 
@@ -818,16 +846,21 @@ rorbk_status rorbk_autotune(rorbk_handle h, const double *b, int32_t precision, 
             char line[512];
             while (fgets(line, sizeof(line), f)) {
                 if (strncmp(line, key, strlen(key)) != 0 || line[strlen(key)] != ' ') continue;
-                int v[5];
+                int v[6];
                 double us0 = 0, us1 = 0;
-                if (sscanf(line + strlen(key), " topk=%d collect=%d mark=%d scatter=%d residual=%d us=%lf,%lf",
-                           &v[0], &v[1], &v[2], &v[3], &v[4], &us0, &us1) == 7) {
+                if (sscanf(line + strlen(key),
+                           " topk=%d collect=%d mark=%d scatter=%d residual=%d unroll=%d us=%lf,%lf", &v[0],
+                           &v[1], &v[2], &v[3], &v[4], &v[5], &us0, &us1) == 8 &&
+                    v[5] >= 0 && v[5] <= kMaxGraphUnroll) {
                     fclose(f);
+                    cudaSetDevice(h->device);
+                    drop_graphs(h);
                     h->tune.topk = v[0];
                     h->tune.collect = v[1];
                     h->tune.mark = v[2];
                     h->tune.scatter = v[3];
                     h->tune.residual = v[4];
+                    h->tune.unroll = v[5];
                     if (out) tuning_out(h, us0, us1, out);
                     return RORBK_OK;
                 }
@@ -836,6 +869,7 @@ rorbk_status rorbk_autotune(rorbk_handle h, const double *b, int32_t precision, 
         }
     }
     cudaSetDevice(h->device);
+    drop_graphs(h);
     const size_t xbytes = (size_t)nr * h->n * sizeof(double);
     double *x0 = nullptr, *x = nullptr;
     if (cudaMalloc(&x0, xbytes) != cudaSuccess || cudaMalloc(&x, xbytes) != cudaSuccess) {
@@ -889,14 +923,31 @@ rorbk_status rorbk_autotune(rorbk_handle h, const double *b, int32_t precision, 
         }
         *fields[f] = best_v;
     }
+    // the graph's unroll, timed on graph-launched iterations (each candidate
+    // captured afresh)
+    if (st == RORBK_OK) {
+        o.host_loop = 0;
+        double gbest = 1e300;
+        int ubest = 1;
+        for (int u : {1, 2, 4, 8}) {
+            h->tune.unroll = u;
+            drop_graphs(h);
+            double us = 0;
+            if ((st = time_it(&us))) break;
+            if (us < 0.98 * gbest) { gbest = us; ubest = u; }
+        }
+        h->tune.unroll = ubest;
+        drop_graphs(h);
+    }
     cudaFree(x0);
     cudaFree(x);
     if (st) { h->tune = saved; return st; }
     if (cache_file) {
         FILE *f = fopen(cache_file, "a");
         if (f) {
-            fprintf(f, "%s topk=%d collect=%d mark=%d scatter=%d residual=%d us=%.3f,%.3f\n", key,
-                    h->tune.topk, h->tune.collect, h->tune.mark, h->tune.scatter, h->tune.residual, us0, cur);
+            fprintf(f, "%s topk=%d collect=%d mark=%d scatter=%d residual=%d unroll=%d us=%.3f,%.3f\n", key,
+                    h->tune.topk, h->tune.collect, h->tune.mark, h->tune.scatter, h->tune.residual,
+                    h->tune.unroll, us0, cur);
             fclose(f);
         }
     }

@@ -39,3 +39,14 @@ def test_traffic_record_is_dropped_for_other_workloads_or_changed_sources(tmp_pa
     inside.write_text(src.replace(marker, marker + "\n// changed"))
     monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(inside), bench.KERNEL_SOURCES[1]))
     assert bench.profiled_traffic("k_residual<float,float>", s) is None
+
+
+def test_block_residual_traffic_record_matches_the_committed_kernel():
+    s = types.SimpleNamespace(m=1 << 20, n=1 << 20, nnz=9692830)
+    t32 = bench.profiled_traffic("k_mres<float,float,16>", s)
+    t64 = bench.profiled_traffic("k_mres<double,float,16>", s)
+    assert t32 is not None and t64 is not None
+    # X's random row gathers re-read part of X (67 / 134 MB against L2)
+    assert 1.0 <= t32 / bench.mres_bytes(s, 16, 4, 4) <= 1.6
+    assert 1.0 <= t64 / bench.mres_bytes(s, 16, 4, 8) <= 2.0
+    assert bench.profiled_traffic("k_mres<float,float,8>", s) is None
