@@ -352,6 +352,14 @@ class _Null:
         return False
 
 
+_T0 = time.time()
+
+
+def note(msg):
+    """A progress line on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.time() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2510_02156_gb300 import binding as B
@@ -376,7 +384,9 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
     clk = ClockSampler(local)
+    note("timed mixed solves")
     mixed = run_solves(h, b, x, s, args, B.PREC_MIXED, args.steps, args.warmup, flush, torch, clk)
+    note("FP64 solves")
     t_step = mixed["time_s"]
     t_step = max_over_ranks(t_step, dist, "cuda")
     fp64 = run_solves(h, b, x, s, args, B.PREC_FP64, args.fp64_steps, 1, flush, torch)
@@ -392,15 +402,23 @@ def run_ours(args, rank, world, local):
                  inner_tol=args.inner_tol)
     e2e_s = time.perf_counter() - t1
 
+    note("incremental residual")
     inc = None if args.no_incremental else incremental_measurement(args, s, h, b, x, flush)
+    note("FAB-GMRES")
     fg = None if args.no_fabgmres else fabgmres_measurement(args)
+    note("differentiable solve")
     ag = None if args.no_autograd else autograd_measurement(args)
+    note("residual-weighted draws")
     weighted = None if args.no_weighted else weighted_measurement(args)
     batched = batched_measurement(args) if args.clone_batched else None
+    note("block of 16 right-hand sides")
     multi = (None if args.no_multi_rhs else
              multi_rhs_measurement(args, s, flush, mixed["time_s"], fp64["time_s"]))
+    note("batched configuration")
     scale = None if args.no_batched_scale else batched_scale_measurement(args, flush)
+    note("dense system")
     dense = None if args.no_dense else dense_measurement(args, flush)
+    note("done with the GPU measurements")
 
     # the sparse residual kernels timed alone, the same kernel and grid as in
     # the solve: FP32 (the inner solve, every iteration) and FP64
@@ -888,35 +906,46 @@ def weighted_measurement(args):
 def autograd_measurement(args):
     """Forward solve and adjoint backward of L = 0.5 ||x - x_t||^2 on the
     262,144-unknown power-law system (1024 blocks of 256 rows), to the bench
-    tolerance, through the torch.autograd.Function.  Wall times include the
-    handles' set-up (the adjoint handle's transpose and equilibration); the
-    solve times are the device loops'."""
+    tolerance, through the torch.autograd.Function, twice on one SolveSpec:
+    the first forward sets its handle up (from device copies of the pattern
+    and values), the second, with every value changed by a relative 1e-3
+    N(0,1), refreshes it on the device (rorbk_update_values).  Wall times
+    include that set-up or refresh and the adjoint handle's set-up (device
+    transpose); the solve times are the device loops'."""
     import torch
     from paper_2510_02156_gb300 import autograd as AG
     from paper_2510_02156_gb300 import workloads as W
     s = W.powerlaw(n=1 << 18, num_blocks=1024, seed=1, lam=args.lam, tol=args.tol,
                    cache=args.cache)
     x_t = torch.as_tensor(np.random.default_rng(26).standard_normal(s.n), device="cuda")
-    vals = torch.tensor(s.values.astype(np.float64), requires_grad=True)
-    b = torch.tensor(s.b, requires_grad=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    x, spec = AG.solve(s.row_ptr, s.col_idx, vals, b, num_blocks=s.num_blocks, lam=s.lam,
-                       tol=s.tol, maxit=args.maxit)
-    loss = 0.5 * ((x - x_t) ** 2).sum()
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    loss.backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    f, a = spec.last_forward, spec.last_adjoint
-    return {"workload": f"power-law sparse square CSR, n={s.n}, nnz={s.nnz}, 1024 blocks of 256, "
-                        f"lambda={s.lam:g}, tol={s.tol:g}; L = 0.5||x - x_t||^2",
-            "forward_s": t1 - t0, "backward_s": t2 - t1,
-            "forward_solve_s": f.time_ms / 1e3, "adjoint_solve_s": a.time_ms / 1e3,
-            "forward_iters": int(f.iters), "adjoint_iters": int(a.iters),
-            "forward_rrn": float(f.rrn), "adjoint_rrn": float(a.rrn),
-            "converged": bool(f.converged and a.converged)}
+    v0 = s.values.astype(np.float64)
+    v1 = v0 * (1.0 + 1e-3 * np.random.default_rng(28).standard_normal(v0.size))
+    spec = AG.SolveSpec(np.asarray(s.row_ptr, np.int32), np.asarray(s.col_idx, np.int32), s.m, s.n,
+                        s.num_blocks, s.lam, tol=s.tol, maxit=args.maxit)
+    out = {"workload": f"power-law sparse square CSR, n={s.n}, nnz={s.nnz}, 1024 blocks of 256, "
+                       f"lambda={s.lam:g}, tol={s.tol:g}; L = 0.5||x - x_t||^2"}
+    for name, v in (("first", v0), ("second", v1)):
+        vals = torch.tensor(v, device="cuda", requires_grad=True)
+        b = torch.tensor(s.b, device="cuda", requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = AG.RorbkSolve.apply(vals, b, spec)
+        loss = 0.5 * ((x - x_t) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        f, a = spec.last_forward, spec.last_adjoint
+        out[name] = {"forward_s": t1 - t0, "backward_s": t2 - t1,
+                     "forward_solve_s": f.time_ms / 1e3, "adjoint_solve_s": a.time_ms / 1e3,
+                     "forward_iters": int(f.iters), "adjoint_iters": int(a.iters),
+                     "forward_rrn": float(f.rrn), "adjoint_rrn": float(a.rrn),
+                     "converged": bool(f.converged and a.converged)}
+    out["handles_set_up"] = spec.setups
+    out["second_forward_wall_over_solve"] = out["second"]["forward_s"] / out["second"]["forward_solve_s"]
+    spec.close()
+    return out
 
 
 def cpu_model():

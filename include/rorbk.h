@@ -254,6 +254,28 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part,
                          double lambda, const rorbk_options *opt,
                          rorbk_handle *out);
 
+/* rorbk_update_values: new values for h's A, same pattern (row_ptr, col_idx,
+ * partition and lambda as set up).  Everything of the set-up that depends on
+ * the values (the SELL copy, row norms, block transposes, centroids, C, P
+ * and its running sum, the static operators W_t, their FP32 copies, and the
+ * column-major copy of the incremental residual if it was built) is formed
+ * again on the device by the set-up's own kernels, so the handle equals a
+ * fresh rorbk_setup with these values bit for bit.  No host copy of A is made
+ * and nothing new is allocated beyond per-call scratch.
+ *   values    : nnz entries in the order A was given in (CSR order; a dense A:
+ *               m x n row-major with leading dimension n), of the handle's
+ *               value type dtype (RORBK_F64 or RORBK_F32).
+ *   on_device : 1 if values is device memory, 0 for host memory.
+ * Handles that share h's set-up (rorbk_clone, rorbk_multi_create) see the new
+ * values too; no solve of any of them may be in flight.  A batch or graph
+ * built earlier stays valid (no buffer moves).  Errors: RORBK_ERR_INVALID_ARG
+ * (NULL values, dtype other than the handle's); RORBK_ERR_NUMERIC (a NaN or Inf
+ * among the values: the handle is left unchanged); RORBK_ERR_UNSUPPORTED for a
+ * handle made by rorbk_setup_adjoint (set up a new one); RORBK_ERR_NOT_SPD
+ * (lambda = 0 and dependent rows: the handle must then be given valid values
+ * again or freed). */
+rorbk_status rorbk_update_values(rorbk_handle h, const void *values, int32_t dtype, int32_t on_device);
+
 /* Solve (Algorithm 1's iteration) from x0 until ||b - A x|| / ||b|| <= tol or
  * maxit iterations.
  *   b  : device, m doubles.   x0 : device, n doubles, or NULL for x0 = 0.

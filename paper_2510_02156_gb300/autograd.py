@@ -16,6 +16,13 @@ in the CUDA library; this module only marshals tensors.
 
 Both solves stop at their own tolerance, so the gradient carries the solve
 error: roughly cond(A) times the tolerance in the relative sense.
+
+The handle lives on the SolveSpec.  The first forward sets it up from device
+copies of the pattern and the values; every later forward with the same
+spec hands the new values to rorbk_update_values, which re-forms the set-up
+on the device (no host copy of A, no new handle).  The adjoint handle is
+built on the device too (rorbk_setup_adjoint).  SolveSpec.close() frees the
+handle.
 """
 from __future__ import annotations
 
@@ -45,6 +52,34 @@ class SolveSpec:
     inner_tol: float = 1e-4
     last_forward: Optional[B.Result] = field(default=None, repr=False)
     last_adjoint: Optional[B.Result] = field(default=None, repr=False)
+    # the cached handle, its device pattern, and which forward's values it holds
+    _handle: Optional[B.Handle] = field(default=None, repr=False)
+    _pattern: Optional[tuple] = field(default=None, repr=False)
+    _holds: int = field(default=0, repr=False)
+    _forwards: int = field(default=0, repr=False)
+    setups: int = 0                            # handles set up (1 after any number of forwards)
+
+    def handle_for(self, vals, version):
+        """The cached handle holding `vals` (device, this spec's value type)."""
+        torch = _torch()
+        if self._handle is None:
+            if self._pattern is None:
+                self._pattern = (torch.as_tensor(self.row_ptr, dtype=torch.int32, device="cuda"),
+                                 torch.as_tensor(self.col_idx, dtype=torch.int32, device="cuda"))
+            rp, ci = self._pattern
+            self._handle = B.Handle(rp, ci, vals, self.m, self.n, self.num_blocks, self.lam,
+                                    precision=self.precision)
+            self.setups += 1
+        elif self._holds != version:
+            self._handle.update_values(vals)
+        self._holds = version
+        return self._handle
+
+    def close(self):
+        """Frees the cached handle."""
+        if self._handle is not None:
+            self._handle.close()
+            self._handle = None
 
 
 def _torch():
@@ -70,26 +105,30 @@ class RorbkSolve:
                 def forward(ctx, values, b, spec):
                     if spec.m != spec.n:
                         raise ValueError("the differentiable solve needs a square A")
-                    vals = values.detach().cpu().numpy()
-                    h = B.Handle(spec.row_ptr, spec.col_idx, vals, spec.m, spec.n,
-                                 spec.num_blocks, spec.lam, precision=spec.precision)
+                    vdt = torch.float32 if values.dtype == torch.float32 else torch.float64
+                    vals = values.detach().to(device="cuda", dtype=vdt).contiguous()
+                    spec._forwards += 1
+                    version = spec._forwards
+                    h = spec.handle_for(vals, version)
                     bd = b.detach().to(device="cuda", dtype=torch.float64).contiguous()
                     x = torch.empty(spec.n, dtype=torch.float64, device="cuda")
                     spec.last_forward = h.solve(bd, x, tol=spec.tol, maxit=spec.maxit,
                                                 seed=spec.seed, precision=spec.precision,
                                                 inner_tol=spec.inner_tol)
-                    ctx.h = h
                     ctx.spec = spec
+                    ctx.version = version
                     ctx.vmeta = (values.dtype, values.device)
                     ctx.bmeta = (b.dtype, b.device)
-                    ctx.save_for_backward(x)
+                    ctx.save_for_backward(x, vals)
                     return x
 
                 @staticmethod
                 def backward(ctx, gx):
-                    (x,) = ctx.saved_tensors
+                    x, vals = ctx.saved_tensors
                     spec = ctx.spec
-                    h = ctx.h
+                    # the handle again holds this forward's values (a later
+                    # forward of the same spec may have replaced them)
+                    h = spec.handle_for(vals, ctx.version)
                     kt = spec.adjoint_blocks or spec.num_blocks
                     adj = h.setup_adjoint(kt, spec.lam, precision=spec.precision)
                     try:
@@ -107,8 +146,6 @@ class RorbkSolve:
                         dvals = dv.to(dtype=ctx.vmeta[0], device=ctx.vmeta[1])
                     if ctx.needs_input_grad[1]:
                         db = g.to(dtype=ctx.bmeta[0], device=ctx.bmeta[1])
-                    h.close()
-                    ctx.h = None
                     return dvals, db, None
 
             cls._fn = _Solve

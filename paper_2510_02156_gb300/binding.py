@@ -82,6 +82,7 @@ _P, _I64, _U64, _D = C.c_void_p, C.c_int64, C.c_uint64, C.c_double
 SIGNATURES = {
     "rorbk_default_options": (None, [_P]),
     "rorbk_setup": (C.c_int, [_P, _P, _D, _P, _P]),
+    "rorbk_update_values": (C.c_int, [_P, _P, C.c_int32, C.c_int32]),
     "rorbk_solve": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P]),
     "rorbk_solve_host": (C.c_int, [_P, _P, _P, _P, _D, _I64, _P, _P]),
     "rorbk_free": (None, [_P]),
@@ -158,6 +159,20 @@ def _ptr(x):
     return x.ctypes.data_as(C.c_void_p)
 
 
+def _is_device(x):
+    return hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)
+
+
+def _value_dtype(t):
+    """F64 / F32 for a torch tensor of float64 / float32 values."""
+    name = str(t.dtype)
+    if name == "torch.float64":
+        return F64
+    if name == "torch.float32":
+        return F32
+    raise ValueError("values must be float64 or float32")
+
+
 def default_options(**kw) -> Options:
     o = Options()
     lib().rorbk_default_options(C.byref(o))
@@ -178,24 +193,35 @@ class Handle:
 
     def __init__(self, row_ptr, col_idx, values, m, n, num_blocks, lam, precision=PREC_FP64,
                  offsets=None, stream=None):
+        """A from host (numpy) arrays, or, for CSR, from device (torch CUDA)
+        tensors: int32 row_ptr and col_idx and float64/float32 values, all on
+        the device (rorbk_matrix.on_device = 1)."""
         self._keep = []
-        vals = np.ascontiguousarray(values)
-        if vals.dtype == np.float32:
-            dt = F32
+        if _is_device(values):
+            if row_ptr is None or not (_is_device(row_ptr) and _is_device(col_idx)):
+                raise ValueError("device values need device row_ptr and col_idx (CSR)")
+            dt = _value_dtype(values)
+            self._keep += [row_ptr, col_idx, values]
+            A = Matrix(FORMAT_CSR, dt, m, n, int(values.numel()), row_ptr.data_ptr(),
+                       col_idx.data_ptr(), values.data_ptr(), 0, 1, 0)
         else:
-            vals = np.ascontiguousarray(vals, dtype=np.float64)
-            dt = F64
-        if row_ptr is None:            # dense row-major m x n
-            if vals.shape != (m, n):
-                raise ValueError("dense values must have shape (m, n)")
-            self._keep.append(vals)
-            A = Matrix(FORMAT_DENSE, dt, m, n, m * n, None, None, vals.ctypes.data, n, 0, 0)
-        else:
-            rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
-            ci = np.ascontiguousarray(col_idx, dtype=np.int32)
-            self._keep += [rp, ci, vals]
-            A = Matrix(FORMAT_CSR, dt, m, n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data,
-                       vals.ctypes.data, 0, 0, 0)
+            vals = np.ascontiguousarray(values)
+            if vals.dtype == np.float32:
+                dt = F32
+            else:
+                vals = np.ascontiguousarray(vals, dtype=np.float64)
+                dt = F64
+            if row_ptr is None:            # dense row-major m x n
+                if vals.shape != (m, n):
+                    raise ValueError("dense values must have shape (m, n)")
+                self._keep.append(vals)
+                A = Matrix(FORMAT_DENSE, dt, m, n, m * n, None, None, vals.ctypes.data, n, 0, 0)
+            else:
+                rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+                ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+                self._keep += [rp, ci, vals]
+                A = Matrix(FORMAT_CSR, dt, m, n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data,
+                           vals.ctypes.data, 0, 0, 0)
         offs = None
         if offsets is not None:
             offs = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -236,6 +262,21 @@ class Handle:
     def initial_solution(self, b, x0, block=0):
         """rorbk_initial_solution (Algorithm 2) on device tensors b (m), x0 (n)."""
         _check(lib().rorbk_initial_solution(self.h, block, _ptr(b), _ptr(x0)), self.h)
+
+    def update_values(self, values):
+        """rorbk_update_values: new values of A (same pattern), a numpy array
+        or a device tensor of the handle's value type; re-forms the set-up on
+        the device."""
+        if _is_device(values):
+            if not values.is_contiguous():
+                raise ValueError("values must be contiguous")
+            dt, on_dev = _value_dtype(values), 1
+        else:
+            values = np.ascontiguousarray(values)
+            if values.dtype not in (np.float32, np.float64):
+                values = np.ascontiguousarray(values, dtype=np.float64)
+            dt, on_dev = (F32 if values.dtype == np.float32 else F64), 0
+        _check(lib().rorbk_update_values(self.h, _ptr(values), dt, on_dev), self.h)
 
     def clone(self):
         """rorbk_clone: a Handle sharing this one's set-up, with its own workspace."""

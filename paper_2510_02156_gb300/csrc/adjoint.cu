@@ -33,6 +33,12 @@
 namespace rorbk {
 namespace {
 
+// c_i = ||A_i||_2 from ||A_i||^2 (1 for a zero row).
+__global__ void k_row_scale(const double *__restrict__ rn, int m, double *__restrict__ c) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        c[i] = rn[i] > 0.0 ? __dsqrt_rn(rn[i]) : 1.0;
+}
+
 // g_i = h_i / c_i (the adjoint solution from the equilibrated iterate).
 __global__ void k_unscale(double *__restrict__ g, const double *__restrict__ c, int m) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
@@ -64,55 +70,44 @@ extern "C" rorbk_status rorbk_setup_adjoint(rorbk_handle h, const rorbk_partitio
     cudaGetDevice(&cur);
     cudaSetDevice(h->device);
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
-    const bool f32 = h->vdtype == RORBK_F32;
-    std::vector<int> rp(m + 1), col(nnz);
-    std::vector<double> v64(f32 ? 0 : nnz);
-    std::vector<float> v32(f32 ? nnz : 0);
     rorbk_status st;
-
     cudaStream_t s = h->stream;
-    if ((st = cuda_check(h, cudaStreamSynchronize(s), "rorbk_setup_adjoint"))) { cudaSetDevice(cur); return st; }
-    cudaError_t e = cudaMemcpy(rp.data(), h->rowptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(col.data(), h->col, nnz * sizeof(int), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && nnz)
-        e = f32 ? cudaMemcpy(v32.data(), h->val32, nnz * sizeof(float), cudaMemcpyDeviceToHost)
-                : cudaMemcpy(v64.data(), h->val, nnz * sizeof(double), cudaMemcpyDeviceToHost);
-    if ((st = cuda_check(h, e, "rorbk_setup_adjoint: copy of A"))) { cudaSetDevice(cur); return st; }
-    // Row norms of A (the column norms of A^T), each summed in stored order.
-    std::vector<double> c(m);
-    for (int64_t i = 0; i < m; ++i) {
-        double ss = 0.0;
-        for (int p = rp[i]; p < rp[i + 1]; ++p) {
-            const double v = f32 ? (double)v32[p] : v64[p];
-            ss = std::fma(v, v, ss);
-        }
-        c[i] = ss > 0.0 ? std::sqrt(ss) : 1.0;
+    // At~ on the device: c_i = ||A_i||_2 from the row norms of the set-up (each
+    // a fused chain over the row in stored order), then the column-major copy
+    // of A with a_ij / c_i: row j of At~ lists the rows i of A that hold
+    // column j, ascending.
+    int *tp = nullptr, *tcol = nullptr;
+    double *t64 = nullptr, *c = nullptr;
+    cudaError_t e = cudaMalloc(&tp, (n + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&tcol, std::max<int64_t>(1, nnz) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&t64, std::max<int64_t>(1, nnz) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c, m * sizeof(double));
+    auto release = [&]() {
+        cudaStreamSynchronize(s);
+        cudaFree(tp);
+        cudaFree(tcol);
+        cudaFree(t64);
+        cudaFree(c);
+        cudaSetDevice(cur);
+    };
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(h, RORBK_ERR_OOM, "rorbk_setup_adjoint: copy of A");
     }
-    // Stable counting sort by column: row j of A^T lists the rows i of A that
-    // hold column j, in ascending i, so its columns are strictly ascending.
-    // Values are a_ij / c_i in FP64.
-    std::vector<int> tp(n + 1, 0), tcol(nnz);
-    std::vector<double> t64(nnz);
-    for (int64_t p = 0; p < nnz; ++p) tp[col[p] + 1]++;
-    for (int64_t j = 0; j < n; ++j) tp[j + 1] += tp[j];
-    std::vector<int> fill(tp.begin(), tp.end() - 1);
-    for (int64_t i = 0; i < m; ++i)
-        for (int p = rp[i]; p < rp[i + 1]; ++p) {
-            const int q = fill[col[p]]++;
-            tcol[q] = (int)i;
-            t64[q] = (f32 ? (double)v32[p] : v64[p]) / c[i];
-        }
+    k_row_scale<<<std::max(1, std::min(8 * h->num_sms, (int)((m + 255) / 256))), 256, 0, s>>>(h->rn, (int)m, c);
+    if ((st = build_csc(h, c, tp, tcol, t64, nullptr))) { release(); return st; }
     rorbk_matrix At;
     At.format = RORBK_FORMAT_CSR;
     At.dtype = RORBK_F64;
     At.m = n;
     At.n = m;
     At.nnz = nnz;
-    At.row_ptr = tp.data();
-    At.col_idx = tcol.data();
-    At.values = t64.data();
+    At.row_ptr = tp;
+    At.col_idx = tcol;
+    At.values = t64;
     At.ld = 0;
-    At.on_device = 0;
+    At.on_device = 1;
     At.reserved_ = 0;
     rorbk_options o;
     rorbk_default_options(&o);
@@ -122,8 +117,7 @@ extern "C" rorbk_status rorbk_setup_adjoint(rorbk_handle h, const rorbk_partitio
     if (st == RORBK_OK) {
         rorbk_ctx *a = *out;
         a->adj_scale = (double *)dev_alloc(a, (size_t)m * sizeof(double));
-        cudaError_t e2 = a->adj_scale ? cudaMemcpy(a->adj_scale, c.data(), m * sizeof(double),
-                                                   cudaMemcpyHostToDevice)
+        cudaError_t e2 = a->adj_scale ? cudaMemcpy(a->adj_scale, c, m * sizeof(double), cudaMemcpyDeviceToDevice)
                                       : cudaErrorMemoryAllocation;
         if (e2 != cudaSuccess) {
             st = a->adj_scale ? cuda_check(a, e2, "rorbk_setup_adjoint: scale")
@@ -133,7 +127,7 @@ extern "C" rorbk_status rorbk_setup_adjoint(rorbk_handle h, const rorbk_partitio
             *out = nullptr;
         }
     }
-    cudaSetDevice(cur);
+    release();
     return st;
 }
 

@@ -1,4 +1,4 @@
-// incremental.cu -- host set-up of the incremental residual.
+// incremental.cu -- set-up of the incremental residual.
 //
 // Algorithm 1 forms the full residual r = b - A x once per iteration, after
 // the static updates, to pick the dynamic block; in Section 3.1's cost count
@@ -18,7 +18,7 @@
 //                                 more (n_static > 3) overflow it, which only
 //                                 makes that iteration's residual exact.
 // The copy costs 16 bytes per nonzero plus 4 per column and is built on the
-// host from the device's CSR (one transfer each way).
+// device (build_csc: a counting placement and merge rounds per column).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,59 +29,56 @@
 #include "internal.cuh"
 
 namespace rorbk {
+namespace {
+
+// The largest number of nonzeros in one block of the partition.
+__global__ void k_max_block_nnz(const int *__restrict__ rowptr, const int *__restrict__ off, int k,
+                                int *__restrict__ out) {
+    int v = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x)
+        v = max(v, rowptr[off[t + 1]] - rowptr[off[t]]);
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
+}  // namespace
 
 rorbk_status ensure_incremental(rorbk_ctx *h) {
     if (h->csc_ptr && h->ilog_col) return RORBK_OK;
     if (h->format != RORBK_FORMAT_CSR)
         return fail(h, RORBK_ERR_UNSUPPORTED, "the incremental residual is built for sparse (CSR) systems");
-    const int64_t m = h->m, n = h->n, nnz = h->nnz;
-    std::vector<int> rp(m + 1), col(nnz);
-    std::vector<double> val(nnz);
+    const int64_t n = h->n, nnz = h->nnz;
     rorbk_status st;
-    if ((st = cuda_check(h, cudaStreamSynchronize(h->stream), "incremental residual set-up"))) return st;
-    cudaError_t e = cudaMemcpy(rp.data(), h->rowptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(col.data(), h->col, nnz * sizeof(int), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(val.data(), h->val, nnz * sizeof(double), cudaMemcpyDeviceToHost);
-    if ((st = cuda_check(h, e, "incremental residual set-up"))) return st;
-    // counting sort of the entries by column; rows stay ascending in a column
-    std::vector<int> cp(n + 1, 0), crow(nnz);
-    std::vector<double> cval(nnz);
-    std::vector<float> cval32(nnz);
-    for (int64_t p = 0; p < nnz; ++p) ++cp[col[p] + 1];
-    for (int64_t c = 0; c < n; ++c) cp[c + 1] += cp[c];
-    std::vector<int> next(cp.begin(), cp.end() - 1);
-    for (int64_t i = 0; i < m; ++i)
-        for (int p = rp[i]; p < rp[i + 1]; ++p) {
-            const int q = next[col[p]]++;
-            crow[q] = (int)i;
-            cval[q] = val[p];
-            cval32[q] = (float)val[p];
-        }
-    int64_t maxblk = 0;
-    for (int64_t t = 0; t < h->k; ++t)
-        maxblk = std::max<int64_t>(maxblk, rp[h->h_off[t + 1]] - rp[h->h_off[t]]);
-    const int64_t cap = std::min<int64_t>(std::max<int64_t>(1 << 16, 4 * maxblk + h->dyn.ecap), INT32_MAX / 2);
-    h->csc_ptr = (int *)dev_alloc(h, (n + 1) * sizeof(int));
-    h->csc_row = (int *)dev_alloc(h, nnz * sizeof(int));
-    h->csc_val = (double *)dev_alloc(h, nnz * sizeof(double));
-    h->csc_val32 = (float *)dev_alloc(h, nnz * sizeof(float));
-    h->ilog_col = (int *)dev_alloc(h, cap * sizeof(int));
-    h->ilog_val = (double *)dev_alloc(h, cap * sizeof(double));
-    if (!h->csc_ptr || !h->csc_row || !h->csc_val || !h->csc_val32 || !h->ilog_col || !h->ilog_val) {
-        h->csc_ptr = nullptr;   // the allocations made stay on the handle's list
-        h->ilog_col = nullptr;
+    cudaStream_t s = h->stream;
+    if ((st = cuda_check(h, cudaStreamSynchronize(s), "incremental residual set-up"))) return st;
+    int *dmax = nullptr;
+    if ((st = cuda_check(h, cudaMalloc(&dmax, sizeof(int)), "incremental residual set-up"))) return st;
+    cudaMemsetAsync(dmax, 0, sizeof(int), s);
+    k_max_block_nnz<<<std::max(1, std::min(h->num_sms, (h->k + 255) / 256)), 256, 0, s>>>(
+        h->rowptr, h->off, h->k, dmax);
+    int maxblk = 0;
+    st = cuda_check(h, cudaMemcpyAsync(&maxblk, dmax, sizeof(int), cudaMemcpyDeviceToHost, s),
+                    "incremental residual set-up");
+    if (!st) st = cuda_check(h, cudaStreamSynchronize(s), "incremental residual set-up");
+    cudaFree(dmax);
+    if (st) return st;
+    const int64_t cap = std::min<int64_t>(std::max<int64_t>(1 << 16, 4LL * maxblk + h->dyn.ecap), INT32_MAX / 2);
+    int *cp = (int *)dev_alloc(h, (n + 1) * sizeof(int));
+    int *crow = (int *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(int));
+    double *cval = (double *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(double));
+    float *cval32 = (float *)dev_alloc(h, std::max<int64_t>(1, nnz) * sizeof(float));
+    int *lcol = (int *)dev_alloc(h, cap * sizeof(int));
+    double *lval = (double *)dev_alloc(h, cap * sizeof(double));
+    if (!cp || !crow || !cval || !cval32 || !lcol || !lval)   // the allocations made stay on the handle's list
         return fail(h, RORBK_ERR_OOM, "incremental residual set-up: out of device memory");
-    }
+    if ((st = build_csc(h, nullptr, cp, crow, cval, cval32))) return st;
+    h->csc_ptr = cp;
+    h->csc_row = crow;
+    h->csc_val = cval;
+    h->csc_val32 = cval32;
+    h->ilog_col = lcol;
+    h->ilog_val = lval;
     h->ilog_cap = (int)cap;
-    e = cudaMemcpy(h->csc_ptr, cp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(h->csc_row, crow.data(), nnz * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(h->csc_val, cval.data(), nnz * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(h->csc_val32, cval32.data(), nnz * sizeof(float), cudaMemcpyHostToDevice);
-    if ((st = cuda_check(h, e, "incremental residual set-up"))) {
-        h->csc_ptr = nullptr;
-        h->ilog_col = nullptr;
-        return st;
-    }
     return RORBK_OK;
 }
 

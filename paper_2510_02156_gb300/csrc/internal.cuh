@@ -248,7 +248,12 @@ void record_setup_error(const std::string &msg);
 void *dev_alloc(rorbk_ctx *h, size_t bytes);
 
 // setup (kernels_setup.cu)
-rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &host_row_ptr);
+// refresh: new values of the same pattern; reuses every buffer (rorbk_update_values)
+rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &host_row_ptr, bool refresh = false);
+// Column-major copy of A built on the device: cp [n+1], crow [nnz] (rows
+// ascending in each column), cval [nnz] = a_ij / scale[i] (scale == NULL: a_ij)
+// and, if cval32 != NULL, its FP32 rounding.
+rorbk_status build_csc(rorbk_ctx *h, const double *scale, int *cp, int *crow, double *cval, float *cval32);
 void widen_values(rorbk_ctx *h, int dtype);   // FP32 <-> FP64 value copies
 void fill_dense_columns(rorbk_ctx *h);        // column indices of a dense A held as CSR
 

@@ -599,12 +599,116 @@ void fill_dense_columns(rorbk_ctx *h) {
     k_dense_cols<<<g, 256, 0, h->stream>>>(h->col, h->nnz, (int)h->n);
 }
 
+// ------------------------------------------------- column-major copy of A
+// Entries of column j in ascending rows.  Count per column, scan, place every
+// entry at a free slot of its column (in any order), then order each column's
+// slots by CSR position with rounds of pairwise merges of runs of 1, 2, 4, ...
+// slots: a slot's place in the merged run is its index in its own run plus the
+// number of slots of the other run that hold a smaller position (positions
+// are distinct).  A row's entries are ascending in position, so the columns
+// list their rows ascending.
+__global__ void k_col_count(const int *__restrict__ col, long long nnz, int *__restrict__ cnt) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nnz;
+         p += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[col[p]], 1);
+}
+
+__global__ void k_col_max(const int *__restrict__ cp, int n, int *__restrict__ out) {
+    int v = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        v = max(v, cp[j + 1] - cp[j]);
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
+__global__ void k_col_place(const int *__restrict__ rowptr, const int *__restrict__ col, int m,
+                            const int *__restrict__ cp, int *__restrict__ fill, int *__restrict__ slot,
+                            int *__restrict__ rowid) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            const int c = col[p];
+            slot[cp[c] + atomicAdd(&fill[c], 1)] = p;
+            rowid[p] = i;
+        }
+}
+
+__global__ void k_col_merge(const int *__restrict__ col, const int *__restrict__ cp,
+                            const int *__restrict__ in, int *__restrict__ out, long long nnz, int run) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int p = in[q];
+        const int c = col[p];
+        const long long s0 = cp[c];
+        const int len = cp[c + 1] - (int)s0, o = (int)(q - s0);
+        const int base = (int)(o / (2LL * run) * (2LL * run));
+        const bool left = o - base < run;
+        const int own0 = left ? base : base + run, oth0 = left ? base + run : base;
+        const int othlen = max(0, min(run, len - oth0));
+        const int *other = in + s0 + oth0;
+        int lo = 0, hi = othlen;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (other[mid] < p) lo = mid + 1; else hi = mid;
+        }
+        out[s0 + base + (o - own0) + lo] = p;
+    }
+}
+
+__global__ void k_col_gather(const int *__restrict__ slot, const int *__restrict__ rowid,
+                             const double *__restrict__ val, const double *__restrict__ scale,
+                             long long nnz, int *__restrict__ crow, double *__restrict__ cval,
+                             float *__restrict__ cval32) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int p = slot[q], i = rowid[p];
+        const double v = scale ? __ddiv_rn(val[p], scale[i]) : val[p];
+        crow[q] = i;
+        cval[q] = v;
+        if (cval32) cval32[q] = __double2float_rn(v);
+    }
+}
+
 // ---------------------------------------------------------------- driver
+// Device scratch of one set-up pass, freed when the pass ends (after the
+// stream has drained).
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> p;
+    explicit Scratch(cudaStream_t s_) : s(s_) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    template <typename T>
+    T *get(size_t count) {
+        void *q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        p.push_back(q);
+        return (T *)q;
+    }
+    ~Scratch() {
+        if (p.empty()) return;
+        cudaStreamSynchronize(s);
+        for (void *q : p) cudaFree(q);
+    }
+};
+
+// A buffer the handle keeps: allocated on the first set-up pass, reused by a
+// refresh of the values (same pattern, same size).
+template <typename T>
+static bool keep(rorbk_ctx *h, T *&ptr, size_t count) {
+    if (!ptr) ptr = (T *)dev_alloc(h, std::max<size_t>(count, 1) * sizeof(T));
+    return ptr != nullptr;
+}
+
+// Exclusive scan of n ints in place; *grand_total_host receives the sum.
 static rorbk_status scan_device(rorbk_ctx *h, int *d, long long n, int *grand_total_host) {
     const int nt = 256;
     long long tiles = (n + nt - 1) / nt;
-    int *sums = (int *)dev_alloc(h, (size_t)(tiles + 1) * sizeof(int));
-    int *tot = (int *)dev_alloc(h, sizeof(int));
+    Scratch sc(h->stream);
+    int *sums = sc.get<int>(tiles + 1);
+    int *tot = sc.get<int>(1);
     if (!sums || !tot) return fail(h, RORBK_ERR_OOM, "scan workspace");
     k_scan_tiles<<<(unsigned)tiles, nt, 0, h->stream>>>(d, d, sums, n);
     k_scan_sums<<<1, 1024, 0, h->stream>>>(sums, (int)tiles, tot);
@@ -615,54 +719,58 @@ static rorbk_status scan_device(rorbk_ctx *h, int *d, long long n, int *grand_to
     return cuda_check(h, cudaStreamSynchronize(h->stream), "scan");
 }
 
-// Rows sorted by length (longest first, ties by row) into slices of 32.
-static rorbk_status build_sell(rorbk_ctx *h, const std::vector<int> &hrp) {
-    const int m = (int)h->m;
-    int maxlen = 0;
-    for (int i = 0; i < m; ++i) maxlen = std::max(maxlen, hrp[i + 1] - hrp[i]);
-    std::vector<int> cnt(maxlen + 2, 0);
-    for (int i = 0; i < m; ++i) cnt[hrp[i + 1] - hrp[i]]++;
-    std::vector<int> start(maxlen + 2, 0);      // descending length order
-    for (int L = maxlen, acc = 0; L >= 0; --L) { start[L] = acc; acc += cnt[L]; }
-    std::vector<int> order(m);
-    for (int i = 0; i < m; ++i) order[start[hrp[i + 1] - hrp[i]]++] = i;
-    const int ns = (m + 31) / 32;
-    std::vector<long long> ptr(ns + 1, 0);
-    std::vector<int> len(ns), row((size_t)ns * 32, -1), rlen((size_t)ns * 32, 0);
-    for (int sl = 0; sl < ns; ++sl) {
-        int L = 0;
-        for (int l = 0; l < 32; ++l) {
-            const int q = sl * 32 + l;
-            if (q < m) {
-                row[q] = order[q];
-                rlen[q] = hrp[order[q] + 1] - hrp[order[q]];
-                L = std::max(L, rlen[q]);
-            }
-        }
-        len[sl] = L;
-        // a dense A's slices span a multiple of 4 entries per lane (its values
-        // are grouped 4 (FP32) or 2 (FP64) entries per lane)
-        const int Lp = h->format == RORBK_FORMAT_DENSE ? (L + 3) & ~3 : L;
-        ptr[sl + 1] = ptr[sl] + 32LL * Lp;
-    }
+// Rows sorted by length (longest first, ties by row) into slices of 32.  On a
+// refresh of the values only the values are copied again.
+static rorbk_status build_sell(rorbk_ctx *h, const std::vector<int> &hrp, bool refresh) {
     auto &S = h->sell;
-    S.nslices = ns;
-    S.ptr = (long long *)dev_alloc(h, (ns + 1) * sizeof(long long));
-    S.len = (int *)dev_alloc(h, ns * sizeof(int));
-    S.row = (int *)dev_alloc(h, (size_t)ns * 32 * sizeof(int));
-    S.rlen = (int *)dev_alloc(h, (size_t)ns * 32 * sizeof(int));
-    const long long ent = std::max(1LL, ptr[ns]);
-    S.col = (int *)dev_alloc(h, ent * sizeof(int));
-    if (h->vdtype == RORBK_F64) S.val = (double *)dev_alloc(h, ent * sizeof(double));
-    if (h->val32) S.val32 = (float *)dev_alloc(h, ent * sizeof(float));
-    if (!S.ptr || !S.len || !S.row || !S.rlen || !S.col || (h->vdtype == RORBK_F64 && !S.val) ||
-        (h->val32 && !S.val32))
-        return fail(h, RORBK_ERR_OOM, "SELL copy of A");
     cudaStream_t st = h->stream;
-    cudaMemcpyAsync(S.ptr, ptr.data(), (ns + 1) * sizeof(long long), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(S.len, len.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(S.row, row.data(), (size_t)ns * 32 * sizeof(int), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(S.rlen, rlen.data(), (size_t)ns * 32 * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (!refresh) {
+        const int m = (int)h->m;
+        int maxlen = 0;
+        for (int i = 0; i < m; ++i) maxlen = std::max(maxlen, hrp[i + 1] - hrp[i]);
+        std::vector<int> cnt(maxlen + 2, 0);
+        for (int i = 0; i < m; ++i) cnt[hrp[i + 1] - hrp[i]]++;
+        std::vector<int> start(maxlen + 2, 0);      // descending length order
+        for (int L = maxlen, acc = 0; L >= 0; --L) { start[L] = acc; acc += cnt[L]; }
+        std::vector<int> order(m);
+        for (int i = 0; i < m; ++i) order[start[hrp[i + 1] - hrp[i]]++] = i;
+        const int ns = (m + 31) / 32;
+        std::vector<long long> ptr(ns + 1, 0);
+        std::vector<int> len(ns), row((size_t)ns * 32, -1), rlen((size_t)ns * 32, 0);
+        for (int sl = 0; sl < ns; ++sl) {
+            int L = 0;
+            for (int l = 0; l < 32; ++l) {
+                const int q = sl * 32 + l;
+                if (q < m) {
+                    row[q] = order[q];
+                    rlen[q] = hrp[order[q] + 1] - hrp[order[q]];
+                    L = std::max(L, rlen[q]);
+                }
+            }
+            len[sl] = L;
+            // a dense A's slices span a multiple of 4 entries per lane (its values
+            // are grouped 4 (FP32) or 2 (FP64) entries per lane)
+            const int Lp = h->format == RORBK_FORMAT_DENSE ? (L + 3) & ~3 : L;
+            ptr[sl + 1] = ptr[sl] + 32LL * Lp;
+        }
+        S.nslices = ns;
+        S.ptr = (long long *)dev_alloc(h, (ns + 1) * sizeof(long long));
+        S.len = (int *)dev_alloc(h, ns * sizeof(int));
+        S.row = (int *)dev_alloc(h, (size_t)ns * 32 * sizeof(int));
+        S.rlen = (int *)dev_alloc(h, (size_t)ns * 32 * sizeof(int));
+        const long long ent = std::max(1LL, ptr[ns]);
+        S.col = (int *)dev_alloc(h, ent * sizeof(int));
+        if (h->vdtype == RORBK_F64) S.val = (double *)dev_alloc(h, ent * sizeof(double));
+        if (h->val32) S.val32 = (float *)dev_alloc(h, ent * sizeof(float));
+        if (!S.ptr || !S.len || !S.row || !S.rlen || !S.col || (h->vdtype == RORBK_F64 && !S.val) ||
+            (h->val32 && !S.val32))
+            return fail(h, RORBK_ERR_OOM, "SELL copy of A");
+        cudaMemcpyAsync(S.ptr, ptr.data(), (ns + 1) * sizeof(long long), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(S.len, len.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(S.row, row.data(), (size_t)ns * 32 * sizeof(int), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(S.rlen, rlen.data(), (size_t)ns * 32 * sizeof(int), cudaMemcpyHostToDevice, st);
+    }
+    const int ns = S.nslices;
     k_sell_fill<<<(unsigned)((ns * 32LL + 255) / 256), 256, 0, st>>>(
         h->rowptr, h->col, h->val, h->val32, ns, S.ptr, S.row, S.rlen, S.col, S.val, S.val32,
         h->format == RORBK_FORMAT_DENSE ? 1 : 0);
@@ -691,11 +799,18 @@ static rorbk_status build_block_order(rorbk_ctx *h, const std::vector<int> &hrp)
                                          cudaMemcpyHostToDevice, h->stream), "block row order");
 }
 
-rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
+// Everything of Algorithm 1's set-up that follows from A: validation, the
+// SELL copy, row norms, block transposes and coupled rows, centroids, C and
+// the proposal, and the static operators.  With refresh (new values, same
+// pattern) every buffer is reused and only the value-dependent parts are
+// formed again, by the same kernels in the same order, so the result equals a
+// fresh set-up bit for bit.
+rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp, bool refresh) {
     cudaStream_t s = h->stream;
     const int m = (int)h->m, n = (int)h->n, k = h->k;
     rorbk_status st;
-    int *flags = (int *)dev_alloc(h, 2 * sizeof(int));
+    Scratch sc(s);
+    int *flags = sc.get<int>(2);
     if (!flags) return fail(h, RORBK_ERR_OOM, "flags");
     cudaMemsetAsync(flags, 0, 2 * sizeof(int), s);
     int gs = std::max(1, std::min(4 * h->num_sms, (m + 255) / 256));
@@ -708,31 +823,25 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
         return fail(h, RORBK_ERR_INVALID_ARG,
                     "CSR structure: row_ptr must be non-decreasing and columns strictly ascending in [0,n)");
     if (hf[0] & 2) return fail(h, RORBK_ERR_NUMERIC, "A holds NaN or Inf");
-    if ((st = build_sell(h, hrp))) return st;
-    if ((st = build_block_order(h, hrp))) return st;
+    if ((st = build_sell(h, hrp, refresh))) return st;
+    if (!refresh && (st = build_block_order(h, hrp))) return st;
     // row norms for the dynamic update: from the FP64 values, and from the
     // FP32 copy that the mixed form's inner solve reads when it differs
-    h->rn = (double *)dev_alloc(h, (size_t)m * sizeof(double));
-    if (!h->rn) return fail(h, RORBK_ERR_OOM, "row norms");
+    if (!keep(h, h->rn, m)) return fail(h, RORBK_ERR_OOM, "row norms");
     k_row_norms<double><<<gs, 256, 0, s>>>(h->rowptr, h->val, m, h->rn);
-    h->rn32 = h->rn;
+    if (!refresh) h->rn32 = h->rn;
     if (h->val32 && h->vdtype == RORBK_F64) {
-        h->rn32 = (double *)dev_alloc(h, (size_t)m * sizeof(double));
-        if (!h->rn32) return fail(h, RORBK_ERR_OOM, "row norms");
+        if (h->rn32 == h->rn) h->rn32 = nullptr;
+        if (!keep(h, h->rn32, m)) return fail(h, RORBK_ERR_OOM, "row norms");
         k_row_norms<float><<<gs, 256, 0, s>>>(h->rowptr, h->val32, m, h->rn32);
     }
 
     // block transpose, coupled rows
     const long long nnz = h->nnz;
-    h->bt.col = (int *)dev_alloc(h, (size_t)(nnz + 16) * sizeof(int));
-    h->bt.row = (uint16_t *)dev_alloc(h, (size_t)(nnz + 16) * sizeof(uint16_t));
-    h->bt.val = (double *)dev_alloc(h, (size_t)(nnz + 16) * sizeof(double));
-    h->bt.seg = (int *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(int));
-    h->bt.seg_ptr = (int *)dev_alloc(h, (size_t)k * sizeof(int));   // segment counts
-    unsigned char *coupled = (unsigned char *)dev_alloc(h, (size_t)m);
-    int *ncoupled = (int *)dev_alloc(h, (size_t)(k + 1) * sizeof(int));
-    if (!h->bt.col || !h->bt.row || !h->bt.val || !h->bt.seg || !h->bt.seg_ptr || !coupled ||
-        !ncoupled)
+    unsigned char *coupled = sc.get<unsigned char>(m);
+    int *ncoupled = sc.get<int>(k + 1);
+    if (!keep(h, h->bt.col, nnz + 16) || !keep(h, h->bt.row, nnz + 16) || !keep(h, h->bt.val, nnz + 16) ||
+        !keep(h, h->bt.seg, nnz) || !keep(h, h->bt.seg_ptr, k) || !coupled || !ncoupled)
         return fail(h, RORBK_ERR_OOM, "block transpose");
     if (h->format == RORBK_FORMAT_DENSE) {
         const int gx = std::max(1, std::min(4 * h->num_sms, (int)((h->nnz / k + 255) / 256)));
@@ -746,8 +855,9 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
 
     // centroids, C row sums, proposal
     {
-        int *colcnt = (int *)dev_alloc(h, (size_t)(n + 1) * sizeof(int));
-        int *fill = (int *)dev_alloc(h, (size_t)(n + 1) * sizeof(int));
+        Scratch cs(s);
+        int *colcnt = cs.get<int>(n + 1);
+        int *fill = cs.get<int>(n + 1);
         if (!colcnt || !fill) return fail(h, RORBK_ERR_OOM, "centroid columns");
         cudaMemsetAsync(colcnt, 0, (size_t)(n + 1) * sizeof(int), s);
         cudaMemsetAsync(fill, 0, (size_t)(n + 1) * sizeof(int), s);
@@ -756,9 +866,9 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
                                            k, colcnt);
         int total = 0;
         if ((st = scan_device(h, colcnt, (long long)n + 1, &total))) return st;
-        int *cb = (int *)dev_alloc(h, (size_t)std::max(1, total) * sizeof(int));
-        double *cv = (double *)dev_alloc(h, (size_t)std::max(1, total) * sizeof(double));
-        double *G = (double *)dev_alloc(h, (size_t)k * k * sizeof(double));
+        int *cb = cs.get<int>(std::max(1, total));
+        double *cv = cs.get<double>(std::max(1, total));
+        double *G = cs.get<double>((size_t)k * k);
         if (!cb || !cv || !G) return fail(h, RORBK_ERR_OOM, "centroid Gram");
         k_centroid_fill<<<gk, 128, 0, s>>>(h->rowptr, h->off, h->bt.col, h->bt.val, h->bt.seg,
                                           h->bt.seg_ptr, k, colcnt, fill, cb, cv);
@@ -790,9 +900,8 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
                 ++h->n_wood;
             }
         if (h->n_wood) {
-            h->wood_ptr = (long long *)dev_alloc(h, (size_t)k * sizeof(long long));
-            h->wood_ss = (double *)dev_alloc(h, (size_t)wtot * sizeof(double));
-            if (!h->wood_ptr || !h->wood_ss) return fail(h, RORBK_ERR_OOM, "s >= n operators");
+            if (!keep(h, h->wood_ptr, k) || !keep(h, h->wood_ss, wtot))
+                return fail(h, RORBK_ERR_OOM, "s >= n operators");
             cudaMemcpyAsync(h->wood_ptr, woodp.data(), (size_t)k * sizeof(long long), cudaMemcpyHostToDevice, s);
         }
         std::vector<int> sptr(k + 1, 0);
@@ -801,20 +910,12 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
             sptr[t + 1] = sptr[t] + hcnt[t];
             wptr[t + 1] = wptr[t] + (long long)hcnt[t] * hcnt[t];
         }
-        h->ops.s_ptr = (int *)dev_alloc(h, (size_t)(k + 1) * sizeof(int));
-        h->ops.w_ptr = (long long *)dev_alloc(h, (size_t)(k + 1) * sizeof(long long));
-        h->ops.s_idx = (uint16_t *)dev_alloc(h, (size_t)std::max(1, sptr[k]) * sizeof(uint16_t));
-        h->ops.s_pos = (int *)dev_alloc(h, (size_t)m * sizeof(int));
-        h->ops.w_ss = (double *)dev_alloc(h, (size_t)std::max(1LL, wptr[k]) * sizeof(double));
-        h->ops.w_diag = (double *)dev_alloc(h, (size_t)m * sizeof(double));
-        double *linv = nullptr;
-        if (cudaMalloc(&linv, (size_t)std::max(1LL, wptr[k]) * sizeof(double)) != cudaSuccess)
-            return fail(h, RORBK_ERR_OOM, "static operator scratch");
-        if (!h->ops.s_ptr || !h->ops.w_ptr || !h->ops.s_idx || !h->ops.s_pos || !h->ops.w_ss ||
-            !h->ops.w_diag) {
-            cudaFree(linv);
+        if (!keep(h, h->ops.s_ptr, k + 1) || !keep(h, h->ops.w_ptr, k + 1) ||
+            !keep(h, h->ops.s_idx, std::max(1, sptr[k])) || !keep(h, h->ops.s_pos, m) ||
+            !keep(h, h->ops.w_ss, std::max(1LL, wptr[k])) || !keep(h, h->ops.w_diag, m))
             return fail(h, RORBK_ERR_OOM, "static operators");
-        }
+        double *linv = sc.get<double>(std::max(1LL, wptr[k]));
+        if (!linv) return fail(h, RORBK_ERR_OOM, "static operator scratch");
         cudaMemcpyAsync(h->ops.s_ptr, sptr.data(), (k + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(h->ops.w_ptr, wptr.data(), (k + 1) * sizeof(long long), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(flags, 0, sizeof(int), s);
@@ -829,39 +930,64 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp) {
                                        h->ops.s_ptr, h->ops.w_ptr, h->ops.s_idx, h->ops.s_pos,
                                        h->ops.w_ss, h->ops.w_diag, linv, h->wood_ptr, flags,
                                        dense_gram ? 1 : 0);
-        double *linv2 = nullptr;
         if (h->n_wood) {
-            if (cudaMalloc(&linv2, (size_t)wtot * sizeof(double)) != cudaSuccess) {
-                cudaFree(linv);
-                return fail(h, RORBK_ERR_OOM, "s >= n operator scratch");
-            }
+            double *linv2 = sc.get<double>(wtot);
+            if (!linv2) return fail(h, RORBK_ERR_OOM, "s >= n operator scratch");
             k_wood_ops<<<k, 256, 0, s>>>(h->rowptr, h->off, (int)n, h->mu, h->wood_ptr, h->bt.col, h->bt.row,
                                          h->bt.val, h->wood_ss, linv2, flags);
         }
         int spd = 0;
         st = cuda_check(h, cudaMemcpyAsync(&spd, flags, sizeof(int), cudaMemcpyDeviceToHost, s), "static ops");
         if (!st) st = cuda_check(h, cudaStreamSynchronize(s), "static ops");
-        cudaFree(linv);
-        if (linv2) cudaFree(linv2);
         if (st) return st;
         if (spd) return fail(h, RORBK_ERR_NOT_SPD, "a static block Gram is not positive definite (lambda = 0 with dependent rows?)");
         if (h->precision_built) {
-            h->ops.w_ss32 = (float *)dev_alloc(h, (size_t)std::max(1LL, wptr[k]) * sizeof(float));
-            h->ops.w_diag32 = (float *)dev_alloc(h, (size_t)m * sizeof(float));
-            h->bt.val32 = (float *)dev_alloc(h, (size_t)(nnz + 16) * sizeof(float));
-            if (!h->ops.w_ss32 || !h->ops.w_diag32 || !h->bt.val32)
+            if (!keep(h, h->ops.w_ss32, std::max(1LL, wptr[k])) || !keep(h, h->ops.w_diag32, m) ||
+                !keep(h, h->bt.val32, nnz + 16))
                 return fail(h, RORBK_ERR_OOM, "fp32 operators");
             k_narrow<<<gs, 256, 0, s>>>(h->ops.w_ss, h->ops.w_ss32, std::max(1LL, wptr[k]));
             k_narrow<<<gs, 256, 0, s>>>(h->ops.w_diag, h->ops.w_diag32, m);
             k_narrow<<<gs, 256, 0, s>>>(h->bt.val, h->bt.val32, nnz);
             if (h->n_wood) {
-                h->wood_ss32 = (float *)dev_alloc(h, (size_t)wtot * sizeof(float));
-                if (!h->wood_ss32) return fail(h, RORBK_ERR_OOM, "fp32 s >= n operators");
+                if (!keep(h, h->wood_ss32, wtot)) return fail(h, RORBK_ERR_OOM, "fp32 s >= n operators");
                 k_narrow<<<gs, 256, 0, s>>>(h->wood_ss, h->wood_ss32, wtot);
             }
         }
     }
     return cuda_check(h, cudaStreamSynchronize(s), "setup");
+}
+
+rorbk_status build_csc(rorbk_ctx *h, const double *scale, int *cp, int *crow, double *cval, float *cval32) {
+    cudaStream_t s = h->stream;
+    const int m = (int)h->m, n = (int)h->n;
+    const long long nnz = h->nnz;
+    rorbk_status st;
+    Scratch sc(s);
+    int *fill = sc.get<int>(n);
+    int *slot = sc.get<int>(nnz), *slot2 = sc.get<int>(nnz), *rowid = sc.get<int>(nnz);
+    int *maxlen = sc.get<int>(1);
+    if (!fill || !slot || !slot2 || !rowid || !maxlen) return fail(h, RORBK_ERR_OOM, "column-major copy of A");
+    const int ge = (int)std::max(1LL, std::min<long long>(8LL * h->num_sms, (nnz + 255) / 256));
+    const int gr = std::max(1, std::min(8 * h->num_sms, (m + 255) / 256));
+    cudaMemsetAsync(cp, 0, (size_t)(n + 1) * sizeof(int), s);
+    cudaMemsetAsync(fill, 0, (size_t)n * sizeof(int), s);
+    cudaMemsetAsync(maxlen, 0, sizeof(int), s);
+    k_col_count<<<ge, 256, 0, s>>>(h->col, nnz, cp);
+    int total = 0;
+    if ((st = scan_device(h, cp, (long long)n + 1, &total))) return st;
+    if (total != nnz) return fail(h, RORBK_ERR_CUDA, "column-major copy of A: entry count");
+    k_col_max<<<std::max(1, std::min(8 * h->num_sms, (n + 255) / 256)), 256, 0, s>>>(cp, n, maxlen);
+    k_col_place<<<gr, 256, 0, s>>>(h->rowptr, h->col, m, cp, fill, slot, rowid);
+    int L = 0;
+    if ((st = cuda_check(h, cudaMemcpyAsync(&L, maxlen, sizeof(int), cudaMemcpyDeviceToHost, s), "column lengths")))
+        return st;
+    if ((st = cuda_check(h, cudaStreamSynchronize(s), "column lengths"))) return st;
+    for (int run = 1; run < L; run *= 2) {
+        k_col_merge<<<ge, 256, 0, s>>>(h->col, cp, slot, slot2, nnz, run);
+        std::swap(slot, slot2);
+    }
+    k_col_gather<<<ge, 256, 0, s>>>(slot, rowid, h->val, scale, nnz, crow, cval, cval32);
+    return cuda_check(h, cudaStreamSynchronize(s), "column-major copy of A");
 }
 
 }  // namespace rorbk

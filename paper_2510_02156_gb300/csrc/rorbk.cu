@@ -340,6 +340,24 @@ static rorbk_options defaults() {
 
 }  // namespace rorbk
 
+namespace rorbk {
+namespace {
+// Counts the entries that are NaN or Inf.
+__global__ void k_count_nonfinite_f64(const double *__restrict__ v, long long nn, int *out) {
+    int c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+        c += !isfinite(v[i]);
+    if (c) atomicAdd(out, c);
+}
+__global__ void k_count_nonfinite_f32(const float *__restrict__ v, long long nn, int *out) {
+    int c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+        c += !isfinite(v[i]);
+    if (c) atomicAdd(out, c);
+}
+}  // namespace
+}  // namespace rorbk
+
 using namespace rorbk;
 
 extern "C" {
@@ -518,6 +536,54 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
     if ((st = build_setup(h, hrp))) return bail(st);
     *out = h;
     return RORBK_OK;
+}
+
+
+rorbk_status rorbk_update_values(rorbk_handle h, const void *values, int32_t dtype, int32_t on_device) {
+    if (!h) return RORBK_ERR_INVALID_ARG;
+    if (!values) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_update_values: values");
+    if (dtype != h->vdtype) return fail(h, RORBK_ERR_INVALID_ARG, "rorbk_update_values: dtype must be the handle's value type");
+    if (h->adj_scale)
+        return fail(h, RORBK_ERR_UNSUPPORTED, "rorbk_update_values: an adjoint handle follows its primal; set up a new one");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    const size_t esz = dtype == RORBK_F64 ? sizeof(double) : sizeof(float);
+    const long long nnz = h->nnz;
+    rorbk_status st = cuda_check(h, cudaStreamSynchronize(s), "rorbk_update_values");
+    // the new values in scratch first, checked before the handle is touched
+    void *tmp = nullptr;
+    int *bad = nullptr;
+    if (!st && nnz) {
+        cudaError_t e = cudaMalloc(&tmp, nnz * esz + sizeof(int));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaSetDevice(cur);
+            return fail(h, RORBK_ERR_OOM, "rorbk_update_values: scratch");
+        }
+        bad = (int *)((char *)tmp + nnz * esz);
+        cudaMemsetAsync(bad, 0, sizeof(int), s);
+        cudaMemcpyAsync(tmp, values, nnz * esz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        const int g = (int)std::max(1LL, std::min<long long>(8LL * h->num_sms, (nnz + 255) / 256));
+        if (dtype == RORBK_F64) k_count_nonfinite_f64<<<g, 256, 0, s>>>((const double *)tmp, nnz, bad);
+        else k_count_nonfinite_f32<<<g, 256, 0, s>>>((const float *)tmp, nnz, bad);
+        int hb = 0;
+        st = cuda_check(h, cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s), "rorbk_update_values");
+        if (!st) st = cuda_check(h, cudaStreamSynchronize(s), "rorbk_update_values");
+        if (!st && hb) st = fail(h, RORBK_ERR_NUMERIC, "rorbk_update_values: the values hold NaN or Inf");
+        if (!st) {
+            cudaMemcpyAsync(dtype == RORBK_F64 ? (void *)h->val : (void *)h->val32, tmp, nnz * esz,
+                            cudaMemcpyDeviceToDevice, s);
+            widen_values(h, dtype);
+            st = cuda_check(h, cudaStreamSynchronize(s), "rorbk_update_values");
+        }
+        cudaFree(tmp);
+    }
+    if (!st) st = build_setup(h, std::vector<int>(), true);
+    if (!st && h->csc_ptr) st = build_csc(h, nullptr, h->csc_ptr, h->csc_row, h->csc_val, h->csc_val32);
+    cudaSetDevice(cur);
+    return st;
 }
 
 // Checks a solve's arguments (h, options) and enqueues on s the copies of b
