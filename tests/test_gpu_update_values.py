@@ -28,16 +28,16 @@ def _other_values(s, seed):
     return v.astype(s.values.dtype)
 
 
-def _solve(h, s, b, precision, residual_mode=B.RESIDUAL_EXACT, maxit=200_000):
+def _solve(h, s, b, precision, residual_mode=B.RESIDUAL_EXACT, maxit=50_000):
     x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
-    r = h.solve(b, x, tol=1e-10, maxit=maxit, seed=4, precision=precision,
+    r = h.solve(b, x, tol=1e-8, maxit=maxit, seed=4, precision=precision,
                 residual_mode=residual_mode)
     return r, x
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_refreshed_handle_equals_a_fresh_set_up(cuda_ok, dtype):
-    s = W.powerlaw(n=1 << 13, num_blocks=32, seed=5, lam=1e-8)
+    s = W.powerlaw(n=1 << 12, num_blocks=16, seed=5, lam=1e-8)
     s = W.System(s.name, s.m, s.n, row_ptr=s.row_ptr, col_idx=s.col_idx,
                  values=s.values.astype(dtype), b=s.b, num_blocks=s.num_blocks, lam=s.lam, tol=s.tol)
     v2 = _other_values(s, 7)
@@ -53,7 +53,7 @@ def test_refreshed_handle_equals_a_fresh_set_up(cuda_ok, dtype):
         c2, r2 = fresh.proposal()
         np.testing.assert_array_equal(c1, c2)
         np.testing.assert_array_equal(r1, r2)
-        for t in (0, 13, 31):
+        for t in (0, 7, 15):
             rows = h.info.max_block_rows
             np.testing.assert_array_equal(h.static_operator(t, rows), fresh.static_operator(t, rows))
         for prec in (B.PREC_FP64, B.PREC_MIXED):
@@ -87,14 +87,14 @@ def test_refresh_reaches_clones_and_blocks(cuda_ok):
             B.Handle.from_system(s2, precision=B.PREC_MIXED) as fresh:
         blk = h.multi(4)
         X = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
-        blk.solve_multi(Bm, X, tol=1e-10, maxit=3, seed=2)       # its graph exists before the refresh
+        blk.solve_multi(Bm, X, tol=1e-8, maxit=3, seed=2)       # its graph exists before the refresh
         h.update_values(v2)
         fb = fresh.multi(4)
         for prec in (B.PREC_FP64, B.PREC_MIXED):
             X1 = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
             X2 = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
-            ra = blk.solve_multi(Bm, X1, tol=1e-10, maxit=100_000, seed=2, precision=prec)
-            rb = fb.solve_multi(Bm, X2, tol=1e-10, maxit=100_000, seed=2, precision=prec)
+            ra = blk.solve_multi(Bm, X1, tol=1e-8, maxit=50_000, seed=2, precision=prec)
+            rb = fb.solve_multi(Bm, X2, tol=1e-8, maxit=50_000, seed=2, precision=prec)
             assert [r.iters for r in ra] == [r.iters for r in rb]
             assert torch.equal(X1, X2)
         blk.close()
@@ -106,13 +106,14 @@ def test_refresh_refuses_bad_values_and_leaves_the_handle(cuda_ok):
     b = _dev(s.b)
     with B.Handle.from_system(s) as h:
         r0, x0 = _solve(h, s, b, B.PREC_FP64)
-        bad = s.values.astype(np.float64).copy()
+        bad = s.values.copy()
         bad[123] = np.nan
         with pytest.raises(B.RorbkError) as e:
             h.update_values(_dev(bad))
         assert e.value.status == -5                  # RORBK_ERR_NUMERIC
+        other = np.float64 if s.values.dtype == np.float32 else np.float32
         with pytest.raises(B.RorbkError) as e:
-            h.update_values(_dev(s.values.astype(np.float32)))   # not the handle's value type
+            h.update_values(_dev(s.values.astype(other)))   # not the handle's value type
         assert e.value.status == -1
         r1, x1 = _solve(h, s, b, B.PREC_FP64)
         assert r1.iters == r0.iters and torch.equal(x1, x0)
@@ -131,7 +132,7 @@ def test_set_up_from_device_arrays_equals_host_set_up(cuda_ok):
     rp = _dev(s.row_ptr.astype(np.int32))
     ci = _dev(s.col_idx.astype(np.int32))
     with B.Handle.from_system(s) as h, \
-            B.Handle(rp, ci, _dev(s.values.astype(np.float64)), s.m, s.n, s.num_blocks, s.lam) as d:
+            B.Handle(rp, ci, _dev(s.values), s.m, s.n, s.num_blocks, s.lam) as d:
         np.testing.assert_array_equal(h.proposal()[0], d.proposal()[0])
         ra, xa = _solve(h, s, b, B.PREC_FP64)
         rb, xb = _solve(d, s, b, B.PREC_FP64)
