@@ -101,6 +101,8 @@ struct BlockT {
     uint16_t *row = nullptr;    // local row in the block
     double *val = nullptr;
     float *val32 = nullptr;
+    uint16_t *off16 = nullptr;  // CSR offset in the block of each entry (blocks of at
+                                // most 65,536 entries; the staged static update)
     int *seg = nullptr;         // segment (distinct column) start positions
     int *seg_ptr = nullptr;     // [k] segment count of block t; its segments
                                 // start at seg[row_ptr[off[t]] ...]

@@ -114,6 +114,7 @@ struct Mat {
     const long long *wood_ptr;
     const T *wood;
     const double *rn;           // ||A_i||^2 of the values this instance reads
+    const uint16_t *bt_off;     // CSR offset in its block of each block-transpose entry
 };
 
 template <typename T>
@@ -125,7 +126,7 @@ Mat<double> make_mat<double>(rorbk_ctx *h) {
                        h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val, h->bt.seg, h->bt.seg_ptr,
                        h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                        h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
-                       h->sell.val32, h->wood_ptr, h->wood_ss, h->rn};
+                       h->sell.val32, h->wood_ptr, h->wood_ss, h->rn, h->bt.off16};
 }
 template <>
 Mat<float> make_mat<float>(rorbk_ctx *h) {
@@ -134,7 +135,7 @@ Mat<float> make_mat<float>(rorbk_ctx *h) {
                       h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val32, h->bt.seg, h->bt.seg_ptr,
                       h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                       h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
-                      h->sell.val32, h->wood_ptr, h->wood_ss32, h->rn32};
+                      h->sell.val32, h->wood_ptr, h->wood_ss32, h->rn32, h->bt.off16};
 }
 
 // -------------------------------------------------------- several columns
@@ -250,7 +251,7 @@ constexpr long long kWaitTries = 1LL << 24;
 
 template <typename T>
 __host__ __device__ constexpr size_t static_stage_bytes() {
-    return (size_t)kStageC * (2 * sizeof(T) + 4 + 4 + 2);
+    return (size_t)kStageC * (2 * sizeof(T) + 4 + 4 + 2 + 2);
 }
 template <typename T>
 __host__ __device__ constexpr size_t static_smem_bytes() {
@@ -261,7 +262,7 @@ template <typename T>
 struct Stage {
     T *val, *btval;
     int *col, *btcol;
-    uint16_t *btrow;
+    uint16_t *btrow, *btoff;
 };
 template <typename T>
 __device__ __forceinline__ Stage<T> stage_at(unsigned char *base) {
@@ -271,6 +272,7 @@ __device__ __forceinline__ Stage<T> stage_at(unsigned char *base) {
     st.col = (int *)(st.btval + kStageC);
     st.btcol = st.col + kStageC;
     st.btrow = (uint16_t *)(st.btcol + kStageC);
+    st.btoff = st.btrow + kStageC;
     return st;
 }
 
@@ -284,7 +286,7 @@ __device__ int stage_issue(const Mat<T> &A, int tau, Stage<T> st, unsigned long 
     const int a0 = p0 & ~7, a1 = (pend + 7) & ~7;     // 16-byte aligned for every array
     const int n = a1 - a0;
     if (n > kStageC) return -1;
-    const unsigned bytes = (unsigned)n * (2u * sizeof(T) + 4u + 4u + 2u);
+    const unsigned bytes = (unsigned)n * (2u * sizeof(T) + 4u + 4u + 2u + 2u);
     fence_proxy_async_smem();
     mbar_expect_tx(bar, bytes);
     bulk_g2s(st.val, A.val + a0, n * sizeof(T), bar);
@@ -292,6 +294,7 @@ __device__ int stage_issue(const Mat<T> &A, int tau, Stage<T> st, unsigned long 
     bulk_g2s(st.col, A.col + a0, n * 4, bar);
     bulk_g2s(st.btcol, A.bt_col + a0, n * 4, bar);
     bulk_g2s(st.btrow, A.bt_row + a0, n * 2, bar);
+    bulk_g2s(st.btoff, A.bt_off + a0, n * 2, bar);
     return a0;
 }
 
@@ -325,17 +328,64 @@ __device__ __forceinline__ void static_update_wood(int n, int ns, const int *bt_
     __syncthreads();
 }
 
+// The draws of one iteration by the whole block.  Thread l < nst forms the
+// target u_l * cdf[k-1] as sample_block does; every thread then counts, for
+// every draw, the entries of its share of the running sum (nondecreasing) that
+// do not exceed the target, and tau_l = min(count, k - 1): the first t with
+// cdf[t] > target, which sample_block's binary search finds.  One coalesced
+// pass over the cdf replaces a chain of log2(k) dependent loads.
+__device__ __forceinline__ void sample_blocks_block(const double *cdf, int k, uint64_t seed, uint64_t sysid,
+                                                    uint64_t it, int nst, double *s_target, int *s_cnt,
+                                                    int *taus) {
+    const int a = threadIdx.x;
+    if (a < nst) {
+        uint64_t w[4];
+        philox4x64_10(it, (uint64_t)a, 0, 0, seed, sysid, w);
+        const double u = (double)(w[0] >> 11) * 0x1.0p-53;
+        s_target[a] = u * cdf[k - 1];
+        s_cnt[a] = 0;
+    }
+    __syncthreads();
+    for (int l = 0; l < nst; ++l) {
+        const double tg = s_target[l];
+        int c = 0;
+        for (int t = a; t < k; t += blockDim.x) c += cdf[t] <= tg;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((a & 31) == 0 && c) atomicAdd(&s_cnt[l], c);
+    }
+    __syncthreads();
+    if (a < nst) taus[a] = min(s_cnt[a], k - 1);
+    __syncthreads();
+}
+
+// Per-row data of a static block that does not depend on x: thread a takes
+// the a-th longest row la of block tau.
+template <typename T>
+struct StaticRow {
+    int la, q0, q1, pos;
+    T bi, wd;
+};
+
 // LOG: the incremental residual's variant, which logs every change of x.
 // WOOD: the variant for handles with blocks in the s >= n form (the other
 // instances compile without that branch).
+// Every x-independent load of an update is issued ahead of the x-dependent
+// chain: the blocks' ranges for all draws at the start, the next block's row
+// order during the current gather, its per-row data during the current dot
+// products; the gather of x and the old values of the scatter come from
+// shared memory when the block is staged.
 template <typename T, bool LOG = false, bool WOOD = false, bool MC = false>
-__global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__ b, T *x,
+__global__ void __launch_bounds__(1024, 1) k_static(Mat<T> A, const T *__restrict__ b, T *x,
                                                  Ctl *ctl, int force_tau, int use_stages,
                                                  int l_begin, int ld_) {
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ T rloc[kMaxBlockRows];
     __shared__ T y[kMaxBlockRows];
     __shared__ int taus[64];
+    __shared__ int s_r0[64], s_s[64], s_p0[64], s_pend[64], s_sb[64], s_nS[64];
+    __shared__ long long s_wb[64];
+    __shared__ double s_target[64];
+    __shared__ int s_cnt[64];
     __shared__ int s_a0[2];
     __shared__ int s_fail;
     if constexpr (MC) {                               // column blockIdx.y of a block of columns
@@ -350,16 +400,26 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
     const int a = threadIdx.x;
     unsigned long long *bar = dsm_u64;                // two mbarriers
     unsigned char *sbase = (unsigned char *)(dsm_u64 + 8);
-    Stage<T> stg[2] = {stage_at<T>(sbase), stage_at<T>(sbase + static_stage_bytes<T>())};
     T *sx = (T *)(sbase + 2 * static_stage_bytes<T>());
+    if (force_tau >= 0) {
+        if (a == 0) taus[0] = force_tau;
+        __syncthreads();
+    } else {
+        sample_blocks_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid,
+                            (uint64_t)(ctl->iter_base + ctl->iter), nst, s_target, s_cnt, taus);
+        if (a < nst && ctl->tr_tau && ctl->iter < ctl->trace_cap) ctl->tr_tau[ctl->iter * nst + a] = taus[a];
+    }
+    // the blocks' ranges and operator offsets, for every draw at once
     if (a < nst) {
-        const long long it = ctl->iter_base + ctl->iter;
-        const int tau = force_tau >= 0 ? force_tau
-                                       : sample_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid,
-                                                      (uint64_t)it, (uint64_t)a);
-        taus[a] = tau;
-        if (force_tau < 0 && ctl->tr_tau && ctl->iter < ctl->trace_cap)
-            ctl->tr_tau[ctl->iter * nst + a] = tau;
+        const int tau = taus[a];
+        const int r0 = A.off[tau], r1 = A.off[tau + 1];
+        s_r0[a] = r0;
+        s_s[a] = r1 - r0;
+        s_sb[a] = A.s_ptr[tau];
+        s_nS[a] = A.s_ptr[tau + 1] - A.s_ptr[tau];
+        s_wb[a] = A.w_ptr[tau];
+        s_p0[a] = A.rowptr[r0];
+        s_pend[a] = A.rowptr[r1];
     }
     const bool inject = ctl->fault == RORBK_FAULT_WAIT_LIMIT && force_tau < 0;
     if (a == 0) {
@@ -370,29 +430,33 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
     }
     __syncthreads();
     if (use_stages && a == 0) {
-        if (nst > 0) s_a0[0] = stage_issue<T>(A, taus[0], stg[0], &bar[0]);
-        if (nst > 1) s_a0[1] = stage_issue<T>(A, taus[1], stg[1], &bar[1]);
+        if (nst > 0) s_a0[0] = stage_issue<T>(A, taus[0], stage_at<T>(sbase), &bar[0]);
+        if (nst > 1) s_a0[1] = stage_issue<T>(A, taus[1], stage_at<T>(sbase + static_stage_bytes<T>()), &bar[1]);
+    }
+    // the first update's per-row data
+    StaticRow<T> cur{0, 0, 0, -1, T(0), T(0)};
+    if (l_begin < nst && a < s_s[l_begin]) {
+        const int r0 = s_r0[l_begin];
+        cur.la = A.bperm[r0 + a];
+        cur.q0 = A.rowptr[r0 + cur.la];
+        cur.q1 = A.rowptr[r0 + cur.la + 1];
+        cur.bi = b[(long long)(r0 + cur.la) * ld];
+        cur.pos = A.s_pos[r0 + cur.la];
+        cur.wd = A.w_diag[r0 + cur.la];
     }
     unsigned phase[2] = {0u, 0u};
     for (int l = l_begin; l < nst; ++l) {
         const int tau = taus[l];
         const int sidx = l & 1;
-        const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
-        const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
-        // x-independent per-row data, loaded before anything waits; thread a
-        // takes the a-th longest row la of the block
-        int q0 = 0, q1 = 0, pos = -1, la = 0;
-        T bi = T(0), wd = T(0);
-        const int sb = A.s_ptr[tau], nS = A.s_ptr[tau + 1] - sb;   // W_tau on the coupled rows
-        const long long wb = A.w_ptr[tau];
-        if (a < s) {
-            la = A.bperm[r0 + a];
-            q0 = A.rowptr[r0 + la];
-            q1 = A.rowptr[r0 + la + 1];
-            bi = b[(long long)(r0 + la) * ld];
-            pos = A.s_pos[r0 + la];
-            wd = A.w_diag[r0 + la];
-        }
+        const int r0 = s_r0[l], s = s_s[l];
+        const int p0 = s_p0[l], pend = s_pend[l];
+        const int sb = s_sb[l], nS = s_nS[l];        // W_tau on the coupled rows
+        const long long wb = s_wb[l];
+        const bool has_next = l + 1 < nst;
+        const int r0n = has_next ? s_r0[l + 1] : 0, sn = has_next ? s_s[l + 1] : 0;
+        // the next block's row order, in flight during this update
+        int la_next = 0;
+        if (has_next && a < sn) la_next = A.bperm[r0n + a];
         __syncthreads();                              // s_a0 of this stage published
         const int a0 = use_stages ? s_a0[sidx] : -1;
         const bool staged = a0 >= 0;
@@ -414,35 +478,60 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
             }
             return;
         }
+        const int la = cur.la;
         T acc = T(0);
         if (staged) {
-            const Stage<T> st = stg[sidx];
-            for (int p = p0 + a; p < pend; p += blockDim.x) sx[p - p0] = x[(long long)st.col[p - a0] * ld];
+            const Stage<T> st = stage_at<T>(sbase + sidx * static_stage_bytes<T>());
+            // x at the block's columns: four loads in flight per thread
+            for (int p = p0 + a; p < pend; p += 4 * (int)blockDim.x) {
+                T v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = p + u * (int)blockDim.x;
+                    v[u] = q < pend ? x[(long long)st.col[q - a0] * ld] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = p + u * (int)blockDim.x;
+                    if (q < pend) sx[q - p0] = v[u];
+                }
+            }
             __syncthreads();
-            for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(st.val[p - a0], sx[p - p0], acc);
+            for (int p = cur.q0; p < cur.q1; ++p) acc = Ar<T>::fma(st.val[p - a0], sx[p - p0], acc);
         } else {
             // a block too large for a stage: every thread runs its own row
             // straight from global memory (loads unrolled ahead of the chain),
             // so the rows proceed side by side however long they are
 #pragma unroll 8
-            for (int p = q0; p < q1; ++p) acc = Ar<T>::fma(A.val[p], x[(long long)A.col[p] * ld], acc);
+            for (int p = cur.q0; p < cur.q1; ++p) acc = Ar<T>::fma(A.val[p], x[(long long)A.col[p] * ld], acc);
         }
-        if (a < s) rloc[la] = Ar<T>::sub(bi, acc);
+        // the next block's per-row data, in flight during the solve below
+        StaticRow<T> nxt{0, 0, 0, -1, T(0), T(0)};
+        if (has_next && a < sn) {
+            nxt.la = la_next;
+            nxt.q0 = A.rowptr[r0n + la_next];
+            nxt.q1 = A.rowptr[r0n + la_next + 1];
+            nxt.bi = b[(long long)(r0n + la_next) * ld];
+            nxt.pos = A.s_pos[r0n + la_next];
+            nxt.wd = A.w_diag[r0n + la_next];
+        }
+        if (a < s) rloc[la] = Ar<T>::sub(cur.bi, acc);
         __syncthreads();
         const long long wp = WOOD ? A.wood_ptr[tau] : -1;
         if (WOOD && wp >= 0) {
             static_update_wood<T>(A.n, A.nseg[tau], A.bt_seg, A.bt_col, A.bt_row, A.bt_val, A.wood + wp, p0,
                                   pend, rloc, y, x, ctl, lg, ld);
-            if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stg[sidx], &bar[sidx]) : -1;
+            if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stage_at<T>(sbase + sidx * static_stage_bytes<T>()), &bar[sidx]) : -1;
+            cur = nxt;
             continue;
         }
         if (a < s) {
-            if (pos < 0) {
-                y[la] = Ar<T>::fma(wd, rloc[la], T(0));
+            if (cur.pos < 0) {
+                y[la] = Ar<T>::fma(cur.wd, rloc[la], T(0));
             } else {
                 // the loads of W's row and of the row indices do not depend on
                 // the chain: unrolled, they are in flight ahead of it
-                const T *Wr = A.w_ss + wb + (long long)pos * nS;
+                const T *Wr = A.w_ss + wb + (long long)cur.pos * nS;
                 T acc2 = T(0);
 #pragma unroll 8
                 for (int q = 0; q < nS; ++q) acc2 = Ar<T>::fma(Wr[q], rloc[A.s_idx[sb + q]], acc2);
@@ -451,14 +540,16 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         }
         __syncthreads();
         if (staged) {
-            const Stage<T> st = stg[sidx];
+            // x's old value of every column comes from the gather above (x
+            // has not changed since); the sum over its rows is unchanged
+            const Stage<T> st = stage_at<T>(sbase + sidx * static_stage_bytes<T>());
             for (int q = p0 + a; q < pend; q += blockDim.x) {
                 const int c = st.btcol[q - a0];
                 if (q > p0 && st.btcol[q - 1 - a0] == c) continue;
                 T acc3 = T(0);
                 for (int u = q; u < pend && st.btcol[u - a0] == c; ++u)
                     acc3 = Ar<T>::fma(st.btval[u - a0], y[st.btrow[u - a0]], acc3);
-                x[(long long)c * ld] = Ar<T>::add(x[(long long)c * ld], acc3);
+                x[(long long)c * ld] = Ar<T>::add(sx[st.btoff[q - a0]], acc3);
                 if (lg) inc_log(ctl, c, (double)acc3);
             }
         } else {
@@ -475,7 +566,8 @@ __global__ void __launch_bounds__(1024) k_static(Mat<T> A, const T *__restrict__
         }
         __syncthreads();
         // this stage is free again: bring in block l + 2
-        if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stg[sidx], &bar[sidx]) : -1;
+        if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stage_at<T>(sbase + sidx * static_stage_bytes<T>()), &bar[sidx]) : -1;
+        cur = nxt;
     }
     // incremental residual: this iteration's residual is exact after a full
     // log or every inc_refresh iterations

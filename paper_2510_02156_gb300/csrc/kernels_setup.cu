@@ -70,7 +70,8 @@ __device__ __forceinline__ int lower_bound_col(const int *col, int lo, int hi, i
 __global__ void k_block_transpose(const int *__restrict__ rowptr, const int *__restrict__ col,
                                   const double *__restrict__ val, const int *__restrict__ off,
                                   int *__restrict__ bt_col, uint16_t *__restrict__ bt_row,
-                                  double *__restrict__ bt_val, int *__restrict__ bt_seg,
+                                  double *__restrict__ bt_val, uint16_t *__restrict__ bt_off,
+                                  int *__restrict__ bt_seg,
                                   int *__restrict__ nseg_out, unsigned char *__restrict__ coupled,
                                   int *__restrict__ ncoupled_out) {
     __shared__ int scan_scratch[33];
@@ -100,6 +101,7 @@ __global__ void k_block_transpose(const int *__restrict__ rowptr, const int *__r
         bt_col[dst] = c;
         bt_row[dst] = (uint16_t)a;
         bt_val[dst] = val[p];
+        bt_off[dst] = (uint16_t)e;
     }
     __syncthreads();
 
@@ -141,7 +143,8 @@ __global__ void k_block_transpose(const int *__restrict__ rowptr, const int *__r
 // (which costs s binary searches per entry: minutes for 256 x 100,000 blocks).
 __global__ void k_block_transpose_dense(const double *__restrict__ val, const int *__restrict__ off,
                                         int n, int *__restrict__ bt_col, uint16_t *__restrict__ bt_row,
-                                        double *__restrict__ bt_val, int *__restrict__ bt_seg,
+                                        double *__restrict__ bt_val, uint16_t *__restrict__ bt_off,
+                                        int *__restrict__ bt_seg,
                                         int *__restrict__ nseg_out, unsigned char *__restrict__ coupled,
                                         int *__restrict__ ncoupled_out) {
     const int t = blockIdx.y;
@@ -155,6 +158,7 @@ __global__ void k_block_transpose_dense(const double *__restrict__ val, const in
         bt_col[p0 + d] = (int)c;
         bt_row[p0 + d] = (uint16_t)a;
         bt_val[p0 + d] = val[p0 + (long long)a * n + c];
+        bt_off[p0 + d] = (uint16_t)((long long)a * n + c);
     }
     for (long long c = gt; c < n; c += gs) bt_seg[p0 + c] = (int)(p0 + c * s);
     for (long long a = gt; a < s; a += gs) coupled[r0 + a] = s > 1 ? 1 : 0;
@@ -841,15 +845,17 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp, bool refresh
     unsigned char *coupled = sc.get<unsigned char>(m);
     int *ncoupled = sc.get<int>(k + 1);
     if (!keep(h, h->bt.col, nnz + 16) || !keep(h, h->bt.row, nnz + 16) || !keep(h, h->bt.val, nnz + 16) ||
+        !keep(h, h->bt.off16, nnz + 16) ||
         !keep(h, h->bt.seg, nnz) || !keep(h, h->bt.seg_ptr, k) || !coupled || !ncoupled)
         return fail(h, RORBK_ERR_OOM, "block transpose");
     if (h->format == RORBK_FORMAT_DENSE) {
         const int gx = std::max(1, std::min(4 * h->num_sms, (int)((h->nnz / k + 255) / 256)));
         k_block_transpose_dense<<<dim3(gx, k), 256, 0, s>>>(h->val, h->off, n, h->bt.col, h->bt.row, h->bt.val,
-                                                            h->bt.seg, h->bt.seg_ptr, coupled, ncoupled);
+                                                            h->bt.off16, h->bt.seg, h->bt.seg_ptr, coupled,
+                                                            ncoupled);
     } else {
         k_block_transpose<<<k, 256, 0, s>>>(h->rowptr, h->col, h->val, h->off, h->bt.col, h->bt.row,
-                                            h->bt.val, h->bt.seg, h->bt.seg_ptr, coupled, ncoupled);
+                                            h->bt.val, h->bt.off16, h->bt.seg, h->bt.seg_ptr, coupled, ncoupled);
     }
     if ((st = cuda_check(h, cudaGetLastError(), "block transpose"))) return st;
 
