@@ -267,7 +267,8 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part,
  *               value type dtype (RORBK_F64 or RORBK_F32).
  *   on_device : 1 if values is device memory, 0 for host memory.
  * Handles that share h's set-up (rorbk_clone, rorbk_multi_create) see the new
- * values too; no solve of any of them may be in flight.  A batch or graph
+ * values too (a clone's own incremental-residual copy is formed again at its
+ * next incremental solve); no solve of any of them may be in flight.  A batch or graph
  * built earlier stays valid (no buffer moves).  Errors: RORBK_ERR_INVALID_ARG
  * (NULL values, dtype other than the handle's); RORBK_ERR_NUMERIC (a NaN or Inf
  * among the values: the handle is left unchanged); RORBK_ERR_UNSUPPORTED for a

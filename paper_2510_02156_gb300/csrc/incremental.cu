@@ -44,7 +44,14 @@ __global__ void k_max_block_nnz(const int *__restrict__ rowptr, const int *__res
 }  // namespace
 
 rorbk_status ensure_incremental(rorbk_ctx *h) {
-    if (h->csc_ptr && h->ilog_col) return RORBK_OK;
+    const int version = h->values_version ? *h->values_version : 0;
+    if (h->csc_ptr && h->ilog_col) {
+        if (h->csc_version == version) return RORBK_OK;
+        // the shared set-up took new values since this copy was formed
+        rorbk_status st = build_csc(h, nullptr, h->csc_ptr, h->csc_row, h->csc_val, h->csc_val32);
+        if (!st) h->csc_version = version;
+        return st;
+    }
     if (h->format != RORBK_FORMAT_CSR)
         return fail(h, RORBK_ERR_UNSUPPORTED, "the incremental residual is built for sparse (CSR) systems");
     const int64_t n = h->n, nnz = h->nnz;
@@ -79,6 +86,7 @@ rorbk_status ensure_incremental(rorbk_ctx *h) {
     h->ilog_col = lcol;
     h->ilog_val = lval;
     h->ilog_cap = (int)cap;
+    h->csc_version = version;
     return RORBK_OK;
 }
 

@@ -145,6 +145,7 @@ struct rorbk_ctx {
     // partition
     std::vector<int64_t> h_off;
     int *off = nullptr;
+    int *blk_nz = nullptr;      // [k+1] first entry of each block, rowptr[off[t]]
     // proposal
     double *cdf = nullptr, *crowsum = nullptr;
     double *pbar = nullptr;             // [k] Pbar_t (the weights before the running sum)
@@ -185,6 +186,11 @@ struct rorbk_ctx {
     // tiles [gram_tiles][gram_splits][128][128]
     float *gram_part = nullptr;
     int gram_tiles = 0, gram_splits = 0;
+    // values_version counts rorbk_update_values calls on the set-up this handle
+    // shares (clones share the counter); csc_version is the count the handle's
+    // own CSC copy was formed at
+    std::shared_ptr<int> values_version;
+    int csc_version = 0;
     int *csc_ptr = nullptr, *csc_row = nullptr;
     double *csc_val = nullptr;
     float *csc_val32 = nullptr;

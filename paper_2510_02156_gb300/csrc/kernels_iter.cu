@@ -115,6 +115,7 @@ struct Mat {
     const T *wood;
     const double *rn;           // ||A_i||^2 of the values this instance reads
     const uint16_t *bt_off;     // CSR offset in its block of each block-transpose entry
+    const int *blk_nz;          // [k+1] first entry of block t: rowptr[off[t]]
 };
 
 template <typename T>
@@ -126,7 +127,7 @@ Mat<double> make_mat<double>(rorbk_ctx *h) {
                        h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val, h->bt.seg, h->bt.seg_ptr,
                        h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                        h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
-                       h->sell.val32, h->wood_ptr, h->wood_ss, h->rn, h->bt.off16};
+                       h->sell.val32, h->wood_ptr, h->wood_ss, h->rn, h->bt.off16, h->blk_nz};
 }
 template <>
 Mat<float> make_mat<float>(rorbk_ctx *h) {
@@ -135,7 +136,7 @@ Mat<float> make_mat<float>(rorbk_ctx *h) {
                       h->ops.s_pos, h->ops.bperm, h->bt.col, h->bt.row, h->bt.val32, h->bt.seg, h->bt.seg_ptr,
                       h->tile_row0, h->ntiles, h->mu, h->val32, h->sell.nslices, h->sell.ptr,
                       h->sell.len, h->sell.row, h->sell.rlen, h->sell.col, h->sell.val,
-                      h->sell.val32, h->wood_ptr, h->wood_ss32, h->rn32, h->bt.off16};
+                      h->sell.val32, h->wood_ptr, h->wood_ss32, h->rn32, h->bt.off16, h->blk_nz};
 }
 
 // -------------------------------------------------------- several columns
@@ -276,12 +277,11 @@ __device__ __forceinline__ Stage<T> stage_at(unsigned char *base) {
     return st;
 }
 
-// Issues the bulk copies of block tau into a stage (thread 0).  Returns the
-// aligned first entry a0, or -1 when the block does not fit a stage.
+// Issues the bulk copies of the block whose entries are [p0, pend) into a
+// stage (thread 0).  Returns the aligned first entry a0, or -1 when the block
+// does not fit a stage.
 template <typename T>
-__device__ int stage_issue(const Mat<T> &A, int tau, Stage<T> st, unsigned long long *bar) {
-    const int r0 = A.off[tau], s = A.off[tau + 1] - r0;
-    const int p0 = A.rowptr[r0], pend = A.rowptr[r0 + s];
+__device__ int stage_issue(const Mat<T> &A, int p0, int pend, Stage<T> st, unsigned long long *bar) {
     if (pend <= p0) return -2;                        // no nonzeros: nothing to stage
     const int a0 = p0 & ~7, a1 = (pend + 7) & ~7;     // 16-byte aligned for every array
     const int n = a1 - a0;
@@ -338,6 +338,13 @@ __device__ __forceinline__ void sample_blocks_block(const double *cdf, int k, ui
                                                     uint64_t it, int nst, double *s_target, int *s_cnt,
                                                     int *taus) {
     const int a = threadIdx.x;
+    constexpr int kHeld = 4;                          // entries held per thread (k <= 4096 in one go)
+    double cv[kHeld];
+#pragma unroll
+    for (int u = 0; u < kHeld; ++u) {
+        const int t = a + u * (int)blockDim.x;
+        cv[u] = t < k ? cdf[t] : 0.0;
+    }
     if (a < nst) {
         uint64_t w[4];
         philox4x64_10(it, (uint64_t)a, 0, 0, seed, sysid, w);
@@ -349,7 +356,9 @@ __device__ __forceinline__ void sample_blocks_block(const double *cdf, int k, ui
     for (int l = 0; l < nst; ++l) {
         const double tg = s_target[l];
         int c = 0;
-        for (int t = a; t < k; t += blockDim.x) c += cdf[t] <= tg;
+#pragma unroll
+        for (int u = 0; u < kHeld; ++u) c += (a + u * (int)blockDim.x < k) && cv[u] <= tg;
+        for (int t = a + kHeld * (int)blockDim.x; t < k; t += blockDim.x) c += cdf[t] <= tg;
         c = __reduce_add_sync(0xffffffffu, c);
         if ((a & 31) == 0 && c) atomicAdd(&s_cnt[l], c);
     }
@@ -418,8 +427,8 @@ __global__ void __launch_bounds__(1024, 1) k_static(Mat<T> A, const T *__restric
         s_sb[a] = A.s_ptr[tau];
         s_nS[a] = A.s_ptr[tau + 1] - A.s_ptr[tau];
         s_wb[a] = A.w_ptr[tau];
-        s_p0[a] = A.rowptr[r0];
-        s_pend[a] = A.rowptr[r1];
+        s_p0[a] = A.blk_nz[tau];
+        s_pend[a] = A.blk_nz[tau + 1];
     }
     const bool inject = ctl->fault == RORBK_FAULT_WAIT_LIMIT && force_tau < 0;
     if (a == 0) {
@@ -430,8 +439,9 @@ __global__ void __launch_bounds__(1024, 1) k_static(Mat<T> A, const T *__restric
     }
     __syncthreads();
     if (use_stages && a == 0) {
-        if (nst > 0) s_a0[0] = stage_issue<T>(A, taus[0], stage_at<T>(sbase), &bar[0]);
-        if (nst > 1) s_a0[1] = stage_issue<T>(A, taus[1], stage_at<T>(sbase + static_stage_bytes<T>()), &bar[1]);
+        if (nst > 0) s_a0[0] = stage_issue<T>(A, s_p0[0], s_pend[0], stage_at<T>(sbase), &bar[0]);
+        if (nst > 1)
+            s_a0[1] = stage_issue<T>(A, s_p0[1], s_pend[1], stage_at<T>(sbase + static_stage_bytes<T>()), &bar[1]);
     }
     // the first update's per-row data
     StaticRow<T> cur{0, 0, 0, -1, T(0), T(0)};
@@ -521,7 +531,7 @@ __global__ void __launch_bounds__(1024, 1) k_static(Mat<T> A, const T *__restric
         if (WOOD && wp >= 0) {
             static_update_wood<T>(A.n, A.nseg[tau], A.bt_seg, A.bt_col, A.bt_row, A.bt_val, A.wood + wp, p0,
                                   pend, rloc, y, x, ctl, lg, ld);
-            if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stage_at<T>(sbase + sidx * static_stage_bytes<T>()), &bar[sidx]) : -1;
+            if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, s_p0[l + 2], s_pend[l + 2], stage_at<T>(sbase + sidx * static_stage_bytes<T>()), &bar[sidx]) : -1;
             cur = nxt;
             continue;
         }
@@ -566,7 +576,7 @@ __global__ void __launch_bounds__(1024, 1) k_static(Mat<T> A, const T *__restric
         }
         __syncthreads();
         // this stage is free again: bring in block l + 2
-        if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, taus[l + 2], stage_at<T>(sbase + sidx * static_stage_bytes<T>()), &bar[sidx]) : -1;
+        if (use_stages && a == 0) s_a0[sidx] = l + 2 < nst ? stage_issue<T>(A, s_p0[l + 2], s_pend[l + 2], stage_at<T>(sbase + sidx * static_stage_bytes<T>()), &bar[sidx]) : -1;
         cur = nxt;
     }
     // incremental residual: this iteration's residual is exact after a full

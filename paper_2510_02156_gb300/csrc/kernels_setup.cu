@@ -54,6 +54,13 @@ __global__ void k_narrow(const double *__restrict__ in, float *__restrict__ out,
         out[i] = (float)in[i];
 }
 
+// First entry of every block: rowptr[off[t]], t = 0..k.
+__global__ void k_block_nz(const int *__restrict__ rowptr, const int *__restrict__ off, int k,
+                           int *__restrict__ out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= k; t += gridDim.x * blockDim.x)
+        out[t] = rowptr[off[t]];
+}
+
 // ---------------------------------------------------------- block transpose
 // One block of threads per static block t.  Entry p of the block's CSR range
 // lands at rank(p) = #entries with a smaller column + #entries in earlier
@@ -827,6 +834,8 @@ rorbk_status build_setup(rorbk_ctx *h, const std::vector<int> &hrp, bool refresh
         return fail(h, RORBK_ERR_INVALID_ARG,
                     "CSR structure: row_ptr must be non-decreasing and columns strictly ascending in [0,n)");
     if (hf[0] & 2) return fail(h, RORBK_ERR_NUMERIC, "A holds NaN or Inf");
+    if (!keep(h, h->blk_nz, k + 1)) return fail(h, RORBK_ERR_OOM, "block entry offsets");
+    k_block_nz<<<std::max(1, (k + 256) / 256), 256, 0, s>>>(h->rowptr, h->off, k, h->blk_nz);
     if ((st = build_sell(h, hrp, refresh))) return st;
     if (!refresh && (st = build_block_order(h, hrp))) return st;
     // row norms for the dynamic update: from the FP64 values, and from the

@@ -421,6 +421,7 @@ rorbk_status rorbk_setup(const rorbk_matrix *A, const rorbk_partition *part, dou
 
     rorbk_ctx *h = new rorbk_ctx();
     rorbk_status st;
+    h->values_version = std::make_shared<int>(0);
     cudaGetDevice(&h->device);
     h->stream = (cudaStream_t)opt.stream;
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -581,7 +582,13 @@ rorbk_status rorbk_update_values(rorbk_handle h, const void *values, int32_t dty
         cudaFree(tmp);
     }
     if (!st) st = build_setup(h, std::vector<int>(), true);
-    if (!st && h->csc_ptr) st = build_csc(h, nullptr, h->csc_ptr, h->csc_row, h->csc_val, h->csc_val32);
+    if (!st && h->values_version) ++*h->values_version;
+    // this handle's own column-major copy now; those of handles sharing the
+    // set-up at their next incremental solve
+    if (!st && h->csc_ptr) {
+        st = build_csc(h, nullptr, h->csc_ptr, h->csc_row, h->csc_val, h->csc_val32);
+        if (!st) h->csc_version = *h->values_version;
+    }
     cudaSetDevice(cur);
     return st;
 }

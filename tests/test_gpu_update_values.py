@@ -88,7 +88,19 @@ def test_refresh_reaches_clones_and_blocks(cuda_ok):
         blk = h.multi(4)
         X = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
         blk.solve_multi(Bm, X, tol=1e-8, maxit=3, seed=2)       # its graph exists before the refresh
+        cl = h.clone()
+        b = _dev(s2.b)
+        _solve(cl, s, b, B.PREC_FP64, B.RESIDUAL_INCREMENTAL, maxit=5)   # the clone's own CSC copy
         h.update_values(v2)
+        # the clone's copy is formed again at its next incremental solve
+        ra, xa = _solve(cl, s2, b, B.PREC_FP64, B.RESIDUAL_INCREMENTAL, maxit=40)
+        rb, xb = _solve(fresh, s2, b, B.PREC_FP64, B.RESIDUAL_INCREMENTAL, maxit=40)
+        assert ra.iters == rb.iters == 40
+        assert float(torch.linalg.norm(xa - xb) / torch.linalg.norm(xb)) <= 1e-10
+        ra, xa = _solve(cl, s2, b, B.PREC_FP64)
+        rb, xb = _solve(fresh, s2, b, B.PREC_FP64)
+        assert ra.iters == rb.iters and torch.equal(xa, xb)
+        cl.close()
         fb = fresh.multi(4)
         for prec in (B.PREC_FP64, B.PREC_MIXED):
             X1 = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
