@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(1024, 1) k_static(Mat<T> A, const T *__restric
     for (int l = l_begin; l < nst; ++l) {
         const int tau = taus[l];
         const int sidx = l & 1;
-        const int r0 = s_r0[l], s = s_s[l];
+        const int s = s_s[l];
         const int p0 = s_p0[l], pend = s_pend[l];
         const int sb = s_sb[l], nS = s_nS[l];        // W_tau on the coupled rows
         const long long wb = s_wb[l];
@@ -987,6 +987,27 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
 }
 
 // ------------------------------------------------------------ exact top-K
+// Small sorts in one block by rank: the key at position q goes to the number
+// of keys that precede it (smaller keys, or equal keys at lower positions), so
+// the result is the ascending order with equal keys in their input order.  It
+// takes one barrier and n comparisons per key (every lane reads the same key:
+// a shared-memory broadcast); up to kRankSortMax keys that costs less than
+// the log2(n)(log2(n)+1)/2 barrier-separated steps of a bitonic network.
+constexpr int kRankSortMax = 256;
+template <typename K>
+__device__ void block_rank_sort(const K *keys, K *out, int n) {
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const K k = keys[q];
+        int rank = 0;
+        for (int u = 0; u < n; ++u) {
+            const K v = keys[u];
+            rank += (v < k) | ((v == k) & (u < q));
+        }
+        out[rank] = k;
+    }
+    __syncthreads();
+}
+
 // Completes the top-K set in one block of threads: the n_in rows above the
 // 22-bit threshold plus the best (need) of the candidates on it, ordered by
 // |r| descending and row ascending.  If more than kEqCap candidates share the
@@ -1011,7 +1032,24 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
     __syncthreads();
     const int nin = s_nin, need = s_need, neq = s_neq;
     for (int a = threadIdx.x; a < nin; a += blockDim.x) sI[a] = in_list[a];
-    if (need > 0 && neq <= kEqCap) {
+    if (need > 0 && neq <= kRankSortMax) {
+        // the need first candidates in top-K order (larger key, then lower
+        // row), each placed by its rank
+        for (int e = threadIdx.x; e < neq; e += blockDim.x) {
+            const int i = eq_list[e];
+            skey[e] = abs_key(r[rpos<MC>(cl, i)]);
+            sidx[e] = i;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < neq; e += blockDim.x) {
+            const unsigned long long ke = skey[e];
+            const int ie = sidx[e];
+            int rank = 0;
+            for (int u = 0; u < neq; ++u) rank += topk_before(skey[u], sidx[u], ke, ie);
+            if (rank < need) sI[nin + rank] = ie;
+        }
+        __syncthreads();
+    } else if (need > 0 && neq <= kEqCap) {
         const int np = next_pow2(neq);
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             if (e < neq) { int i = eq_list[e]; skey[e] = abs_key(r[rpos<MC>(cl, i)]); sidx[e] = i; }
@@ -1087,6 +1125,13 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
     }
     __syncthreads();
     // ascending order
+    if (K <= 2 * kRankSortMax) {
+        int *tmp = (int *)skey;                       // the rows are distinct
+        block_rank_sort<int>(sI, tmp, K);
+        for (int a = threadIdx.x; a < K; a += blockDim.x) sI[a] = tmp[a];
+        __syncthreads();
+        return;
+    }
     const int np = next_pow2(K);
     for (int a = threadIdx.x; a < np; a += blockDim.x)
         skey[a] = a < K ? (unsigned long long)(unsigned)sI[a] : ~0ull;
@@ -1324,9 +1369,13 @@ __device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use
     for (int j = tid; j < kSymMax; j += blockDim.x) { S.level[j] = 0; s_cnt[j] = 0; }
     if (tid == 0) s_cnt[kSymMax] = 0;
     __syncthreads();
-    for (int i = tid; i < nS; i += blockDim.x)
-        for (int j = 0; j < i; ++j)
-            if (G[pidx(i, j)] != 0.0) atomicOr(&S.col[j * kSymW + (i >> 5)], 1u << (i & 31));
+    for (int q = tid; q < nS * (nS - 1) / 2; q += blockDim.x) {   // entry (i, j), j < i, packed by rows
+        int i = (int)((sqrtf(8.0f * (float)q + 1.0f) + 1.0f) * 0.5f);
+        while (i * (i - 1) / 2 > q) --i;
+        while ((i + 1) * i / 2 <= q) ++i;
+        const int j = q - i * (i - 1) / 2;
+        if (G[pidx(i, j)] != 0.0) atomicOr(&S.col[j * kSymW + (i >> 5)], 1u << (i & 31));
+    }
     __syncthreads();
     if (tid < 32) {                     // one warp: elimination tree and fill
         for (int j = 0; j < nS; ++j) {
@@ -1360,16 +1409,16 @@ __device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use
     }
     for (int j = tid; j < nS; j += blockDim.x) atomicAdd(&s_cnt[S.level[j]], 1);
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0) {                     // levels are below nS
         int nl = 0, acc = 0;
-        for (int L = 0; L < kSymMax; ++L) {
+        for (int L = 0; L < nS; ++L) {
             if (s_cnt[L]) nl = L + 1;
             const int c = s_cnt[L];
             S.lvl_off[L] = (int16_t)acc;
             acc += c;
             s_cnt[L] = 0;
         }
-        S.lvl_off[kSymMax] = (int16_t)acc;
+        for (int L = nS; L <= kSymMax; ++L) S.lvl_off[L] = (int16_t)acc;
         *s_nlev = nl;
         s_cost_lvl = 0;
         s_cost_col = 0;
@@ -1394,10 +1443,12 @@ __device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use
         if (tid == 0) S.eoff[nS] = carry;
         __syncthreads();
     }
-    // cost model (cycles): FP64 fma ~70, sqrt/div ~500 each, barrier ~100
-    if (tid < 32) {
+    // cost model (cycles): FP64 fma ~70, sqrt/div ~500 each, barrier ~100;
+    // one warp per level
+    {
+        const int warp = tid >> 5, nwarps = blockDim.x >> 5;
         long long lvl = 0;
-        for (int L = 0; L < *s_nlev; ++L) {
+        for (int L = warp; L < *s_nlev; L += nwarps) {
             int mr = 0, mc = 0;
             for (int q = S.lvl_off[L] + lane; q < S.lvl_off[L + 1]; q += 32) {
                 const int j = S.order[q];
@@ -1410,11 +1461,12 @@ __device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use
             }
             lvl += (long long)(2 * mr + mc) * 90 + 2300;
         }
-        if (lane == 0) {
-            s_cost_lvl = lvl;
-            s_cost_col = (long long)nS * (1300 + 2 * 800);
-            *s_use_levels = s_cost_lvl < s_cost_col;
-        }
+        if (lane == 0 && lvl) atomicAdd((unsigned long long *)&s_cost_lvl, (unsigned long long)lvl);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_cost_col = (long long)nS * (1300 + 2 * 800);
+        *s_use_levels = s_cost_lvl < s_cost_col;
     }
     __syncthreads();
 }
@@ -1584,10 +1636,17 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
     }
     // shared entries (found with repeats by the grid pass): sort, drop repeats
     unsigned long long *keys = nraw <= kShCap ? sk : D.skeys;
-    const int np = next_pow2(max(nraw, 1));
-    for (int q = tid; q < np; q += blockDim.x) keys[q] = q < nraw ? D.raw[q] : ~0ull;
-    __syncthreads();
-    block_bitonic_sort(keys, np);
+    if (nraw <= kRankSortMax) {
+        unsigned long long *tmp = (unsigned long long *)Gs;   // free until the Gram
+        for (int q = tid; q < nraw; q += blockDim.x) tmp[q] = D.raw[q];
+        __syncthreads();
+        block_rank_sort<unsigned long long>(tmp, keys, nraw);
+    } else {
+        const int np = next_pow2(max(nraw, 1));
+        for (int q = tid; q < np; q += blockDim.x) keys[q] = q < nraw ? D.raw[q] : ~0ull;
+        __syncthreads();
+        block_bitonic_sort(keys, np);
+    }
     int nsh_run = 0;
     for (int base = 0; base < nraw; base += blockDim.x) {
         const int q = base + tid;
@@ -1635,11 +1694,18 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
                                                 ((unsigned long long)u << 22) | (unsigned long long)w;
             }
     }
-    const int npp = next_pow2(max(npk, 1));
     __syncthreads();
-    for (int q = npk + tid; q < npp; q += blockDim.x) pkeys[q] = ~0ull;
-    __syncthreads();
-    block_bitonic_sort(pkeys, npp);
+    if (npk <= kRankSortMax) {
+        unsigned long long *tmp = (unsigned long long *)Gs;   // free until the Gram
+        for (int q = tid; q < npk; q += blockDim.x) tmp[q] = pkeys[q];
+        __syncthreads();
+        block_rank_sort<unsigned long long>(tmp, pkeys, npk);
+    } else {
+        const int npp = next_pow2(max(npk, 1));
+        for (int q = npk + tid; q < npp; q += blockDim.x) pkeys[q] = ~0ull;
+        __syncthreads();
+        block_bitonic_sort(pkeys, npp);
+    }
     // coupled set S in ascending row order
     int cnt = 0;
     for (int base = 0; base < K; base += blockDim.x) {
@@ -1705,7 +1771,7 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
 // Gathers the nonzeros of A_I (row order), marks each column's lowest entry
 // and entry count, forms ||A_i||^2 + mu; the last block factors.
 template <typename T, bool MC = false>
-__global__ void __launch_bounds__(512) k_dyn_mark(Mat<T> A, const T *__restrict__ r, Dyn D,
+__global__ void __launch_bounds__(512, 1) k_dyn_mark(Mat<T> A, const T *__restrict__ r, Dyn D,
                                                   Ctl *ctl, int check_done, Cols cl) {
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ int is_last;
