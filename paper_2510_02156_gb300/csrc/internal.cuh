@@ -76,7 +76,13 @@ struct Ctl {
     double *log_val;       // [log_cap] their increments
     const double *scdf;    // the running sum the static draws use (P's, or the weighted one)
     int fault;             // RORBK_FAULT_* injected by the host (tests of the failure paths)
+    // the next iteration's draws and their blocks' ranges, formed ahead by the
+    // top-K pass (pre_it = that iteration's Philox counter + 1; 0: none)
+    long long pre_it;
+    int pre_tau[8], pre_r0[8], pre_s[8], pre_p0[8], pre_pend[8], pre_sb[8], pre_nS[8];
+    long long pre_wb[8];
 };
+constexpr int kPreDraws = 8;           // draws per iteration formed ahead (n_static <= 8)
 
 // Sparse operator of one static block t (Section 3.1's stored inverse
 // W_t = (A_t A_t^T + mu I)^{-1}).  Rows of the block that share no column

@@ -334,11 +334,11 @@ __device__ __forceinline__ void static_update_wood(int n, int ns, const int *bt_
 // do not exceed the target, and tau_l = min(count, k - 1): the first t with
 // cdf[t] > target, which sample_block's binary search finds.  One coalesced
 // pass over the cdf replaces a chain of log2(k) dependent loads.
+template <int kHeld>                                  // entries held per thread (k <= kHeld * blockDim in one go)
 __device__ __forceinline__ void sample_blocks_block(const double *cdf, int k, uint64_t seed, uint64_t sysid,
                                                     uint64_t it, int nst, double *s_target, int *s_cnt,
                                                     int *taus) {
     const int a = threadIdx.x;
-    constexpr int kHeld = 4;                          // entries held per thread (k <= 4096 in one go)
     double cv[kHeld];
 #pragma unroll
     for (int u = 0; u < kHeld; ++u) {
@@ -410,16 +410,31 @@ __global__ void __launch_bounds__(1024, 1) k_static(Mat<T> A, const T *__restric
     unsigned long long *bar = dsm_u64;                // two mbarriers
     unsigned char *sbase = (unsigned char *)(dsm_u64 + 8);
     T *sx = (T *)(sbase + 2 * static_stage_bytes<T>());
+    const long long cnt = ctl->iter_base + ctl->iter;
+    // the draws and ranges formed ahead by the previous iteration's top-K pass
+    const bool planned = force_tau < 0 && nst <= kPreDraws && ctl->pre_it == cnt + 1;
     if (force_tau >= 0) {
         if (a == 0) taus[0] = force_tau;
         __syncthreads();
+    } else if (planned) {
+        if (a < nst) {
+            taus[a] = ctl->pre_tau[a];
+            s_r0[a] = ctl->pre_r0[a];
+            s_s[a] = ctl->pre_s[a];
+            s_sb[a] = ctl->pre_sb[a];
+            s_nS[a] = ctl->pre_nS[a];
+            s_wb[a] = ctl->pre_wb[a];
+            s_p0[a] = ctl->pre_p0[a];
+            s_pend[a] = ctl->pre_pend[a];
+        }
     } else {
-        sample_blocks_block(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid,
-                            (uint64_t)(ctl->iter_base + ctl->iter), nst, s_target, s_cnt, taus);
-        if (a < nst && ctl->tr_tau && ctl->iter < ctl->trace_cap) ctl->tr_tau[ctl->iter * nst + a] = taus[a];
+        sample_blocks_block<4>(ctl->scdf ? ctl->scdf : A.cdf, A.k, ctl->seed, ctl->sysid, (uint64_t)cnt, nst,
+                               s_target, s_cnt, taus);
     }
+    if (force_tau < 0 && a < nst && ctl->tr_tau && ctl->iter < ctl->trace_cap)
+        ctl->tr_tau[ctl->iter * nst + a] = taus[a];
     // the blocks' ranges and operator offsets, for every draw at once
-    if (a < nst) {
+    if (!planned && a < nst) {
         const int tau = taus[a];
         const int r0 = A.off[tau], r1 = A.off[tau + 1];
         s_r0[a] = r0;
@@ -945,6 +960,7 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
         hist2 += blockIdx.y * kHistBins;
     }
     if (check_done && (ctl->done || ctl->halt)) return;
+
     const unsigned sel1 = (unsigned)ctl->sel1;
     const int mp = MC ? cl.mpos : m;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
@@ -1377,7 +1393,40 @@ __device__ void symbolic(const double *G, int nS, Sym S, int *s_nlev, int *s_use
         if (G[pidx(i, j)] != 0.0) atomicOr(&S.col[j * kSymW + (i >> 5)], 1u << (i & 31));
     }
     __syncthreads();
-    if (tid < 32) {                     // one warp: elimination tree and fill
+    if (nS <= 64 && tid < 32) {
+        // one warp, every column's structure in registers: lane l holds
+        // columns l and l + 32 as 64-bit row masks (rows below the diagonal)
+        // and their levels.  Column j's parent p is its first row; p takes
+        // j's other rows (fill) and a level above j's.
+        unsigned long long m0 = 0ull, m1 = 0ull;
+        int lv0 = 0, lv1 = 0;
+        if (lane < nS) m0 = ((unsigned long long)S.col[lane * kSymW + 1] << 32) | S.col[lane * kSymW];
+        if (lane + 32 < nS)
+            m1 = ((unsigned long long)S.col[(lane + 32) * kSymW + 1] << 32) | S.col[(lane + 32) * kSymW];
+        for (int j = 0; j < nS; ++j) {
+            const bool hi = j >= 32;                  // uniform across the warp
+            const unsigned long long mj = __shfl_sync(0xffffffffu, hi ? m1 : m0, j & 31);
+            const int lvj = __shfl_sync(0xffffffffu, hi ? lv1 : lv0, j & 31);
+            if (mj) {
+                const int p = __ffsll((long long)mj) - 1;
+                const unsigned long long add = mj & ~(1ull << p);
+                if ((p & 31) == lane) {
+                    if (p < 32) { m0 |= add; lv0 = max(lv0, lvj + 1); }
+                    else { m1 |= add; lv1 = max(lv1, lvj + 1); }
+                }
+            }
+        }
+        if (lane < nS) {
+            S.col[lane * kSymW] = (unsigned)m0;
+            S.col[lane * kSymW + 1] = (unsigned)(m0 >> 32);
+            S.level[lane] = (int16_t)lv0;
+        }
+        if (lane + 32 < nS) {
+            S.col[(lane + 32) * kSymW] = (unsigned)m1;
+            S.col[(lane + 32) * kSymW + 1] = (unsigned)(m1 >> 32);
+            S.level[lane + 32] = (int16_t)lv1;
+        }
+    } else if (tid < 32) {              // one warp: elimination tree and fill
         for (int j = 0; j < nS; ++j) {
             const unsigned w = lane < kSymW ? S.col[j * kSymW + lane] : 0u;
             const unsigned bal = __ballot_sync(0xffffffffu, w != 0u);
@@ -1770,11 +1819,51 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
 
 // Gathers the nonzeros of A_I (row order), marks each column's lowest entry
 // and entry count, forms ||A_i||^2 + mu; the last block factors.
+// What the dynamic update needs to form the next iteration's draws ahead of
+// them (cdf == nullptr: not formed).
+struct Plan {
+    const double *cdf;
+    int k;
+    const int *off, *s_ptr, *blk_nz;
+    const long long *w_ptr;
+};
+
+// The next iteration's draws and their blocks' ranges, which depend on
+// neither x nor r, formed by one block of the dynamic update while its last
+// block factors (so that the next sampled updates start at once).  The
+// residual-weighted draws are formed by k_static itself.
+__device__ void plan_next(const Plan &pl, Ctl *ctl) {
+    if (ctl->weighted || ctl->n_static > kPreDraws) return;
+    __shared__ int taus[64], s_cnt[64];
+    __shared__ double s_target[64];
+    const int nst = ctl->n_static;
+    const long long next = ctl->iter_base + ctl->iter + 1;
+    sample_blocks_block<8>(pl.cdf, pl.k, ctl->seed, ctl->sysid, (uint64_t)next, nst, s_target, s_cnt, taus);
+    const int a = threadIdx.x;
+    if (a < nst) {
+        const int tau = taus[a];
+        ctl->pre_tau[a] = tau;
+        ctl->pre_r0[a] = pl.off[tau];
+        ctl->pre_s[a] = pl.off[tau + 1] - pl.off[tau];
+        ctl->pre_sb[a] = pl.s_ptr[tau];
+        ctl->pre_nS[a] = pl.s_ptr[tau + 1] - pl.s_ptr[tau];
+        ctl->pre_wb[a] = pl.w_ptr[tau];
+        ctl->pre_p0[a] = pl.blk_nz[tau];
+        ctl->pre_pend[a] = pl.blk_nz[tau + 1];
+    }
+    __syncthreads();
+    if (a == 0) {
+        __threadfence();
+        ctl->pre_it = next + 1;
+    }
+}
+
 template <typename T, bool MC = false>
 __global__ void __launch_bounds__(512, 1) k_dyn_mark(Mat<T> A, const T *__restrict__ r, Dyn D,
-                                                  Ctl *ctl, int check_done, Cols cl) {
+                                                  Ctl *ctl, int check_done, Cols cl, Plan pl) {
     extern __shared__ unsigned long long dsm_u64[];
     __shared__ int is_last;
+    __shared__ unsigned s_tk;
     if constexpr (MC) {
         ctl += blockIdx.y;
         r += blockIdx.y * cl.rs;
@@ -1838,9 +1927,16 @@ __global__ void __launch_bounds__(512, 1) k_dyn_mark(Mat<T> A, const T *__restri
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        s_tk = atomicAdd(&ctl->ticket, 1u);
+        is_last = s_tk == gridDim.x - 1;
+    }
     __syncthreads();
-    if (!is_last) return;
+    if (!is_last) {
+        // the first block done plans the next draws while the last one factors
+        if (s_tk == 0 && pl.cdf) plan_next(pl, ctl);
+        return;
+    }
     __threadfence();
     dyn_factor<T, MC>(r, K, D, ctl, dsm_u64, cl);
     if (threadIdx.x == 0) ctl->ticket = 0;
@@ -2589,6 +2685,7 @@ __global__ void __launch_bounds__(256) k_inner_prep(const double *__restrict__ r
         in->halt = !(bn > 0.0 && in->maxit > 0);
         in->status = 0;
         in->ticket = 0;
+        in->pre_it = 0;
         in->n_in = 0;
         in->n_eq = 0;
         in->trace_cap = 0;
@@ -3074,6 +3171,7 @@ __global__ void __launch_bounds__(256) k_mr_inner_prep(const double *__restrict_
             in->halt = 1;
         }
         in->ticket = 0;
+        in->pre_it = 0;
         in->n_in = 0;
         in->n_eq = 0;
         in->trace_cap = 0;
@@ -3132,6 +3230,12 @@ static Dyn dyn_bufs(rorbk_ctx *h) {
                h->dyn.erow, h->dyn.ecap, h->dyn.owner, h->dyn.shared, h->dyn.segpos,
                h->dyn.epoch, h->dyn.raw, h->dyn.skeys, h->dyn.pkeys, h->dyn.pcap, h->dyn.g,
                h->K, (int)h->n, h->dyn.skcap};
+}
+
+// The sparse path's plan of the next draws (the dense path samples its own).
+static Plan plan_of(rorbk_ctx *h) {
+    if (h->format != RORBK_FORMAT_CSR) return Plan{};
+    return Plan{h->cdf, h->k, h->off, h->ops.s_ptr, h->blk_nz, h->ops.w_ptr};
 }
 
 static int grid_stream(rorbk_ctx *h, int m) {
@@ -3330,7 +3434,8 @@ static void launch_dynamic_tail(rorbk_ctx *h, const T *r, T *x, Ctl *ctl, int ch
     }
     Mat<T> A = make_mat<T>(h);
     k_dyn_mark<T><<<grid_mark(h), 512, factor_smem_bytes(), h->stream>>>(A, r, dyn_bufs(h), ctl,
-                                                                        check_done, one_col((int)h->m));
+                                                                        check_done, one_col((int)h->m),
+                                                                        count_iter ? plan_of(h) : Plan{});
     (inc ? k_dyn_scatter<T, true> : k_dyn_scatter<T, false>)<<<grid_scatter(h), 512, 0, h->stream>>>(
         x, (int)h->n, dyn_bufs(h), ctl, count_iter, use_cond, (cudaGraphConditionalHandle)hcond,
         one_col((int)h->m));
@@ -3446,7 +3551,7 @@ static void launch_mr_iteration_t(rorbk_ctx *h, const T *b, T *x, T *r, Ctl *ctl
     k_topk_collect<T, true><<<dim3(grid_collect(h), nr), 512, collect_smem_bytes(), st>>>(
         r, m, K, h->rowptr, h->in_list, h->eq_list, dyn_bufs(h), ctl, 1, cl);
     k_dyn_mark<T, true><<<dim3(grid_mark(h), nr), 512, factor_smem_bytes(), st>>>(
-        A, r, dyn_bufs(h), ctl, 1, cl);
+        A, r, dyn_bufs(h), ctl, 1, cl, plan_of(h));
     k_dyn_scatter<T, false, true><<<dim3(grid_scatter(h), nr), 512, 0, st>>>(
         x, (int)h->n, dyn_bufs(h), ctl, 1, use_cond, (cudaGraphConditionalHandle)hcond, cl);
 }
