@@ -1647,6 +1647,137 @@ __device__ void column_solve(const double *G, int nS, double *z, unsigned char *
     __syncthreads();
 }
 
+// ---- the factor by connected components of the coupled rows ------------------
+// Rows of S that are not linked through shared columns, directly or through
+// other rows, form independent diagonal blocks of G: their factors and solves
+// never touch one another, and every entry of L and z receives, in the same
+// ascending order, the updates of the whole-matrix right-looking factor and
+// column solves (packed_cholesky, column_solve; zero multipliers skipped as
+// there).  The components come from union-find over the Gram's nonzero pairs
+// (roots hooked to the smaller root, then pointer jumping), their members
+// listed ascending; one warp factors and solves each.  Returns false, with G
+// and z untouched, when a component has more than kCompMax rows or the
+// union-find did not settle; the caller then takes the other paths.
+constexpr int kCompMax = 32;
+template <bool RC>
+__device__ bool component_factor(double *G, int nS, const unsigned long long *pkeys, int npk,
+                                 const int16_t *spos, double *z, int *bad) {
+    __shared__ int par[kSymMax], cid[kSymMax], csz[kSymMax], cst[kSymMax + 1], memb[kSymMax];
+    __shared__ int sc[33];
+    __shared__ int s_changed, s_max, s_nc;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    for (int q = tid; q < nS; q += blockDim.x) { par[q] = q; csz[q] = 0; }
+    if (tid == 0) { s_changed = 1; s_max = 0; }
+    __syncthreads();
+    for (int rnd = 0; rnd < 64 && s_changed; ++rnd) {
+        __syncthreads();
+        if (tid == 0) s_changed = 0;
+        __syncthreads();
+        for (int q = tid; q < npk; q += blockDim.x) {
+            const unsigned long long pr = pkeys[q] >> 44;
+            if (q > 0 && (pkeys[q - 1] >> 44) == pr) continue;   // one visit per row pair
+            int u = spos[(int)(pr >> 10)], v = spos[(int)(pr & 1023)];
+            while (par[u] != u) u = par[u];                   // par[x] <= x: the walk ends
+            while (par[v] != v) v = par[v];
+            if (u != v) {
+                atomicMin(&par[max(u, v)], min(u, v));
+                s_changed = 1;
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < nS; q += blockDim.x) {
+            int r = par[q];
+            while (par[r] != r) r = par[r];
+            par[q] = r;
+        }
+        __syncthreads();
+    }
+    if (s_changed) return false;
+    // components numbered by their roots, sizes, members ascending
+    const int isroot = tid < nS && par[tid] == tid;
+    int nc;
+    const int pre = nS <= (int)blockDim.x ? block_exclusive_scan(isroot, sc, &nc) : 0;
+    if (nS > (int)blockDim.x) return false;                   // not reached: nS <= kSymMax
+    if (isroot) cid[tid] = pre;
+    __syncthreads();
+    for (int q = tid; q < nS; q += blockDim.x) atomicAdd(&csz[cid[par[q]]], 1);
+    __syncthreads();
+    const int size = tid < nc ? csz[tid] : 0;
+    int tot;
+    const int st = block_exclusive_scan(size, sc, &tot);
+    if (tid < nc) cst[tid] = st;
+    if (tid == 0) { cst[nc] = tot; s_nc = nc; }
+    if (size) atomicMax(&s_max, size);
+    __syncthreads();
+    if (s_max > kCompMax) return false;
+    for (int q = tid; q < nS; q += blockDim.x) {
+        const int root = par[q];
+        int rank = 0;
+        for (int u = 0; u < q; ++u) rank += par[u] == root;
+        memb[cst[cid[root]] + rank] = q;
+    }
+    __syncthreads();
+    // one warp per component: right-looking factor, then the two solves
+    for (int c = wid; c < s_nc; c += nw) {
+        const int *M = memb + cst[c];
+        const int n = cst[c + 1] - cst[c];
+        for (int j = 0; j < n; ++j) {
+            const int mj = M[j];
+            if (lane == 0) {
+                double d = G[pidx(mj, mj)];
+                if (!(d > 0.0)) { *bad = 1; d = 1.0; }
+                G[pidx(mj, mj)] = chol_diag<RC>(d);
+            }
+            __syncwarp();
+            const double l = G[pidx(mj, mj)];
+            int any = 0;
+            for (int i = j + 1 + lane; i < n; i += 32) {
+                const double v = G[pidx(M[i], mj)];
+                if (v != 0.0) { G[pidx(M[i], mj)] = chol_div<RC>(v, l); any = 1; }
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            __syncwarp();
+            const int t = n - j - 1;                          // trailing rows j+1 .. n-1
+            for (int e = lane; e < t * (t + 1) / 2; e += 32) {
+                int ai = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);   // e = ai (ai + 1) / 2 + bi
+                while (ai * (ai + 1) / 2 > e) --ai;
+                while ((ai + 1) * (ai + 2) / 2 <= e) ++ai;
+                const int bi = e - ai * (ai + 1) / 2;
+                const int a = M[j + 1 + ai], b = M[j + 1 + bi];
+                const double la = G[pidx(a, mj)];
+                if (la == 0.0) continue;
+                const double lb = G[pidx(b, mj)];
+                if (lb != 0.0) G[pidx(a, b)] = __fma_rn(-la, lb, G[pidx(a, b)]);
+            }
+            __syncwarp();
+        }
+        for (int j = 0; j < n; ++j) {                        // forward
+            const int mj = M[j];
+            if (lane == 0) z[mj] = chol_div<RC>(z[mj], G[pidx(mj, mj)]);
+            __syncwarp();
+            const double zj = z[mj];
+            for (int i = j + 1 + lane; i < n; i += 32) {
+                const double lij = G[pidx(M[i], mj)];
+                if (lij != 0.0) z[M[i]] = __fma_rn(-lij, zj, z[M[i]]);
+            }
+            __syncwarp();
+        }
+        for (int j = n - 1; j >= 0; --j) {                   // backward
+            const int mj = M[j];
+            if (lane == 0) z[mj] = chol_div<RC>(z[mj], G[pidx(mj, mj)]);
+            __syncwarp();
+            const double zj = z[mj];
+            for (int i = lane; i < j; i += 32) {
+                const double lji = G[pidx(mj, M[i])];
+                if (lji != 0.0) z[M[i]] = __fma_rn(-lji, zj, z[M[i]]);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
 // The factor step of the dynamic update, run by the last block of
 // k_dyn_mark: coupled rows S (rows sharing a column inside I), the Gram on S
 // from the shared columns only (each entry summed over ascending columns), its
@@ -1790,7 +1921,11 @@ __device__ void dyn_factor(const T *__restrict__ r, int K, Dyn D, Ctl *ctl,
     __syncthreads();
     for (int q = tid; q < nS; q += blockDim.x) z[q] = (double)r[rpos<MC>(cl, D.I[sidx[q]])];
     __syncthreads();
-    if (nS > 0) {
+    bool by_comp = false;
+    if (nS > 0 && nS <= kSymMax) by_comp = component_factor<RC>(G, nS, pkeys, npk, spos, z, &s_bad);
+    if (by_comp) {
+        if (tid == 0) s_uselev = 0;
+    } else if (nS > 0) {
         if (nS <= kSymMax) symbolic(G, nS, S, &s_nlev, &s_uselev);
         else if (tid == 0) s_uselev = 0;
         __syncthreads();
