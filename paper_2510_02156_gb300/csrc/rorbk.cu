@@ -1001,8 +1001,10 @@ rorbk_status rorbk_autotune(rorbk_handle h, const double *b, int32_t precision, 
     if (st == RORBK_OK) {
         o.host_loop = 0;
         double gbest = 1e300;
-        int ubest = 1;
-        for (int u : {1, 2, 4, 8}) {
+        int ubest = kGraphUnroll;
+        // the default first: another count is kept only if it is 2% faster
+        for (int u : {kGraphUnroll, 1, 2, 8}) {
+            if (u == kGraphUnroll && gbest < 1e300) continue;
             h->tune.unroll = u;
             drop_graphs(h);
             double us = 0;
