@@ -653,10 +653,12 @@ __device__ __forceinline__ void hist_add(unsigned *hist, unsigned bin, bool acti
 // finalize: 1 = convergence test + first radix level (iteration), 2 = ||r||^2
 // only (single-step API).  DN: A is dense, so entry j of a row is in column j
 // and the column indices are not read (x_j is the same for the warp's lanes).
-constexpr int kDnAhead = 4;      // dense residual: 16-byte loads per lane in flight
+constexpr int kDnAhead = 8;      // dense residual: 16-byte loads per lane in flight
 
+// (a dense A: three blocks per SM, so that each lane keeps kDnAhead loads in
+// flight without spilling)
 template <typename T, typename V, bool DN = false>
-__global__ void __launch_bounds__(256, 4) k_residual(Mat<T> A, const T *__restrict__ b,
+__global__ void __launch_bounds__(256, DN ? 3 : 4) k_residual(Mat<T> A, const T *__restrict__ b,
                                                   const T *__restrict__ x, T *__restrict__ r,
                                                   double *partials, unsigned *hist1, Ctl *ctl,
                                                   int finalize) {
@@ -3394,11 +3396,19 @@ int grid_scatter(rorbk_ctx *h) { return tuned(h->tune.scatter, 2 * h->num_sms / 
 
 int residual_grid(rorbk_ctx *h) {
     int per_sm = 0, per_sm32 = 0;
-    if (h->vdtype == RORBK_F32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, float>, 256, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, double>, 256, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_residual<float, float>, 256, 0);
+    if (h->format == RORBK_FORMAT_DENSE) {
+        if (h->vdtype == RORBK_F32)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, float, true>, 256, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, double, true>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_residual<float, float, true>, 256, 0);
+    } else {
+        if (h->vdtype == RORBK_F32)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, float>, 256, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<double, double>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_residual<float, float>, 256, 0);
+    }
     return std::max(1, std::min(per_sm, per_sm32 > 0 ? per_sm32 : per_sm)) * h->num_sms;
 }
 
