@@ -1,7 +1,8 @@
 // kernels_iter.cu -- the ROR-BK iteration (Algorithm 1's loop body).
 //
 //   k_begin        ||b||, x0, loop state; sets the loop condition
-//   k_static       l = 1..n_static: draw tau (Philox), r_tau = b_tau - A_tau x,
+//   k_static       l = 1..n_static: draw tau (Philox; formed ahead by the
+//                  previous k_dyn_mark when it can be), r_tau = b_tau - A_tau x,
 //                  y = W_tau r_tau, x += A_tau^T y   (one block of threads)
 //   k_residual     r = b - A x over nnz-balanced row tiles, ||r||^2, the
 //                  convergence test, and the first radix histogram of |r|
@@ -10,7 +11,7 @@
 //                  the last block completes the exact top-K set
 //   k_dyn_mark     gathers A_I, marks shared columns, Gram diagonal; the last
 //                  block factors G = A_I A_I^T + mu I on the coupled rows and
-//                  solves for y
+//                  solves for y, the first block done forms the next draws
 //   k_dyn_scatter  x += A_I^T y; ends the iteration, sets the loop condition
 //
 // Compute type T is double (the plain method) or float (the inner solve of
@@ -19,9 +20,10 @@
 // order; A^T y per column over ascending rows; Gram entries over ascending
 // columns; column-ordered triangular solves), so the iterates reproduce the
 // FP64 definition exactly.  FP64 arithmetic on this part has a long latency,
-// so chains are kept short: the Cholesky of the coupled rows is scheduled
-// along its elimination tree (all columns of one tree level at once), which
-// performs the same operations on every entry in the same order.
+// so chains are kept short: the Cholesky of the coupled rows runs per
+// connected component (one warp each), or, for components above 32 rows,
+// along its elimination tree (all columns of one tree level at once); both
+// perform the same operations on every entry in the same order.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
