@@ -32,6 +32,7 @@
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "topk_key.cuh"
 
 namespace rorbk {
 
@@ -79,6 +80,11 @@ __device__ __forceinline__ VecT<T, VEC> vload(const T *p) {
     }
     return r;
 }
+
+// The radix key of |v| in the top-K passes: the FP64 bit pattern of |v|, for
+// an FP32 value formed with integer operations (topk_key.cuh).
+__device__ __forceinline__ unsigned long long topk_key(double v) { return abs_key(v); }
+__device__ __forceinline__ unsigned long long topk_key(float v) { return topk_key_f32_bits(__float_as_uint(v)); }
 
 // Matrix and operator pointers for one compute type.
 template <typename T>
@@ -853,7 +859,7 @@ __global__ void __launch_bounds__(256) k_inc_finish(const T *__restrict__ r, int
         if (act) {
             const T ri = r[i];
             rr = __fma_rn((double)ri, (double)ri, rr);
-            bin = (unsigned)(abs_key(ri) >> 52);
+            bin = (unsigned)(topk_key(ri) >> 52);
         }
         hist_add(hist, bin, act);
     }
@@ -930,7 +936,7 @@ __global__ void __launch_bounds__(256) k_topk_hist1(const T *__restrict__ r, int
             v[u] = i < mp ? r[i] : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < kScanU; ++u) hist_add(hist, act[u] ? (unsigned)(abs_key(v[u]) >> 52) : 0u, act[u]);
+        for (int u = 0; u < kScanU; ++u) hist_add(hist, act[u] ? (unsigned)(topk_key(v[u]) >> 52) : 0u, act[u]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
@@ -982,7 +988,7 @@ __global__ void __launch_bounds__(256) k_topk_hist2(const T *__restrict__ r, int
         }
 #pragma unroll
         for (int u = 0; u < kScanU; ++u) {
-            const unsigned long long key = abs_key(v[u]);
+            const unsigned long long key = topk_key(v[u]);
             if (act[u] && (unsigned)(key >> 52) == sel1) atomicAdd(&hist[(unsigned)(key >> 41) & 2047u], 1u);
         }
     }
@@ -1057,7 +1063,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
         // row), each placed by its rank
         for (int e = threadIdx.x; e < neq; e += blockDim.x) {
             const int i = eq_list[e];
-            skey[e] = abs_key(r[rpos<MC>(cl, i)]);
+            skey[e] = topk_key(r[rpos<MC>(cl, i)]);
             sidx[e] = i;
         }
         __syncthreads();
@@ -1072,7 +1078,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
     } else if (need > 0 && neq <= kEqCap) {
         const int np = next_pow2(neq);
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
-            if (e < neq) { int i = eq_list[e]; skey[e] = abs_key(r[rpos<MC>(cl, i)]); sidx[e] = i; }
+            if (e < neq) { int i = eq_list[e]; skey[e] = topk_key(r[rpos<MC>(cl, i)]); sidx[e] = i; }
             else { skey[e] = 0ull; sidx[e] = 0x7fffffff; }
         }
         __syncthreads();
@@ -1097,7 +1103,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
             const unsigned long long pref = s_pref;
             const int sh = s_shift;
             for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                unsigned long long key = abs_key(r[rpos<MC>(cl, i)]);
+                unsigned long long key = topk_key(r[rpos<MC>(cl, i)]);
                 if ((key >> sh) == pref)
                     atomicAdd(&shist[(unsigned)((key >> nshift) & ((1ull << digit_bits) - 1))], 1u);
             }
@@ -1117,7 +1123,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
             // rows strictly above the chosen digit are in
             const int dig = s_dig;
             for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                unsigned long long key = abs_key(r[rpos<MC>(cl, i)]);
+                unsigned long long key = topk_key(r[rpos<MC>(cl, i)]);
                 if ((key >> sh) == pref &&
                     (int)((key >> nshift) & ((1ull << digit_bits) - 1)) > dig)
                     sI[atomicAdd(&s_fill, 1)] = i;
@@ -1135,7 +1141,7 @@ __device__ void finalize_topk(const T *__restrict__ r, int m, int K, const int *
         int taken = 0;
         for (int base = 0; base < m && taken < want; base += blockDim.x) {
             int i = base + threadIdx.x;
-            int f = (i < m && abs_key(r[rpos<MC>(cl, i)]) == T0) ? 1 : 0;
+            int f = (i < m && topk_key(r[rpos<MC>(cl, i)]) == T0) ? 1 : 0;
             int total;
             int pre = block_exclusive_scan(f, sc, &total);
             if (f && taken + pre < want) sI[s_fill + taken + pre] = i;
@@ -1270,7 +1276,7 @@ __global__ void __launch_bounds__(512) k_topk_collect(const T *__restrict__ r, i
 #pragma unroll
         for (int u = 0; u < kScanU; ++u) {
             if (row[u] < 0) continue;
-            const unsigned long long pre = abs_key(v[u]) >> 41;
+            const unsigned long long pre = topk_key(v[u]) >> 41;
             if (pre < P) continue;
             const int i = MC && cl.perm ? cl.perm[row[u]] : row[u];   // the row at this position
             if (i < 0) continue;
